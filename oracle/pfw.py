@@ -1,0 +1,119 @@
+"""Polyatomic Frank-Wolfe (Algorithm 2) in FP64 (test infrastructure only).
+
+Steps per iteration k = 0, 1, 2, ... (Algorithm 2 with Sect. 4.1):
+
+  0. dirty residual    eta_k = Phi*(V - Phi I_k)     (on every pixel)
+  1a. exploration      I_{k+1} = select(eta_k)
+  1b. active set       S_{k+1} = S_k u I_{k+1}        (kept in ascending raster order)
+  2.  reweighting      I_{k+1} = argmin over supp in S_{k+1} of the LASSO, by APGD
+                       warm-started from I_k (0 on the new atoms), early-stopped at eps_k
+  3.  pruning          S_{k+1} = supp(I_{k+1})
+  4.  stop             relative objective improvement (F_k - F_{k+1}) / F_k < tol
+
+Readings where the paper gives no value (the GPU path uses the same ones):
+
+  * select rule "R2" (default): I = {p : |mu_k[p]| >= 1 - delta}, mu_k = eta_k / lambda,
+    the empirical dual certificate (Sect. 3.2 / 4.1);
+    select rule "R1" (the literal exploration set of Algorithm 2):
+    I = {p : |eta_k[p]| >= ||eta_k||_inf - 2 Delta / (k + 2)}, Delta = (1 - delta) lambda_max;
+  * eps_k = max(eps_min, eps0 * 2^-k), eps0 = 1e-2, eps_min = 1e-5;
+  * objective F_k = 1/2 ||V - Phi I_k||^2 + lambda ||I_k||_1, F_0 = 1/2 ||V||^2;
+  * tol = 1e-4 (Sect. 5.1), at most max_fw iterations.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import lasso, operators
+
+
+@dataclasses.dataclass
+class SolveResult:
+    idx: np.ndarray          # int64 sorted support (raster indices)
+    x: np.ndarray            # float64 weights on the support
+    mu: np.ndarray           # final certificate, N x N
+    objective: float
+    iterations: int
+    converged: bool
+    lambda_: float
+    history: list
+
+
+def select_r2(mu: np.ndarray, delta: float) -> np.ndarray:
+    """Pixels whose certificate magnitude reaches 1 - delta (ascending raster order)."""
+    return np.nonzero(np.abs(mu) >= 1.0 - delta)[0]
+
+
+def select_r1(eta: np.ndarray, k: int, Delta: float) -> np.ndarray:
+    """Exploration set of Algorithm 2: |eta| >= ||eta||_inf - 2 Delta / (k + 2)."""
+    a = np.abs(eta)
+    return np.nonzero(a >= a.max() - 2.0 * Delta / (k + 2))[0]
+
+
+def eps_schedule(k: int, eps0: float = 1e-2, eps_min: float = 1e-5) -> float:
+    return max(eps_min, eps0 * 2.0 ** (-k))
+
+
+def duality_gap(uvw, N, fov, V, lam, idx, x) -> float:
+    """F(x) - D(theta) with the dual-feasible scaling theta = r min(1, lambda / ||Phi* r||_inf).
+
+    D(theta) = 1/2 ||V||^2 - 1/2 ||V - theta||^2 is the LASSO dual objective
+    (complex data as a real vector space with inner product Re<.,.>).
+    """
+    V = np.asarray(V, dtype=np.complex128)
+    r = operators.residual(uvw, N, fov, V, idx, x)
+    g = np.max(np.abs(operators.adjoint(uvw, N, fov, r)))
+    theta = r * min(1.0, lam / g) if g > 0 else r
+    F = 0.5 * float(np.vdot(r, r).real) + lam * float(np.sum(np.abs(x)))
+    D = 0.5 * float(np.vdot(V, V).real) - 0.5 * float(np.vdot(V - theta, V - theta).real)
+    return F - D
+
+
+def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
+          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None) -> SolveResult:
+    V = np.asarray(V, dtype=np.complex128)
+    if lmax is None:
+        lmax = operators.lambda_max(uvw, N, fov, V)
+    Delta = (1.0 - delta) * lmax
+    S = np.zeros(0, dtype=np.int64)
+    x = np.zeros(0)
+    r = V.copy()
+    F_prev = 0.5 * float(np.vdot(V, V).real)
+    history = []
+    converged = False
+    k = 0
+    for k in range(max_fw):
+        eta = operators.adjoint(uvw, N, fov, r)                 # dirty residual, all pixels
+        if rule == "R2":
+            new = select_r2(eta / lam, delta)
+        elif rule == "R1":
+            new = select_r1(eta, k, Delta)
+        else:
+            raise ValueError(rule)
+        n_new = int(np.setdiff1d(new, S).size)
+        S_next = np.union1d(S, new).astype(np.int64)            # sorted, unique
+        x0 = np.zeros(S_next.size)
+        if S.size:
+            x0[np.searchsorted(S_next, S)] = x                   # warm start on old atoms
+        l, m, n = operators.pixel_lmn(N, fov, S_next)
+        A = operators.phase_block(uvw, l, m, n)                  # Phi restricted to S_next
+        eps = eps_schedule(k, eps0, eps_min)
+        xs, n_it, L = lasso.apgd(A, V, lam, x0, eps, apgd_max_iter)
+        keep = xs != 0.0                                          # pruning
+        S, x = S_next[keep], xs[keep]
+        r = V - A[:, keep] @ x
+        F = 0.5 * float(np.vdot(r, r).real) + lam * float(np.sum(np.abs(x)))
+        rel = (F_prev - F) / F_prev if F_prev > 0 else 0.0
+        history.append(dict(k=k, n_new=n_new,
+                            n_active=int(S_next.size), n_support=int(S.size),
+                            mu_inf=float(np.max(np.abs(eta)) / lam), objective=F,
+                            rel_improvement=rel, apgd_iterations=int(n_it), L=float(L),
+                            eps=eps))
+        F_prev = F
+        if rel < tol:
+            converged = True
+            break
+    mu = operators.adjoint(uvw, N, fov, r).reshape(N, N) / lam
+    return SolveResult(S, x, mu, F_prev, k + 1, converged, lam, history)
