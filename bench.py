@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the PolyCLEAN hot path on one GB300 (or N independent replicas).
+
+One step = one full PolyCLEAN solve (Algorithm 2 to a 1e-4 relative objective
+improvement) of the 512 x 512, M = 200k w-stacked synthetic workload
+(40-station Earth-rotation layout, 50 log-normal point sources, 20 dB SNR,
+lambda = 0.1 lambda_max, delta = 0.01), with the plan built and V resident in
+HBM before the timed region. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PolyCLEAN solve time at 1e-4 rel. objective; gridding vis/s vs HBM roofline; p99"
+UNIT = "solves/s"
+WORKLOAD = "medium_512_w"
+# Frank-Wolfe iterations the GPU solve of this workload runs (measured); the
+# reference arm scales its per-certificate oracle time by this count.
+FW_CERTIFICATES = {"medium_512_w": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+# ------------------------------------------------------------------ workload
+
+def make_inputs(abi, synth, name, device):
+    """Plan and visibilities on the device. V = Phi(sky) + noise with Phi the
+    library's own forward operator; the noise level sets the workload's SNR."""
+    import numpy as np
+    import torch
+    wl = synth.WORKLOADS[name]()
+    uvw = torch.from_numpy(wl.uvw).to(device)
+    plan = abi.pc_plan_create(uvw, wl.N, wl.fov)
+    Vc = abi.pc_forward_sparse(plan, torch.from_numpy(wl.sky_idx).to(device),
+                               torch.from_numpy(wl.sky_flux.astype(np.float32)).to(device))
+    p_sig = float((Vc.abs() ** 2).mean())
+    noise = torch.from_numpy(wl.noise.astype(np.complex64)).to(device)
+    V = (Vc + synth.noise_sigma(p_sig, wl.snr_db) * noise).contiguous()
+    torch.cuda.synchronize()
+    return wl, uvw, plan, V
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+# ------------------------------------------------------------------ roofline
+
+def roofline(prof, info, wl, history, steps, peaks):
+    """Achieved vs peak for the dominant kernel class over the timed region."""
+    ms = {k: v[2] for k, v in prof.items()}
+    dom = max(ms, key=ms.get)
+    launches = prof[dom][0]
+    avg_ms = ms[dom] / max(launches, 1)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    M, N, G, P = wl.M, wl.N, info["grid_side"], info["n_planes"]
+    out = {"kernel": dom, "avg_launch_ms": avg_ms, "launches": launches}
+    if dom == "grid":
+        # 20 B per visibility (complex64 residual + three float32 coordinates)
+        # + the grid planes written once
+        b = 20.0 * M + 8.0 * P * G * G
+        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    elif dom == "fft_rows":
+        b = 8.0 * P * G * G + 8.0 * P * N * G
+        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    elif dom == "fft_cols":
+        b = 8.0 * P * N * G + 16.0 * N * N + 4.0 * N * N
+        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    elif dom == "apgd":
+        # one S x S FP32 GEMV per iteration (G read from shared memory or L2)
+        it = sum(h["apgd_iterations"] * h["n_active"] ** 2 * 4.0 for h in history)
+        b = it * steps / max(launches, 1)
+        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    elif dom == "gram":
+        f = sum(8.0 * M * h["n_new"] * (h["n_active"] + 1) for h in history) * steps / max(launches, 1)
+        fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+        out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=fp32, unit="TFLOP/s")
+    elif dom == "residual":
+        pairs = sum(M * h["n_support"] for h in history) * steps / max(launches, 1)
+        out.update(bound="alu", achieved=pairs / (avg_ms * 1e-3) / 1e9, peak=None,
+                   unit="Gpairs/s")
+    else:
+        out.update(bound="hbm", achieved=None, peak=hbm, unit="GB/s")
+    if out.get("achieved") is not None and out.get("peak"):
+        out["frac"] = out["achieved"] / out["peak"]
+    else:
+        out["frac"] = None
+    out["traffic"] = None
+    return out
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def oracle_sample_seconds(name: str, n_pix: int, seed: int = 0) -> tuple[float, int]:
+    """Time the FP64 oracle's direct-sum adjoint on n_pix seeded pixels of the
+    workload's certificate (one thread). Returns (seconds, n_pix)."""
+    code = (
+        "import sys, time, numpy as np; sys.path.insert(0, %r)\n"
+        "from oracle import operators\n"
+        "from paper_2406_01342_gb300 import synth\n"
+        "wl = synth.WORKLOADS[%r]()\n"
+        "V = operators.forward(wl.uvw, wl.N, wl.fov, wl.sky_idx, wl.sky_flux) + wl.noise\n"
+        "pix = np.sort(np.random.default_rng(%d).choice(wl.N * wl.N, %d, replace=False))\n"
+        "t = time.perf_counter(); operators.adjoint(wl.uvw, wl.N, wl.fov, V, pix); "
+        "print(time.perf_counter() - t)\n" % (ROOT, name, seed, n_pix))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return float(out.stdout.strip().splitlines()[-1]), n_pix
+
+
+def oracle_solves_per_s(name: str, n_pix: int, certificates: int, seed: int = 0):
+    from paper_2406_01342_gb300 import synth
+    wl = synth.WORKLOADS[name]()
+    sec, n = oracle_sample_seconds(name, n_pix, seed)
+    per_cert = sec * (wl.N * wl.N) / n
+    solve_s = per_cert * certificates
+    sample = (f"FP64 oracle direct-sum adjoint on {n} seeded pixels x all {wl.M} visibilities "
+              f"({sec:.2f} s, 1 thread), extrapolated to {wl.N}x{wl.N} pixels x {certificates} "
+              f"certificates per solve (forward and sub-solver costs not counted: an upper bound "
+              f"on oracle solves/s)")
+    return 1.0 / solve_s, sample
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    certs = FW_CERTIFICATES.get(args.workload) or 12
+    vals = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        v, sample = oracle_solves_per_s(args.workload, 256, certs, seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2406_01342_gb300 import abi, build, synth
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(world)
+    abi.load()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    wl, uvw, plan, V = make_inputs(abi, synth, args.workload, device)
+    info = abi.pc_plan_info(plan)
+    lmax = abi.pc_lambda_max(plan, V)
+    lam = wl.alpha * lmax
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
+
+    def step():
+        return abi.pc_solve(plan, V, lam, wl.delta, want_mu=True, history=256)
+
+    n_warm = max(3, args.warmup)          # at least three untimed warm-up solves
+    for _ in range(n_warm):
+        res = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        abi.pc_profile_begin()
+        for i in range(args.steps):
+            flush_l2(l2_flush)
+            starts[i].record(stream)
+            res = step()
+            ends[i].record(stream)
+        prof = abi.pc_profile_end()
+        torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = max_over_ranks(world, sum(step_ms))
+    value = world * args.steps / (total_ms * 1e-3)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+    rl = roofline(prof, info, wl, res["history"], args.steps, peaks)
+    grid_ms = prof.get("grid", (1, 1, float("nan")))[2] / max(prof.get("grid", (1,))[0], 1)
+    vis_per_s = wl.M / (grid_ms * 1e-3) if grid_ms == grid_ms else None
+    gpu_launches = sum(v[1] for v in prof.values())
+
+    # end to end through the C ABI on host buffers (plan + lambda_max + solve + copies)
+    e2e = None
+    if not args.no_e2e:
+        uvw_h = torch.from_numpy(wl.uvw).pin_memory()
+        V_h = V.cpu().pin_memory()
+        n_sup = 0
+        for _ in range(2):
+            r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta)
+        t = []
+        for i in range(args.steps):
+            flush_l2(l2_flush)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta)
+            t.append(time.perf_counter() - t0)
+            n_sup = len(r["idx"])
+        e2e_s = max_over_ranks(world, sum(t))
+        e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(wl.M * (24 + 8)),
+               "d2h_bytes_per_step": int(n_sup * 8 + 64)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            v, sample = oracle_solves_per_s(args.workload, 1024, res["iterations"] + 2)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        except Exception as e:  # the oracle leg never hides the GPU result
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {e}"[:300]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": n_warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl.N}x{wl.N} image, M={wl.M} visibilities, "
+                                   f"{info['n_planes']} w-planes, {wl.sky_idx.size} point sources, "
+                                   f"lambda={wl.alpha} lambda_max, delta={wl.delta}",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "solve_time_s": total_ms / args.steps / 1e3,
+            "solve": {"iterations": res["iterations"], "support": int(res["idx"].numel()),
+                      "objective": res["objective"], "converged": res["converged"]},
+            "gridding_vis_per_s": vis_per_s,
+            "kernels_ms": {k: round(v[2] / args.steps, 4) for k, v in prof.items()},
+            "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+            "roofline_kernel": {k: rl[k] for k in ("kernel", "avg_launch_ms", "launches")},
+            "peaks_source": "MEASURED_PEAKS.json (measured)" if "_fallback" not in peaks else "fallback",
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
+            "cpu_baseline": cpu, "wall_s": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * polyclean.h -- C ABI of the GB300 (sm_103a) PolyCLEAN hot path.
+ *
+ * The library implements, as hand-written CUDA kernels, the operators and the
+ * solver loop of PolyCLEAN (Polyatomic Frank-Wolfe for the LASSO imaging
+ * problem, Sect. 3.1 and Algorithm 2 of the paper):
+ *
+ *   Phi  : R^{N x N} -> C^M   Phi(I)[k]  = sum_p I_p / n_p exp(-j2pi(u_k l_p + v_k m_p + w_k (n_p - 1)))
+ *                             (the discrete forward equation, Sect. 2.2)
+ *   Phi* : C^M -> R^{N x N}   Phi*(h)[p] = Re sum_k h_k / n_p exp(+j2pi(u_k l_p + v_k m_p + w_k (n_p - 1)))
+ *                             (the adjoint equation, Sect. 2.2)
+ *   mu   = Phi*(V - Phi x) / lambda          (dual certificate, Sect. 3.2)
+ *   lambda_max = ||Phi* V||_inf              (Sect. 4.4)
+ *   argmin_x 1/2 ||V - Phi x||^2 + lambda ||x||_1 by Polyatomic Frank-Wolfe (Algorithm 2)
+ *
+ * Conventions shared by every call:
+ *   - uvw: float64, M x 3 row-major, in wavelengths.
+ *   - Image: N x N float32 row-major; raster index p = i*N + j; i indexes the
+ *     direction cosine l and j indexes m, l_i = (i - N/2) fov/N,
+ *     m_j = (j - N/2) fov/N (N even), n = sqrt(1 - l^2 - m^2).
+ *   - Visibilities: interleaved complex float32 (pc_c32), original order of uvw.
+ *   - Sparse images: strictly ascending unique raster indices (int32) plus
+ *     float32 weights.
+ *   - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *     name ends in _host. A host pointer where a device pointer is expected is
+ *     rejected with PC_ERR_INVALID_ARG; there is no CPU fallback.
+ *   - Every call is ordered on the given CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream). Calls that return values in host
+ *     memory (*_host outputs, pc_solve_stats) synchronise that stream.
+ *   - A plan owns its device workspace. Calls on one plan must not overlap
+ *     (they share the workspace); use one plan per concurrent stream.
+ *   - Return value: PC_OK (0) or a negative pc_status. pc_last_error()
+ *     returns a thread-local message describing the last failure.
+ */
+#ifndef POLYCLEAN_H
+#define POLYCLEAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PC_ABI_VERSION 1
+
+typedef enum {
+  PC_OK = 0,
+  PC_ERR_INVALID_ARG = -1,   /* bad size, NULL, host pointer, non-finite input      */
+  PC_ERR_OOM = -2,           /* device allocation failed; the plan stays valid       */
+  PC_ERR_CUDA = -3,          /* a CUDA runtime call failed (message has the text)     */
+  PC_ERR_NOT_CONVERGED = -4, /* iteration cap reached; the returned result is valid  */
+  PC_ERR_TIMEOUT = -5,       /* a bounded device wait expired                         */
+  PC_ERR_NUMERIC = -6,       /* NaN/Inf met in a result                               */
+  PC_ERR_CAPACITY = -7       /* support larger than the caller's output capacity     */
+} pc_status;
+
+typedef struct { float re, im; } pc_c32;
+
+typedef struct pc_plan_s* pc_plan_t;
+
+/* Plan options. Zero-initialise and set version = PC_ABI_VERSION; a zero field
+ * takes its default. */
+typedef struct {
+  int32_t version;
+  int32_t kernel_width;   /* ES kernel width W in grid cells (default 7; 4..8)         */
+  int32_t tile;           /* gridding tile side in cells (default 32; 16 or 32)         */
+  int32_t max_planes;     /* cap on the number of w-planes (default 256)                */
+} pc_plan_opts;
+
+/* Solver options (Algorithm 2 and its sub-solver). Zero fields take defaults. */
+typedef struct {
+  int32_t version;
+  int32_t select_rule;    /* 2 (default): |mu| >= 1 - delta;  1: |eta| >= ||eta||_inf - 2 Delta/(k+2) */
+  int32_t max_fw;         /* Frank-Wolfe iteration cap (default 100)                                 */
+  int32_t apgd_max_iter;  /* sub-solver iteration cap (default 10000)                                */
+  int32_t gram_mode;      /* 0 (default): FP32 CUDA-core support contraction                          */
+  int32_t reserved0;
+  double  tol;            /* stop when (F_k - F_{k+1}) / F_k < tol (default 1e-4, Sect. 5.1)          */
+  double  eps0;           /* sub-solver accuracy eps_k = max(eps_min, eps0 2^-k) (default 1e-2)       */
+  double  eps_min;        /* (default 1e-5)                                                           */
+  double  lambda_max;     /* for rule 1: lambda_max if known (<= 0: computed)                        */
+} pc_solve_opts;
+
+/* Per-iteration record of pc_solve (host memory). */
+typedef struct {
+  int32_t k;              /* Frank-Wolfe iteration                                   */
+  int32_t n_new;          /* atoms added by the exploration step                     */
+  int32_t n_active;       /* |S_k u I_{k+1}| before the reweighting                  */
+  int32_t n_support;      /* |S_{k+1}| after pruning                                 */
+  int32_t apgd_iterations;
+  int32_t reserved0;
+  double  mu_inf;         /* ||mu_k||_inf (eta_k / lambda) at the start of iteration k */
+  double  objective;      /* F(I_{k+1})                                              */
+  double  rel_improvement;
+  double  lipschitz;
+} pc_iter_record;
+
+typedef struct {
+  int32_t status;         /* PC_OK or PC_ERR_NOT_CONVERGED                          */
+  int32_t iterations;     /* Frank-Wolfe iterations run                             */
+  int32_t n_support;      /* entries written to idx_out / x_out                     */
+  int32_t n_history;      /* records written to history (<= history_capacity)       */
+  double  objective;      /* final F                                                */
+  double  lambda;         /* lambda used                                            */
+  double  mu_inf;         /* ||mu||_inf of the final certificate                    */
+  double  sumsq_V;        /* ||V||^2                                                */
+} pc_solve_stats;
+
+/* ------------------------------------------------------------------ plan */
+
+/* Build a plan for M visibilities (uvw_dev, M x 3 float64) and an N x N image
+ * with full field-of-view side fov_rad (direction cosine units). Sorts and bins
+ * the visibilities by (gridding tile, w-plane), precomputes the kernel
+ * corrections and allocates the gridding / FFT workspace (the plan owns it).
+ * Sect. 2.2 (pixel grid, operators) and Sect. 4.2 (the operator is evaluated
+ * with a non-uniform FFT: here exponential-of-semicircle gridding on a 2x
+ * oversampled grid with w-stacking). N must be even, 16 <= N <= 4096.
+ * M may be 0 (all operators then return zeros). */
+int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
+                   const pc_plan_opts* opts, void* stream, pc_plan_t* plan_out);
+void pc_plan_destroy(pc_plan_t plan);
+
+/* Plan geometry: oversampled grid side, tile side, number of w-planes, number
+ * of binned (replicated) visibility slots, kernel width. Any pointer may be NULL. */
+int pc_plan_info(pc_plan_t plan, int32_t* grid_side, int32_t* tile, int32_t* n_planes,
+                 int64_t* n_slots, int32_t* kernel_width, double* dw);
+
+/* ------------------------------------------------------------------ operators */
+
+/* y = Phi restricted to the support: y[k] = sum_s x[s]/n_s exp(-j2pi theta_ks),
+ * direct sum over the support (the forward equation of Sect. 2.2 for a sparse
+ * image; the paper evaluates it as a type-3 NUFFT, Sect. 4.2).
+ * idx_dev: S ascending raster indices; x_dev: S weights; y_dev: M outputs. */
+int pc_forward_sparse(pc_plan_t plan, const int32_t* idx_dev, const float* x_dev, int32_t S,
+                      pc_c32* y_dev, void* stream);
+
+/* out[s] = Phi*(y)[idx[s]]: the adjoint restricted to S pixels, direct sum. */
+int pc_adjoint_sparse(pc_plan_t plan, const pc_c32* y_dev, const int32_t* idx_dev, int32_t S,
+                      float* out_dev, void* stream);
+
+/* img = Phi*(y) on all N x N pixels (the adjoint equation of Sect. 2.2), by
+ * gridding on the oversampled grid, w-stacking, 2-D inverse FFT and kernel
+ * correction. With y = V this is the dirty image. img_dev: N*N floats. */
+int pc_adjoint_grid(pc_plan_t plan, const pc_c32* y_dev, float* img_dev, void* stream);
+
+/* lambda_max = ||Phi* V||_inf (Sect. 4.4), returned in host memory. */
+int pc_lambda_max(pc_plan_t plan, const pc_c32* V_dev, double* lambda_max_host, void* stream);
+
+/* mu = Phi*(V - Phi x) / lambda (Sect. 3.2), x given on a support of S pixels.
+ * mu_dev: N*N floats. mu_inf_host (may be NULL): ||mu||_inf. sumsq_host (may
+ * be NULL): ||V - Phi x||^2 accumulated in float64. */
+int pc_certificate(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev,
+                   const float* x_dev, int32_t S, double lambda, float* mu_dev,
+                   double* mu_inf_host, double* sumsq_host, void* stream);
+
+/* ------------------------------------------------------------------ hot-path steps */
+
+/* Exploration + union (Algorithm 2, steps 1a/1b). From a certificate mu (N*N)
+ * select I = {p : |mu_p| >= thr} and write the ascending union of I with the
+ * support prev_idx (n_prev entries, ascending) to out_idx (capacity cap).
+ * *n_out_host receives |S u I|. PC_ERR_CAPACITY if it exceeds cap (nothing
+ * else is written then). */
+int pc_select(pc_plan_t plan, const float* mu_dev, float thr, const int32_t* prev_idx_dev,
+              int32_t n_prev, int32_t* out_idx_dev, int32_t cap, int32_t* n_out_host,
+              void* stream);
+
+/* Support contraction (step 2 of Algorithm 2, in Gram form): for the S atoms
+ * idx, G = Re(Phi_S^H Phi_S) (S x S, row-major, leading dimension ldg) and
+ * b = Re(Phi_S^H V) (S). FP32 products of phases generated on the fly,
+ * float64 accumulation across visibility slices. */
+int pc_gram(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev, int32_t S,
+            float* G_dev, int32_t ldg, float* b_dev, void* stream);
+
+/* Restricted LASSO by monotone FISTA on the Gram form (Sect. 3.4 / 4.1):
+ * min_x 1/2 x^T G x - b^T x + lambda ||x||_1, warm start x_dev (in/out),
+ * step 1/L with L = 1.01 x power-iteration estimate of the top eigenvalue of G,
+ * stop when ||z - y|| <= eps ||z|| or after max_iter iterations.
+ * iters_host / lipschitz_host (may be NULL) receive the iteration count and L. */
+int pc_apgd(const float* G_dev, int32_t ldg, const float* b_dev, int32_t S, double lambda,
+            double eps, int32_t max_iter, float* x_dev, int32_t* iters_host,
+            double* lipschitz_host, void* stream);
+
+/* ------------------------------------------------------------------ solver */
+
+/* PolyCLEAN solve (Algorithm 2): argmin_x 1/2||V - Phi x||^2 + lambda||x||_1.
+ * Writes the support (ascending raster indices) and weights to idx_out_dev /
+ * x_out_dev (capacity cap), the final certificate to mu_out_dev (N*N, may be
+ * NULL), statistics to *stats_host and up to history_capacity iteration
+ * records to history_host (may be NULL). delta is the exploration parameter
+ * (rule 2: atoms with |mu| >= 1 - delta; rule 1: quality of Algorithm 2).
+ * Returns PC_OK, PC_ERR_NOT_CONVERGED (result valid) or an error. */
+int pc_solve(pc_plan_t plan, const pc_c32* V_dev, double lambda, double delta,
+             const pc_solve_opts* opts, int32_t* idx_out_dev, float* x_out_dev, int32_t cap,
+             float* mu_out_dev, pc_solve_stats* stats_host, pc_iter_record* history_host,
+             int32_t history_capacity, void* stream);
+
+/* End-to-end call on HOST buffers: copies uvw (M x 3 float64) and V (M
+ * complex) to the device, builds a plan, solves with lambda = alpha *
+ * lambda_max, copies the support and weights back (capacity cap), frees
+ * everything. The host buffers may be pageable or pinned. */
+int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32_t N,
+                  double fov_rad, double alpha, double delta, const pc_solve_opts* opts,
+                  int32_t* idx_out_host, float* x_out_host, int32_t cap,
+                  pc_solve_stats* stats_host, void* stream);
+
+/* ------------------------------------------------------------------ profiling */
+
+/* Per-kernel-class timing with CUDA events recorded on the launching stream.
+ * pc_profile_begin() clears the records and starts recording every kernel
+ * launch of the library; pc_profile_end() synchronises on the recorded
+ * events, stops recording and writes one entry per kernel class (at most
+ * cap entries; *n_out receives the number of classes seen). Recording costs
+ * two event records per launch; it is off unless begun. Not thread-safe. */
+typedef struct {
+  char name[32];          /* kernel class, e.g. "grid", "fft_rows", "apgd"        */
+  int64_t launches;       /* timed launcher calls of this class                    */
+  int64_t kernels;        /* CUDA kernels (and memsets) those calls launched       */
+  double total_ms;        /* sum of event-measured launch durations              */
+} pc_kernel_time;
+
+int pc_profile_begin(void);
+int pc_profile_end(pc_kernel_time* out_host, int32_t cap, int32_t* n_out_host);
+
+/* ------------------------------------------------------------------ misc */
+
+const char* pc_last_error(void);
+int pc_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYCLEAN_H */

@@ -1,0 +1,154 @@
+// Error reporting, device-pointer checks and grow-only device buffers.
+#include <cstdarg>
+#include <cstring>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+static thread_local char g_last_error[1024] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+void clear_error() { g_last_error[0] = 0; }
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error state of this query
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int DevBuf::ensure(size_t nbytes) {
+  if (nbytes <= bytes && p != nullptr) return PC_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+  size_t want = nbytes < 256 ? 256 : nbytes;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return fail(PC_ERR_OOM, "device allocation of %zu bytes failed: %s", want,
+                cudaGetErrorString(e));
+  }
+  bytes = want;
+  return PC_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+}  // namespace pc
+
+extern "C" const char* pc_last_error(void) { return pc::g_last_error; }
+
+extern "C" int pc_abi_version(void) { return PC_ABI_VERSION; }
+
+// ------------------------------------------------------------------ kernel timing
+
+namespace pc {
+namespace {
+
+const char* const kProfNames[PROF_NCLASSES] = {"plan",     "grid",          "fft_rows", "fft_cols",
+                                               "residual", "gram",          "gram_finalize",
+                                               "apgd",     "select",        "misc"};
+
+struct ProfRec {
+  int cls;
+  int kernels;
+  cudaEvent_t a, b;
+};
+
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_pool;
+size_t g_pool_used = 0;
+
+cudaEvent_t pool_event() {
+  if (g_pool_used < g_pool.size()) return g_pool[g_pool_used++];
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_pool.push_back(e);
+  ++g_pool_used;
+  return e;
+}
+
+}  // namespace
+
+int prof_start(int cls, cudaStream_t st) {
+  if (!g_prof_on) return -1;
+  cudaEvent_t a = pool_event(), b = pool_event();
+  if (!a || !b) return -1;
+  cudaEventRecord(a, st);
+  g_prof.push_back(ProfRec{cls, 0, a, b});
+  return (int)g_prof.size() - 1;
+}
+
+void prof_stop(int token, cudaStream_t st, int kernels) {
+  if (token < 0 || token >= (int)g_prof.size()) return;
+  cudaEventRecord(g_prof[token].b, st);
+  g_prof[token].kernels = kernels;
+}
+
+}  // namespace pc
+
+extern "C" int pc_profile_begin(void) {
+  pc::g_prof.clear();
+  pc::g_pool_used = 0;
+  pc::g_prof_on = true;
+  return PC_OK;
+}
+
+extern "C" int pc_profile_end(pc_kernel_time* out, int32_t cap, int32_t* n_out) {
+  using namespace pc;
+  g_prof_on = false;
+  double tot[PROF_NCLASSES] = {0};
+  int64_t cnt[PROF_NCLASSES] = {0};
+  int64_t nk[PROF_NCLASSES] = {0};
+  for (const ProfRec& r : g_prof) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PC_ERR_CUDA, "pc_profile_end: event synchronisation failed");
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      tot[r.cls] += ms;
+      cnt[r.cls] += 1;
+      nk[r.cls] += r.kernels;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  g_prof.clear();
+  g_pool_used = 0;
+  int n = 0;
+  for (int c = 0; c < PROF_NCLASSES; ++c) {
+    if (!cnt[c]) continue;
+    if (out && n < cap) {
+      std::snprintf(out[n].name, sizeof(out[n].name), "%s", kProfNames[c]);
+      out[n].launches = cnt[c];
+      out[n].kernels = nk[c];
+      out[n].total_ms = tot[c];
+    }
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  return PC_OK;
+}

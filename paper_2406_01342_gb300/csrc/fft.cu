@@ -1,0 +1,219 @@
+// Pruned 2-D inverse FFT of every w-plane and the image-domain epilogue.
+//
+// After gridding, plane q holds grid_q[b][a] (a contiguous). The adjoint
+// needs, for image pixel (i, j) with i' = i - N/2, j' = j - N/2,
+//
+//   F_q[i'][j'] = sum_{a,b} grid_q[b][a] e^{+j 2 pi (a i' + b j') / G}
+//   mu[i][j]    = Re{ c_ij sum_q e^{+j 2 pi q t_ij} F_q[i'][j'] } * scale
+//
+// with c_ij = e^{j 2 pi w0 s_ij} / (n_ij psi(i'/G) psi(j'/G) psi(t_ij)),
+// t_ij = dw (s_ij - s_c), s = n - 1 (the w-screen of Sect. 2.1 and the
+// 1/n of the adjoint equation of Sect. 2.2); scale = 1/lambda for the
+// certificate of Sect. 3.2.
+//
+// Pass 1 (k_fft_rows): for each plane and row b, a length-G inverse FFT
+// along a, keeping the N outputs i' in [-N/2, N/2), stored transposed as
+// X_q[i][b] so that pass 2 reads contiguous rows.
+// Pass 2 (k_fft_cols): one CTA per image row i; for every plane a length-G
+// inverse FFT along b, keep N outputs, apply the plane phase and accumulate
+// in registers; then the per-pixel correction, write mu and its max |mu|.
+// Both passes run radix-4 (plus one radix-2) Stockham stages in shared memory
+// with a twiddle table e^{+2 pi i k / G}.
+#include "pc_internal.cuh"
+
+namespace pc {
+
+// Stockham autosort inverse FFT of `rows` rows of length G (row stride S)
+// held in buffer a, using b as scratch. All threads of the block take part.
+// Returns the buffer holding the result.
+__device__ float2* fft_rows_smem(float2* a, float2* b, int rows, int G, int logG, int S,
+                                 const float2* __restrict__ tw) {
+  const int nthr = blockDim.x;
+  int ns = 1;
+  if (logG & 1) {
+    const int half = G >> 1;
+    for (int f = threadIdx.x; f < rows * half; f += nthr) {
+      const int r = f / half, j = f - r * half;
+      const float2 v0 = a[r * S + j], v1 = a[r * S + j + half];
+      b[r * S + 2 * j] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      b[r * S + 2 * j + 1] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    ns = 2;
+  }
+  const int quarter = G >> 2;
+  for (; ns < G; ns <<= 2) {
+    const int step = G / (4 * ns);
+    for (int f = threadIdx.x; f < rows * quarter; f += nthr) {
+      const int r = f / quarter, j = f - r * quarter;
+      const int k = j & (ns - 1);
+      const float2* ar = a + r * S;
+      float2 v0 = ar[j], v1 = ar[j + quarter], v2 = ar[j + 2 * quarter], v3 = ar[j + 3 * quarter];
+      if (ns > 1) {
+        v1 = cmul(v1, tw[k * step]);
+        v2 = cmul(v2, tw[2 * k * step]);
+        v3 = cmul(v3, tw[3 * k * step]);
+      }
+      const float2 s0 = make_float2(v0.x + v2.x, v0.y + v2.y);
+      const float2 d0 = make_float2(v0.x - v2.x, v0.y - v2.y);
+      const float2 s1 = make_float2(v1.x + v3.x, v1.y + v3.y);
+      const float2 d1 = make_float2(v1.x - v3.x, v1.y - v3.y);
+      float2* br = b + r * S + (j - k) * 4 + k;
+      br[0] = make_float2(s0.x + s1.x, s0.y + s1.y);
+      br[ns] = make_float2(d0.x - d1.y, d0.y + d1.x);        // d0 + i d1
+      br[2 * ns] = make_float2(s0.x - s1.x, s0.y - s1.y);
+      br[3 * ns] = make_float2(d0.x + d1.y, d0.y - d1.x);    // d0 - i d1
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+__global__ void __launch_bounds__(256)
+k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int logG, int N, int R,
+           const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  const int S = G + 1;
+  float2* A = sm;
+  float2* B = sm + R * S;
+  const int q = blockIdx.y;
+  const int b0 = blockIdx.x * R;
+  const float2* src = grid + ((size_t)q * G + b0) * G;
+  for (int f = threadIdx.x; f < R * G; f += blockDim.x) {
+    const int r = f / G, a = f - r * G;
+    A[r * S + a] = src[(size_t)r * G + a];
+  }
+  __syncthreads();
+  const float2* res = fft_rows_smem(A, B, R, G, logG, S, tw);
+  float2* dst = X + (size_t)q * N * G + b0;
+  const int mask = G - 1, hN = N >> 1;
+  for (int f = threadIdx.x; f < N * R; f += blockDim.x) {
+    const int i = f / R, r = f - i * R;
+    dst[(size_t)i * G + r] = res[r * S + ((i - hN + G) & mask)];
+  }
+}
+
+template <int JPT>
+__global__ void __launch_bounds__(256)
+k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* __restrict__ mu,
+           int G, int logG, int N, int P, int wstack, const float2* __restrict__ tw, float scale,
+           unsigned* __restrict__ maxbits) {
+  extern __shared__ float2 sm[];
+  float2* A = sm;
+  float2* B = sm + G;
+  const int i = blockIdx.x;
+  const int mask = G - 1, hN = N >> 1;
+  float2 acc[JPT];
+  float4 pt[JPT];
+#pragma unroll
+  for (int jj = 0; jj < JPT; ++jj) {
+    acc[jj] = make_float2(0.f, 0.f);
+    const int j = threadIdx.x + jj * blockDim.x;
+    pt[jj] = j < N ? pix[(size_t)i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int q = 0; q < P; ++q) {
+    const float2* src = X + ((size_t)q * N + i) * G;
+    for (int a = threadIdx.x; a < G; a += blockDim.x) A[a] = src[a];
+    __syncthreads();
+    const float2* res = fft_rows_smem(A, B, 1, G, logG, G, tw);
+    const float qf = (float)q;
+#pragma unroll
+    for (int jj = 0; jj < JPT; ++jj) {
+      const int j = threadIdx.x + jj * blockDim.x;
+      if (j < N) {
+        const float2 v = res[(j - hN + G) & mask];
+        if (wstack) {
+          // q t in turns, with t = t_hi + t_lo, reduced exactly before sincospi
+          const float p = qf * pt[jj].z;
+          const float e = fmaf(qf, pt[jj].z, -p) + qf * pt[jj].w;
+          const float th = (p - rintf(p)) + e;
+          float sn, cs;
+          sincospif(2.0f * th, &sn, &cs);
+          acc[jj].x += v.x * cs - v.y * sn;
+          acc[jj].y += v.x * sn + v.y * cs;
+        } else {
+          acc[jj].x += v.x;
+          acc[jj].y += v.y;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  float amax = 0.0f;
+#pragma unroll
+  for (int jj = 0; jj < JPT; ++jj) {
+    const int j = threadIdx.x + jj * blockDim.x;
+    if (j < N) {
+      const float m = (pt[jj].x * acc[jj].x - pt[jj].y * acc[jj].y) * scale;
+      mu[(size_t)i * N + j] = m;
+      amax = fmaxf(amax, fabsf(m));
+      if (m != m) amax = __int_as_float(0x7fc00000);
+    }
+  }
+  unsigned bits = __float_as_uint(amax);
+  for (int off = 16; off; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+  if ((threadIdx.x & 31) == 0 && maxbits) atomicMax(maxbits, bits);
+}
+
+int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
+  ProfScope prof_scope_(PROF_FFT_ROWS, st);
+  // rows per CTA: R * (G + 1) * 8 bytes * 2 buffers <= ~132 KB
+  int R = 8192 / p->G;
+  if (R < 1) R = 1;
+  if (R > 64) R = 64;
+  const size_t smem = (size_t)2 * R * (p->G + 1) * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    PC_CUDA(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  dim3 grid(p->G / R, p->P);
+  prof_scope_.kernels = 1;
+  k_fft_rows<<<grid, 256, smem, st>>>(p->grid, p->fft1, p->G, p->logG, p->N, R, p->twiddle);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
+                             cudaStream_t st) {
+  ProfScope prof_scope_(PROF_FFT_COLS, st);
+  const size_t smem = (size_t)2 * p->G * sizeof(float2);
+  const int jpt = (p->N + 255) / 256;
+  prof_scope_.kernels = 1;
+  const int ws = p->wstack ? 1 : 0;
+#define PC_COLS_CASE(J)                                                                         \
+  case J: {                                                                                     \
+    static bool attr_set = false;                                                               \
+    if (!attr_set) {                                                                            \
+      PC_CUDA(cudaFuncSetAttribute(k_fft_cols<J>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                   200 * 1024));                                                \
+      attr_set = true;                                                                          \
+    }                                                                                           \
+    k_fft_cols<J><<<p->N, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->G, p->logG, p->N, p->P,  \
+                                           ws, p->twiddle, scale, maxbits);                     \
+    break;                                                                                      \
+  }
+  switch (jpt) {
+    PC_COLS_CASE(1)
+    PC_COLS_CASE(2)
+    case 3:
+    PC_COLS_CASE(4)
+    case 5: case 6: case 7:
+    PC_COLS_CASE(8)
+    case 9: case 10: case 11: case 12: case 13: case 14: case 15:
+    PC_COLS_CASE(16)
+    default:
+      return fail(PC_ERR_INVALID_ARG, "fft: image side %d too large", p->N);
+  }
+#undef PC_COLS_CASE
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+}  // namespace pc

@@ -1,0 +1,190 @@
+// Internal declarations of the PolyCLEAN GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "polyclean.h"
+
+namespace pc {
+
+// ------------------------------------------------------------------ errors
+
+int fail(int code, const char* fmt, ...);          // records a message, returns code
+void clear_error();
+
+#define PC_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return ::pc::fail(e_ == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA,    \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,     \
+                        __LINE__);                                                     \
+  } while (0)
+
+#define PC_LAUNCH_CHECK() PC_CUDA(cudaGetLastError())
+
+#define PC_TRY(expr)              \
+  do {                            \
+    int s_ = (expr);              \
+    if (s_ != PC_OK) return s_;   \
+  } while (0)
+
+// Device pointer check: true for device or managed memory of any device.
+bool is_device_ptr(const void* p);
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t nbytes);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Kernel timing (see pc_profile_begin): prof_start() returns a token or -1
+// when recording is off; prof_stop() records the end event of that token.
+enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
+                 PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
+                 PROF_NCLASSES };
+int prof_start(int cls, cudaStream_t st);
+void prof_stop(int token, cudaStream_t st, int kernels);
+
+// Records the launches of one launcher function; `kernels` counts the CUDA
+// kernels and memsets it issued (set before the scope ends).
+struct ProfScope {
+  int token;
+  cudaStream_t st;
+  int kernels = 0;
+  ProfScope(int cls, cudaStream_t s) : token(prof_start(cls, s)), st(s) {}
+  ~ProfScope() { prof_stop(token, st, kernels); }
+};
+
+// ------------------------------------------------------------------ constants
+
+constexpr int kMaxW = 8;              // largest supported ES kernel width
+constexpr int kGlNodes = 48;          // Gauss-Legendre nodes on [0, 1] for the ES transform
+
+// Exponential-of-semicircle kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1
+// (Barnett, Magland & af Klinteberg 2019). z is clamped into the support.
+__device__ __forceinline__ float es_kernel(float z, float beta) {
+  float q = fmaxf(1.0f - z * z, 0.0f);
+  return expf(beta * (sqrtf(q) - 1.0f));
+}
+
+// Phase of visibility k at atom s, in turns, reduced to [-1/2, 1/2]:
+//   theta = i' U_k + j' V_k + w_k (n_s - 1)
+// i' U + j' V is formed exactly in 32-bit fixed-point turns (wrapping
+// arithmetic is exact reduction mod 1), the w-term as a double-float product.
+// vis = {U_fx, V_fx, w_hi, w_lo}; atom = {packed (i',j'), s_hi, s_lo, scale}.
+__device__ __forceinline__ float phase_turns(int4 vis, float4 atom) {
+  int packed = __float_as_int(atom.x);
+  int ip = packed >> 16;                       // arithmetic shift: signed i'
+  int jp = (int)(short)(packed & 0xffff);      // signed j'
+  unsigned th = (unsigned)ip * (unsigned)vis.x + (unsigned)jp * (unsigned)vis.y;
+  float t_lm = (float)(int)th * 2.3283064365386963e-10f;   // 2^-32
+  float w_hi = __int_as_float(vis.z), w_lo = __int_as_float(vis.w);
+  float p = w_hi * atom.y;
+  float e = fmaf(w_hi, atom.y, -p);
+  e = fmaf(w_hi, atom.z, e);
+  e = fmaf(w_lo, atom.y, e);
+  float t = t_lm + (p - rintf(p)) + e;
+  return t - rintf(t);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ------------------------------------------------------------------ kernels (host launchers)
+
+// sparse.cu
+int launch_make_atoms(const int32_t* idx, const float* x, int S, int N, double dl, float4* atoms,
+                      cudaStream_t st);
+int launch_residual(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int S,
+                    float2* out, double* sumsq, cudaStream_t st);
+int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* atomsA, int nA,
+                const float4* atomsB, int nB, bool with_v, double* acc, int ldacc,
+                cudaStream_t st);
+int launch_gram_finalize(const double* acc, int ldacc, const int32_t* rows, int nrows, int ncols,
+                         bool with_v, const int32_t* oldpos, float* G, int ldg, float* b,
+                         cudaStream_t st);
+int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double dl,
+                       float4* atoms, int* dflag, cudaStream_t st);
+
+// select.cu
+int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark, int32_t* out,
+                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st);
+int launch_mark(uint8_t* mark, const int32_t* idx, int n, uint8_t value, cudaStream_t st);
+int launch_old_positions(const int32_t* newidx, int n_new, const int32_t* oldidx, int n_old,
+                         int32_t* oldpos, cudaStream_t st);
+int launch_compact_nonzero(const float* x, int n, int32_t* keep, int32_t* count_dev,
+                           cudaStream_t st);
+int launch_compact_new(const int32_t* oldpos, int n, int32_t* rows, int32_t* count_dev,
+                       cudaStream_t st);
+
+// apgd.cu
+int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
+             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st);
+
+// grid.cu / fft.cu
+int launch_grid(pc_plan_s* p, const float2* r, cudaStream_t st);
+int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
+int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
+                             cudaStream_t st);
+
+}  // namespace pc
+
+// ------------------------------------------------------------------ plan object
+
+struct pc_plan_s {
+  int device = 0;
+  int64_t M = 0;
+  int N = 0;          // image side
+  int G = 0;          // oversampled grid side (power of two >= 2N)
+  int logG = 0;
+  int T = 32;         // gridding tile side
+  int nT = 0;         // tiles per side = G / T
+  int W = 7;          // ES kernel width
+  int P = 1;          // number of w-planes (1: no w-stacking)
+  int Qg = 1;         // planes per gridding CTA
+  double fov = 0, dl = 0, beta = 0;
+  double w0 = 0, dw = 1, s_c = 0, w_min = 0, w_max = 0;
+  bool wstack = false;
+  int64_t n_slots = 0;
+  int n_sub = 0;
+
+  // per visibility
+  int4* vis_fx = nullptr;        // {U_fx, V_fx, w_hi, w_lo}
+  // binned slots (sorted by tile, plane start)
+  int2* slot_vis = nullptr;      // {visibility, (a0 + 64) | (b0 + 64) << 8 | plane_start << 16}
+  float4* slot_geom = nullptr;   // {gu - a0, gv - b0, xw - plane_start, tau (turns)}
+  int4* subs = nullptr;          // gridding sub-problems {tile, plane group, start, end}
+  // image-domain tables
+  float4* pix_tab = nullptr;     // per pixel {Re c d, Im c d, t_hi, t_lo}
+  float2* twiddle = nullptr;     // e^{+2 pi i k / G}
+  // workspaces
+  float2* grid = nullptr;        // P x G x G  (b-major rows, a contiguous)
+  float2* fft1 = nullptr;        // P x N x G  (after the pass along a)
+  float2* resid = nullptr;       // M
+  float* mu = nullptr;           // N x N
+  uint8_t* mark = nullptr;       // N x N membership marks (kept all-zero between calls)
+  double* dscal = nullptr;       // 8 float64 scalars
+  unsigned* uscal = nullptr;     // 8 uint scalars
+  int32_t* iscal = nullptr;      // 8 int scalars
+  int32_t* sel_blocks = nullptr; // per-block counts of the select
+  int sel_blocks_n = 0;
+
+  // solver workspace (grown on demand)
+  pc::DevBuf atomsA, atomsB, idxA, idxB, xA, xB, oldpos, newrows, keep, GA, GB, bA, bB, acc;
+
+  std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
+};

@@ -1,0 +1,642 @@
+// Plan construction: visibility binning by (gridding tile, w-plane), stable
+// radix sort, sub-problem list, per-pixel kernel-correction table, workspace.
+//
+// The adjoint Phi* of Sect. 2.2 is evaluated as a type-1 non-uniform FFT
+// (Sect. 4.2): each visibility is spread with an exponential-of-semicircle
+// kernel of width W onto a 2x (or more) oversampled uv grid of side G, and
+// onto P w-planes (w-stacking, the w-term of Sect. 2.1); every plane is
+// inverse-FFT'd and the image is corrected for the kernel's Fourier transform,
+// the w-screen and the 1/n factor.
+//
+// Geometry (all in FP64 here, once per plan):
+//   g_u = frac(u dl) G  in [0, G)   grid coordinate in cells (the uv grid is G-periodic)
+//   x_w = (w - w0) / dw             plane coordinate
+//   planes p = ceil(x_w - W/2) ... + W - 1, with dw = 1 / (2 (s_max - s_min)),
+//   s = n - 1 over the image, so that |dw (s - s_c)| <= 1/4 (oversampling 2 in w).
+// Each visibility is replicated into every tile its W x W footprint touches
+// (at most 2 x 2 tiles since W <= T), so a gridding CTA only ever reads the
+// visibilities that touch its own tile.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+// ------------------------------------------------------------------ host math
+
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on the Legendre recurrence).
+static void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[i] = 0.5 * (1.0 + z);
+    w[i] = 0.5 * 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Fourier transform of the ES kernel in cell units at frequency t (cycles per cell):
+//   psi(t) = int_{-W/2}^{W/2} phi(2y/W) e^{-j 2 pi y t} dy = W int_0^1 phi(z) cos(pi W z t) dz.
+static double psi_hat_host(double t, int W, double beta, const std::vector<double>& gx,
+                           const std::vector<double>& gw) {
+  double s = 0.0;
+  for (size_t q = 0; q < gx.size(); ++q) {
+    double z = gx[q];
+    double phi = std::exp(beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0));
+    s += gw[q] * phi * std::cos(M_PI * W * z * t);
+  }
+  return W * s;
+}
+
+// ------------------------------------------------------------------ device kernels
+
+// Order-preserving map of a double to uint64 (for atomic min / max).
+__device__ __forceinline__ unsigned long long ordered_bits(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void k_uvw_scan(const double* __restrict__ uvw, int64_t M,
+                           unsigned long long* wmin, unsigned long long* wmax, int* bad) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  int nonfinite = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+    if (!isfinite(u) || !isfinite(v) || !isfinite(w)) nonfinite = 1;
+    unsigned long long o = ordered_bits(w);
+    lo = o < lo ? o : lo;
+    hi = o > hi ? o : hi;
+  }
+  for (int off = 16; off; off >>= 1) {
+    unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, off);
+    unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, off);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+    nonfinite |= __shfl_xor_sync(0xffffffffu, nonfinite, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(wmin, lo);
+    atomicMax(wmax, hi);
+    if (nonfinite) atomicOr(bad, 1);
+  }
+}
+
+struct BinGeom {
+  double dl, w0, dw, s_c;
+  int G, T, nT, W, P;
+  unsigned nbins;
+};
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Grid coordinate in cells of a baseline component: frac(u dl) G in [0, G).
+__device__ __forceinline__ double grid_coord(double u, double dl, int G, double* frac_out) {
+  double U = u * dl;
+  double f = U - rint(U);
+  *frac_out = f;
+  double g = f * G;
+  if (g < 0.0) g += G;
+  if (g >= G) g -= G;
+  return g;
+}
+
+// Per visibility: fixed-point phase coefficients and up to 4 bin keys (one per
+// tile touched by the footprint); unused key slots get the key nbins.
+__global__ void k_vis_prep(const double* __restrict__ uvw, int64_t M, BinGeom g,
+                           int4* __restrict__ vis_fx, unsigned* __restrict__ keys,
+                           unsigned* __restrict__ ids) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+  double fu, fv;
+  double gu = grid_coord(u, g.dl, g.G, &fu);
+  double gv = grid_coord(v, g.dl, g.G, &fv);
+  // 32-bit fixed-point turns of u dl and v dl (two's complement wrap = mod 1)
+  int Ufx = (int)(unsigned)(long long)llrint(fu * 4294967296.0);
+  int Vfx = (int)(unsigned)(long long)llrint(fv * 4294967296.0);
+  float w_hi = (float)w;
+  float w_lo = (float)(w - (double)w_hi);
+  vis_fx[k] = make_int4(Ufx, Vfx, __float_as_int(w_hi), __float_as_int(w_lo));
+
+  int a0 = (int)ceil(gu - 0.5 * g.W);
+  int b0 = (int)ceil(gv - 0.5 * g.W);
+  int ta0 = floor_div(a0, g.T), ta1 = floor_div(a0 + g.W - 1, g.T);
+  int tb0 = floor_div(b0, g.T), tb1 = floor_div(b0 + g.W - 1, g.T);
+  int ps = 0;
+  if (g.P > 1) ps = (int)ceil((w - g.w0) / g.dw - 0.5 * g.W);
+  for (int c = 0; c < 4; ++c) {
+    int ta = ta0 + (c & 1), tb = tb0 + (c >> 1);
+    unsigned key = g.nbins;
+    if (ta <= ta1 && tb <= tb1) {
+      int tu = ((ta % g.nT) + g.nT) % g.nT;
+      int tv = ((tb % g.nT) + g.nT) % g.nT;
+      key = (unsigned)((tv * g.nT + tu) * g.P + ps);
+    }
+    keys[4 * k + c] = key;
+    ids[4 * k + c] = (unsigned)(4 * k + c);
+  }
+}
+
+// ---- stable LSD radix sort, 8-bit digits, 4096 keys per block
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_ITEMS = RS_THREADS * RS_ROUNDS;
+
+__global__ void k_rs_hist(const unsigned* __restrict__ keys, int64_t n, int shift,
+                          unsigned* __restrict__ hist, int nblk) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_ITEMS;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of L unsigned values by one block of 1024 threads.
+__global__ void k_scan_single(unsigned* __restrict__ a, int64_t L) {
+  __shared__ unsigned warp_tot[32];
+  int64_t chunk = (L + blockDim.x - 1) / blockDim.x;
+  int64_t lo = threadIdx.x * chunk, hi = lo + chunk < L ? lo + chunk : L;
+  unsigned s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += a[i];
+  // block exclusive scan of s
+  unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned incl = s;
+  for (int off = 1; off < 32; off <<= 1) {
+    unsigned t = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned t = warp_tot[lane];
+    unsigned ti = t;
+    for (int off = 1; off < 32; off <<= 1) {
+      unsigned u = __shfl_up_sync(0xffffffffu, ti, off);
+      if (lane >= off) ti += u;
+    }
+    warp_tot[lane] = ti - t;
+  }
+  __syncthreads();
+  unsigned run = warp_tot[wid] + incl - s;
+  for (int64_t i = lo; i < hi; ++i) {
+    unsigned v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
+                             unsigned* __restrict__ kout, unsigned* __restrict__ vout, int64_t n,
+                             int shift, const unsigned* __restrict__ hist, int nblk) {
+  __shared__ unsigned s_base[256];
+  __shared__ unsigned s_w[RS_THREADS / 32][256];
+  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_base[tid] = hist[(int64_t)tid * nblk + blockIdx.x];
+  int64_t base = (int64_t)blockIdx.x * RS_ITEMS;
+  unsigned lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    for (int w = 0; w < RS_THREADS / 32; ++w) s_w[w][tid] = 0;
+    __syncthreads();
+    int64_t i = base + r * RS_THREADS + tid;
+    bool valid = i < n;
+    unsigned key = valid ? kin[i] : 0u;
+    unsigned val = valid ? vin[i] : 0u;
+    unsigned d = valid ? ((key >> shift) & 255u) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    unsigned rank = __popc(peers & lt_mask);
+    if (valid && lane == __ffs(peers) - 1) s_w[warp][d] = __popc(peers);
+    __syncthreads();
+    unsigned run = 0;
+    for (int w = 0; w < RS_THREADS / 32; ++w) {
+      unsigned c = s_w[w][tid];
+      s_w[w][tid] = run;
+      run += c;
+    }
+    __syncthreads();
+    if (valid) {
+      unsigned pos = s_base[d] + s_w[warp][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    s_base[tid] += run;
+  }
+}
+
+// off[b] = first sorted position with key >= b, for b in [0, nbins]; keys <= nbins.
+__global__ void k_bin_offsets(const unsigned* __restrict__ keys, int64_t n, unsigned nbins,
+                              int* __restrict__ off) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j > n) return;
+  long long kcur = j < n ? (long long)keys[j] : (long long)nbins;
+  long long kprev = j == 0 ? -1 : (long long)keys[j - 1];
+  for (long long b = kprev + 1; b <= kcur && b <= (long long)nbins; ++b) off[b] = (int)j;
+}
+
+// Slot records in sorted order.
+__global__ void k_slot_gather(const double* __restrict__ uvw, const unsigned* __restrict__ ids,
+                              int64_t n_slots, BinGeom g, int2* __restrict__ slot_vis,
+                              float4* __restrict__ slot_geom) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n_slots) return;
+  unsigned id = ids[j];
+  int64_t k = id >> 2;
+  int c = id & 3;
+  double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+  double fu, fv;
+  double gu = grid_coord(u, g.dl, g.G, &fu);
+  double gv = grid_coord(v, g.dl, g.G, &fv);
+  int a0 = (int)ceil(gu - 0.5 * g.W);
+  int b0 = (int)ceil(gv - 0.5 * g.W);
+  int ta = floor_div(a0, g.T) + (c & 1);
+  int tb = floor_div(b0, g.T) + (c >> 1);
+  int a0l = a0 - ta * g.T;   // footprint start relative to the tile, in [-W+1, T-1]
+  int b0l = b0 - tb * g.T;
+  float xw = 0.0f, tau = 0.0f;
+  int ps = 0;
+  if (g.P > 1) {
+    double x = (w - g.w0) / g.dw;
+    ps = (int)ceil(x - 0.5 * g.W);
+    xw = (float)(x - ps);
+    double tt = (w - g.w0) * g.s_c;     // pre-twiddle e^{j 2 pi (w - w0) s_c}, in turns
+    tau = (float)(tt - rint(tt));
+  }
+  slot_vis[j] = make_int2((int)k, (a0l + 64) | ((b0l + 64) << 8) | (ps << 16));
+  slot_geom[j] = make_float4((float)(gu - a0), (float)(gv - b0), xw, tau);
+}
+
+struct PixGeom {
+  double dl, w0, dw, s_c, beta;
+  int N, W;
+  bool wstack;
+};
+
+// Per-pixel epilogue coefficients: {Re, Im} of e^{j 2 pi w0 s} / (n psi(i') psi(j') psi_w(t))
+// and t = dw (s - s_c) as a double-float (hi, lo).
+__global__ void k_pix_tab(PixGeom g, const double* __restrict__ psi_uv,
+                          const double* __restrict__ glx, const double* __restrict__ glw,
+                          int nq, float4* __restrict__ out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t NN = (int64_t)g.N * g.N;
+  if (p >= NN) return;
+  int i = (int)(p / g.N), j = (int)(p % g.N);
+  double l = (i - g.N / 2) * g.dl, m = (j - g.N / 2) * g.dl;
+  double r2 = l * l + m * m;
+  double n = sqrt(1.0 - r2);
+  double s = -r2 / (1.0 + n);        // n - 1 without cancellation
+  double t = 0.0, psiw = 1.0;
+  if (g.wstack) {
+    t = g.dw * (s - g.s_c);
+    double acc = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      double z = glx[q];
+      double phi = exp(g.beta * (sqrt(fmax(0.0, 1.0 - z * z)) - 1.0));
+      acc += glw[q] * phi * cospi(g.W * z * t);
+    }
+    psiw = g.W * acc;
+  }
+  double ct = g.w0 * s;
+  ct -= rint(ct);
+  double sn, cs;
+  sincospi(2.0 * ct, &sn, &cs);
+  double d = 1.0 / (n * psi_uv[i] * psi_uv[j] * psiw);
+  float t_hi = (float)t;
+  float t_lo = (float)(t - (double)t_hi);
+  out[p] = make_float4((float)(cs * d), (float)(sn * d), t_hi, t_lo);
+}
+
+static int dev_alloc(pc_plan_s* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(PC_ERR_OOM, "plan: device allocation of %zu bytes failed: %s", bytes,
+                cudaGetErrorString(e));
+  }
+  p->owned.push_back(*ptr);
+  return PC_OK;
+}
+
+template <class T>
+static int dev_alloc_t(pc_plan_s* p, T** ptr, size_t count) {
+  return dev_alloc(p, reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+// Temporary device buffers of plan construction, freed on every exit path.
+struct TmpBufs {
+  std::vector<void*> v;
+  ~TmpBufs() {
+    for (void* q : v) cudaFree(q);
+  }
+  int alloc(void** ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return fail(PC_ERR_OOM, "plan: temporary allocation of %zu bytes failed", bytes);
+    }
+    v.push_back(*ptr);
+    return PC_OK;
+  }
+};
+
+static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_planes) {
+  const int64_t M = p->M;
+  const int N = p->N;
+  TmpBufs tmp;
+
+  // ---- w range and finiteness
+  if (M > 0) {
+    unsigned long long* dmm;
+    int* dbad;
+    PC_TRY(tmp.alloc((void**)&dmm, 2 * sizeof(unsigned long long) + sizeof(int) * 2));
+    dbad = reinterpret_cast<int*>(dmm + 2);
+    unsigned long long init[2] = {~0ull, 0ull};
+    int zero[2] = {0, 0};
+    PC_CUDA(cudaMemcpyAsync(dmm, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(dbad, zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+    int blocks = (int)std::min<int64_t>(4096, (M + 255) / 256);
+    k_uvw_scan<<<blocks, 256, 0, st>>>(uvw, M, dmm, dmm + 1, dbad);
+    PC_LAUNCH_CHECK();
+    unsigned long long hmm[2];
+    int hbad[2];
+    PC_CUDA(cudaMemcpyAsync(hmm, dmm, sizeof(hmm), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaMemcpyAsync(hbad, dbad, sizeof(hbad), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    if (hbad[0]) return fail(PC_ERR_INVALID_ARG, "plan: uvw contains NaN or Inf");
+    auto unmap = [](unsigned long long o) {
+      unsigned long long b = (o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o;
+      double d;
+      std::memcpy(&d, &b, sizeof(d));
+      return d;
+    };
+    p->w_min = unmap(hmm[0]);
+    p->w_max = unmap(hmm[1]);
+  }
+
+  // ---- geometry
+  p->G = 32;
+  while (p->G < 2 * N) p->G *= 2;
+  p->logG = 0;
+  while ((1 << p->logG) < p->G) ++p->logG;
+  p->nT = p->G / p->T;
+  p->dl = p->fov / N;
+  p->beta = 2.30 * p->W;
+  const double half = 0.5 * N * p->dl;
+  const double r2c = 2.0 * half * half;
+  const double s_min = -r2c / (1.0 + std::sqrt(1.0 - r2c));
+  const double s_max = 0.0;
+  if (M > 0 && p->w_max > p->w_min) {
+    p->wstack = true;
+    p->dw = 1.0 / (2.0 * (s_max - s_min));
+    long long planes = (long long)std::ceil((p->w_max - p->w_min) / p->dw) + p->W;
+    if (planes > max_planes)
+      return fail(PC_ERR_INVALID_ARG, "plan: %lld w-planes needed, max_planes is %d", planes,
+                  max_planes);
+    p->P = (int)planes;
+    p->w0 = p->w_min - 0.5 * p->W * p->dw;
+    p->s_c = 0.5 * (s_min + s_max);
+  } else {
+    p->wstack = false;
+    p->P = 1;
+    p->dw = 1.0;
+    p->w0 = M > 0 ? p->w_min : 0.0;
+    p->s_c = 0.0;
+  }
+  {
+    int ngroups = ceil_div(p->P, 12);
+    p->Qg = ceil_div(p->P, ngroups);
+  }
+
+  // ---- tables: ES transform, twiddles, per-pixel corrections
+  std::vector<double> gx, gw;
+  gauss_legendre01(kGlNodes, gx, gw);
+  std::vector<double> psi(N);
+  for (int i = 0; i < N; ++i) psi[i] = psi_hat_host((double)(i - N / 2) / p->G, p->W, p->beta, gx, gw);
+  double *d_psi, *d_gx, *d_gw;
+  PC_TRY(tmp.alloc((void**)&d_psi, sizeof(double) * (N + 2 * kGlNodes)));
+  d_gx = d_psi + N;
+  d_gw = d_gx + kGlNodes;
+  PC_CUDA(cudaMemcpyAsync(d_psi, psi.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaMemcpyAsync(d_gx, gx.data(), sizeof(double) * kGlNodes, cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaMemcpyAsync(d_gw, gw.data(), sizeof(double) * kGlNodes, cudaMemcpyHostToDevice, st));
+  const int64_t NN = (int64_t)N * N;
+  PC_TRY(dev_alloc_t(p, &p->pix_tab, NN));
+  {
+    PixGeom pg{p->dl, p->w0, p->dw, p->s_c, p->beta, N, p->W, p->wstack};
+    k_pix_tab<<<ceil_div(NN, 256), 256, 0, st>>>(pg, d_psi, d_gx, d_gw, kGlNodes, p->pix_tab);
+    PC_LAUNCH_CHECK();
+  }
+  std::vector<float2> tw(p->G);
+  for (int k = 0; k < p->G; ++k) {
+    double a = 2.0 * M_PI * k / p->G;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  PC_TRY(dev_alloc_t(p, &p->twiddle, p->G));
+  PC_CUDA(cudaMemcpyAsync(p->twiddle, tw.data(), sizeof(float2) * p->G, cudaMemcpyHostToDevice, st));
+
+  // ---- workspaces
+  PC_TRY(dev_alloc_t(p, &p->grid, (size_t)p->P * p->G * p->G));
+  PC_TRY(dev_alloc_t(p, &p->fft1, (size_t)p->P * N * p->G));
+  PC_TRY(dev_alloc_t(p, &p->resid, (size_t)std::max<int64_t>(M, 1)));
+  PC_TRY(dev_alloc_t(p, &p->mu, (size_t)NN));
+  PC_TRY(dev_alloc_t(p, &p->mark, (size_t)NN));
+  PC_CUDA(cudaMemsetAsync(p->mark, 0, NN, st));
+  PC_TRY(dev_alloc_t(p, &p->dscal, 8));
+  PC_TRY(dev_alloc_t(p, &p->uscal, 8));
+  PC_TRY(dev_alloc_t(p, &p->iscal, 8));
+  p->sel_blocks_n = ceil_div(NN, 4096);
+  PC_TRY(dev_alloc_t(p, &p->sel_blocks, (size_t)p->sel_blocks_n + 1));
+  PC_TRY(dev_alloc_t(p, &p->vis_fx, (size_t)std::max<int64_t>(M, 1)));
+
+  if (M == 0) {
+    p->n_slots = 0;
+    p->n_sub = 0;
+    PC_TRY(dev_alloc_t(p, &p->slot_vis, 1));
+    PC_TRY(dev_alloc_t(p, &p->slot_geom, 1));
+    PC_TRY(dev_alloc_t(p, &p->subs, 1));
+    PC_CUDA(cudaStreamSynchronize(st));
+    return PC_OK;
+  }
+
+  // ---- binning keys
+  const unsigned nbins = (unsigned)((int64_t)p->nT * p->nT * p->P);
+  if ((int64_t)p->nT * p->nT * p->P >= (1ll << 31))
+    return fail(PC_ERR_INVALID_ARG, "plan: too many (tile, plane) bins");
+  const int64_t nkeys = 4 * M;
+  unsigned *k0, *k1, *v0, *v1, *hist;
+  int* off;
+  PC_TRY(tmp.alloc((void**)&k0, sizeof(unsigned) * nkeys));
+  PC_TRY(tmp.alloc((void**)&k1, sizeof(unsigned) * nkeys));
+  PC_TRY(tmp.alloc((void**)&v0, sizeof(unsigned) * nkeys));
+  PC_TRY(tmp.alloc((void**)&v1, sizeof(unsigned) * nkeys));
+  const int nblk = ceil_div(nkeys, RS_ITEMS);
+  PC_TRY(tmp.alloc((void**)&hist, sizeof(unsigned) * 256 * (size_t)nblk));
+  PC_TRY(tmp.alloc((void**)&off, sizeof(int) * ((size_t)nbins + 1)));
+  BinGeom bg{p->dl, p->w0, p->dw, p->s_c, p->G, p->T, p->nT, p->W, p->P, nbins};
+  k_vis_prep<<<ceil_div(M, 256), 256, 0, st>>>(uvw, M, bg, p->vis_fx, k0, v0);
+  PC_LAUNCH_CHECK();
+
+  // ---- stable radix sort of the keys (values = slot ids)
+  int nbits = 1;
+  while ((1ull << nbits) <= nbins) ++nbits;
+  unsigned *kin = k0, *vin = v0, *kout = k1, *vout = v1;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(kin, nkeys, shift, hist, nblk);
+    PC_LAUNCH_CHECK();
+    k_scan_single<<<1, 1024, 0, st>>>(hist, 256 * (int64_t)nblk);
+    PC_LAUNCH_CHECK();
+    k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(kin, vin, kout, vout, nkeys, shift, hist, nblk);
+    PC_LAUNCH_CHECK();
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  k_bin_offsets<<<ceil_div(nkeys + 1, 256), 256, 0, st>>>(kin, nkeys, nbins, off);
+  PC_LAUNCH_CHECK();
+  std::vector<int> hoff((size_t)nbins + 1);
+  PC_CUDA(cudaMemcpyAsync(hoff.data(), off, sizeof(int) * hoff.size(), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  p->n_slots = hoff[nbins];
+
+  PC_TRY(dev_alloc_t(p, &p->slot_vis, (size_t)std::max<int64_t>(p->n_slots, 1)));
+  PC_TRY(dev_alloc_t(p, &p->slot_geom, (size_t)std::max<int64_t>(p->n_slots, 1)));
+  if (p->n_slots > 0) {
+    k_slot_gather<<<ceil_div(p->n_slots, 256), 256, 0, st>>>(uvw, vin, p->n_slots, bg,
+                                                             p->slot_vis, p->slot_geom);
+    PC_LAUNCH_CHECK();
+  }
+
+  // ---- gridding sub-problems: (tile, plane group) ranges split into chunks
+  const int kMaxSlotsPerSub = 2048;
+  std::vector<int4> subs;
+  const int ngroups = ceil_div(p->P, p->Qg);
+  for (int t = 0; t < p->nT * p->nT; ++t) {
+    for (int gq = 0; gq < ngroups; ++gq) {
+      int q0 = gq * p->Qg;
+      int ps_lo = 0, ps_hi = 0;
+      if (p->wstack) {
+        ps_lo = std::max(0, q0 - p->W + 1);
+        ps_hi = std::min(p->P - 1, q0 + p->Qg - 1);
+      }
+      int s0 = hoff[(size_t)t * p->P + ps_lo];
+      int s1 = hoff[(size_t)t * p->P + ps_hi + 1];
+      for (int s = s0; s < s1; s += kMaxSlotsPerSub)
+        subs.push_back(make_int4(t, gq, s, std::min(s1, s + kMaxSlotsPerSub)));
+    }
+  }
+  p->n_sub = (int)subs.size();
+  PC_TRY(dev_alloc_t(p, &p->subs, std::max<size_t>(subs.size(), 1)));
+  if (!subs.empty())
+    PC_CUDA(cudaMemcpyAsync(p->subs, subs.data(), sizeof(int4) * subs.size(),
+                            cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
+                              const pc_plan_opts* opts, void* stream, pc_plan_t* plan_out) {
+  clear_error();
+  if (!plan_out) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: plan_out is NULL");
+  *plan_out = nullptr;
+  if (opts && opts->version != PC_ABI_VERSION)
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: opts->version %d != %d", opts->version,
+                PC_ABI_VERSION);
+  if (M < 0 || M > (1ll << 29))
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: M = %lld out of range [0, 2^29]", (long long)M);
+  if (N < 16 || N > 4096 || (N & 1))
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: N = %d must be even and in [16, 4096]", N);
+  if (!(fov_rad > 0.0) || !(fov_rad < 1.4))
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: fov_rad = %g must be in (0, 1.4)", fov_rad);
+  if (M > 0 && !is_device_ptr(uvw_dev))
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: uvw_dev is not a device pointer");
+  int W = (opts && opts->kernel_width) ? opts->kernel_width : 7;
+  int T = (opts && opts->tile) ? opts->tile : 32;
+  int maxP = (opts && opts->max_planes) ? opts->max_planes : 256;
+  if (W < 4 || W > kMaxW) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: kernel_width %d not in [4, 8]", W);
+  if (T != 16 && T != 32) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: tile %d not 16 or 32", T);
+  if (maxP < 1 || maxP > 4096) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: max_planes %d", maxP);
+
+  pc_plan_s* p = new pc_plan_s();
+  cudaGetDevice(&p->device);
+  p->M = M;
+  p->N = N;
+  p->fov = fov_rad;
+  p->W = W;
+  p->T = T;
+  int rc = build_plan(p, uvw_dev, (cudaStream_t)stream, maxP);
+  if (rc != PC_OK) {
+    pc_plan_destroy(p);
+    return rc;
+  }
+  *plan_out = p;
+  return PC_OK;
+}
+
+extern "C" void pc_plan_destroy(pc_plan_t p) {
+  if (!p) return;
+  for (void* q : p->owned) cudaFree(q);
+  p->atomsA.release();
+  p->atomsB.release();
+  p->idxA.release();
+  p->idxB.release();
+  p->xA.release();
+  p->xB.release();
+  p->oldpos.release();
+  p->newrows.release();
+  p->keep.release();
+  p->GA.release();
+  p->GB.release();
+  p->bA.release();
+  p->bB.release();
+  p->acc.release();
+  delete p;
+}
+
+extern "C" int pc_plan_info(pc_plan_t p, int32_t* grid_side, int32_t* tile, int32_t* n_planes,
+                            int64_t* n_slots, int32_t* kernel_width, double* dw) {
+  if (!p) return fail(PC_ERR_INVALID_ARG, "pc_plan_info: NULL plan");
+  if (grid_side) *grid_side = p->G;
+  if (tile) *tile = p->T;
+  if (n_planes) *n_planes = p->P;
+  if (n_slots) *n_slots = p->n_slots;
+  if (kernel_width) *kernel_width = p->W;
+  if (dw) *dw = p->dw;
+  return PC_OK;
+}

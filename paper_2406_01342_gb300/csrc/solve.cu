@@ -1,0 +1,601 @@
+// C ABI entry points: operators, hot-path steps and the Polyatomic
+// Frank-Wolfe driver (Algorithm 2). The driver runs on the host and keeps all
+// state on the device; it reads back a handful of scalars per Frank-Wolfe
+// iteration (objective, ||mu||_inf, |S u I|, |supp|) to size the next launches
+// and to take the stopping decision.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+namespace {
+
+// Gdst[i][j] = Gsrc[map[i]][map[j]] where both map entries are >= 0.
+__global__ void k_gather_sym(const float* __restrict__ Gsrc, int lds, const int32_t* __restrict__ map,
+                             int n, float* __restrict__ Gdst, int ldd) {
+  const int i = blockIdx.y;
+  const int mi = map[i];
+  if (mi < 0) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int mj = map[j];
+    if (mj >= 0) Gdst[(size_t)i * ldd + j] = Gsrc[(size_t)mi * lds + mj];
+  }
+}
+
+// dst[i] = map[i] >= 0 ? src[map[i]] : fill
+template <class T>
+__global__ void k_gather_vec(const T* __restrict__ src, const int32_t* __restrict__ map, int n,
+                             T* __restrict__ dst, T fill) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = map[i];
+  dst[i] = m >= 0 ? src[m] : fill;
+}
+
+// sum |x| in float64 (one block)
+__global__ void k_l1(const float* __restrict__ x, int n, double* __restrict__ out) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs((double)x[i]);
+  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    *out = t;
+  }
+}
+
+int gather_sym(const float* Gsrc, int lds, const int32_t* map, int n, float* Gdst, int ldd,
+               cudaStream_t st) {
+  ProfScope prof_scope_(PROF_MISC, st);
+  if (n <= 0) return PC_OK;
+  dim3 grid(std::max(1, std::min(ceil_div(n, 256), 32)), n);
+  prof_scope_.kernels = 1;
+  k_gather_sym<<<grid, 256, 0, st>>>(Gsrc, lds, map, n, Gdst, ldd);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+template <class T>
+int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStream_t st) {
+  ProfScope prof_scope_(PROF_MISC, st);
+  if (n <= 0) return PC_OK;
+  prof_scope_.kernels = 1;
+  k_gather_vec<T><<<ceil_div(n, 256), 256, 0, st>>>(src, map, n, dst, fill);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
+
+int adjoint_grid_impl(pc_plan_s* p, const float2* h, float* img, float scale, unsigned* maxbits,
+                      cudaStream_t st) {
+  PC_TRY(launch_grid(p, h, st));
+  PC_TRY(launch_fft_rows(p, st));
+  PC_TRY(launch_fft_cols_epilogue(p, img, scale, maxbits, st));
+  return PC_OK;
+}
+
+int check_plan(pc_plan_s* p, const char* fn) {
+  if (!p) return fail(PC_ERR_INVALID_ARG, "%s: NULL plan", fn);
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device)
+    return fail(PC_ERR_INVALID_ARG, "%s: plan was built on device %d, current is %d", fn,
+                p->device, dev);
+  return PC_OK;
+}
+
+int check_dev(const void* ptr, bool needed, const char* fn, const char* name) {
+  if (!needed) return PC_OK;
+  if (!is_device_ptr(ptr)) return fail(PC_ERR_INVALID_ARG, "%s: %s is not a device pointer", fn, name);
+  return PC_OK;
+}
+
+int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t st) {
+  PC_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+float bits_to_float(unsigned b) {
+  float f;
+  std::memcpy(&f, &b, sizeof(f));
+  return f;
+}
+
+// Small per-device scratch for pc_apgd (no plan): 4 ints + 4 doubles.
+int apgd_scratch(void** out) {
+  static std::map<int, void*> bufs;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto it = bufs.find(dev);
+  if (it != bufs.end()) {
+    *out = it->second;
+    return PC_OK;
+  }
+  void* p = nullptr;
+  PC_CUDA(cudaMalloc(&p, 64));
+  bufs[dev] = p;
+  *out = p;
+  return PC_OK;
+}
+
+}  // namespace
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" int pc_forward_sparse(pc_plan_t p, const int32_t* idx, const float* x, int32_t S,
+                                 pc_c32* y, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_forward_sparse"));
+  if (S < 0) return fail(PC_ERR_INVALID_ARG, "pc_forward_sparse: S < 0");
+  PC_TRY(check_dev(idx, S > 0, "pc_forward_sparse", "idx_dev"));
+  PC_TRY(check_dev(x, S > 0, "pc_forward_sparse", "x_dev"));
+  PC_TRY(check_dev(y, p->M > 0, "pc_forward_sparse", "y_dev"));
+  cudaStream_t st = SS(stream);
+  PC_TRY(p->atomsA.ensure(sizeof(float4) * std::max(S, 1)));
+  PC_TRY(make_atoms_checked(idx, x, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
+  PC_TRY(launch_residual(p->vis_fx, nullptr, p->M, p->atomsA.as<float4>(), S,
+                         reinterpret_cast<float2*>(y), nullptr, st));
+  return PC_OK;
+}
+
+extern "C" int pc_adjoint_sparse(pc_plan_t p, const pc_c32* y, const int32_t* idx, int32_t S,
+                                 float* out, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_adjoint_sparse"));
+  if (S < 0) return fail(PC_ERR_INVALID_ARG, "pc_adjoint_sparse: S < 0");
+  if (S == 0) return PC_OK;
+  PC_TRY(check_dev(idx, true, "pc_adjoint_sparse", "idx_dev"));
+  PC_TRY(check_dev(out, true, "pc_adjoint_sparse", "out_dev"));
+  PC_TRY(check_dev(y, p->M > 0, "pc_adjoint_sparse", "y_dev"));
+  cudaStream_t st = SS(stream);
+  PC_TRY(p->atomsA.ensure(sizeof(float4) * S));
+  PC_TRY(p->acc.ensure(sizeof(double) * (size_t)S));
+  PC_TRY(make_atoms_checked(idx, nullptr, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
+  PC_TRY(launch_gram(p->vis_fx, reinterpret_cast<const float2*>(y), p->M, p->atomsA.as<float4>(),
+                     S, nullptr, 0, true, p->acc.as<double>(), 1, st));
+  PC_TRY(launch_gram_finalize(p->acc.as<double>(), 1, nullptr, S, 0, true, nullptr, nullptr, 0,
+                              out, st));
+  return PC_OK;
+}
+
+extern "C" int pc_adjoint_grid(pc_plan_t p, const pc_c32* y, float* img, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_adjoint_grid"));
+  PC_TRY(check_dev(y, p->M > 0, "pc_adjoint_grid", "y_dev"));
+  PC_TRY(check_dev(img, true, "pc_adjoint_grid", "img_dev"));
+  return adjoint_grid_impl(p, reinterpret_cast<const float2*>(y), img, 1.0f, nullptr, SS(stream));
+}
+
+extern "C" int pc_lambda_max(pc_plan_t p, const pc_c32* V, double* out, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_lambda_max"));
+  PC_TRY(check_dev(V, p->M > 0, "pc_lambda_max", "V_dev"));
+  if (!out) return fail(PC_ERR_INVALID_ARG, "pc_lambda_max: NULL output");
+  cudaStream_t st = SS(stream);
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+  PC_TRY(adjoint_grid_impl(p, reinterpret_cast<const float2*>(V), p->mu, 1.0f, p->uscal, st));
+  unsigned b = 0;
+  PC_TRY(sync_read(&b, p->uscal, sizeof(b), st));
+  const float f = bits_to_float(b);
+  if (!std::isfinite(f)) return fail(PC_ERR_NUMERIC, "pc_lambda_max: non-finite dirty image");
+  *out = (double)f;
+  return PC_OK;
+}
+
+extern "C" int pc_certificate(pc_plan_t p, const pc_c32* V, const int32_t* idx, const float* x,
+                              int32_t S, double lambda, float* mu, double* mu_inf_host,
+                              double* sumsq_host, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_certificate"));
+  if (S < 0) return fail(PC_ERR_INVALID_ARG, "pc_certificate: S < 0");
+  if (!(lambda > 0.0) || !std::isfinite(lambda))
+    return fail(PC_ERR_INVALID_ARG, "pc_certificate: lambda must be positive and finite");
+  PC_TRY(check_dev(V, p->M > 0, "pc_certificate", "V_dev"));
+  PC_TRY(check_dev(idx, S > 0, "pc_certificate", "idx_dev"));
+  PC_TRY(check_dev(x, S > 0, "pc_certificate", "x_dev"));
+  PC_TRY(check_dev(mu, true, "pc_certificate", "mu_dev"));
+  cudaStream_t st = SS(stream);
+  PC_TRY(p->atomsA.ensure(sizeof(float4) * std::max(S, 1)));
+  PC_TRY(make_atoms_checked(idx, x, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
+  PC_CUDA(cudaMemsetAsync(p->dscal, 0, sizeof(double), st));
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+  PC_TRY(launch_residual(p->vis_fx, reinterpret_cast<const float2*>(V), p->M,
+                         p->atomsA.as<float4>(), S, p->resid, p->dscal, st));
+  PC_TRY(adjoint_grid_impl(p, p->resid, mu, (float)(1.0 / lambda), p->uscal, st));
+  if (mu_inf_host || sumsq_host) {
+    unsigned b = 0;
+    double ss = 0.0;
+    PC_CUDA(cudaMemcpyAsync(&b, p->uscal, sizeof(b), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaMemcpyAsync(&ss, p->dscal, sizeof(ss), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    if (mu_inf_host) *mu_inf_host = (double)bits_to_float(b);
+    if (sumsq_host) *sumsq_host = ss;
+  }
+  return PC_OK;
+}
+
+extern "C" int pc_select(pc_plan_t p, const float* mu, float thr, const int32_t* prev, int32_t n_prev,
+                         int32_t* out, int32_t cap, int32_t* n_out_host, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_select"));
+  if (n_prev < 0 || cap < 0 || !n_out_host) return fail(PC_ERR_INVALID_ARG, "pc_select: bad sizes");
+  PC_TRY(check_dev(mu, true, "pc_select", "mu_dev"));
+  PC_TRY(check_dev(prev, n_prev > 0, "pc_select", "prev_idx_dev"));
+  PC_TRY(check_dev(out, cap > 0, "pc_select", "out_idx_dev"));
+  cudaStream_t st = SS(stream);
+  const int64_t npix = (int64_t)p->N * p->N;
+  if (n_prev > 0) {
+    PC_TRY(p->atomsA.ensure(sizeof(float4) * n_prev));
+    PC_TRY(make_atoms_checked(prev, nullptr, n_prev, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
+  }
+  PC_TRY(launch_mark(p->mark, prev, n_prev, 1, st));
+  PC_TRY(launch_select(mu, npix, thr, p->mark, out, p->iscal, p->sel_blocks, cap, st));
+  PC_TRY(launch_mark(p->mark, prev, n_prev, 0, st));
+  int32_t n = 0;
+  PC_TRY(sync_read(&n, p->iscal, sizeof(n), st));
+  *n_out_host = n;
+  if (n > cap) return fail(PC_ERR_CAPACITY, "pc_select: %d atoms exceed capacity %d", n, cap);
+  return PC_OK;
+}
+
+extern "C" int pc_gram(pc_plan_t p, const pc_c32* V, const int32_t* idx, int32_t S, float* G,
+                       int32_t ldg, float* b, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_gram"));
+  if (S < 0 || ldg < S) return fail(PC_ERR_INVALID_ARG, "pc_gram: need S >= 0 and ldg >= S");
+  if (S == 0) return PC_OK;
+  PC_TRY(check_dev(idx, true, "pc_gram", "idx_dev"));
+  PC_TRY(check_dev(G, true, "pc_gram", "G_dev"));
+  const bool with_v = V != nullptr;
+  PC_TRY(check_dev(V, with_v && p->M > 0, "pc_gram", "V_dev"));
+  PC_TRY(check_dev(b, with_v, "pc_gram", "b_dev"));
+  cudaStream_t st = SS(stream);
+  PC_TRY(p->atomsA.ensure(sizeof(float4) * S));
+  PC_TRY(make_atoms_checked(idx, nullptr, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
+  const int ldacc = S + 1;
+  PC_TRY(p->acc.ensure(sizeof(double) * (size_t)S * ldacc));
+  PC_TRY(launch_gram(p->vis_fx, reinterpret_cast<const float2*>(V), p->M, p->atomsA.as<float4>(), S,
+                     p->atomsA.as<float4>(), S, with_v, p->acc.as<double>(), ldacc, st));
+  PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, nullptr, S, S, with_v, nullptr, G, ldg,
+                              b, st));
+  return PC_OK;
+}
+
+extern "C" int pc_apgd(const float* G, int32_t ldg, const float* b, int32_t S, double lambda,
+                       double eps, int32_t max_iter, float* x, int32_t* iters_host,
+                       double* lipschitz_host, void* stream) {
+  clear_error();
+  if (S < 0 || ldg < S || max_iter < 1 || !(lambda >= 0.0) || !(eps >= 0.0))
+    return fail(PC_ERR_INVALID_ARG, "pc_apgd: bad arguments");
+  if (S == 0) return PC_OK;
+  PC_TRY(check_dev(G, true, "pc_apgd", "G_dev"));
+  PC_TRY(check_dev(b, true, "pc_apgd", "b_dev"));
+  PC_TRY(check_dev(x, true, "pc_apgd", "x_dev"));
+  cudaStream_t st = SS(stream);
+  void* scr = nullptr;
+  PC_TRY(apgd_scratch(&scr));
+  int* d_it = static_cast<int*>(scr);
+  double* d_d = reinterpret_cast<double*>(static_cast<char*>(scr) + 16);
+  PC_TRY(run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, d_it, d_d, d_d + 1, st));
+  if (iters_host || lipschitz_host) {
+    int it = 0;
+    double L = 0.0;
+    PC_CUDA(cudaMemcpyAsync(&it, d_it, sizeof(it), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaMemcpyAsync(&L, d_d, sizeof(L), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    if (iters_host) *iters_host = it;
+    if (lipschitz_host) *lipschitz_host = L;
+  }
+  return PC_OK;
+}
+
+// ------------------------------------------------------------------ the solver
+
+namespace {
+
+inline int round4(int n) { return (n + 3) & ~3; }
+
+struct SolveCfg {
+  int rule = 2, max_fw = 100, apgd_max = 10000;
+  double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
+};
+
+}  // namespace
+
+extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double delta,
+                        const pc_solve_opts* opts, int32_t* idx_out, float* x_out, int32_t cap,
+                        float* mu_out, pc_solve_stats* stats, pc_iter_record* hist,
+                        int32_t hist_cap, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_solve"));
+  if (opts && opts->version != PC_ABI_VERSION)
+    return fail(PC_ERR_INVALID_ARG, "pc_solve: opts->version %d != %d", opts->version, PC_ABI_VERSION);
+  if (!(lambda > 0.0) || !std::isfinite(lambda))
+    return fail(PC_ERR_INVALID_ARG, "pc_solve: lambda must be positive and finite");
+  if (!(delta > 0.0 && delta <= 1.0)) return fail(PC_ERR_INVALID_ARG, "pc_solve: delta must be in (0, 1]");
+  if (cap < 0 || hist_cap < 0) return fail(PC_ERR_INVALID_ARG, "pc_solve: negative capacity");
+  PC_TRY(check_dev(V_, p->M > 0, "pc_solve", "V_dev"));
+  PC_TRY(check_dev(idx_out, cap > 0, "pc_solve", "idx_out_dev"));
+  PC_TRY(check_dev(x_out, cap > 0, "pc_solve", "x_out_dev"));
+  if (mu_out) PC_TRY(check_dev(mu_out, true, "pc_solve", "mu_out_dev"));
+  SolveCfg c;
+  if (opts) {
+    if (opts->select_rule) c.rule = opts->select_rule;
+    if (opts->max_fw) c.max_fw = opts->max_fw;
+    if (opts->apgd_max_iter) c.apgd_max = opts->apgd_max_iter;
+    if (opts->tol > 0) c.tol = opts->tol;
+    if (opts->eps0 > 0) c.eps0 = opts->eps0;
+    if (opts->eps_min > 0) c.eps_min = opts->eps_min;
+    if (opts->lambda_max > 0) c.lmax = opts->lambda_max;
+  }
+  if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: select_rule must be 1 or 2");
+  cudaStream_t st = SS(stream);
+  const float2* V = reinterpret_cast<const float2*>(V_);
+  const int64_t npix = (int64_t)p->N * p->N;
+  const float inv_lam = (float)(1.0 / lambda);
+
+  // capacities of the working set (grown on demand)
+  int wcap = 1024;
+  auto grow = [&](int need) -> int {
+    if (need <= wcap && p->idxB.p) return PC_OK;
+    while (wcap < need) wcap *= 2;
+    const size_t g = (size_t)round4(wcap) * round4(wcap) * sizeof(float);
+    PC_TRY(p->idxA.ensure(sizeof(int32_t) * wcap));
+    PC_TRY(p->idxB.ensure(sizeof(int32_t) * wcap));
+    PC_TRY(p->xA.ensure(sizeof(float) * wcap));
+    PC_TRY(p->xB.ensure(sizeof(float) * wcap));
+    PC_TRY(p->bA.ensure(sizeof(float) * wcap));
+    PC_TRY(p->bB.ensure(sizeof(float) * wcap));
+    PC_TRY(p->oldpos.ensure(sizeof(int32_t) * wcap));
+    PC_TRY(p->newrows.ensure(sizeof(int32_t) * wcap));
+    PC_TRY(p->keep.ensure(sizeof(int32_t) * wcap));
+    PC_TRY(p->atomsA.ensure(sizeof(float4) * wcap));
+    PC_TRY(p->atomsB.ensure(sizeof(float4) * wcap));
+    PC_TRY(p->GA.ensure(g));
+    PC_TRY(p->GB.ensure(g));
+    return PC_OK;
+  };
+  PC_TRY(grow(1024));
+
+  // ||V||^2 and r = V
+  PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
+  PC_TRY(launch_residual(p->vis_fx, V, p->M, nullptr, 0, p->resid, p->dscal, st));
+  double sumsqV = 0.0;
+  PC_TRY(sync_read(&sumsqV, p->dscal, sizeof(double), st));
+
+  int nS = 0, ldA = 4;
+  double F_prev = 0.5 * sumsqV, F = F_prev, Delta = -1.0;
+  if (c.rule == 1 && c.lmax > 0) Delta = (1.0 - delta) * c.lmax;
+  int n_hist = 0, k = 0, status = PC_ERR_NOT_CONVERGED;
+  double mu_inf = 0.0;
+  pc_iter_record cur{};
+  bool have_cur = false;
+
+  for (k = 0;; ++k) {
+    if (k > 0) {
+      // residual and objective of the current iterate
+      double sc[2] = {0.0, 0.0};
+      PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
+      PC_TRY(launch_make_atoms(p->idxA.as<int32_t>(), p->xA.as<float>(), nS, p->N, p->dl,
+                               p->atomsA.as<float4>(), st));
+      PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), nS, p->resid, p->dscal, st));
+      if (nS > 0) {
+        ProfScope prof_scope_(PROF_MISC, st);
+        prof_scope_.kernels = 1;
+        k_l1<<<1, 256, 0, st>>>(p->xA.as<float>(), nS, p->dscal + 1);
+        PC_LAUNCH_CHECK();
+      }
+      PC_TRY(sync_read(sc, p->dscal, sizeof(sc), st));
+      F = 0.5 * sc[0] + lambda * sc[1];
+      const double rel = F_prev > 0 ? (F_prev - F) / F_prev : 0.0;
+      if (have_cur) {
+        cur.objective = F;
+        cur.rel_improvement = rel;
+        if (n_hist < hist_cap && hist) hist[n_hist] = cur;
+        ++n_hist;
+        have_cur = false;
+      }
+      F_prev = F;
+      if (!std::isfinite(F)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite objective at iteration %d", k);
+      if (rel < c.tol) { status = PC_OK; break; }
+      if (k >= c.max_fw) { status = PC_ERR_NOT_CONVERGED; break; }
+    }
+    // certificate mu_k = Phi*(r) / lambda
+    PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+    PC_TRY(adjoint_grid_impl(p, p->resid, p->mu, inv_lam, p->uscal, st));
+    unsigned mb = 0;
+    PC_TRY(sync_read(&mb, p->uscal, sizeof(mb), st));
+    mu_inf = (double)bits_to_float(mb);
+    if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
+    float thr;
+    if (c.rule == 2) {
+      thr = (float)(1.0 - delta);
+    } else {
+      if (Delta < 0) Delta = (1.0 - delta) * lambda * mu_inf;   // lambda_max = ||Phi* V||_inf at k = 0
+      thr = (float)(mu_inf - 2.0 * Delta / ((k + 2) * lambda));
+    }
+    // exploration and union, ascending raster order
+    int n_act = 0;
+    for (;;) {
+      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), nS, 1, st));
+      PC_TRY(launch_select(p->mu, npix, thr, p->mark, p->idxB.as<int32_t>(), p->iscal,
+                           p->sel_blocks, wcap, st));
+      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), nS, 0, st));
+      PC_TRY(sync_read(&n_act, p->iscal, sizeof(int), st));
+      if (n_act <= wcap) break;
+      if (n_act > 60000) return fail(PC_ERR_CAPACITY, "pc_solve: active set of %d atoms too large", n_act);
+      // grow, keeping the current support and weights
+      int32_t* old_idx = nullptr;
+      float* old_x = nullptr;
+      float* old_b = nullptr;
+      float* old_G = nullptr;
+      const int old_ld = ldA;
+      const size_t gbytes = (size_t)nS * old_ld * sizeof(float);
+      PC_CUDA(cudaMalloc(&old_idx, sizeof(int32_t) * std::max(nS, 1) * 3 + gbytes + 16));
+      old_x = reinterpret_cast<float*>(old_idx + std::max(nS, 1));
+      old_b = old_x + std::max(nS, 1);
+      old_G = old_b + std::max(nS, 1);
+      PC_CUDA(cudaMemcpyAsync(old_idx, p->idxA.p, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st));
+      PC_CUDA(cudaMemcpyAsync(old_x, p->xA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
+      PC_CUDA(cudaMemcpyAsync(old_b, p->bA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
+      PC_CUDA(cudaMemcpyAsync(old_G, p->GA.p, gbytes, cudaMemcpyDeviceToDevice, st));
+      PC_CUDA(cudaStreamSynchronize(st));
+      int rc = grow(n_act);
+      if (rc == PC_OK) {
+        cudaMemcpyAsync(p->idxA.p, old_idx, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(p->xA.p, old_x, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(p->bA.p, old_b, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(p->GA.p, old_G, gbytes, cudaMemcpyDeviceToDevice, st);
+        cudaStreamSynchronize(st);
+      }
+      cudaFree(old_idx);
+      PC_TRY(rc);
+      PC_LAUNCH_CHECK();
+    }
+    const int n_new = n_act - nS;
+    cur = pc_iter_record{};
+    cur.k = k;
+    cur.n_new = n_new;
+    cur.n_active = n_act;
+    cur.mu_inf = mu_inf;
+    have_cur = true;
+
+    int n_sup = 0;
+    if (n_act > 0) {
+      const int ldB = round4(n_act);
+      int32_t* oldpos = p->oldpos.as<int32_t>();
+      PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
+      PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
+      // old-old block, b and warm start
+      PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
+      PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
+      PC_TRY(gather_vec<float>(p->xA.as<float>(), oldpos, n_act, p->xB.as<float>(), 0.f, st));
+      // Gram rows of the new atoms against every active atom, plus b
+      if (n_new > 0) {
+        PC_TRY(launch_make_atoms(p->idxB.as<int32_t>(), nullptr, n_act, p->N, p->dl,
+                                 p->atomsB.as<float4>(), st));
+        PC_TRY(gather_vec<float4>(p->atomsB.as<float4>(), p->newrows.as<int32_t>(), n_new,
+                                  p->atomsA.as<float4>(), make_float4(0.f, 0.f, 0.f, 0.f), st));
+        const int ldacc = n_act + 1;
+        PC_TRY(p->acc.ensure(sizeof(double) * (size_t)n_new * ldacc));
+        PC_TRY(launch_gram(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_new, p->atomsB.as<float4>(),
+                           n_act, true, p->acc.as<double>(), ldacc, st));
+        PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, p->newrows.as<int32_t>(), n_new,
+                                    n_act, true, oldpos, p->GB.as<float>(), ldB, p->bB.as<float>(), st));
+      }
+      // reweighting: restricted LASSO by APGD
+      const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
+      int32_t* d_it = p->iscal + 2;
+      PC_TRY(run_apgd(p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
+                      p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st));
+      // pruning
+      PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
+      int32_t hi[4];
+      double hd[2];
+      PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
+      PC_CUDA(cudaMemcpyAsync(hd, p->dscal + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
+      PC_CUDA(cudaStreamSynchronize(st));
+      n_sup = hi[3];
+      cur.apgd_iterations = hi[2];
+      cur.lipschitz = hd[0];
+      const int32_t* keep = p->keep.as<int32_t>();
+      const int ldNew = round4(std::max(n_sup, 1));
+      PC_TRY(gather_vec<int32_t>(p->idxB.as<int32_t>(), keep, n_sup, p->idxA.as<int32_t>(), 0, st));
+      PC_TRY(gather_vec<float>(p->xB.as<float>(), keep, n_sup, p->xA.as<float>(), 0.f, st));
+      PC_TRY(gather_vec<float>(p->bB.as<float>(), keep, n_sup, p->bA.as<float>(), 0.f, st));
+      PC_TRY(gather_sym(p->GB.as<float>(), ldB, keep, n_sup, p->GA.as<float>(), ldNew, st));
+      ldA = ldNew;
+    }
+    nS = n_sup;
+    cur.n_support = n_sup;
+  }
+
+  // final certificate at the returned iterate (its residual is in p->resid)
+  float* mu_dst = mu_out ? mu_out : p->mu;
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+  PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, inv_lam, p->uscal, st));
+  unsigned mb = 0;
+  PC_TRY(sync_read(&mb, p->uscal, sizeof(mb), st));
+  if (stats) {
+    stats->status = status;
+    stats->iterations = k;
+    stats->n_support = nS;
+    stats->n_history = std::min(n_hist, hist_cap);
+    stats->objective = F;
+    stats->lambda = lambda;
+    stats->mu_inf = (double)bits_to_float(mb);
+    stats->sumsq_V = sumsqV;
+  }
+  if (nS > cap) return fail(PC_ERR_CAPACITY, "pc_solve: support of %d atoms exceeds capacity %d", nS, cap);
+  if (nS > 0) {
+    PC_CUDA(cudaMemcpyAsync(idx_out, p->idxA.p, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(x_out, p->xA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
+  }
+  if (status == PC_ERR_NOT_CONVERGED)
+    fail(PC_ERR_NOT_CONVERGED, "pc_solve: no convergence after %d Frank-Wolfe iterations", k);
+  return status;
+}
+
+extern "C" int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32_t N,
+                             double fov_rad, double alpha, double delta, const pc_solve_opts* opts,
+                             int32_t* idx_out_host, float* x_out_host, int32_t cap,
+                             pc_solve_stats* stats_host, void* stream) {
+  clear_error();
+  if (M < 0 || (M > 0 && (!uvw_host || !V_host)) || cap < 0 || (cap > 0 && (!idx_out_host || !x_out_host)))
+    return fail(PC_ERR_INVALID_ARG, "pc_solve_host: bad arguments");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(PC_ERR_INVALID_ARG, "pc_solve_host: alpha must be in (0, 1]");
+  cudaStream_t st = SS(stream);
+  void* buf = nullptr;
+  const size_t b_uvw = sizeof(double) * 3 * (size_t)std::max<int64_t>(M, 1);
+  const size_t b_V = sizeof(pc_c32) * (size_t)std::max<int64_t>(M, 1);
+  const size_t b_idx = sizeof(int32_t) * (size_t)std::max(cap, 1);
+  const size_t b_x = sizeof(float) * (size_t)std::max(cap, 1);
+  PC_CUDA(cudaMalloc(&buf, b_uvw + b_V + b_idx + b_x + 64));
+  char* base = static_cast<char*>(buf);
+  double* d_uvw = reinterpret_cast<double*>(base);
+  pc_c32* d_V = reinterpret_cast<pc_c32*>(base + b_uvw);
+  int32_t* d_idx = reinterpret_cast<int32_t*>(base + b_uvw + b_V);
+  float* d_x = reinterpret_cast<float*>(base + b_uvw + b_V + b_idx);
+  int rc = PC_OK;
+  pc_plan_t plan = nullptr;
+  pc_solve_stats local{};
+  do {
+    if (M > 0) {
+      if (cudaMemcpyAsync(d_uvw, uvw_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(d_V, V_host, sizeof(pc_c32) * M, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = fail(PC_ERR_CUDA, "pc_solve_host: host-to-device copy failed");
+        break;
+      }
+    }
+    rc = pc_plan_create(d_uvw, M, N, fov_rad, nullptr, stream, &plan);
+    if (rc != PC_OK) break;
+    double lmax = 0.0;
+    rc = pc_lambda_max(plan, d_V, &lmax, stream);
+    if (rc != PC_OK) break;
+    if (!(lmax > 0.0)) {   // V == 0: the solution is x = 0
+      local.status = PC_OK;
+      local.n_support = 0;
+      break;
+    }
+    rc = pc_solve(plan, d_V, alpha * lmax, delta, opts, d_idx, d_x, cap, nullptr, &local, nullptr, 0, stream);
+    if (rc != PC_OK && rc != PC_ERR_NOT_CONVERGED) break;
+    const int n = std::min(local.n_support, cap);
+    if (n > 0) {
+      cudaMemcpyAsync(idx_out_host, d_idx, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(x_out_host, d_x, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PC_ERR_CUDA, "pc_solve_host: device-to-host copy failed");
+  } while (0);
+  if (plan) pc_plan_destroy(plan);
+  cudaFree(buf);
+  if (stats_host) *stats_host = local;
+  return rc;
+}

@@ -1,0 +1,174 @@
+"""GPU parity of the operators (the forward and adjoint equations of Sect. 2.2,
+the certificate of Sect. 3.2, lambda_max of Sect. 4.4) against the FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-5 for every operator output (FP32 kernels
+against FP64 direct sums), as the accuracy target of the hot path states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import operators
+from tests.helpers import rel_l2, to_dev, workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2406_01342_gb300 import abi as _abi, build
+    build.build()
+    _abi.load()
+    return _abi
+
+
+CASES = [("tiny_64_coplanar", {}), ("small_wide_w", {}), ("medium_512_w", {"M": 20_000})]
+
+
+def _plan(abi, wl, **kw):
+    return abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov, **kw)
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+def test_plan_geometry(abi, name, kw):
+    wl, V = workload(name, **kw)
+    plan = _plan(abi, wl)
+    info = abi.pc_plan_info(plan)
+    assert info["grid_side"] >= 2 * wl.N and info["grid_side"] % info["tile"] == 0
+    assert wl.M <= info["n_slots"] <= 4 * wl.M
+    if np.all(wl.uvw[:, 2] == 0):
+        assert info["n_planes"] == 1
+    else:
+        assert info["n_planes"] > info["kernel_width"]
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+def test_forward_sparse(abi, name, kw):
+    wl, V = workload(name, **kw)
+    plan = _plan(abi, wl)
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(wl.N * wl.N, 37, replace=False)).astype(np.int32)
+    x = rng.normal(size=37).astype(np.float32)
+    y = abi.pc_forward_sparse(plan, to_dev(idx), to_dev(x)).cpu().numpy()
+    ref = operators.forward(wl.uvw, wl.N, wl.fov, idx, x.astype(np.float64))
+    assert rel_l2(y, ref) <= TOL
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+def test_adjoint_grid(abi, name, kw):
+    wl, V = workload(name, **kw)
+    plan = _plan(abi, wl)
+    img = abi.pc_adjoint_grid(plan, to_dev(V.astype(np.complex64))).cpu().numpy().ravel()
+    if wl.N <= 64:
+        pix = np.arange(wl.N * wl.N)
+    else:
+        pix = np.sort(np.random.default_rng(4).choice(wl.N * wl.N, 2048, replace=False))
+    ref = operators.adjoint(wl.uvw, wl.N, wl.fov, V.astype(np.complex64).astype(np.complex128), pix)
+    assert rel_l2(img[pix], ref) <= TOL
+
+
+@pytest.mark.parametrize("name,kw", CASES[:2])
+def test_adjoint_sparse(abi, name, kw):
+    wl, V = workload(name, **kw)
+    plan = _plan(abi, wl)
+    idx = np.sort(np.random.default_rng(5).choice(wl.N * wl.N, 300, replace=False)).astype(np.int32)
+    Vs = V.astype(np.complex64)
+    out = abi.pc_adjoint_sparse(plan, to_dev(Vs), to_dev(idx)).cpu().numpy()
+    ref = operators.adjoint(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128), idx)
+    assert rel_l2(out, ref) <= TOL
+
+
+def test_lambda_max_and_certificate(abi):
+    wl, V = workload("small_wide_w")
+    plan = _plan(abi, wl)
+    Vs = V.astype(np.complex64)
+    Vd = to_dev(Vs)
+    lmax = abi.pc_lambda_max(plan, Vd)
+    ref_lmax = operators.lambda_max(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128))
+    assert abs(lmax - ref_lmax) <= TOL * ref_lmax
+    lam = 0.1 * ref_lmax
+    idx = wl.sky_idx.astype(np.int32)
+    x = wl.sky_flux.astype(np.float32)
+    mu, mu_inf, sumsq = abi.pc_certificate(plan, Vd, to_dev(idx), to_dev(x), lam)
+    ref = operators.certificate(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128), lam, idx,
+                                x.astype(np.float64))
+    assert rel_l2(mu.cpu().numpy().ravel(), ref) <= TOL
+    assert abs(mu_inf - np.abs(ref).max()) <= 1e-4 * np.abs(ref).max()
+    r = operators.residual(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128), idx, x.astype(np.float64))
+    assert abs(sumsq - np.vdot(r, r).real) <= 1e-5 * np.vdot(r, r).real
+
+
+def test_gram_and_b(abi):
+    wl, V = workload("small_wide_w")
+    plan = _plan(abi, wl)
+    idx = np.sort(np.random.default_rng(6).choice(wl.N * wl.N, 150, replace=False)).astype(np.int32)
+    Vs = V.astype(np.complex64)
+    G, b = abi.pc_gram(plan, to_dev(Vs), to_dev(idx))
+    l, m, n = operators.pixel_lmn(wl.N, wl.fov, idx)
+    A = operators.phase_block(wl.uvw, l, m, n)
+    Gref = np.real(A.conj().T @ A)
+    bref = np.real(A.conj().T @ Vs.astype(np.complex128))
+    Gg = G.cpu().numpy()
+    assert np.array_equal(Gg, Gg.T)
+    assert rel_l2(Gg, Gref) <= TOL
+    assert rel_l2(b.cpu().numpy(), bref) <= TOL
+
+
+def test_select_is_exact(abi):
+    """Exploration + union (Algorithm 2 steps 1a/1b): index work, bit-exact."""
+    wl, V = workload("tiny_64_coplanar")
+    plan = _plan(abi, wl)
+    rng = np.random.default_rng(7)
+    mu = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
+    prev = np.sort(rng.choice(wl.N * wl.N, 40, replace=False)).astype(np.int32)
+    thr = np.float32(1.9)
+    out = abi.pc_select(plan, to_dev(mu), float(thr), to_dev(prev), 4096).cpu().numpy()
+    ref = np.union1d(np.nonzero(np.abs(mu.ravel()) >= thr)[0], prev)
+    assert out.tolist() == ref.tolist()
+    with pytest.raises(abi.PcError) as e:
+        abi.pc_select(plan, to_dev(mu), float(thr), to_dev(prev), 10)
+    assert e.value.status == abi.PC_ERR_CAPACITY
+
+
+def test_empty_and_degenerate(abi):
+    wl, V = workload("tiny_64_coplanar")
+    # M = 0: every operator returns zeros
+    empty = abi.pc_plan_create(torch.zeros(0, 3, dtype=torch.float64, device="cuda"), 32, 0.01)
+    img = abi.pc_adjoint_grid(empty, torch.zeros(0, dtype=torch.complex64, device="cuda"))
+    assert float(img.abs().max()) == 0.0
+    plan = _plan(abi, wl)
+    # empty support: Phi x = 0
+    y = abi.pc_forward_sparse(plan, torch.zeros(0, dtype=torch.int32, device="cuda"),
+                              torch.zeros(0, dtype=torch.float32, device="cuda"))
+    assert float(y.abs().max()) == 0.0
+    # host pointers are rejected, never computed on the CPU
+    with pytest.raises(ValueError):
+        abi.pc_adjoint_grid(plan, torch.zeros(wl.M, dtype=torch.complex64))
+    # invalid support (not ascending)
+    with pytest.raises(abi.PcError) as e:
+        abi.pc_forward_sparse(plan, to_dev(np.array([5, 3], np.int32)), to_dev(np.ones(2, np.float32)))
+    assert e.value.status == abi.PC_ERR_INVALID_ARG
+    with pytest.raises(abi.PcError):
+        abi.pc_plan_create(to_dev(wl.uvw), 63, wl.fov)
+
+
+def test_full_size_medium_sampled(abi):
+    """The 512 x 512, M = 200k workload timed by the benchmark: operators on
+    seeded samples of pixels and visibilities."""
+    wl, V = workload("medium_512_w")
+    plan = _plan(abi, wl)
+    Vs = V.astype(np.complex64)
+    img = abi.pc_adjoint_grid(plan, to_dev(Vs)).cpu().numpy().ravel()
+    rng = np.random.default_rng(8)
+    pix = np.sort(rng.choice(wl.N * wl.N, 1024, replace=False))
+    pix = np.union1d(pix, wl.sky_idx)                      # include the brightest pixels
+    ref = operators.adjoint(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128), pix)
+    assert rel_l2(img[pix], ref) <= TOL
+    y = abi.pc_forward_sparse(plan, to_dev(wl.sky_idx), to_dev(wl.sky_flux.astype(np.float32))).cpu().numpy()
+    ks = np.sort(rng.choice(wl.M, 20_000, replace=False))
+    yref = operators.forward(wl.uvw[ks], wl.N, wl.fov, wl.sky_idx, wl.sky_flux.astype(np.float32).astype(np.float64))
+    assert rel_l2(y[ks], yref) <= TOL
