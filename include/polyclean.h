@@ -203,6 +203,30 @@ int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32
                   int32_t* idx_out_host, float* x_out_host, int32_t cap,
                   pc_solve_stats* stats_host, void* stream);
 
+/* ------------------------------------------------------------------ allocation-free variant */
+
+/* The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory: code that runs inside an arena which handed
+ * out all its memory at start-up, real-time pipelines with a fixed memory
+ * budget, or hosts that forbid allocation while work is queued. Building a
+ * plan allocates, so this variant of pc_adjoint_sparse takes the raw uvw
+ * array (M x 3 float64, device) and the geometry (N, fov_rad) instead:
+ * out[s] = Phi*(y)[idx[s]] for S pixels (direct sum, same phases as the plan
+ * path). The caller passes every input and output; the only scratch is a
+ * file-scope __device__ array of PC_NOALLOC_MAX_PIXELS float64 accumulators
+ * (64 KB per device that loads the library, held until the process exits).
+ * The call never allocates or frees device memory. S > PC_NOALLOC_MAX_PIXELS
+ * is rejected with PC_ERR_INVALID_ARG. An index outside [0, N*N) gives NaN
+ * in its output slot (no ordering is required). All calls share the scratch
+ * array and each clears the part it uses: calls whose kernels overlap on
+ * the GPU race on it and must be serialised. The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress, that device current);
+ * make that first call before any stream capture. */
+#define PC_NOALLOC_MAX_PIXELS 8192
+int pc_adjoint_sparse_noalloc(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
+                              const pc_c32* y_dev, const int32_t* idx_dev, int32_t S,
+                              float* out_dev, void* stream);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Per-kernel-class timing with CUDA events recorded on the launching stream.

@@ -29,7 +29,7 @@ EXPORTS = [
     "pc_plan_create", "pc_plan_destroy", "pc_plan_info", "pc_forward_sparse",
     "pc_adjoint_sparse", "pc_adjoint_grid", "pc_lambda_max", "pc_certificate", "pc_select",
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
-    "pc_last_error", "pc_abi_version",
+    "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc",
 ]
 
 
@@ -112,6 +112,7 @@ def load(path: str | None = None):
                             _P, _I32, _P]),
         "pc_solve_host": (_I32, [_P, _P, _I64, _I32, _D, _D, _D, _P, _P, _P, _I32,
                                  ctypes.POINTER(pc_solve_stats), _P]),
+        "pc_adjoint_sparse_noalloc": (_I32, [_P, _I64, _I32, _D, _P, _P, _I32, _P, _P]),
         "pc_profile_begin": (_I32, []),
         "pc_profile_end": (_I32, [ctypes.POINTER(pc_kernel_time), _I32, ctypes.POINTER(_I32)]),
         "pc_last_error": (ctypes.c_char_p, []),
@@ -331,3 +332,15 @@ def pc_profile_end() -> dict:
     _check(load().pc_profile_end(recs, 32, ctypes.byref(n)))
     return {r.name.decode(): (int(r.launches), int(r.kernels), float(r.total_ms))
             for r in recs[: min(n.value, 32)]}
+
+
+def pc_adjoint_sparse_noalloc(uvw: torch.Tensor, N: int, fov: float, y: torch.Tensor,
+                              idx: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Allocation-free Phi*(y) at the pixels idx, written into the caller's `out`
+    (no plan; the library allocates nothing, see include/polyclean.h)."""
+    M = int(uvw.shape[0])
+    _check(load().pc_adjoint_sparse_noalloc(
+        _dev(uvw, torch.float64, "uvw") if M else None, M, int(N), float(fov),
+        _dev(y, torch.complex64, "y") if M else None, _dev(idx, torch.int32, "idx"),
+        int(idx.numel()), _dev(out, torch.float32, "out"), _stream(stream)))
+    return out
