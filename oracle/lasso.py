@@ -9,9 +9,8 @@ with an accelerated proximal-gradient method (APGD / FISTA, Beck & Teboulle
 the Frank-Wolfe iterations (Sect. 4.1). The paper gives no constants, so this
 module fixes them (the same readings are used by the GPU path):
 
-  * step 1/L with L = 1.01 x the Rayleigh quotient of power iteration on
-    Re(A^H A) from the all-ones vector, run until the quotient changes by less
-    than 1e-6 (relative), at most 200 iterations;
+  * step 1/L with L = 1.01 x the largest eigenvalue of Re(A^H A), the Hessian
+    of the data term (here by a dense symmetric eigensolver);
   * the monotone FISTA variant (Beck & Teboulle 2009, "MFISTA"): the proximal
     point z is accepted only if it does not increase the objective;
   * stop when the proximal-gradient step ||z - y||_2 <= eps ||z||_2, or after
@@ -43,25 +42,13 @@ def gram_apply(A, v):
     return np.real(A.conj().T @ (A @ v))
 
 
-def lipschitz(A, rtol: float = 1e-6, max_iter: int = 200) -> float:
-    """1.01 x largest eigenvalue of Re(A^H A) by power iteration from all ones."""
+def lipschitz(A) -> float:
+    """1.01 x the largest eigenvalue of Re(A^H A) (exact, numpy.linalg.eigvalsh)."""
     s = A.shape[1]
     if s == 0:
         return 1.0
-    v = np.ones(s) / math.sqrt(s)
-    rq_prev = 0.0
-    rq = 0.0
-    for _ in range(max_iter):
-        w = gram_apply(A, v)
-        rq = float(v @ w)
-        nw = float(np.linalg.norm(w))
-        if nw == 0.0:
-            return 1.0
-        v = w / nw
-        if abs(rq - rq_prev) <= rtol * abs(rq):
-            break
-        rq_prev = rq
-    return 1.01 * rq
+    ev = float(np.linalg.eigvalsh(np.real(A.conj().T @ A))[-1])
+    return 1.01 * ev if ev > 0.0 else 1.0
 
 
 def apgd(A, V, lam, x0, eps, max_iter=10_000, L=None):
