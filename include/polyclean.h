@@ -63,7 +63,7 @@ typedef struct pc_plan_s* pc_plan_t;
 typedef struct {
   int32_t version;
   int32_t kernel_width;   /* ES kernel width W in grid cells (default 7; 4..8)         */
-  int32_t tile;           /* gridding tile side in cells (default 32; 16 or 32)         */
+  int32_t tile;           /* gridding tile side in cells (32, the only supported value) */
   int32_t max_planes;     /* cap on the number of w-planes (default 256)                */
 } pc_plan_opts;
 
@@ -73,7 +73,7 @@ typedef struct {
   int32_t select_rule;    /* 2 (default): |mu| >= 1 - delta;  1: |eta| >= ||eta||_inf - 2 Delta/(k+2) */
   int32_t max_fw;         /* Frank-Wolfe iteration cap (default 100)                                 */
   int32_t apgd_max_iter;  /* sub-solver iteration cap (default 10000)                                */
-  int32_t gram_mode;      /* 0 (default): FP32 CUDA-core support contraction                          */
+  int32_t gram_mode;      /* 0 (default): tensor cores for large blocks; 1: FP32 only; 2: tensor cores */
   int32_t reserved0;
   double  tol;            /* stop when (F_k - F_{k+1}) / F_k < tol (default 1e-4, Sect. 5.1)          */
   double  eps0;           /* sub-solver accuracy eps_k = max(eps_min, eps0 2^-k) (default 1e-2)       */
@@ -166,10 +166,14 @@ int pc_select(pc_plan_t plan, const float* mu_dev, float thr, const int32_t* pre
 
 /* Support contraction (step 2 of Algorithm 2, in Gram form): for the S atoms
  * idx, G = Re(Phi_S^H Phi_S) (S x S, row-major, leading dimension ldg) and
- * b = Re(Phi_S^H V) (S). FP32 products of phases generated on the fly,
- * float64 accumulation across visibility slices. */
+ * b = Re(Phi_S^H V) (S; skipped when V_dev is NULL). The phase matrix is
+ * generated tile by tile and never stored. mode 1: FP32 CUDA-core products;
+ * mode 2: tcgen05 tensor cores on split-FP16 (hi + lo) operands with FP32
+ * accumulation (hi*hi + hi*lo + lo*hi); mode 0: tensor cores when S*S >= 4096.
+ * Both accumulate K-slices in float64. PC_ERR_TIMEOUT if a bounded
+ * tensor-core wait expired. */
 int pc_gram(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev, int32_t S,
-            float* G_dev, int32_t ldg, float* b_dev, void* stream);
+            float* G_dev, int32_t ldg, float* b_dev, int32_t mode, void* stream);
 
 /* Restricted LASSO by monotone FISTA on the Gram form (Sect. 3.4 / 4.1):
  * min_x 1/2 x^T G x - b^T x + lambda ||x||_1, warm start x_dev (in/out),

@@ -105,7 +105,7 @@ def load(path: str | None = None):
         "pc_certificate": (_I32, [_P, _P, _P, _P, _I32, _D, _P, ctypes.POINTER(_D),
                                   ctypes.POINTER(_D), _P]),
         "pc_select": (_I32, [_P, _P, _F, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _P]),
-        "pc_gram": (_I32, [_P, _P, _P, _I32, _P, _I32, _P, _P]),
+        "pc_gram": (_I32, [_P, _P, _P, _I32, _P, _I32, _P, _I32, _P]),
         "pc_apgd": (_I32, [_P, _I32, _P, _I32, _D, _D, _I32, _P, ctypes.POINTER(_I32),
                            ctypes.POINTER(_D), _P]),
         "pc_solve": (_I32, [_P, _P, _D, _D, _P, _P, _P, _I32, _P, ctypes.POINTER(pc_solve_stats),
@@ -249,13 +249,13 @@ def pc_select(plan: Plan, mu: torch.Tensor, thr: float, prev_idx: torch.Tensor, 
     return out[: n.value]
 
 
-def pc_gram(plan: Plan, V: torch.Tensor | None, idx: torch.Tensor, stream=None):
+def pc_gram(plan: Plan, V: torch.Tensor | None, idx: torch.Tensor, mode: int = 0, stream=None):
     S = int(idx.numel())
     G = torch.empty(S, S, dtype=torch.float32, device=idx.device)
     b = torch.empty(S, dtype=torch.float32, device=idx.device) if V is not None else None
     _check(load().pc_gram(plan.handle, _dev(V, torch.complex64, "V"), _dev(idx, torch.int32, "idx"),
                           S, _dev(G, torch.float32, "G"), S, _dev(b, torch.float32, "b"),
-                          _stream(stream)))
+                          int(mode), _stream(stream)))
     return G, b
 
 
@@ -271,9 +271,9 @@ def pc_apgd(G: torch.Tensor, b: torch.Tensor, lam: float, eps: float, max_iter: 
 
 
 def _solve_opts(select_rule=0, max_fw=0, apgd_max_iter=0, tol=0.0, eps0=0.0, eps_min=0.0,
-                lambda_max=0.0):
-    return pc_solve_opts(PC_ABI_VERSION, select_rule, max_fw, apgd_max_iter, 0, 0, tol, eps0,
-                         eps_min, lambda_max)
+                lambda_max=0.0, gram_mode=0):
+    return pc_solve_opts(PC_ABI_VERSION, select_rule, max_fw, apgd_max_iter, gram_mode, 0, tol,
+                         eps0, eps_min, lambda_max)
 
 
 def pc_solve(plan: Plan, V: torch.Tensor, lam: float, delta: float, cap: int = 65536,

@@ -5,9 +5,11 @@
 //   f(x) = 1/2 x^T G x - b^T x + lambda ||x||_1,   G = Re(Phi_S^H Phi_S), b = Re(Phi_S^H V)
 //
 // Readings (the paper gives no constants): step 1/L with L = 1.01 x the
-// power-iteration estimate of the top eigenvalue of G from the all-ones vector
-// (until it changes by < 1e-6 relative, at most 200 iterations); the monotone
-// FISTA variant; stop when ||z - y|| <= eps ||z||.
+// largest eigenvalue of G; the monotone FISTA variant; stop when
+// ||z - y|| <= eps ||z||. The eigenvalue comes from Lanczos on G started from
+// the all-ones vector: the largest Ritz value of the tridiagonal matrix (by
+// Sturm-count multisection), until it changes by < 1e-6 relative between
+// checks every 4 steps, at most 64 steps (or n, or an invariant subspace).
 //
 // GB300 mapping: one thread-block cluster (16 CTAs when the device allows it,
 // else 8). CTA r owns a contiguous block of rows of G (cached in its shared
@@ -77,7 +79,7 @@ __device__ Smem carve(float* base, const ApgdArgs& a) {
   s.Gz = p; p += a.rows_per;
   s.bb = p; p += a.rows_per;
   p = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
-  s.part = reinterpret_cast<double*>(p); p += 2 * 8;
+  s.part = reinterpret_cast<double*>(p); p += 2 * 16;   // two partial-sum buffers of 8
   s.Gc = p;
   return s;
 }
@@ -142,19 +144,75 @@ __device__ void block_sums(double v[NPART], double* part, double* scratch) {
   __syncthreads();
 }
 
-// Sum the published partials of all CTAs in rank order.
-__device__ void cluster_sums(cg::cluster_group& cl, const Smem& s, double out[NPART]) {
-  const int CS = (int)cl.num_blocks();
-  for (int q = 0; q < NPART; ++q) out[q] = 0.0;
-  for (int rr = 0; rr < CS; ++rr) {
-    const double* rp = cl.map_shared_rank(s.part, rr);
-    for (int q = 0; q < NPART; ++q) out[q] += rp[q];
+constexpr int LZ_MAX = 64;
+
+// Largest eigenvalue of the symmetric tridiagonal matrix (diagonal al[0..m),
+// off-diagonal be[0..m-1)) by multisection with Sturm counts: warp 0 narrows
+// the Gershgorin interval 33-fold per round, in FP32 on the matrix scaled by
+// its Gershgorin bound (relative accuracy ~1e-6, enough for a step size that
+// carries a 1 % margin). Same inputs in every CTA give the same result.
+__device__ double tridiag_top(const double* al, const double* be, int m, double* s_out) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double glo = 1e300, ghi = -1e300;
+    for (int i = 0; i < m; ++i) {
+      const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+      glo = fmin(glo, al[i] - r);
+      ghi = fmax(ghi, al[i] + r);
+    }
+    const double scale = fmax(fabs(glo), fabs(ghi)) > 0.0 ? fmax(fabs(glo), fabs(ghi)) : 1.0;
+    float lo = (float)(glo / scale), hi = (float)(ghi / scale);
+    for (int round = 0; round < 8; ++round) {
+      const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
+      int below = 0;                          // eigenvalues below x = negative LDL^T pivots
+      float d = (float)(al[0] / scale) - x;
+      if (d == 0.0f) d = -1e-30f;
+      below += d < 0.0f;
+      for (int i = 1; i < m; ++i) {
+        const float bi = (float)(be[i - 1] / scale);
+        d = ((float)(al[i] / scale) - x) - bi * bi / d;
+        if (d == 0.0f) d = -1e-30f;
+        below += d < 0.0f;
+      }
+      const unsigned has_top = __ballot_sync(0xffffffffu, below < m);   // an eigenvalue >= x
+      const int L = has_top ? 31 - __clz(has_top) : -1;
+      const float xl = __shfl_sync(0xffffffffu, x, L >= 0 ? L : 0);
+      const float xr = __shfl_sync(0xffffffffu, x, L + 1 < 32 ? (L + 1 >= 0 ? L + 1 : 0) : 31);
+      const float nlo = L >= 0 ? xl : lo;
+      const float nhi = L < 31 ? xr : hi;
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) *s_out = (double)hi * scale;
   }
+  __syncthreads();
+  return *s_out;
+}
+
+// Sum the published partials of all CTAs: warp 0 reads each CTA's partials
+// once over distributed shared memory and reduces them with a fixed butterfly
+// (the same order in every CTA, so every CTA takes the same decisions).
+__device__ void cluster_sums(cg::cluster_group& cl, double* part, double* s_tot,
+                             double out[NPART]) {
+  const int CS = (int)cl.num_blocks();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double* rp = lane < CS ? cl.map_shared_rank(part, lane) : nullptr;
+    for (int q = 0; q < NPART; ++q) {
+      double v = rp ? rp[q] : 0.0;
+      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) s_tot[q] = v;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < NPART; ++q) out[q] = s_tot[q];
 }
 
 __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   extern __shared__ __align__(16) float apgd_sm[];
   __shared__ double scratch[(APGD_THREADS / 32) * NPART];
+  __shared__ double s_tot[NPART];
+  __shared__ double s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const Smem s = carve(apgd_sm, a);
@@ -171,36 +229,64 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     const bool own = r < nr;
     s.bb[r] = own ? a.b[r0 + r] : 0.f;
     s.x[r] = own ? a.x[r0 + r] : 0.f;
-    s.pub[r] = own ? rsqrtf((float)a.n) : 0.f;      // power-iteration start: all ones / sqrt(n)
+    const float v0 = own ? rsqrtf((float)a.n) : 0.f;   // Lanczos start: all ones / sqrt(n)
+    s.y[r] = v0;        // v_j
+    s.z[r] = 0.f;       // v_{j-1}
+    s.pub[r] = v0;
   }
   __syncthreads();
 
-  // ---- Lipschitz constant by power iteration
-  double rq = 0.0, rq_prev = 0.0;
-  for (int it = 0; it < 200; ++it) {
+  // ---- Lipschitz constant: Lanczos, two cluster reductions per step
+  // (alpha = v^T G v first, then ||w||); the second uses the other partial buffer.
+  double* part2 = s.part + 8;
+  double theta = 0.0, theta_prev = 0.0, beta_prev = 0.0;
+  int m = 0;
+  for (int j = 0; j < LZ_MAX; ++j) {
     cl.sync();
     gather(cl, s, a);
     __syncthreads();
-    gemv_rows(s, a, r0, nr, s.Gz);
+    gemv_rows(s, a, r0, nr, s.Gz);                  // w = G v_j
     __syncthreads();
     double v[NPART] = {0, 0, 0, 0, 0};
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      v[0] += (double)s.zfull[r0 + r] * s.Gz[r];
-      v[1] += (double)s.Gz[r] * s.Gz[r];
-    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) v[0] += (double)s.y[r] * s.Gz[r];
     block_sums(v, s.part, scratch);
     cl.sync();
     double tot[NPART];
-    cluster_sums(cl, s, tot);
-    rq = tot[0];
-    const double nw = sqrt(tot[1]);
-    const float inv = nw > 0.0 ? (float)(1.0 / nw) : 0.f;
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) s.pub[r] = s.Gz[r] * inv;
-    if (nw == 0.0) { rq = 1.0; break; }
-    if (fabs(rq - rq_prev) <= 1e-6 * fabs(rq)) break;
-    rq_prev = rq;
+    cluster_sums(cl, s.part, s_tot, tot);
+    const double alpha = tot[0];
+    const float fa = (float)alpha, fb = (float)beta_prev;
+    double v2[NPART] = {0, 0, 0, 0, 0};
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      const float w = s.Gz[r] - fa * s.y[r] - fb * s.z[r];
+      s.Gz[r] = w;
+      v2[0] += (double)w * w;
+    }
+    block_sums(v2, part2, scratch);
+    cl.sync();
+    cluster_sums(cl, part2, s_tot, tot);
+    const double beta = sqrt(tot[0]);
+    if (threadIdx.x == 0) {
+      s_al[j] = alpha;
+      s_be[j] = beta;
+    }
+    m = j + 1;
+    __syncthreads();
+    const bool last = (m == a.n) || (m == LZ_MAX) || !(beta > 1e-7 * fabs(alpha));
+    if (last || (m % 4) == 0) {
+      theta = tridiag_top(s_al, s_be, m, &s_theta);
+      if (last || fabs(theta - theta_prev) <= 1e-6 * fabs(theta)) break;
+      theta_prev = theta;
+    }
+    const float inv = (float)(1.0 / beta);
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      const float vn = s.Gz[r] * inv;
+      s.z[r] = s.y[r];
+      s.y[r] = vn;
+      s.pub[r] = vn;
+    }
+    beta_prev = beta;
   }
-  const double L = 1.01 * (rq > 0.0 ? rq : 1.0);
+  const double L = 1.01 * (theta > 0.0 ? theta : 1.0);
   const float invL = (float)(1.0 / L);
   const float thr = (float)(a.lam / L);
 
@@ -222,7 +308,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     block_sums(v, s.part, scratch);
     cl.sync();
     double tot[NPART];
-    cluster_sums(cl, s, tot);
+    cluster_sums(cl, s.part, s_tot, tot);
     Fx = 0.5 * tot[0] - tot[1] + (double)a.lam * tot[2];
   }
   for (int r = threadIdx.x; r < nr; r += blockDim.x) {
@@ -259,7 +345,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     block_sums(v, s.part, scratch);
     cl.sync();
     double tot[NPART];
-    cluster_sums(cl, s, tot);
+    cluster_sums(cl, s.part, s_tot, tot);
     const double Fz = 0.5 * tot[0] - tot[1] + (double)a.lam * tot[2];
     const double step = sqrt(tot[3]);
     const double nz = sqrt(tot[4]);
@@ -301,10 +387,13 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     cs_max = (e == cudaSuccess) ? 16 : 8;
     if (e != cudaSuccess) cudaGetLastError();
   }
-  int CS = cs_max;
+  // cluster size: about 64 rows per CTA, a power of two, at most cs_max
+  int CS = 1;
+  while (CS < cs_max && CS * 64 < S) CS *= 2;
   const int n_pad = (S + 3) & ~3;
   int rows_per = ceil_div(S, CS);
   size_t base_bytes = sizeof(float) * ((size_t)n_pad + 8 * (size_t)rows_per) + 16 + 16 * sizeof(double);
+  // (two partial-sum buffers of 8 doubles each follow the vectors)
   const size_t limit = 200 * 1024;
   if (base_bytes > limit)
     return fail(PC_ERR_CAPACITY, "apgd: support of %d atoms exceeds the cluster solver", S);

@@ -63,9 +63,10 @@ extern "C" int pc_abi_version(void) { return PC_ABI_VERSION; }
 namespace pc {
 namespace {
 
-const char* const kProfNames[PROF_NCLASSES] = {"plan",     "grid",          "fft_rows", "fft_cols",
-                                               "residual", "gram",          "gram_finalize",
-                                               "apgd",     "select",        "misc"};
+const char* const kProfNames[PROF_NCLASSES] = {"plan",     "grid",     "fft_rows", "fft_cols",
+                                               "residual", "gram_fp32", "gram_finalize",
+                                               "apgd",     "select",   "misc",     "gram_tc",
+                                               "gram_thin"};
 
 struct ProfRec {
   int cls;

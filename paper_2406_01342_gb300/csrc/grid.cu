@@ -6,10 +6,20 @@
 //
 // with phi the exponential-of-semicircle kernel of width W (in cells / planes)
 // and tau_k = e^{j 2 pi (w_k - w0) s_c} the pre-twiddle that centres the
-// w-screen frequencies. One CTA per gridding sub-problem (a tile of T x T
-// cells, a group of Qg planes and at most 2048 binned visibilities): the
-// visibilities are streamed with coalesced 16-byte loads, the tile is
-// accumulated in shared memory, then added to the grid in HBM.
+// w-screen frequencies.
+//
+// One CTA per gridding sub-problem: a 32 x 32 tile, a group of at most 8
+// planes and at most 1024 binned visibilities (every visibility whose
+// footprint touches the tile was binned into it at plan time). The tile is
+// accumulated in registers, not in shared memory: warp w owns rows
+// [4w, 4w + 4) of the tile for every plane of the group, lane a owns column a.
+// Visibilities are processed in chunks of 256: first each thread evaluates
+// the kernel weights of one visibility (W in u, W in v, one per plane of the
+// group) into shared memory, then every warp sweeps the chunk, skips the
+// visibilities whose footprint misses its 4 rows, and accumulates
+// h * phi_u[a] * phi_v[b] * phi_w[q] with plain FMAs. No atomics touch shared
+// memory; the finished tile is added to the grid with vector reductions
+// (sub-problems of one tile may run on several CTAs).
 #include "pc_internal.cuh"
 
 namespace pc {
@@ -19,76 +29,105 @@ __device__ __forceinline__ void red_add_f32x2(float2* addr, float2 v) {
                : "memory");
 }
 
-template <int W>
+constexpr int GRID_T = 32;        // tile side (one lane per column)
+constexpr int GRID_CHUNK = 256;   // visibilities staged per chunk
+constexpr int GRID_ROWS = 4;      // tile rows per warp (8 warps x 4 = 32)
+
+template <int W, int QMAX>
 __global__ void __launch_bounds__(256)
 k_grid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
-       const float4* __restrict__ slot_geom, const float2* __restrict__ h, int G, int T, int nT,
-       int P, int Qg, float beta, int wstack, float2* __restrict__ grid) {
-  extern __shared__ float2 acc[];  // [Qg][T][T]
+       const float4* __restrict__ slot_geom, const float2* __restrict__ h, int G, int nT, int P,
+       int Qg, float beta, int wstack, float2* __restrict__ grid) {
+  __shared__ float s_fu[GRID_CHUNK][8];
+  __shared__ float s_fv[GRID_CHUNK][8];
+  __shared__ float s_fw[GRID_CHUNK][QMAX];
+  __shared__ float2 s_h[GRID_CHUNK];
+  __shared__ int s_ab[GRID_CHUNK];        // (a0 + 64) | (b0 + 64) << 8
+
   const int4 sub = subs[blockIdx.x];
   const int tu = sub.x % nT, tv = sub.x / nT;
   const int q0 = sub.y * Qg;
   const int Q = min(Qg, P - q0);
-  const int TT = T * T;
-  for (int c = threadIdx.x; c < Q * TT; c += blockDim.x) acc[c] = make_float2(0.f, 0.f);
-  __syncthreads();
-
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = warp * GRID_ROWS;
   const float two_over_w = 2.0f / W;
-  for (int j = sub.z + threadIdx.x; j < sub.w; j += blockDim.x) {
-    const int2 sv = slot_vis[j];
-    const float4 gm = slot_geom[j];
-    float2 hv = h[sv.x];
-    const int a0 = (sv.y & 0xff) - 64;
-    const int b0 = ((sv.y >> 8) & 0xff) - 64;
-    const int ps = sv.y >> 16;
-    float fu[W], fv[W];
+
+  float2 acc[GRID_ROWS][QMAX];
 #pragma unroll
-    for (int c = 0; c < W; ++c) {
-      fu[c] = es_kernel((c - gm.x) * two_over_w, beta);
-      fv[c] = es_kernel((c - gm.y) * two_over_w, beta);
+  for (int r = 0; r < GRID_ROWS; ++r)
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) acc[r][q] = make_float2(0.f, 0.f);
+
+  for (int c0 = sub.z; c0 < sub.w; c0 += GRID_CHUNK) {
+    const int cnt = min(GRID_CHUNK, sub.w - c0);
+    // ---- phase 1: kernel weights of one visibility per thread
+    if (tid < cnt) {
+      const int j = c0 + tid;
+      const int2 sv = slot_vis[j];
+      const float4 gm = slot_geom[j];
+      float2 hv = h[sv.x];
+      if (wstack) {
+        float sn, cs;
+        sincospif(2.0f * gm.w, &sn, &cs);
+        hv = cmul(hv, make_float2(cs, sn));
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        s_fu[tid][c] = es_kernel((c - gm.x) * two_over_w, beta);
+        s_fv[tid][c] = es_kernel((c - gm.y) * two_over_w, beta);
+      }
+      const int ps = sv.y >> 16;
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        const int cw = q0 + q - ps;
+        float f = 0.f;
+        if (q < Q)
+          f = wstack ? ((cw >= 0 && cw < W) ? es_kernel((cw - gm.z) * two_over_w, beta) : 0.f) : 1.f;
+        s_fw[tid][q] = f;
+      }
+      s_h[tid] = hv;
+      s_ab[tid] = sv.y & 0xffff;
     }
-    int cw_lo = 0, cw_hi = 1;
-    float fw[W];
-    if (wstack) {
-      float sn, cs;
-      sincospif(2.0f * gm.w, &sn, &cs);
-      hv = cmul(hv, make_float2(cs, sn));
+    __syncthreads();
+    // ---- phase 2: every warp accumulates its 4-row band
+    for (int t = 0; t < cnt; ++t) {
+      const int ab = s_ab[t];
+      const int b0 = ((ab >> 8) & 0xff) - 64;
+      if (b0 > r0 + GRID_ROWS - 1 || b0 + W - 1 < r0) continue;     // warp-uniform
+      const int da = lane - ((ab & 0xff) - 64);
+      const float wu = (da >= 0 && da < W) ? s_fu[t][da] : 0.f;
+      const float2 hh = s_h[t];
+      const float2 hu = make_float2(hh.x * wu, hh.y * wu);
+      float fw[QMAX];
 #pragma unroll
-      for (int c = 0; c < W; ++c) fw[c] = es_kernel((c - gm.z) * two_over_w, beta);
-      cw_lo = max(0, q0 - ps);
-      cw_hi = min(W, q0 + Q - ps);
-    } else {
+      for (int q = 0; q < QMAX; ++q) fw[q] = s_fw[t][q];
 #pragma unroll
-      for (int c = 0; c < W; ++c) fw[c] = 1.0f;
-    }
-    for (int cw = cw_lo; cw < cw_hi; ++cw) {
-      const float2 hw = make_float2(hv.x * fw[cw], hv.y * fw[cw]);
-      float2* plane = acc + (ps + cw - q0) * TT;
+      for (int r = 0; r < GRID_ROWS; ++r) {
+        const int db = r0 + r - b0;
+        const float wv = (db >= 0 && db < W) ? s_fv[t][db] : 0.f;
+        const float2 hr = make_float2(hu.x * wv, hu.y * wv);
 #pragma unroll
-      for (int bb = 0; bb < W; ++bb) {
-        const int bl = b0 + bb;
-        if (bl < 0 || bl >= T) continue;
-        const float2 hb = make_float2(hw.x * fv[bb], hw.y * fv[bb]);
-        float2* row = plane + bl * T;
-#pragma unroll
-        for (int aa = 0; aa < W; ++aa) {
-          const int al = a0 + aa;
-          if (al < 0 || al >= T) continue;
-          atomicAdd(&row[al].x, hb.x * fu[aa]);
-          atomicAdd(&row[al].y, hb.y * fu[aa]);
+        for (int q = 0; q < QMAX; ++q) {
+          acc[r][q].x = fmaf(hr.x, fw[q], acc[r][q].x);
+          acc[r][q].y = fmaf(hr.y, fw[q], acc[r][q].y);
         }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
+  // ---- add the band to the grid (plane-major, b rows, a contiguous)
   const size_t GG = (size_t)G * G;
-  for (int c = threadIdx.x; c < Q * TT; c += blockDim.x) {
-    const float2 v = acc[c];
-    if (v.x == 0.0f && v.y == 0.0f) continue;
-    const int q = c / TT, rem = c % TT;
-    const int bl = rem / T, al = rem % T;
-    float2* dst = grid + (size_t)(q0 + q) * GG + (size_t)(tv * T + bl) * G + (tu * T + al);
-    red_add_f32x2(dst, v);
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    if (q >= Q) break;
+#pragma unroll
+    for (int r = 0; r < GRID_ROWS; ++r) {
+      const float2 v = acc[r][q];
+      if (v.x == 0.f && v.y == 0.f) continue;
+      float2* dst = grid + (size_t)(q0 + q) * GG + (size_t)(tv * GRID_T + r0 + r) * G +
+                    (tu * GRID_T + lane);
+      red_add_f32x2(dst, v);
+    }
   }
 }
 
@@ -98,22 +137,20 @@ int launch_grid(pc_plan_s* p, const float2* h, cudaStream_t st) {
   PC_CUDA(cudaMemsetAsync(p->grid, 0, bytes, st));
   prof_scope_.kernels = 1;
   if (p->n_sub == 0) return PC_OK;
+  if (p->T != GRID_T || p->Qg > 8)
+    return fail(PC_ERR_INVALID_ARG, "gridding: needs 32-cell tiles and <= 8 planes per group");
   prof_scope_.kernels = 2;
-  const size_t smem = (size_t)p->Qg * p->T * p->T * sizeof(float2);
   const float beta = (float)p->beta;
   const int ws = p->wstack ? 1 : 0;
-#define PC_GRID_CASE(WW)                                                                     \
-  case WW: {                                                                                 \
-    static bool attr_set = false;                                                            \
-    if (!attr_set) {                                                                         \
-      PC_CUDA(cudaFuncSetAttribute(k_grid<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                   200 * 1024));                                             \
-      attr_set = true;                                                                       \
-    }                                                                                        \
-    k_grid<WW><<<p->n_sub, 256, smem, st>>>(p->subs, p->slot_vis, p->slot_geom, h, p->G,     \
-                                             p->T, p->nT, p->P, p->Qg, beta, ws, p->grid);   \
-    break;                                                                                   \
-  }
+#define PC_GRID_CASE(WW)                                                                      \
+  case WW:                                                                                    \
+    if (p->Qg == 1)                                                                           \
+      k_grid<WW, 1><<<p->n_sub, 256, 0, st>>>(p->subs, p->slot_vis, p->slot_geom, h, p->G,    \
+                                               p->nT, p->P, p->Qg, beta, ws, p->grid);        \
+    else                                                                                      \
+      k_grid<WW, 8><<<p->n_sub, 256, 0, st>>>(p->subs, p->slot_vis, p->slot_geom, h, p->G,    \
+                                               p->nT, p->P, p->Qg, beta, ws, p->grid);        \
+    break;
   switch (p->W) {
     PC_GRID_CASE(4)
     PC_GRID_CASE(5)

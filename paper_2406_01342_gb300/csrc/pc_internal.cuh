@@ -54,7 +54,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // when recording is off; prof_stop() records the end event of that token.
 enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
-                 PROF_NCLASSES };
+                 PROF_GRAM_TC, PROF_GRAM_THIN, PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
 void prof_stop(int token, cudaStream_t st, int kernels);
 
@@ -113,10 +113,18 @@ int launch_residual(const int4* vis_fx, const float2* V, int64_t M, const float4
                     float2* out, double* sumsq, cudaStream_t st);
 int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* atomsA, int nA,
                 const float4* atomsB, int nB, bool with_v, double* acc, int ldacc,
-                cudaStream_t st);
+                cudaStream_t st, bool clear = true);
+// gram_tc.cu: tensor-core rows of the Gram (acc cleared by the caller)
+int launch_gram_tc(const int4* vis_fx, int64_t M, const float4* atomsA, int nA,
+                   const float4* atomsB, int nB, double* acc, int ldacc, int* err_dev,
+                   cudaStream_t st);
 int launch_gram_finalize(const double* acc, int ldacc, const int32_t* rows, int nrows, int ncols,
-                         bool with_v, const int32_t* oldpos, float* G, int ldg, float* b,
-                         cudaStream_t st);
+                         const int32_t* oldpos, float* G, int ldg, cudaStream_t st);
+// thin contraction: rows = nA atoms (+ the V row when V != null), see sparse.cu
+int launch_gram_thin(const int4* vis_fx, const float2* V, int64_t M, const float4* atomsA, int nA,
+                     const float4* atomsB, int nB, double* acc, int ldacc, double* b64,
+                     cudaStream_t st);
+int launch_d2f(const double* in, int n, float* out, cudaStream_t st);
 int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double dl,
                        float4* atoms, int* dflag, cudaStream_t st);
 

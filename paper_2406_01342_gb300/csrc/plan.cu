@@ -437,7 +437,7 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
     p->s_c = 0.0;
   }
   {
-    int ngroups = ceil_div(p->P, 12);
+    int ngroups = ceil_div(p->P, 8);      // gridding keeps <= 8 planes of a tile in registers
     p->Qg = ceil_div(p->P, ngroups);
   }
 
@@ -540,7 +540,7 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   }
 
   // ---- gridding sub-problems: (tile, plane group) ranges split into chunks
-  const int kMaxSlotsPerSub = 2048;
+  const int kMaxSlotsPerSub = 1024;
   std::vector<int4> subs;
   const int ngroups = ceil_div(p->P, p->Qg);
   for (int t = 0; t < p->nT * p->nT; ++t) {
@@ -590,7 +590,7 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   int T = (opts && opts->tile) ? opts->tile : 32;
   int maxP = (opts && opts->max_planes) ? opts->max_planes : 256;
   if (W < 4 || W > kMaxW) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: kernel_width %d not in [4, 8]", W);
-  if (T != 16 && T != 32) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: tile %d not 16 or 32", T);
+  if (T != 32) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: tile %d must be 32", T);
   if (maxP < 1 || maxP > 4096) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: max_planes %d", maxP);
 
   pc_plan_s* p = new pc_plan_s();

@@ -72,6 +72,28 @@ int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStre
 
 inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
 
+// Gram rows of nA atoms against nB atoms into acc (nA x ldacc float64) and,
+// when V is given, b64[c] = Re(Phi_B^H V)[c] for the nB column atoms; both are
+// cleared here. Up to 15 rows (16 with the V row) take the thin kernel (no
+// tile padding); larger blocks take the tensor cores (mode 0 when the block
+// has >= 4096 entries, or mode 2) or the FP32 CUDA-core tile kernel (mode 1),
+// and b comes from the thin kernel's V row. err_dev receives the tensor-core
+// kernel's timeout flag.
+int gram_rows(pc_plan_s* p, const float2* V, const float4* atomsA, int nA, const float4* atomsB,
+              int nB, double* acc, int ldacc, double* b64, int mode, int* err_dev, cudaStream_t st) {
+  if (nA > 0) PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nA * ldacc, st));
+  if (V) PC_CUDA(cudaMemsetAsync(b64, 0, sizeof(double) * (size_t)nB, st));
+  if (nA + (V ? 1 : 0) <= 16 && mode != 2)
+    return launch_gram_thin(p->vis_fx, V, p->M, atomsA, nA, atomsB, nB, acc, ldacc, b64, st);
+  const bool tc = mode == 2 || (mode == 0 && (int64_t)nA * nB >= 64 * 64);
+  if (tc)
+    PC_TRY(launch_gram_tc(p->vis_fx, p->M, atomsA, nA, atomsB, nB, acc, ldacc, err_dev, st));
+  else
+    PC_TRY(launch_gram(p->vis_fx, nullptr, p->M, atomsA, nA, atomsB, nB, false, acc, ldacc, st, false));
+  if (V) PC_TRY(launch_gram_thin(p->vis_fx, V, p->M, nullptr, 0, atomsB, nB, nullptr, 0, b64, st));
+  return PC_OK;
+}
+
 int adjoint_grid_impl(pc_plan_s* p, const float2* h, float* img, float scale, unsigned* maxbits,
                       cudaStream_t st) {
   PC_TRY(launch_grid(p, h, st));
@@ -159,10 +181,10 @@ extern "C" int pc_adjoint_sparse(pc_plan_t p, const pc_c32* y, const int32_t* id
   PC_TRY(p->atomsA.ensure(sizeof(float4) * S));
   PC_TRY(p->acc.ensure(sizeof(double) * (size_t)S));
   PC_TRY(make_atoms_checked(idx, nullptr, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
-  PC_TRY(launch_gram(p->vis_fx, reinterpret_cast<const float2*>(y), p->M, p->atomsA.as<float4>(),
-                     S, nullptr, 0, true, p->acc.as<double>(), 1, st));
-  PC_TRY(launch_gram_finalize(p->acc.as<double>(), 1, nullptr, S, 0, true, nullptr, nullptr, 0,
-                              out, st));
+  PC_CUDA(cudaMemsetAsync(p->acc.p, 0, sizeof(double) * (size_t)S, st));
+  PC_TRY(launch_gram_thin(p->vis_fx, reinterpret_cast<const float2*>(y), p->M, nullptr, 0,
+                          p->atomsA.as<float4>(), S, nullptr, 0, p->acc.as<double>(), st));
+  PC_TRY(launch_d2f(p->acc.as<double>(), S, out, st));
   return PC_OK;
 }
 
@@ -247,10 +269,11 @@ extern "C" int pc_select(pc_plan_t p, const float* mu, float thr, const int32_t*
 }
 
 extern "C" int pc_gram(pc_plan_t p, const pc_c32* V, const int32_t* idx, int32_t S, float* G,
-                       int32_t ldg, float* b, void* stream) {
+                       int32_t ldg, float* b, int32_t mode, void* stream) {
   clear_error();
   PC_TRY(check_plan(p, "pc_gram"));
   if (S < 0 || ldg < S) return fail(PC_ERR_INVALID_ARG, "pc_gram: need S >= 0 and ldg >= S");
+  if (mode < 0 || mode > 2) return fail(PC_ERR_INVALID_ARG, "pc_gram: mode must be 0, 1 or 2");
   if (S == 0) return PC_OK;
   PC_TRY(check_dev(idx, true, "pc_gram", "idx_dev"));
   PC_TRY(check_dev(G, true, "pc_gram", "G_dev"));
@@ -260,12 +283,17 @@ extern "C" int pc_gram(pc_plan_t p, const pc_c32* V, const int32_t* idx, int32_t
   cudaStream_t st = SS(stream);
   PC_TRY(p->atomsA.ensure(sizeof(float4) * S));
   PC_TRY(make_atoms_checked(idx, nullptr, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
-  const int ldacc = S + 1;
-  PC_TRY(p->acc.ensure(sizeof(double) * (size_t)S * ldacc));
-  PC_TRY(launch_gram(p->vis_fx, reinterpret_cast<const float2*>(V), p->M, p->atomsA.as<float4>(), S,
-                     p->atomsA.as<float4>(), S, with_v, p->acc.as<double>(), ldacc, st));
-  PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, nullptr, S, S, with_v, nullptr, G, ldg,
-                              b, st));
+  const int ldacc = S;
+  PC_TRY(p->acc.ensure(sizeof(double) * ((size_t)S * ldacc + S)));
+  double* b64 = p->acc.as<double>() + (size_t)S * ldacc;
+  PC_CUDA(cudaMemsetAsync(p->iscal + 4, 0, sizeof(int32_t), st));
+  PC_TRY(gram_rows(p, reinterpret_cast<const float2*>(V), p->atomsA.as<float4>(), S,
+                   p->atomsA.as<float4>(), S, p->acc.as<double>(), ldacc, b64, mode, p->iscal + 4, st));
+  PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, nullptr, S, S, nullptr, G, ldg, st));
+  if (with_v) PC_TRY(launch_d2f(b64, S, b, st));
+  int32_t err = 0;
+  PC_TRY(sync_read(&err, p->iscal + 4, sizeof(err), st));
+  if (err) return fail(PC_ERR_TIMEOUT, "pc_gram: a bounded tensor-core wait expired");
   return PC_OK;
 }
 
@@ -304,7 +332,7 @@ namespace {
 inline int round4(int n) { return (n + 3) & ~3; }
 
 struct SolveCfg {
-  int rule = 2, max_fw = 100, apgd_max = 10000;
+  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0;
   double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
 };
 
@@ -335,8 +363,10 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     if (opts->eps0 > 0) c.eps0 = opts->eps0;
     if (opts->eps_min > 0) c.eps_min = opts->eps_min;
     if (opts->lambda_max > 0) c.lmax = opts->lambda_max;
+    c.gram_mode = opts->gram_mode;
   }
   if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: select_rule must be 1 or 2");
+  if (c.gram_mode < 0 || c.gram_mode > 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: gram_mode must be 0, 1 or 2");
   cudaStream_t st = SS(stream);
   const float2* V = reinterpret_cast<const float2*>(V_);
   const int64_t npix = (int64_t)p->N * p->N;
@@ -365,7 +395,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
   };
   PC_TRY(grow(1024));
 
-  // ||V||^2 and r = V
+  // ||V||^2 and r = V; tensor-core timeout flag cleared
+  PC_CUDA(cudaMemsetAsync(p->iscal + 4, 0, sizeof(int32_t), st));
   PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
   PC_TRY(launch_residual(p->vis_fx, V, p->M, nullptr, 0, p->resid, p->dscal, st));
   double sumsqV = 0.0;
@@ -474,22 +505,24 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       int32_t* oldpos = p->oldpos.as<int32_t>();
       PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
       PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
-      // old-old block, b and warm start
+      // old-old block and warm start (b of old atoms kept when no atom is new)
       PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
-      PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
       PC_TRY(gather_vec<float>(p->xA.as<float>(), oldpos, n_act, p->xB.as<float>(), 0.f, st));
-      // Gram rows of the new atoms against every active atom, plus b
+      if (n_new == 0) PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
+      // Gram rows of the new atoms against every active atom; b for every active atom
       if (n_new > 0) {
         PC_TRY(launch_make_atoms(p->idxB.as<int32_t>(), nullptr, n_act, p->N, p->dl,
                                  p->atomsB.as<float4>(), st));
         PC_TRY(gather_vec<float4>(p->atomsB.as<float4>(), p->newrows.as<int32_t>(), n_new,
                                   p->atomsA.as<float4>(), make_float4(0.f, 0.f, 0.f, 0.f), st));
-        const int ldacc = n_act + 1;
-        PC_TRY(p->acc.ensure(sizeof(double) * (size_t)n_new * ldacc));
-        PC_TRY(launch_gram(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_new, p->atomsB.as<float4>(),
-                           n_act, true, p->acc.as<double>(), ldacc, st));
+        const int ldacc = n_act;
+        PC_TRY(p->acc.ensure(sizeof(double) * ((size_t)n_new * ldacc + n_act)));
+        double* b64 = p->acc.as<double>() + (size_t)n_new * ldacc;
+        PC_TRY(gram_rows(p, V, p->atomsA.as<float4>(), n_new, p->atomsB.as<float4>(), n_act,
+                         p->acc.as<double>(), ldacc, b64, c.gram_mode, p->iscal + 4, st));
         PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, p->newrows.as<int32_t>(), n_new,
-                                    n_act, true, oldpos, p->GB.as<float>(), ldB, p->bB.as<float>(), st));
+                                    n_act, oldpos, p->GB.as<float>(), ldB, st));
+        PC_TRY(launch_d2f(b64, n_act, p->bB.as<float>(), st));
       }
       // reweighting: restricted LASSO by APGD
       const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
@@ -498,11 +531,12 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
                       p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st));
       // pruning
       PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
-      int32_t hi[4];
+      int32_t hi[5];
       double hd[2];
       PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
       PC_CUDA(cudaMemcpyAsync(hd, p->dscal + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
       PC_CUDA(cudaStreamSynchronize(st));
+      if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded tensor-core wait expired");
       n_sup = hi[3];
       cur.apgd_iterations = hi[2];
       cur.lipschitz = hd[0];

@@ -200,14 +200,106 @@ k_gram(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
   }
 }
 
-// Write Gram rows of the "new" atoms into G (and their mirror columns), and b.
+constexpr int THIN_RMAX = 16;     // rows (atoms + the V row) of the thin contraction
+constexpr int THIN_COLS = 128;    // columns (atoms) per CTA
+constexpr int THIN_CHUNK = 256;   // visibilities staged per chunk
+constexpr int THIN_SLICE = 4096;  // visibilities per CTA
+
+// Thin contraction for a few rows: for row r < nA (an atom of atomsA) and
+// column c (an atom of atomsB)
+//   acc[r][c] += sum_k Re(conj(Phi[k, A_r]) Phi[k, B_c])
+// and, when V is given, the extra row
+//   b64[c]    += sum_k Re(conj(Phi[k, B_c]) V_k)
+// over one slice of visibilities. Thread (c, half) generates the phase of its
+// column atom for every other visibility of a chunk; the row phases of the
+// chunk are generated once into shared memory. No tile padding: the cost is
+// one phase per (visibility, column) plus 2 FMAs per row.
+__global__ void __launch_bounds__(256)
+k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
+            const float4* __restrict__ atomsA, int nA, const float4* __restrict__ atomsB, int nB,
+            double* __restrict__ acc, int ldacc, double* __restrict__ b64) {
+  __shared__ float sRe[THIN_RMAX][THIN_CHUNK];
+  __shared__ float sIm[THIN_RMAX][THIN_CHUNK];
+  __shared__ int4 sVis[THIN_CHUNK];
+  __shared__ float4 sA[THIN_RMAX];
+  __shared__ float sRed[THIN_RMAX][THIN_COLS];
+  const int rows = nA + (V ? 1 : 0);
+  const int tid = threadIdx.x, col = tid % THIN_COLS, half = tid / THIN_COLS;
+  const int c_glob = blockIdx.x * THIN_COLS + col;
+  const float4 bt = c_glob < nB ? atomsB[c_glob] : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid < THIN_RMAX) sA[tid] = tid < nA ? atomsA[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t k_lo = (int64_t)blockIdx.y * THIN_SLICE;
+  const int64_t k_hi = min(M, k_lo + THIN_SLICE);
+  float outer[THIN_RMAX];
+#pragma unroll
+  for (int r = 0; r < THIN_RMAX; ++r) outer[r] = 0.f;
+  for (int64_t k0 = k_lo; k0 < k_hi; k0 += THIN_CHUNK) {
+    const int cnt = (int)min((int64_t)THIN_CHUNK, k_hi - k0);
+    __syncthreads();
+    sVis[tid] = tid < cnt ? vis[k0 + tid] : make_int4(0, 0, 0, 0);
+    __syncthreads();
+    for (int e = tid; e < rows * THIN_CHUNK; e += blockDim.x) {
+      const int r = e / THIN_CHUNK, t = e - r * THIN_CHUNK;
+      float re = 0.f, im = 0.f;
+      if (t < cnt) {
+        if (r < nA) {
+          float sn, cs;
+          sincospif(2.0f * phase_turns(sVis[t], sA[r]), &sn, &cs);
+          re = cs * sA[r].w;
+          im = sn * sA[r].w;
+        } else {
+          const float2 v = V[k0 + t];
+          re = v.x;
+          im = -v.y;
+        }
+      }
+      sRe[r][t] = re;
+      sIm[r][t] = im;
+    }
+    __syncthreads();
+    float inner[THIN_RMAX];
+#pragma unroll
+    for (int r = 0; r < THIN_RMAX; ++r) inner[r] = 0.f;
+    for (int t = half; t < cnt; t += 2) {
+      float sn, cs;
+      sincospif(2.0f * phase_turns(sVis[t], bt), &sn, &cs);
+      const float br = cs * bt.w, bi = sn * bt.w;
+#pragma unroll
+      for (int r = 0; r < THIN_RMAX; ++r)
+        if (r < rows) inner[r] = fmaf(sRe[r][t], br, fmaf(sIm[r][t], bi, inner[r]));
+    }
+#pragma unroll
+    for (int r = 0; r < THIN_RMAX; ++r) outer[r] += inner[r];
+  }
+  __syncthreads();
+  if (half == 1)
+#pragma unroll
+    for (int r = 0; r < THIN_RMAX; ++r) sRed[r][col] = outer[r];
+  __syncthreads();
+  if (half == 0 && c_glob < nB) {
+#pragma unroll
+    for (int r = 0; r < THIN_RMAX; ++r) {
+      if (r >= rows) break;
+      const double v = (double)outer[r] + (double)sRed[r][col];
+      if (r < nA) atomicAdd(&acc[(size_t)r * ldacc + c_glob], v);
+      else atomicAdd(&b64[c_glob], v);
+    }
+  }
+}
+
+__global__ void k_d2f(const double* __restrict__ in, int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+// Write Gram rows of the "new" atoms into G (and their mirror columns).
 // Row r of acc belongs to the atom at position rows[r]; a column c that is
 // also new (oldpos[c] < 0) is written only from the row whose position is
 // <= c, so that G stays exactly symmetric.
 __global__ void k_gram_finalize(const double* __restrict__ acc, int ldacc,
                                 const int32_t* __restrict__ rows, int nrows, int ncols,
-                                int with_v, const int32_t* __restrict__ oldpos,
-                                float* __restrict__ G, int ldg, float* __restrict__ b) {
+                                const int32_t* __restrict__ oldpos,
+                                float* __restrict__ G, int ldg) {
   const int r = blockIdx.y;
   if (r >= nrows) return;
   const int pr = rows ? rows[r] : r;
@@ -218,7 +310,6 @@ __global__ void k_gram_finalize(const double* __restrict__ acc, int ldacc,
     G[(size_t)pr * ldg + c] = v;
     G[(size_t)c * ldg + pr] = v;
   }
-  if (with_v && blockIdx.x == 0 && threadIdx.x == 0) b[pr] = (float)acc[(size_t)r * ldacc + ncols];
 }
 
 }  // namespace
@@ -260,11 +351,13 @@ int launch_residual(const int4* vis_fx, const float2* V, int64_t M, const float4
 
 int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* atomsA, int nA,
                 const float4* atomsB, int nB, bool with_v, double* acc, int ldacc,
-                cudaStream_t st) {
+                cudaStream_t st, bool clear) {
   ProfScope prof_scope_(PROF_GRAM, st);
   const int nBe = nB + (with_v ? 1 : 0);
-  PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nA * ldacc, st));
-  prof_scope_.kernels = 1;
+  if (clear) {
+    PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nA * ldacc, st));
+    prof_scope_.kernels = 1;
+  }
   if (M <= 0 || nA <= 0 || nBe <= 0) return PC_OK;
   static bool attr_set = false;
   const size_t smem = (size_t)4 * GKC * GT * sizeof(float);
@@ -273,22 +366,42 @@ int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* at
     attr_set = true;
   }
   dim3 grid(ceil_div(nBe, GT), ceil_div(nA, GT), ceil_div(M, GKS));
-  prof_scope_.kernels = 2;
+  prof_scope_.kernels += 1;
   k_gram<<<grid, 256, smem, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, with_v ? 1 : 0, acc,
                                   ldacc);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
 
+int launch_gram_thin(const int4* vis_fx, const float2* V, int64_t M, const float4* atomsA, int nA,
+                     const float4* atomsB, int nB, double* acc, int ldacc, double* b64,
+                     cudaStream_t st) {
+  ProfScope prof_scope_(PROF_GRAM_THIN, st);
+  if (M <= 0 || nB <= 0 || (nA <= 0 && !V)) return PC_OK;
+  if (nA + (V ? 1 : 0) > THIN_RMAX) return fail(PC_ERR_INVALID_ARG, "thin Gram: too many rows");
+  prof_scope_.kernels = 1;
+  dim3 grid(ceil_div(nB, THIN_COLS), ceil_div(M, THIN_SLICE));
+  k_gram_thin<<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+int launch_d2f(const double* in, int n, float* out, cudaStream_t st) {
+  ProfScope prof_scope_(PROF_MISC, st);
+  if (n <= 0) return PC_OK;
+  prof_scope_.kernels = 1;
+  k_d2f<<<ceil_div(n, 256), 256, 0, st>>>(in, n, out);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
 int launch_gram_finalize(const double* acc, int ldacc, const int32_t* rows, int nrows, int ncols,
-                         bool with_v, const int32_t* oldpos, float* G, int ldg, float* b,
-                         cudaStream_t st) {
+                         const int32_t* oldpos, float* G, int ldg, cudaStream_t st) {
   ProfScope prof_scope_(PROF_GRAM_FINALIZE, st);
   if (nrows <= 0) return PC_OK;
   dim3 grid(std::max(1, std::min(ceil_div(ncols, 256), 64)), nrows);
   prof_scope_.kernels = 1;
-  k_gram_finalize<<<grid, 256, 0, st>>>(acc, ldacc, rows, nrows, ncols, with_v ? 1 : 0, oldpos,
-                                        G, ldg, b);
+  k_gram_finalize<<<grid, 256, 0, st>>>(acc, ldacc, rows, nrows, ncols, oldpos, G, ldg);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

@@ -102,12 +102,18 @@ def test_lambda_max_and_certificate(abi):
     assert abs(sumsq - np.vdot(r, r).real) <= 1e-5 * np.vdot(r, r).real
 
 
-def test_gram_and_b(abi):
-    wl, V = workload("small_wide_w")
+@pytest.mark.parametrize("mode,S,name,kw", [(1, 150, "small_wide_w", {}),
+                                            (2, 150, "small_wide_w", {}),
+                                            (2, 300, "medium_512_w", {"M": 20_000}),
+                                            (2, 37, "tiny_64_coplanar", {})])
+def test_gram_and_b(abi, mode, S, name, kw):
+    """Support contraction: FP32 CUDA cores (mode 1) and split-FP16 tcgen05 tensor
+    cores (mode 2), several tiles and a ragged tail, against the FP64 Gram."""
+    wl, V = workload(name, **kw)
     plan = _plan(abi, wl)
-    idx = np.sort(np.random.default_rng(6).choice(wl.N * wl.N, 150, replace=False)).astype(np.int32)
+    idx = np.sort(np.random.default_rng(6).choice(wl.N * wl.N, S, replace=False)).astype(np.int32)
     Vs = V.astype(np.complex64)
-    G, b = abi.pc_gram(plan, to_dev(Vs), to_dev(idx))
+    G, b = abi.pc_gram(plan, to_dev(Vs), to_dev(idx), mode=mode)
     l, m, n = operators.pixel_lmn(wl.N, wl.fov, idx)
     A = operators.phase_block(wl.uvw, l, m, n)
     Gref = np.real(A.conj().T @ A)

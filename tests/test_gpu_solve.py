@@ -99,3 +99,17 @@ def test_solve_host_buffers(abi):
     dev = abi.pc_solve(plan, Vd, lam, wl.delta)
     assert res["idx"].tolist() == dev["idx"].cpu().numpy().tolist()
     assert np.allclose(res["x"], dev["x"].cpu().numpy(), rtol=1e-5, atol=0)
+
+
+def test_tensor_core_and_fp32_gram_give_the_same_solve(abi):
+    """The 512 x 512, M = 200k benchmark workload: the solve with the tensor-core
+    support contraction and with the FP32 one end on the same support and objective."""
+    wl, V = workload("medium_512_w")
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    Vd = to_dev(V.astype(np.complex64))
+    lam = wl.alpha * abi.pc_lambda_max(plan, Vd)
+    a = abi.pc_solve(plan, Vd, lam, wl.delta, gram_mode=1)
+    b = abi.pc_solve(plan, Vd, lam, wl.delta, gram_mode=2)
+    assert a["idx"].cpu().numpy().tolist() == b["idx"].cpu().numpy().tolist()
+    assert abs(a["objective"] - b["objective"]) <= 1e-6 * a["objective"]
+    assert a["converged"] and b["converged"]
