@@ -190,8 +190,15 @@ def roofline(prof, info, wl, history, steps, peaks):
         it = sum(h["apgd_iterations"] * h["n_active"] ** 2 * 4.0 for h in history)
         b = it * steps / max(launches, 1)
         out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
-    elif dom == "gram":
-        f = sum(8.0 * M * h["n_new"] * (h["n_active"] + 1) for h in history) * steps / max(launches, 1)
+    elif dom == "gram_tc":
+        # split-FP16 tensor work: 3 products x 4 flops (Re*Re + Im*Im) per visibility and
+        # (new atom, active atom) pair, for the Frank-Wolfe iterations that used the tensor cores
+        tc = [h for h in history if h["n_new"] >= 16 and h["n_new"] * h["n_active"] >= 4096]
+        f = sum(12.0 * M * h["n_new"] * h["n_active"] for h in tc) * steps / max(launches, 1)
+        out.update(bound="tensor", achieved=f / (avg_ms * 1e-3) / 1e12,
+                   peak=peaks.get("bf16_tflops", 1900.0), unit="TFLOP/s")
+    elif dom in ("gram_fp32", "gram_thin"):
+        f = sum(4.0 * M * h["n_new"] * h["n_active"] for h in history) * steps / max(launches, 1)
         fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
         out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=fp32, unit="TFLOP/s")
     elif dom == "residual":

@@ -88,7 +88,7 @@ typedef struct {
   int32_t n_active;       /* |S_k u I_{k+1}| before the reweighting                  */
   int32_t n_support;      /* |S_{k+1}| after pruning                                 */
   int32_t apgd_iterations;
-  int32_t reserved0;
+  int32_t lanczos_steps;  /* Lanczos steps of the step-size estimate                */
   double  mu_inf;         /* ||mu_k||_inf (eta_k / lambda) at the start of iteration k */
   double  objective;      /* F(I_{k+1})                                              */
   double  rel_improvement;

@@ -55,7 +55,7 @@ class pc_solve_opts(ctypes.Structure):
 class pc_iter_record(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("n_new", ctypes.c_int32), ("n_active", ctypes.c_int32),
                 ("n_support", ctypes.c_int32), ("apgd_iterations", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("mu_inf", ctypes.c_double),
+                ("lanczos_steps", ctypes.c_int32), ("mu_inf", ctypes.c_double),
                 ("objective", ctypes.c_double), ("rel_improvement", ctypes.c_double),
                 ("lipschitz", ctypes.c_double)]
 
@@ -293,7 +293,8 @@ def pc_solve(plan: Plan, V: torch.Tensor, lam: float, delta: float, cap: int = 6
     _check(status, allow=(PC_OK, PC_ERR_NOT_CONVERGED))
     n = st.n_support
     recs = [dict(k=h.k, n_new=h.n_new, n_active=h.n_active, n_support=h.n_support,
-                 apgd_iterations=h.apgd_iterations, mu_inf=h.mu_inf, objective=h.objective,
+                 apgd_iterations=h.apgd_iterations, lanczos_steps=h.lanczos_steps,
+                 mu_inf=h.mu_inf, objective=h.objective,
                  rel_improvement=h.rel_improvement, lipschitz=h.lipschitz)
             for h in hist[: st.n_history]]
     return dict(idx=idx[:n], x=x[:n], mu=mu, status=st.status, iterations=st.iterations,

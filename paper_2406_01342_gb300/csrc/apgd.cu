@@ -9,17 +9,23 @@
 // ||z - y|| <= eps ||z||. The eigenvalue comes from Lanczos on G started from
 // the all-ones vector: the largest Ritz value of the tridiagonal matrix (by
 // Sturm-count multisection), until it changes by < 1e-6 relative between
-// checks every 4 steps, at most 64 steps (or n, or an invariant subspace).
+// checks every 8 steps, at most 64 steps (or n, or an invariant subspace).
 //
-// GB300 mapping: one thread-block cluster (16 CTAs when the device allows it,
-// else 8). CTA r owns a contiguous block of rows of G (cached in its shared
-// memory when it fits) and of every vector. Each iteration does one GEMV:
-// the CTAs publish their slice of the proximal point z in shared memory, a
-// cluster barrier, every CTA gathers the whole z through distributed shared
-// memory, multiplies its rows, publishes five float64 partial sums, a second
+// GB300 mapping: one thread-block cluster, as few CTAs as let each CTA keep
+// its rows of G in shared memory (1 CTA up to n ~ 220, 16 for n ~ 900). CTA r
+// owns a contiguous block of rows of G and of every vector. Each iteration does
+// one GEMV: the CTAs publish their slice of the proximal point z in shared
+// memory, a cluster barrier, every CTA gathers the whole z through distributed
+// shared memory, multiplies its rows, publishes its partial sums, a second
 // barrier, and every CTA reduces the partials in the same order (so all take
 // identical decisions). G z is the only matrix product per iteration: G y and
 // G x are kept as linear combinations of previous products.
+//
+// Arithmetic: FP32 vectors; the reductions that drive decisions (objective,
+// step norm) are carried as double-float pairs (hi + lo, exact products and
+// error-free sums), which gives about 44 bits without float64 instructions --
+// float64 has a low rate and long dependent latency on this GPU and made each
+// iteration take ~10 us.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -30,6 +36,43 @@ namespace cg = cooperative_groups;
 
 namespace pc {
 namespace {
+
+// ---- double-float arithmetic (Dekker / Knuth error-free transformations)
+struct Df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Df df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+  Df s = df_two_sum(a.hi, b.hi);
+  const float e = s.lo + a.lo + b.lo;
+  const float hi = s.hi + e;
+  return {hi, e - (hi - s.hi)};
+}
+__device__ __forceinline__ Df df_prod(float a, float b) {   // exact a * b
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ Df df_scale(Df a, float b) {
+  const float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  const float hi = p + e;
+  return {hi, e - (hi - p)};
+}
+__device__ __forceinline__ Df df_neg(Df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ bool df_le(Df a, Df b) {          // a <= b
+  const Df d = df_add(a, df_neg(b));
+  return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
+}
+__device__ __forceinline__ Df df_shfl_xor(Df a, int off) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+}
 
 struct ApgdArgs {
   const float* G;
@@ -43,14 +86,16 @@ struct ApgdArgs {
   int* out_iters;
   double* out_L;
   double* out_F;
+  int* out_lanczos;
   int rows_per;
   int n_pad;
   int cache;      // 1: rows of G cached in shared memory
   int vec_ok;     // 1: float4 loads of G rows are aligned
 };
 
-constexpr int APGD_THREADS = 512;
+constexpr int APGD_THREADS = 256;
 constexpr int NPART = 5;
+constexpr int LZ_MAX = 64;
 
 struct Smem {
   float* zfull;   // n_pad
@@ -62,7 +107,7 @@ struct Smem {
   float* z;
   float* Gz;
   float* bb;
-  double* part;   // NPART
+  Df* part;       // 2 buffers of 8 partial sums (the second for back-to-back reductions)
   float* Gc;      // rows_per * n_pad (optional)
 };
 
@@ -79,14 +124,13 @@ __device__ Smem carve(float* base, const ApgdArgs& a) {
   s.Gz = p; p += a.rows_per;
   s.bb = p; p += a.rows_per;
   p = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
-  s.part = reinterpret_cast<double*>(p); p += 2 * 16;   // two partial-sum buffers of 8
+  s.part = reinterpret_cast<Df*>(p); p += 2 * 16;
   s.Gc = p;
   return s;
 }
 
 // Gather the published slices of every CTA into zfull.
 __device__ void gather(cg::cluster_group& cl, const Smem& s, const ApgdArgs& a) {
-  const int CS = (int)cl.num_blocks();
   for (int idx = threadIdx.x; idx < a.n; idx += blockDim.x) {
     const int rr = idx / a.rows_per;
     const int off = idx - rr * a.rows_per;
@@ -94,84 +138,128 @@ __device__ void gather(cg::cluster_group& cl, const Smem& s, const ApgdArgs& a) 
     s.zfull[idx] = remote[off];
   }
   for (int idx = a.n + threadIdx.x; idx < a.n_pad; idx += blockDim.x) s.zfull[idx] = 0.f;
-  (void)CS;
 }
 
-// out[r] = G[r0 + r, :] . zfull for the nr own rows; one warp per row.
+// out[r] = G[r0 + r, :] . zfull for the nr own rows. A warp takes 4 rows at
+// a time (independent accumulators and shuffle chains, so their latencies
+// overlap); full float4 groups inside [0, n), then a scalar tail: columns >= n
+// of a caller's G are never read.
 __device__ void gemv_rows(const Smem& s, const ApgdArgs& a, int r0, int nr, float* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < nr; r += nw) {
-    const float* row = a.cache ? s.Gc + (size_t)r * a.n_pad : a.G + (size_t)(r0 + r) * a.ldg;
-    float acc = 0.f;
-    if (a.cache || a.vec_ok) {
-      // full float4 groups inside [0, n), then a scalar tail: columns >= n of a
-      // caller's G are never read
-      const float4* r4 = reinterpret_cast<const float4*>(row);
-      const float4* z4 = reinterpret_cast<const float4*>(s.zfull);
-      const int n4 = a.n >> 2;
-      for (int c = lane; c < n4; c += 32) {
-        const float4 g = r4[c];
-        const float4 z = z4[c];
-        acc = fmaf(g.x, z.x, acc);
-        acc = fmaf(g.y, z.y, acc);
-        acc = fmaf(g.z, z.z, acc);
-        acc = fmaf(g.w, z.w, acc);
-      }
-      for (int c = 4 * n4 + lane; c < a.n; c += 32) acc = fmaf(row[c], s.zfull[c], acc);
-    } else {
-      for (int c = lane; c < a.n; c += 32) acc = fmaf(row[c], s.zfull[c], acc);
+  const bool vec = a.cache || a.vec_ok;
+  const int n4 = a.n >> 2;
+  const float4* z4 = reinterpret_cast<const float4*>(s.zfull);
+  for (int rb = 4 * warp; rb < nr; rb += 4 * nw) {
+    const float* rows[4];
+    float acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = min(rb + q, nr - 1);
+      rows[q] = a.cache ? s.Gc + (size_t)r * a.n_pad : a.G + (size_t)(r0 + r) * a.ldg;
+      acc[q] = 0.f;
     }
-    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) out[r] = acc;
+    if (vec) {
+      for (int c = lane; c < n4; c += 32) {
+        const float4 z = z4[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 g = reinterpret_cast<const float4*>(rows[q])[c];
+          acc[q] = fmaf(g.x, z.x, acc[q]);
+          acc[q] = fmaf(g.y, z.y, acc[q]);
+          acc[q] = fmaf(g.z, z.z, acc[q]);
+          acc[q] = fmaf(g.w, z.w, acc[q]);
+        }
+      }
+      for (int c = 4 * n4 + lane; c < a.n; c += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(rows[q][c], s.zfull[c], acc[q]);
+    } else {
+      for (int c = lane; c < a.n; c += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(rows[q][c], s.zfull[c], acc[q]);
+    }
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if (lane < 4 && rb + lane < nr) {
+      float v = acc[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (lane == q) v = acc[q];
+      out[rb + lane] = v;
+    }
   }
 }
 
-// Block-wide float64 sums of NPART per-thread values, written to part[] by thread 0.
-__device__ void block_sums(double v[NPART], double* part, double* scratch) {
+// Block-wide double-float sums of NPART per-thread values, written to part[] by thread 0.
+__device__ void block_sums(Df v[NPART], Df* part, Df* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = 0; q < NPART; ++q)
-    for (int off = 16; off; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+  for (int off = 16; off; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) v[q] = df_add(v[q], df_shfl_xor(v[q], off));
   if (lane == 0)
+#pragma unroll
     for (int q = 0; q < NPART; ++q) scratch[warp * NPART + q] = v[q];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < NPART; ++q) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += scratch[w * NPART + q];
-      part[q] = t;
-    }
+  if (threadIdx.x < NPART) {
+    Df t = {0.f, 0.f};
+    for (int w = 0; w < nw; ++w) t = df_add(t, scratch[w * NPART + threadIdx.x]);
+    part[threadIdx.x] = t;
   }
   __syncthreads();
 }
 
-constexpr int LZ_MAX = 64;
+// Sum the published partials of all CTAs: warp 0 reads each CTA's partials
+// once over distributed shared memory and reduces them with a fixed butterfly
+// (the same order in every CTA, so every CTA takes the same decisions).
+__device__ void cluster_sums(cg::cluster_group& cl, Df* part, Df* s_tot, Df out[NPART]) {
+  const int CS = (int)cl.num_blocks();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const Df* rp = lane < CS ? cl.map_shared_rank(part, lane) : nullptr;
+    Df v[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) v[q] = rp ? rp[q] : Df{0.f, 0.f};
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < NPART; ++q) v[q] = df_add(v[q], df_shfl_xor(v[q], off));
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NPART; ++q) s_tot[q] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NPART; ++q) out[q] = s_tot[q];
+}
 
 // Largest eigenvalue of the symmetric tridiagonal matrix (diagonal al[0..m),
 // off-diagonal be[0..m-1)) by multisection with Sturm counts: warp 0 narrows
-// the Gershgorin interval 33-fold per round, in FP32 on the matrix scaled by
-// its Gershgorin bound (relative accuracy ~1e-6, enough for a step size that
+// the Gershgorin interval 33-fold per round, on the matrix scaled by its
+// Gershgorin bound (relative accuracy ~1e-6, enough for a step size that
 // carries a 1 % margin). Same inputs in every CTA give the same result.
-__device__ double tridiag_top(const double* al, const double* be, int m, double* s_out) {
+__device__ float tridiag_top(const float* al, const float* be, int m, float* s_out) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    double glo = 1e300, ghi = -1e300;
+    float glo = 3e38f, ghi = -3e38f;
     for (int i = 0; i < m; ++i) {
-      const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
-      glo = fmin(glo, al[i] - r);
-      ghi = fmax(ghi, al[i] + r);
+      const float r = (i > 0 ? fabsf(be[i - 1]) : 0.f) + (i + 1 < m ? fabsf(be[i]) : 0.f);
+      glo = fminf(glo, al[i] - r);
+      ghi = fmaxf(ghi, al[i] + r);
     }
-    const double scale = fmax(fabs(glo), fabs(ghi)) > 0.0 ? fmax(fabs(glo), fabs(ghi)) : 1.0;
-    float lo = (float)(glo / scale), hi = (float)(ghi / scale);
+    float scale = fmaxf(fabsf(glo), fabsf(ghi));
+    if (!(scale > 0.f)) scale = 1.f;
+    const float inv = 1.f / scale;
+    float lo = glo * inv, hi = ghi * inv;
     for (int round = 0; round < 8; ++round) {
-      const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
+      const float x = lo + (hi - lo) * (float)(lane + 1) * (1.0f / 33.0f);
       int below = 0;                          // eigenvalues below x = negative LDL^T pivots
-      float d = (float)(al[0] / scale) - x;
+      float d = al[0] * inv - x;
       if (d == 0.0f) d = -1e-30f;
       below += d < 0.0f;
       for (int i = 1; i < m; ++i) {
-        const float bi = (float)(be[i - 1] / scale);
-        d = ((float)(al[i] / scale) - x) - bi * bi / d;
-        if (d == 0.0f) d = -1e-30f;
+        const float bi = be[i - 1] * inv;
+        d = (al[i] * inv - x) - __fdividef(bi * bi, d);
+        if (d == 0.0f || !isfinite(d)) d = -1e-30f;
         below += d < 0.0f;
       }
       const unsigned has_top = __ballot_sync(0xffffffffu, below < m);   // an eigenvalue >= x
@@ -183,41 +271,23 @@ __device__ double tridiag_top(const double* al, const double* be, int m, double*
       lo = nlo;
       hi = nhi;
     }
-    if (lane == 0) *s_out = (double)hi * scale;
+    if (lane == 0) *s_out = hi * scale;
   }
   __syncthreads();
   return *s_out;
 }
 
-// Sum the published partials of all CTAs: warp 0 reads each CTA's partials
-// once over distributed shared memory and reduces them with a fixed butterfly
-// (the same order in every CTA, so every CTA takes the same decisions).
-__device__ void cluster_sums(cg::cluster_group& cl, double* part, double* s_tot,
-                             double out[NPART]) {
-  const int CS = (int)cl.num_blocks();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    const double* rp = lane < CS ? cl.map_shared_rank(part, lane) : nullptr;
-    for (int q = 0; q < NPART; ++q) {
-      double v = rp ? rp[q] : 0.0;
-      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0) s_tot[q] = v;
-    }
-  }
-  __syncthreads();
-  for (int q = 0; q < NPART; ++q) out[q] = s_tot[q];
-}
-
 __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   extern __shared__ __align__(16) float apgd_sm[];
-  __shared__ double scratch[(APGD_THREADS / 32) * NPART];
-  __shared__ double s_tot[NPART];
-  __shared__ double s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
+  __shared__ Df scratch[(APGD_THREADS / 32) * NPART];
+  __shared__ Df s_tot[NPART];
+  __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const Smem s = carve(apgd_sm, a);
   const int r0 = rank * a.rows_per;
   const int nr = max(0, min(a.n, r0 + a.rows_per) - r0);
+  Df* part2 = s.part + 8;
 
   if (a.cache) {
     for (int e = threadIdx.x; e < nr * a.n_pad; e += blockDim.x) {
@@ -225,21 +295,19 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
       s.Gc[e] = c < a.n ? a.G[(size_t)(r0 + r) * a.ldg + c] : 0.f;
     }
   }
+  const float v0 = rsqrtf((float)a.n);        // Lanczos start: all ones / sqrt(n)
   for (int r = threadIdx.x; r < a.rows_per; r += blockDim.x) {
     const bool own = r < nr;
     s.bb[r] = own ? a.b[r0 + r] : 0.f;
     s.x[r] = own ? a.x[r0 + r] : 0.f;
-    const float v0 = own ? rsqrtf((float)a.n) : 0.f;   // Lanczos start: all ones / sqrt(n)
-    s.y[r] = v0;        // v_j
-    s.z[r] = 0.f;       // v_{j-1}
-    s.pub[r] = v0;
+    s.y[r] = own ? v0 : 0.f;    // v_j
+    s.z[r] = 0.f;               // v_{j-1}
+    s.pub[r] = own ? v0 : 0.f;
   }
   __syncthreads();
 
-  // ---- Lipschitz constant: Lanczos, two cluster reductions per step
-  // (alpha = v^T G v first, then ||w||); the second uses the other partial buffer.
-  double* part2 = s.part + 8;
-  double theta = 0.0, theta_prev = 0.0, beta_prev = 0.0;
+  // ---- Lipschitz constant: Lanczos (alpha = v^T G v, then beta = ||w||)
+  float theta = 0.f, theta_prev = 0.f, beta_prev = 0.f;
   int m = 0;
   for (int j = 0; j < LZ_MAX; ++j) {
     cl.sync();
@@ -247,37 +315,36 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     __syncthreads();
     gemv_rows(s, a, r0, nr, s.Gz);                  // w = G v_j
     __syncthreads();
-    double v[NPART] = {0, 0, 0, 0, 0};
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) v[0] += (double)s.y[r] * s.Gz[r];
+    Df v[NPART] = {};
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) v[0] = df_add(v[0], df_prod(s.y[r], s.Gz[r]));
     block_sums(v, s.part, scratch);
     cl.sync();
-    double tot[NPART];
+    Df tot[NPART];
     cluster_sums(cl, s.part, s_tot, tot);
-    const double alpha = tot[0];
-    const float fa = (float)alpha, fb = (float)beta_prev;
-    double v2[NPART] = {0, 0, 0, 0, 0};
+    const float alpha = tot[0].hi + tot[0].lo;
+    Df v2[NPART] = {};
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      const float w = s.Gz[r] - fa * s.y[r] - fb * s.z[r];
+      const float w = s.Gz[r] - alpha * s.y[r] - beta_prev * s.z[r];
       s.Gz[r] = w;
-      v2[0] += (double)w * w;
+      v2[0] = df_add(v2[0], df_prod(w, w));
     }
     block_sums(v2, part2, scratch);
     cl.sync();
     cluster_sums(cl, part2, s_tot, tot);
-    const double beta = sqrt(tot[0]);
+    const float beta = sqrtf(fmaxf(tot[0].hi + tot[0].lo, 0.f));
     if (threadIdx.x == 0) {
       s_al[j] = alpha;
       s_be[j] = beta;
     }
     m = j + 1;
     __syncthreads();
-    const bool last = (m == a.n) || (m == LZ_MAX) || !(beta > 1e-7 * fabs(alpha));
-    if (last || (m % 4) == 0) {
+    const bool last = (m == a.n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
+    if (last || (m % 8) == 0) {
       theta = tridiag_top(s_al, s_be, m, &s_theta);
-      if (last || fabs(theta - theta_prev) <= 1e-6 * fabs(theta)) break;
+      if (last || fabsf(theta - theta_prev) <= 1e-6f * fabsf(theta)) break;
       theta_prev = theta;
     }
-    const float inv = (float)(1.0 / beta);
+    const float inv = 1.f / beta;
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
       const float vn = s.Gz[r] * inv;
       s.z[r] = s.y[r];
@@ -286,9 +353,9 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     }
     beta_prev = beta;
   }
-  const double L = 1.01 * (theta > 0.0 ? theta : 1.0);
-  const float invL = (float)(1.0 / L);
-  const float thr = (float)(a.lam / L);
+  const float L = 1.01f * (theta > 0.f ? theta : 1.f);
+  const float invL = 1.f / L;
+  const float thr = a.lam * invL;
 
   // ---- initial G x
   for (int r = threadIdx.x; r < nr; r += blockDim.x) s.pub[r] = s.x[r];
@@ -297,19 +364,19 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   __syncthreads();
   gemv_rows(s, a, r0, nr, s.Gx);
   __syncthreads();
-  double Fx;
+  Df Fx;
   {
-    double v[NPART] = {0, 0, 0, 0, 0};
+    Df v[NPART] = {};
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      v[0] += (double)s.x[r] * s.Gx[r];
-      v[1] += (double)s.bb[r] * s.x[r];
-      v[2] += fabs((double)s.x[r]);
+      v[0] = df_add(v[0], df_prod(s.x[r], s.Gx[r]));
+      v[1] = df_add(v[1], df_prod(s.bb[r], s.x[r]));
+      v[2] = df_add(v[2], Df{fabsf(s.x[r]), 0.f});
     }
     block_sums(v, s.part, scratch);
     cl.sync();
-    double tot[NPART];
+    Df tot[NPART];
     cluster_sums(cl, s.part, s_tot, tot);
-    Fx = 0.5 * tot[0] - tot[1] + (double)a.lam * tot[2];
+    Fx = df_add(df_add(df_scale(tot[0], 0.5f), df_neg(tot[1])), df_scale(tot[2], a.lam));
   }
   for (int r = threadIdx.x; r < nr; r += blockDim.x) {
     s.y[r] = s.x[r];
@@ -318,7 +385,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   __syncthreads();
 
   // ---- monotone FISTA
-  double t = 1.0;
+  float t = 1.f;
   int it = 0;
   for (it = 1; it <= a.max_iter; ++it) {
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
@@ -332,26 +399,26 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     __syncthreads();
     gemv_rows(s, a, r0, nr, s.Gz);
     __syncthreads();
-    double v[NPART] = {0, 0, 0, 0, 0};
+    Df v[NPART] = {};
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      const double zr = s.z[r];
-      v[0] += zr * s.Gz[r];
-      v[1] += (double)s.bb[r] * zr;
-      v[2] += fabs(zr);
-      const double d = zr - (double)s.y[r];
-      v[3] += d * d;
-      v[4] += zr * zr;
+      const float zr = s.z[r];
+      v[0] = df_add(v[0], df_prod(zr, s.Gz[r]));
+      v[1] = df_add(v[1], df_prod(s.bb[r], zr));
+      v[2] = df_add(v[2], Df{fabsf(zr), 0.f});
+      const float d = zr - s.y[r];
+      v[3] = df_add(v[3], df_prod(d, d));
+      v[4] = df_add(v[4], df_prod(zr, zr));
     }
     block_sums(v, s.part, scratch);
     cl.sync();
-    double tot[NPART];
+    Df tot[NPART];
     cluster_sums(cl, s.part, s_tot, tot);
-    const double Fz = 0.5 * tot[0] - tot[1] + (double)a.lam * tot[2];
-    const double step = sqrt(tot[3]);
-    const double nz = sqrt(tot[4]);
-    const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    const bool accept = Fz <= Fx;
-    const float c1 = (float)(t / t1), c2 = (float)((t - 1.0) / t1);
+    const Df Fz = df_add(df_add(df_scale(tot[0], 0.5f), df_neg(tot[1])), df_scale(tot[2], a.lam));
+    const float step = sqrtf(tot[3].hi + tot[3].lo);
+    const float nz = sqrtf(tot[4].hi + tot[4].lo);
+    const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+    const bool accept = df_le(Fz, Fx);
+    const float c1 = t / t1, c2 = (t - 1.f) / t1;
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
       const float xo = s.x[r], Gxo = s.Gx[r];
       const float xn = accept ? s.z[r] : xo;
@@ -364,14 +431,15 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
     if (accept) Fx = Fz;
     t = t1;
     __syncthreads();
-    if (step <= (double)a.eps * nz) break;
+    if (step <= a.eps * nz) break;
   }
   if (it > a.max_iter) it = a.max_iter;
   for (int r = threadIdx.x; r < nr; r += blockDim.x) a.x[r0 + r] = s.x[r];
   if (rank == 0 && threadIdx.x == 0) {
     if (a.out_iters) *a.out_iters = it;
-    if (a.out_L) *a.out_L = L;
-    if (a.out_F) *a.out_F = Fx;
+    if (a.out_L) *a.out_L = (double)L;
+    if (a.out_F) *a.out_F = (double)Fx.hi + (double)Fx.lo;
+    if (a.out_lanczos) *a.out_lanczos = m;
   }
   cl.sync();   // no CTA leaves while others may still read its shared memory
 }
@@ -379,28 +447,38 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
 }  // namespace
 
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
-             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st) {
+             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
+             int* lanczos) {
   if (S <= 0) return PC_OK;
   static int cs_max = 0;
+  static size_t smem_set = 0;
   if (cs_max == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_apgd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cs_max = (e == cudaSuccess) ? 16 : 8;
     if (e != cudaSuccess) cudaGetLastError();
   }
-  // cluster size: about 64 rows per CTA, a power of two, at most cs_max
-  int CS = 1;
-  while (CS < cs_max && CS * 64 < S) CS *= 2;
+  // cluster size: the smallest power of two whose CTAs can each cache their
+  // rows of G in shared memory (fewer CTAs = cheaper barriers), else cs_max
   const int n_pad = (S + 3) & ~3;
-  int rows_per = ceil_div(S, CS);
-  size_t base_bytes = sizeof(float) * ((size_t)n_pad + 8 * (size_t)rows_per) + 16 + 16 * sizeof(double);
-  // (two partial-sum buffers of 8 doubles each follow the vectors)
   const size_t limit = 200 * 1024;
+  auto bytes_for = [&](int cs, bool cached) {
+    const size_t rp = (size_t)ceil_div(S, cs);
+    return sizeof(float) * ((size_t)n_pad + 8 * rp) + 16 + 16 * sizeof(Df) +
+           (cached ? sizeof(float) * rp * n_pad : 0);
+  };
+  int CS = 1;
+  while (CS < cs_max && bytes_for(CS, true) > limit) CS *= 2;
+  int rows_per = ceil_div(S, CS);
+  size_t base_bytes = bytes_for(CS, false);
   if (base_bytes > limit)
     return fail(PC_ERR_CAPACITY, "apgd: support of %d atoms exceeds the cluster solver", S);
   const size_t cache_bytes = sizeof(float) * (size_t)rows_per * n_pad;
   const int cache = (base_bytes + cache_bytes <= limit) ? 1 : 0;
   const size_t smem = base_bytes + (cache ? cache_bytes : 0);
-  PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem_set == 0) {   // the largest size any launch may ask for, set once
+    PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+    smem_set = limit;
+  }
 
   ApgdArgs a;
   a.G = G;
@@ -414,6 +492,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
   a.out_iters = iters;
   a.out_L = L;
   a.out_F = Fx;
+  a.out_lanczos = lanczos;
   a.rows_per = rows_per;
   a.n_pad = n_pad;
   a.cache = cache;
@@ -441,7 +520,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     // fall back to a portable cluster size
     cudaGetLastError();
     cs_max = 8;
-    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st);
+    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st, lanczos);
   }
   PC_CUDA(e);
   return PC_OK;

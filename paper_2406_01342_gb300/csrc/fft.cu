@@ -77,13 +77,13 @@ __device__ float2* fft_rows_smem(float2* a, float2* b, int rows, int G, int logG
 
 __global__ void __launch_bounds__(256)
 k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int logG, int N, int R,
-           const float2* __restrict__ tw) {
+           const float2* __restrict__ tw, const int* __restrict__ active_rows) {
   extern __shared__ float2 sm[];
   const int S = G + 1;
   float2* A = sm;
   float2* B = sm + R * S;
   const int q = blockIdx.y;
-  const int b0 = blockIdx.x * R;
+  const int b0 = active_rows[blockIdx.x * R];     // R consecutive active rows (R divides 32)
   const float2* src = grid + ((size_t)q * G + b0) * G;
   for (int f = threadIdx.x; f < R * G; f += blockDim.x) {
     const int r = f / G, a = f - r * G;
@@ -163,19 +163,22 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
 
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_ROWS, st);
-  // rows per CTA: R * (G + 1) * 8 bytes * 2 buffers <= ~132 KB
-  int R = 8192 / p->G;
+  if (p->n_active_rows == 0) return PC_OK;     // all-zero grid: the output stays zero
+  // rows per CTA: R * (G + 1) * 8 bytes * 2 buffers <= ~66 KB (3 CTAs per SM);
+  // R divides the 32-row tile so a CTA's rows are consecutive active rows
+  int R = 4096 / p->G;
   if (R < 1) R = 1;
-  if (R > 64) R = 64;
+  if (R > 32) R = 32;
   const size_t smem = (size_t)2 * R * (p->G + 1) * sizeof(float2);
   static bool attr_set = false;
   if (!attr_set) {
     PC_CUDA(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  dim3 grid(p->G / R, p->P);
+  dim3 grid(p->n_active_rows / R, p->P);
   prof_scope_.kernels = 1;
-  k_fft_rows<<<grid, 256, smem, st>>>(p->grid, p->fft1, p->G, p->logG, p->N, R, p->twiddle);
+  k_fft_rows<<<grid, 256, smem, st>>>(p->grid, p->fft1, p->G, p->logG, p->N, R, p->twiddle,
+                                      p->active_rows);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

@@ -37,7 +37,7 @@ constexpr int TC_KV = 32;              // visibilities per stage
 constexpr int TC_ROW_BYTES = 4 * TC_KV; // 64 fp16 K-elements per row per stage = 128 bytes
 constexpr int TC_SLICE = 8192;         // visibilities per CTA (float64 flush per slice)
 constexpr int TC_SUB = 4;              // stages per fast-accumulator sub-slice (128 visibilities)
-constexpr int TC_THREADS = 384;
+constexpr int TC_THREADS = 768;
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;
 
 // K-major, no-swizzle canonical layout: core matrices of 8 rows x 16 bytes;
@@ -218,7 +218,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
   bool slow_empty = true;
 
   const int nstages = (int)((k_hi - k_lo + TC_KV - 1) / TC_KV);
-  const float4 my_atom = tid < nrows ? sAtom[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
   int committed[2] = {0, 0};
   bool timed_out = false;
 
@@ -236,14 +235,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
       sVis[((s + 1) & 1) * TC_KV + tid] = k < k_hi ? g.vis[k] : make_int4(0, 0, 0, 0);
     }
     unsigned char* sb = stage_base + b * stage_bytes;
-    if (tid < nrows) {
-      const bool isA = tid < TC_M;
-      const int row = isA ? tid : tid - TC_M;
+    // items (row, K-group of 4 visibilities): a warp covers 32 consecutive rows
+    // of one K-group, so its 16-byte stores fill whole 128-byte wavefronts.
+    // Warp 0 issues the MMAs and generates nothing, so a blocking MMA issue
+    // never delays the next stage's operands.
+    for (int f = tid - 32; f < nrows * (TC_KV / 4); f += blockDim.x - 32) {
+      if (f < 0) break;
+      const int kg = f / nrows, rr = f - kg * nrows;
+      const bool isA = rr < TC_M;
+      const int row = isA ? rr : rr - TC_M;
+      const float4 my_atom = sAtom[rr];
       unsigned char* hi_base = isA ? sb : sb + 2 * a_bytes;
       unsigned char* lo_base = isA ? sb + a_bytes : sb + 2 * a_bytes + b_bytes;
       const int4* vs = sVis + b * TC_KV;
-#pragma unroll 2
-      for (int kg = 0; kg < TC_KV / 4; ++kg) {
+      {
         __half2 h[4], l[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {

@@ -131,12 +131,25 @@ k_grid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
   }
 }
 
+// Zero the grid rows that visibilities can reach (every plane); the other
+// rows are never written and stay zero.
+__global__ void k_zero_rows(float2* __restrict__ grid, const int* __restrict__ rows, int n_rows,
+                            int G, int P) {
+  const int rr = blockIdx.x, q = blockIdx.y;
+  if (rr >= n_rows) return;
+  float4* dst = reinterpret_cast<float4*>(grid + ((size_t)q * G + rows[rr]) * G);
+  for (int c = threadIdx.x; c < G / 2; c += blockDim.x) dst[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 int launch_grid(pc_plan_s* p, const float2* h, cudaStream_t st) {
   ProfScope prof_scope_(PROF_GRID, st);
-  const size_t bytes = (size_t)p->P * p->G * p->G * sizeof(float2);
-  PC_CUDA(cudaMemsetAsync(p->grid, 0, bytes, st));
+  if (p->n_sub == 0) return PC_OK;        // nothing is ever written: the grid stays zero
+  {
+    dim3 zg(p->n_active_rows, p->P);
+    k_zero_rows<<<zg, 256, 0, st>>>(p->grid, p->active_rows, p->n_active_rows, p->G, p->P);
+    PC_LAUNCH_CHECK();
+  }
   prof_scope_.kernels = 1;
-  if (p->n_sub == 0) return PC_OK;
   if (p->T != GRID_T || p->Qg > 8)
     return fail(PC_ERR_INVALID_ARG, "gridding: needs 32-cell tiles and <= 8 planes per group");
   prof_scope_.kernels = 2;

@@ -141,7 +141,8 @@ int launch_compact_new(const int32_t* oldpos, int n, int32_t* rows, int32_t* cou
 
 // apgd.cu
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
-             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st);
+             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
+             int* lanczos = nullptr);
 
 // grid.cu / fft.cu
 int launch_grid(pc_plan_s* p, const float2* r, cudaStream_t st);
@@ -176,6 +177,8 @@ struct pc_plan_s {
   int2* slot_vis = nullptr;      // {visibility, (a0 + 64) | (b0 + 64) << 8 | plane_start << 16}
   float4* slot_geom = nullptr;   // {gu - a0, gv - b0, xw - plane_start, tau (turns)}
   int4* subs = nullptr;          // gridding sub-problems {tile, plane group, start, end}
+  int* active_rows = nullptr;    // grid rows b that visibilities can reach (ascending)
+  int n_active_rows = 0;
   // image-domain tables
   float4* pix_tab = nullptr;     // per pixel {Re c d, Im c d, t_hi, t_lo}
   float2* twiddle = nullptr;     // e^{+2 pi i k / G}

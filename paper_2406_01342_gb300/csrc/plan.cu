@@ -470,7 +470,11 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
 
   // ---- workspaces
   PC_TRY(dev_alloc_t(p, &p->grid, (size_t)p->P * p->G * p->G));
+  PC_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * (size_t)p->P * p->G * p->G, st));
   PC_TRY(dev_alloc_t(p, &p->fft1, (size_t)p->P * N * p->G));
+  // columns b of the transposed pass-1 output whose grid rows never hold a
+  // visibility stay zero for every certificate: clear them once here
+  PC_CUDA(cudaMemsetAsync(p->fft1, 0, sizeof(float2) * (size_t)p->P * N * p->G, st));
   PC_TRY(dev_alloc_t(p, &p->resid, (size_t)std::max<int64_t>(M, 1)));
   PC_TRY(dev_alloc_t(p, &p->mu, (size_t)NN));
   PC_TRY(dev_alloc_t(p, &p->mark, (size_t)NN));
@@ -562,6 +566,20 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   if (!subs.empty())
     PC_CUDA(cudaMemcpyAsync(p->subs, subs.data(), sizeof(int4) * subs.size(),
                             cudaMemcpyHostToDevice, st));
+  // grid rows that any visibility can reach: the rows of tile rows with a sub-problem
+  {
+    std::vector<char> row_on(p->nT, 0);
+    for (const int4& s : subs) row_on[s.x / p->nT] = 1;
+    std::vector<int> rows;
+    for (int tv = 0; tv < p->nT; ++tv)
+      if (row_on[tv])
+        for (int b = 0; b < p->T; ++b) rows.push_back(tv * p->T + b);
+    p->n_active_rows = (int)rows.size();
+    PC_TRY(dev_alloc_t(p, &p->active_rows, std::max<size_t>(rows.size(), 1)));
+    if (!rows.empty())
+      PC_CUDA(cudaMemcpyAsync(p->active_rows, rows.data(), sizeof(int) * rows.size(),
+                              cudaMemcpyHostToDevice, st));
+  }
   PC_CUDA(cudaStreamSynchronize(st));
   return PC_OK;
 }

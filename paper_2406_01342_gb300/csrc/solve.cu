@@ -528,10 +528,10 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
       int32_t* d_it = p->iscal + 2;
       PC_TRY(run_apgd(p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
-                      p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st));
+                      p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st, p->iscal + 5));
       // pruning
       PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
-      int32_t hi[5];
+      int32_t hi[6];
       double hd[2];
       PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
       PC_CUDA(cudaMemcpyAsync(hd, p->dscal + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
@@ -539,6 +539,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded tensor-core wait expired");
       n_sup = hi[3];
       cur.apgd_iterations = hi[2];
+      cur.lanczos_steps = hi[5];
       cur.lipschitz = hd[0];
       const int32_t* keep = p->keep.as<int32_t>();
       const int ldNew = round4(std::max(n_sup, 1));

@@ -203,7 +203,7 @@ k_gram(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
 constexpr int THIN_RMAX = 16;     // rows (atoms + the V row) of the thin contraction
 constexpr int THIN_COLS = 128;    // columns (atoms) per CTA
 constexpr int THIN_CHUNK = 256;   // visibilities staged per chunk
-constexpr int THIN_SLICE = 4096;  // visibilities per CTA
+constexpr int THIN_SLICE = 1024;  // visibilities per CTA
 
 // Thin contraction for a few rows: for row r < nA (an atom of atomsA) and
 // column c (an atom of atomsB)
@@ -244,7 +244,7 @@ k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
       if (t < cnt) {
         if (r < nA) {
           float sn, cs;
-          sincospif(2.0f * phase_turns(sVis[t], sA[r]), &sn, &cs);
+          __sincosf(6.283185307179586f * phase_turns(sVis[t], sA[r]), &sn, &cs);
           re = cs * sA[r].w;
           im = sn * sA[r].w;
         } else {
@@ -262,7 +262,7 @@ k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
     for (int r = 0; r < THIN_RMAX; ++r) inner[r] = 0.f;
     for (int t = half; t < cnt; t += 2) {
       float sn, cs;
-      sincospif(2.0f * phase_turns(sVis[t], bt), &sn, &cs);
+      __sincosf(6.283185307179586f * phase_turns(sVis[t], bt), &sn, &cs);
       const float br = cs * bt.w, bi = sn * bt.w;
 #pragma unroll
       for (int r = 0; r < THIN_RMAX; ++r)
