@@ -171,7 +171,9 @@ int pc_select(pc_plan_t plan, const float* mu_dev, float thr, const int32_t* pre
  * mode 2: tcgen05 tensor cores on split-FP16 (hi + lo) operands with FP32
  * accumulation (hi*hi + hi*lo + lo*hi); mode 0: tensor cores when S*S >= 4096.
  * Both accumulate K-slices in float64. PC_ERR_TIMEOUT if a bounded
- * tensor-core wait expired. */
+ * tensor-core wait expired. mode 3 is a self-test of that path: the tensor-core
+ * kernel withholds its MMAs, its first buffer wait expires after about 2 s and
+ * the call returns PC_ERR_TIMEOUT with the CUDA context intact. */
 int pc_gram(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev, int32_t S,
             float* G_dev, int32_t ldg, float* b_dev, int32_t mode, void* stream);
 

@@ -162,6 +162,7 @@ struct TcArgs {
   double* acc;
   int ldacc;
   int* err;
+  int withhold;    // self-test: issue no MMA / commit, so the first buffer wait expires
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
     }
-    if (tid == 0) {
+    if (tid == 0 && !g.withhold) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_hi = smem_u32(sb), a_lo = a_hi + a_bytes;
       const uint32_t b_hi = a_hi + 2 * a_bytes, b_lo = b_hi + b_bytes;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
       }
       mma_commit(smem_u32(&mbar[b]));
     }
-    committed[b] += 1;
+    if (!g.withhold) committed[b] += 1;
   }
 
   // drain: wait for the last commit on each buffer (bounded)
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
 // cleared by the caller); err_dev (int) is set to 1 if a bounded wait expired.
 int launch_gram_tc(const int4* vis_fx, int64_t M, const float4* atomsA, int nA,
                    const float4* atomsB, int nB, double* acc, int ldacc, int* err_dev,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool withhold) {
   ProfScope prof_scope_(PROF_GRAM_TC, st);
   if (M <= 0 || nA <= 0 || nB <= 0) return PC_OK;
   const int NT = nB > 128 ? 256 : (nB > 64 ? 128 : 64);
@@ -362,7 +363,7 @@ int launch_gram_tc(const int4* vis_fx, int64_t M, const float4* atomsA, int nA,
     PC_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     attr_set = true;
   }
-  TcArgs a{vis_fx, M, atomsA, nA, atomsB, nB, NT, acc, ldacc, err_dev};
+  TcArgs a{vis_fx, M, atomsA, nA, atomsB, nB, NT, acc, ldacc, err_dev, withhold ? 1 : 0};
   dim3 grid(ceil_div(nB, NT), ceil_div(nA, TC_M), ceil_div(M, TC_SLICE));
   prof_scope_.kernels = 1;
   k_gram_tc<<<grid, TC_THREADS, smem, st>>>(a);

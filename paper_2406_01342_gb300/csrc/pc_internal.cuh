@@ -117,7 +117,7 @@ int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* at
 // gram_tc.cu: tensor-core rows of the Gram (acc cleared by the caller)
 int launch_gram_tc(const int4* vis_fx, int64_t M, const float4* atomsA, int nA,
                    const float4* atomsB, int nB, double* acc, int ldacc, int* err_dev,
-                   cudaStream_t st);
+                   cudaStream_t st, bool withhold = false);
 int launch_gram_finalize(const double* acc, int ldacc, const int32_t* rows, int nrows, int ncols,
                          const int32_t* oldpos, float* G, int ldg, cudaStream_t st);
 // thin contraction: rows = nA atoms (+ the V row when V != null), see sparse.cu

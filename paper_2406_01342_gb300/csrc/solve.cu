@@ -83,11 +83,12 @@ int gram_rows(pc_plan_s* p, const float2* V, const float4* atomsA, int nA, const
               int nB, double* acc, int ldacc, double* b64, int mode, int* err_dev, cudaStream_t st) {
   if (nA > 0) PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nA * ldacc, st));
   if (V) PC_CUDA(cudaMemsetAsync(b64, 0, sizeof(double) * (size_t)nB, st));
-  if (nA + (V ? 1 : 0) <= 16 && mode != 2)
+  if (nA + (V ? 1 : 0) <= 16 && mode < 2)
     return launch_gram_thin(p->vis_fx, V, p->M, atomsA, nA, atomsB, nB, acc, ldacc, b64, st);
-  const bool tc = mode == 2 || (mode == 0 && (int64_t)nA * nB >= 64 * 64);
+  const bool tc = mode >= 2 || (mode == 0 && (int64_t)nA * nB >= 64 * 64);
   if (tc)
-    PC_TRY(launch_gram_tc(p->vis_fx, p->M, atomsA, nA, atomsB, nB, acc, ldacc, err_dev, st));
+    PC_TRY(launch_gram_tc(p->vis_fx, p->M, atomsA, nA, atomsB, nB, acc, ldacc, err_dev, st,
+                          mode == 3));
   else
     PC_TRY(launch_gram(p->vis_fx, nullptr, p->M, atomsA, nA, atomsB, nB, false, acc, ldacc, st, false));
   if (V) PC_TRY(launch_gram_thin(p->vis_fx, V, p->M, nullptr, 0, atomsB, nB, nullptr, 0, b64, st));
@@ -273,7 +274,7 @@ extern "C" int pc_gram(pc_plan_t p, const pc_c32* V, const int32_t* idx, int32_t
   clear_error();
   PC_TRY(check_plan(p, "pc_gram"));
   if (S < 0 || ldg < S) return fail(PC_ERR_INVALID_ARG, "pc_gram: need S >= 0 and ldg >= S");
-  if (mode < 0 || mode > 2) return fail(PC_ERR_INVALID_ARG, "pc_gram: mode must be 0, 1 or 2");
+  if (mode < 0 || mode > 3) return fail(PC_ERR_INVALID_ARG, "pc_gram: mode must be 0, 1, 2 or 3");
   if (S == 0) return PC_OK;
   PC_TRY(check_dev(idx, true, "pc_gram", "idx_dev"));
   PC_TRY(check_dev(G, true, "pc_gram", "G_dev"));

@@ -178,3 +178,18 @@ def test_full_size_medium_sampled(abi):
     ks = np.sort(rng.choice(wl.M, 20_000, replace=False))
     yref = operators.forward(wl.uvw[ks], wl.N, wl.fov, wl.sky_idx, wl.sky_flux.astype(np.float32).astype(np.float64))
     assert rel_l2(y[ks], yref) <= TOL
+
+
+def test_tensor_core_bounded_wait_reports_timeout(abi):
+    """Failure detection without a GPU fault: with its MMAs withheld (mode 3) the
+    tensor-core kernel's bounded mbarrier wait expires, the kernel frees its
+    tensor memory and returns, the host reports PC_ERR_TIMEOUT, and the context
+    keeps working."""
+    wl, V = workload("small_wide_w")
+    plan = _plan(abi, wl)
+    idx = np.sort(np.random.default_rng(6).choice(wl.N * wl.N, 150, replace=False)).astype(np.int32)
+    with pytest.raises(abi.PcError) as e:
+        abi.pc_gram(plan, to_dev(V.astype(np.complex64)), to_dev(idx), mode=3)
+    assert e.value.status == abi.PC_ERR_TIMEOUT
+    G, b = abi.pc_gram(plan, to_dev(V.astype(np.complex64)), to_dev(idx), mode=2)
+    assert np.isfinite(G.cpu().numpy()).all()
