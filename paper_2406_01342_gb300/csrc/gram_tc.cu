@@ -1,30 +1,40 @@
 // Support contraction on the 5th-generation tensor cores (tcgen05):
 //
-//   G[a][b] = Re(Phi_A^H Phi_B)[a][b] = sum_k Re(Phi[k,a]) Re(Phi[k,b]) + Im(Phi[k,a]) Im(Phi[k,b])
+//   G[a][c] = Re(Phi_A^H Phi_C)[a][c] = sum_k Re(Phi[k,a]) Re(Phi[k,c]) + Im(Phi[k,a]) Im(Phi[k,c])
+//   b[a]    = Re(Phi_A^H V)[a]
 //
-// for a tile of 128 "new" atoms (rows, the MMA M dimension) against up to 256
-// active atoms (columns, N), contracting over the visibilities (K: for each
-// visibility its real and imaginary part, interleaved). The phase matrix is
-// never stored: every CTA generates, stage by stage, the K-major operand
-// tiles of 32 visibilities straight into shared memory (exact fixed-point
-// lattice turns + double-float w-term, then sin/cos), as split FP16 pairs
-// x = hi + lo, and one elected thread issues three MMAs per K-step
-// (hi*hi + hi*lo + lo*hi, FP32 accumulate in tensor memory). Two stage
-// buffers alternate: the tensor core works on stage s while the CTA
-// generates stage s+1; an mbarrier signalled by tcgen05.commit tells the
-// generators when a buffer is free again.
+// for the "new" atoms a (the MMA M dimension) against every active atom c and
+// the visibility vector V (N), contracting over the visibilities (K: for each
+// visibility its real and imaginary part, interleaved).
+//
+// Two kernels per K-chunk:
+//  1. k_phase_gen evaluates every phase once -- exact fixed-point lattice turns
+//     plus a double-float w-term, then sin/cos -- splits each value into
+//     FP16 hi + lo and writes both into HBM in the exact K-major core-matrix
+//     layout the tensor core reads (8 rows x 16 bytes per core matrix). Rows
+//     are ordered as the caller gives the atoms (new atoms first), then one
+//     row for V scaled by an exact power of two (so it fits FP16).
+//  2. k_gram_bulk is a warp-specialised GEMM: one producer thread streams the
+//     A tile (128 new atoms) and the B tile (up to 256 rows) of each 16-
+//     visibility stage into one of four shared-memory buffers with
+//     cp.async.bulk (completion counted in bytes on an mbarrier); four MMA
+//     warps wait for a full buffer, one thread issues three tcgen05 MMAs per
+//     K-step (hi*hi + hi*lo + lo*hi, FP32 accumulate in tensor memory) and
+//     commits to the buffer's "empty" mbarrier, which the producer waits on
+//     before refilling it. CTAs with the same K-slice run together, so a slice
+//     of the phase buffer is read from HBM once and then from L2.
 //
 // Accumulation: the tensor core adds each MMA result into its FP32 accumulator
-// with truncation, so a long accumulation drifts low (measured: 2.6e-5 relative
-// after ~750 adds). The CTA therefore accumulates a sub-slice of 128
-// visibilities (48 MMA adds) in a "fast" TMEM accumulator, then adds it,
-// rounded to nearest on the CUDA cores, into a "slow" TMEM accumulator
-// (tcgen05.ld / tcgen05.st); after its K-slice of 8192 visibilities it adds the
-// slow accumulator to a float64 accumulator in HBM.
+// with truncation (measured: 2.6e-5 relative drift after ~750 adds). Each
+// sub-slice of 128 visibilities therefore accumulates in a "fast" TMEM buffer
+// that the MMA warps then add, rounded to nearest, into a "slow" TMEM buffer
+// (tcgen05.ld / tcgen05.st); each 8192-visibility K-slice is added to a
+// float64 accumulator in HBM.
 //
-// Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the
-// kernel sets *err, drains with bounded waits, frees its tensor memory and
-// returns, so the host reports PC_ERR_TIMEOUT instead of hanging the GPU.
+// Every mbarrier wait is bounded (about 2 s of SM clock) and also watches a
+// shared abort flag; on expiry the kernel sets *err, waits (bounded) for the
+// copies and MMAs it issued, frees its tensor memory and returns, so the host
+// reports PC_ERR_TIMEOUT instead of hanging the GPU.
 #include <cuda_fp16.h>
 
 #include "pc_internal.cuh"
@@ -32,33 +42,27 @@
 namespace pc {
 namespace {
 
-constexpr int TC_M = 128;              // MMA M (rows = atoms of the A tile)
-constexpr int TC_KV = 32;              // visibilities per stage
-constexpr int TC_ROW_BYTES = 4 * TC_KV; // 64 fp16 K-elements per row per stage = 128 bytes
-constexpr int TC_SLICE = 8192;         // visibilities per CTA (float64 flush per slice)
-constexpr int TC_SUB = 4;              // stages per fast-accumulator sub-slice (128 visibilities)
-constexpr int TC_THREADS = 768;
-constexpr long long TC_WAIT_CYCLES = 4000000000ll;
-
-// K-major, no-swizzle canonical layout: core matrices of 8 rows x 16 bytes;
-// the 8 K-groups of a row-group are adjacent (LBO = 128 B), row-groups are
-// 1024 B apart (SBO).
-constexpr uint32_t TC_LBO = 128;
-constexpr uint32_t TC_SBO = 1024;
+constexpr int GB_M = 128;               // MMA M (rows of the A tile)
+constexpr int GB_KV = 16;               // visibilities per stage
+constexpr int GB_ROW_BYTES = 4 * GB_KV; // 16 complex fp16 per row per stage = 64 bytes
+constexpr int GB_KG = GB_KV / 4;        // 16-byte K-groups per row per stage
+constexpr uint32_t GB_LBO = 128;        // K-adjacent core matrices
+constexpr uint32_t GB_SBO = GB_KG * 128; // 8-row groups (512 bytes)
+constexpr int GB_NBUF = 4;              // stage buffers
+constexpr int GB_SLICE = 8192;          // visibilities per CTA (one float64 flush)
+constexpr int GB_SUB = 8;               // stages per fast-accumulator sub-slice (128 visibilities)
+constexpr int GB_THREADS = 160;         // warps 0-3: MMA group; warp 4: producer
+constexpr long long GB_WAIT_CYCLES = 4000000000ll;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint32_t core_off(int row, int kg) {
-  return (uint32_t)((row >> 3) * TC_SBO + kg * TC_LBO + (row & 7) * 16);
-}
-
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((TC_LBO >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((TC_SBO >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)((GB_LBO >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((GB_SBO >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;              // descriptor version of tcgen05; no swizzle
   return d;
 }
@@ -95,11 +99,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait for the completion of the phase with the given parity.
-__device__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+// Bounded wait for the completion of the phase with the given parity; gives up
+// early when another thread has raised the abort flag.
+__device__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
   const long long t0 = clock64();
   while (!mbar_try(mbar, parity)) {
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > GB_WAIT_CYCLES) return false;
   }
   return true;
 }
@@ -132,14 +138,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// slow += fast (or slow = fast when first) for the 128-lane x NT accumulator;
-// warps 0..7: lane quadrant (warp & 3), column half (warp >> 2).
+// slow += fast (slow = fast when first) for this warp's 32 accumulator lanes
+// (lane quadrant = warp, warps 0..3) and all NT columns.
 __device__ void fold_fast_into_slow(uint32_t t_fast, uint32_t t_slow, int NT, bool first) {
-  const int warp = threadIdx.x >> 5;
-  if (warp >= 8) return;
-  const int q = warp & 3, half = warp >> 2, cols = NT / 2;
+  const int q = threadIdx.x >> 5;
   const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-  for (int c0 = half * cols; c0 < (half + 1) * cols; c0 += 32) {
+  __syncwarp();
+  for (int c0 = 0; c0 < NT; c0 += 32) {
     uint32_t f[32], s[32];
     tmem_ld32(t_fast + lane_off + (uint32_t)c0, f);
     if (!first) {
@@ -151,223 +156,344 @@ __device__ void fold_fast_into_slow(uint32_t t_fast, uint32_t t_slow, int NT, bo
   }
 }
 
-struct TcArgs {
-  const int4* vis;
-  int64_t M;
-  const float4* atomsA;
-  int nA;
-  const float4* atomsB;
-  int nB;
-  int NT;          // columns per CTA (64, 128 or 256)
+__device__ __forceinline__ void named_sync_mma_group() {
+  asm volatile("barrier.sync 1, 128;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ phase generation
+
+// max |Re V|, |Im V| over the visibilities (as float bits, non-negative floats order as uints).
+__global__ void k_vmax(const float2* __restrict__ V, int64_t M, unsigned* __restrict__ bits) {
+  float m = 0.f;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = V[k];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(bits, __float_as_uint(m));
+}
+
+// scale[0] = 2^-e, scale[1] = 2^e with 2^e > max component of V (exact powers of two).
+__global__ void k_vscale(const unsigned* __restrict__ bits, float* __restrict__ scale) {
+  const float m = __uint_as_float(*bits);
+  int e = 0;
+  if (m > 0.f && isfinite(m)) e = ilogbf(m) + 1;
+  scale[0] = ldexpf(1.f, -e);
+  scale[1] = ldexpf(1.f, e);
+}
+
+// One uint4 (4 visibilities of one row, FP16 re/im pairs) per item; item order
+// equals memory order: [stage][row group][K-group][row in group].
+__global__ void __launch_bounds__(256)
+k_phase_gen(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t k0, int64_t k_end,
+            const float4* __restrict__ atoms, int n_atoms, int v_row, int rows_pad, int n_stages,
+            const float* __restrict__ vscale, uint4* __restrict__ hi, uint4* __restrict__ lo) {
+  const int64_t items = (int64_t)n_stages * rows_pad * GB_KG;
+  const float sc = V ? vscale[0] : 0.f;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < items;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx & 7);
+    const int kg = (int)((idx >> 3) % GB_KG);
+    const int64_t rest = (idx >> 3) / GB_KG;
+    const int g = (int)(rest % (rows_pad / 8));
+    const int64_t stage = rest / (rows_pad / 8);
+    const int row = 8 * g + r;
+    const int64_t kbase = k0 + stage * GB_KV + kg * 4;
+    __half2 h[4], l[4];
+    float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool is_atom = row < n_atoms, is_v = row == v_row;
+    if (is_atom) at = atoms[row];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t k = kbase + v;
+      float re = 0.f, im = 0.f;
+      if (k < k_end) {
+        if (is_atom) {
+          float sn, cs;
+          __sincosf(6.283185307179586f * phase_turns(vis[k], at), &sn, &cs);
+          re = cs * at.w;
+          im = sn * at.w;
+        } else if (is_v) {
+          const float2 vv = V[k];
+          re = vv.x * sc;
+          im = -vv.y * sc;
+        }
+      }
+      h[v] = __floats2half2_rn(re, im);
+      const float2 hf = __half22float2(h[v]);
+      l[v] = __floats2half2_rn(re - hf.x, im - hf.y);
+    }
+    uint4 hv, lv;
+    hv.x = *reinterpret_cast<uint32_t*>(&h[0]);
+    hv.y = *reinterpret_cast<uint32_t*>(&h[1]);
+    hv.z = *reinterpret_cast<uint32_t*>(&h[2]);
+    hv.w = *reinterpret_cast<uint32_t*>(&h[3]);
+    lv.x = *reinterpret_cast<uint32_t*>(&l[0]);
+    lv.y = *reinterpret_cast<uint32_t*>(&l[1]);
+    lv.z = *reinterpret_cast<uint32_t*>(&l[2]);
+    lv.w = *reinterpret_cast<uint32_t*>(&l[3]);
+    hi[idx] = hv;
+    lo[idx] = lv;
+  }
+}
+
+// ------------------------------------------------------------------ bulk-copy GEMM
+
+struct GbArgs {
+  const unsigned char* hi;   // phase buffer (this chunk)
+  const unsigned char* lo;
+  int rows_pad;
+  int n_stages;              // stages in this chunk
+  int nA;                    // rows of A (new atoms, the first rows)
+  int nB;                    // columns: atoms + the V row
+  int v_col;                 // column index of V, or -1
+  const float* vscale;       // [1] = 2^e, multiplies the V column
+  int NT;
   double* acc;
   int ldacc;
   int* err;
-  int withhold;    // self-test: issue no MMA / commit, so the first buffer wait expires
+  int withhold;              // self-test: issue no MMA / commit, so the first buffer wait expires
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(TcArgs g) {
-  extern __shared__ __align__(1024) unsigned char tc_sm[];
+__global__ void __launch_bounds__(GB_THREADS, 1) k_gram_bulk(GbArgs g) {
+  extern __shared__ __align__(1024) unsigned char gb_sm[];
+  __shared__ __align__(8) uint64_t full_bar[GB_NBUF];
+  __shared__ __align__(8) uint64_t empty_bar[GB_NBUF];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+  __shared__ int s_issued, s_consumed, s_last;   // stages copied / consumed, last committed
+  __shared__ int s_go[2], s_go_end;              // MMA-group decisions published by its thread 0
+
   const int NT = g.NT;
-  const int a_bytes = TC_M * TC_ROW_BYTES;
-  const int b_bytes = NT * TC_ROW_BYTES;
-  const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
-  unsigned char* stage_base = tc_sm;
-  float4* sAtom = reinterpret_cast<float4*>(tc_sm + 2 * stage_bytes);   // 128 + NT atoms
-  int4* sVis = reinterpret_cast<int4*>(sAtom + TC_M + NT);              // [2][TC_KV]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sVis + 2 * TC_KV);       // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
-  int* s_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const int a_bytes = GB_M * GB_ROW_BYTES;            // 8 KB
+  const int b_bytes = NT * GB_ROW_BYTES;              // NT * 64
+  const int buf_bytes = 2 * a_bytes + 2 * b_bytes;
+  const uint32_t tx_bytes = (uint32_t)buf_bytes;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int a0 = blockIdx.y * GB_M, b0 = blockIdx.x * NT;
+  const int s_lo = blockIdx.z * (GB_SLICE / GB_KV);
+  const int s_hi = min(g.n_stages, s_lo + GB_SLICE / GB_KV);
+  const int nst = max(0, s_hi - s_lo);
+  const uint32_t ncols = (uint32_t)(2 * NT);          // fast + slow accumulators
+  const size_t stage_stride = (size_t)g.rows_pad * GB_ROW_BYTES;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int a_base = blockIdx.y * TC_M, b_base = blockIdx.x * NT;
-  const int64_t k_lo = (int64_t)blockIdx.z * TC_SLICE;
-  const int64_t k_hi = min(g.M, k_lo + TC_SLICE);
-  const int nrows = TC_M + NT;
-  const uint32_t ncols = (uint32_t)(2 * NT);   // fast + slow accumulators, power of two
-
-  for (int r = tid; r < nrows; r += blockDim.x) {
-    float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r < TC_M) {
-      if (a_base + r < g.nA) at = g.atomsA[a_base + r];
-    } else if (b_base + r - TC_M < g.nB) {
-      at = g.atomsB[b_base + r - TC_M];
-    }
-    sAtom[r] = at;
-  }
-  if (tid < TC_KV) {
-    const int64_t k = k_lo + tid;
-    sVis[tid] = k < k_hi ? g.vis[k] : make_int4(0, 0, 0, 0);
-  }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    for (int b = 0; b < GB_NBUF; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[b])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *s_flag = 0;
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    s_last = -1;
   }
+  __syncwarp();
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
+                     smem_u32(&tmem_slot)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = tmem_slot;
   const uint32_t t_fast = tmem, t_slow = tmem + (uint32_t)NT;
-  const uint32_t idesc = instr_desc(TC_M, NT);
-  bool slow_empty = true;
 
-  const int nstages = (int)((k_hi - k_lo + TC_KV - 1) / TC_KV);
-  int committed[2] = {0, 0};
-  bool timed_out = false;
-
-  for (int s = 0; s < nstages; ++s) {
-    const int b = s & 1;
-    bool bad = false;
-    if (s >= 2) bad = !mbar_wait_bounded(smem_u32(&mbar[b]), (uint32_t)(((s - 2) >> 1) & 1));
-    if (__syncthreads_or(bad)) {
-      timed_out = true;
-      break;
-    }
-    // prefetch the next stage's visibilities into the other staging slot
-    if (tid < TC_KV) {
-      const int64_t k = k_lo + (int64_t)(s + 1) * TC_KV + tid;
-      sVis[((s + 1) & 1) * TC_KV + tid] = k < k_hi ? g.vis[k] : make_int4(0, 0, 0, 0);
-    }
-    unsigned char* sb = stage_base + b * stage_bytes;
-    // items (row, K-group of 4 visibilities): a warp covers 32 consecutive rows
-    // of one K-group, so its 16-byte stores fill whole 128-byte wavefronts.
-    // Warp 0 issues the MMAs and generates nothing, so a blocking MMA issue
-    // never delays the next stage's operands.
-    for (int f = tid - 32; f < nrows * (TC_KV / 4); f += blockDim.x - 32) {
-      if (f < 0) break;
-      const int kg = f / nrows, rr = f - kg * nrows;
-      const bool isA = rr < TC_M;
-      const int row = isA ? rr : rr - TC_M;
-      const float4 my_atom = sAtom[rr];
-      unsigned char* hi_base = isA ? sb : sb + 2 * a_bytes;
-      unsigned char* lo_base = isA ? sb + a_bytes : sb + 2 * a_bytes + b_bytes;
-      const int4* vs = sVis + b * TC_KV;
-      {
-        __half2 h[4], l[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int kv = kg * 4 + v;
-          const bool live = k_lo + (int64_t)s * TC_KV + kv < k_hi;
-          float sn = 0.f, cs = 0.f;
-          if (live) __sincosf(6.283185307179586f * phase_turns(vs[kv], my_atom), &sn, &cs);
-          const float re = cs * my_atom.w, im = sn * my_atom.w;
-          h[v] = __floats2half2_rn(re, im);
-          const float2 hf = __half22float2(h[v]);
-          l[v] = __floats2half2_rn(re - hf.x, im - hf.y);
+  if (warp == 4) {
+    // ---------------- producer: one thread streams the stage tiles
+    if ((tid & 31) == 0) {
+      for (int i = 0; i < nst; ++i) {
+        const int b = i % GB_NBUF;
+        if (i >= GB_NBUF && !mbar_wait(smem_u32(&empty_bar[b]), (uint32_t)(((i / GB_NBUF) - 1) & 1), &s_abort)) {
+          s_abort = 1;
+          break;
         }
-        uint4 hv, lv;
-        hv.x = *reinterpret_cast<uint32_t*>(&h[0]);
-        hv.y = *reinterpret_cast<uint32_t*>(&h[1]);
-        hv.z = *reinterpret_cast<uint32_t*>(&h[2]);
-        hv.w = *reinterpret_cast<uint32_t*>(&h[3]);
-        lv.x = *reinterpret_cast<uint32_t*>(&l[0]);
-        lv.y = *reinterpret_cast<uint32_t*>(&l[1]);
-        lv.z = *reinterpret_cast<uint32_t*>(&l[2]);
-        lv.w = *reinterpret_cast<uint32_t*>(&l[3]);
-        const uint32_t off = core_off(row, kg);
-        *reinterpret_cast<uint4*>(hi_base + off) = hv;
-        *reinterpret_cast<uint4*>(lo_base + off) = lv;
+        if (s_abort) break;
+        const size_t soff = (size_t)(s_lo + i) * stage_stride;
+        unsigned char* dst = gb_sm + (size_t)b * buf_bytes;
+        const uint32_t fb = smem_u32(&full_bar[b]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(tx_bytes)
+                     : "memory");
+        const unsigned char* srcs[4] = {g.hi + soff + (size_t)a0 * GB_ROW_BYTES,
+                                        g.lo + soff + (size_t)a0 * GB_ROW_BYTES,
+                                        g.hi + soff + (size_t)b0 * GB_ROW_BYTES,
+                                        g.lo + soff + (size_t)b0 * GB_ROW_BYTES};
+        const uint32_t dsts[4] = {smem_u32(dst), smem_u32(dst + a_bytes), smem_u32(dst + 2 * a_bytes),
+                                  smem_u32(dst + 2 * a_bytes + b_bytes)};
+        const uint32_t sizes[4] = {(uint32_t)a_bytes, (uint32_t)a_bytes, (uint32_t)b_bytes,
+                                   (uint32_t)b_bytes};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  dsts[c]),
+              "l"(srcs[c]), "r"(sizes[c]), "r"(fb)
+              : "memory");
+        s_issued = i + 1;
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    const bool new_sub = s > 0 && (s % TC_SUB) == 0;
-    if (new_sub) {
-      // fold the finished sub-slice: wait for the MMAs of stage s-1, slow += fast
-      bool bad2 = !mbar_wait_bounded(smem_u32(&mbar[(s - 1) & 1]), (uint32_t)(((s - 1) >> 1) & 1));
-      if (__syncthreads_or(bad2)) {
-        timed_out = true;
+    __syncwarp();
+  } else {
+    // ---------------- MMA group (warps 0..3). Thread 0 does every wait and
+    // publishes the outcome; the group reads it after a named barrier, so all
+    // 128 threads take the same branch and always meet at the same barriers.
+    const uint32_t idesc = instr_desc(GB_M, NT);
+    bool slow_empty = true;
+    bool ok = true;
+    int last = -1;     // last stage whose MMAs were committed
+    for (int i = 0; i < nst; ++i) {
+      const int b = i % GB_NBUF;
+      const bool fold = i > 0 && (i % GB_SUB) == 0 && !g.withhold;
+      if (tid == 0) {
+        bool good = mbar_wait(smem_u32(&full_bar[b]), (uint32_t)((i / GB_NBUF) & 1), &s_abort);
+        // folding needs the MMAs of stage i-1 finished
+        if (good && fold)
+          good = mbar_wait(smem_u32(&empty_bar[(i - 1) % GB_NBUF]), (uint32_t)(((i - 1) / GB_NBUF) & 1),
+                           &s_abort);
+        if (!good) s_abort = 1;
+        if (good) s_consumed = i + 1;
+        s_go[i & 1] = good ? 1 : 0;   // double-buffered: read before the next barrier
+      }
+      named_sync_mma_group();
+      if (!s_go[i & 1]) {
+        ok = false;
         break;
       }
+      if (fold) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        fold_fast_into_slow(t_fast, t_slow, NT, slow_empty);
+        slow_empty = false;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        named_sync_mma_group();
+      }
+      if (tid == 0 && !g.withhold) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_hi = smem_u32(gb_sm + (size_t)b * buf_bytes), a_lo = a_hi + a_bytes;
+        const uint32_t b_hi = a_hi + 2 * a_bytes, b_lo = b_hi + b_bytes;
+#pragma unroll
+        for (int ks = 0; ks < GB_KG / 2; ++ks) {     // K = 16 fp16 elements per MMA
+          const uint32_t koff = ks * 2 * GB_LBO;
+          const uint32_t acc_on = ((i % GB_SUB) | ks) != 0;
+          mma_f16(t_fast, smem_desc(a_hi + koff), smem_desc(b_hi + koff), idesc, acc_on);
+          mma_f16(t_fast, smem_desc(a_hi + koff), smem_desc(b_lo + koff), idesc, 1u);
+          mma_f16(t_fast, smem_desc(a_lo + koff), smem_desc(b_hi + koff), idesc, 1u);
+        }
+        mma_commit(smem_u32(&empty_bar[b]));
+        s_last = i;
+      }
+      if (!g.withhold) last = i;
+    }
+    // wait for the last commit, fold the last sub-slice, add to the float64 accumulator
+    if (ok && last >= 0) {
+      if (tid == 0) {
+        const bool good =
+            mbar_wait(smem_u32(&empty_bar[last % GB_NBUF]), (uint32_t)((last / GB_NBUF) & 1), &s_abort);
+        if (!good) s_abort = 1;
+        s_go_end = good ? 1 : 0;
+      }
+      named_sync_mma_group();
+      ok = s_go_end != 0;
+    }
+    if (ok && last >= 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       fold_fast_into_slow(t_fast, t_slow, NT, slow_empty);
-      slow_empty = false;
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-    }
-    if (tid == 0 && !g.withhold) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = smem_u32(sb), a_lo = a_hi + a_bytes;
-      const uint32_t b_hi = a_hi + 2 * a_bytes, b_lo = b_hi + b_bytes;
+      const int q = warp, lane = tid & 31;
+      const int row = a0 + 32 * q + lane;
+      const float vmul = g.vscale ? g.vscale[1] : 1.f;
+      for (int c0 = 0; c0 < NT; c0 += 32) {
+        uint32_t r[32];
+        __syncwarp();
+        tmem_ld32(t_slow + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
+        if (row < g.nA) {
 #pragma unroll
-      for (int ks = 0; ks < TC_KV / 8; ++ks) {       // K = 16 fp16 elements per MMA
-        const uint32_t koff = ks * 2 * TC_LBO;
-        mma_f16(t_fast, smem_desc(a_hi + koff), smem_desc(b_hi + koff), idesc,
-                ((s % TC_SUB) | ks) != 0);
-        mma_f16(t_fast, smem_desc(a_hi + koff), smem_desc(b_lo + koff), idesc, 1u);
-        mma_f16(t_fast, smem_desc(a_lo + koff), smem_desc(b_hi + koff), idesc, 1u);
-      }
-      mma_commit(smem_u32(&mbar[b]));
-    }
-    if (!g.withhold) committed[b] += 1;
-  }
-
-  // drain: wait for the last commit on each buffer (bounded)
-  bool drained = true;
-  for (int b = 0; b < 2; ++b)
-    if (committed[b] > 0 && !mbar_wait_bounded(smem_u32(&mbar[b]), (uint32_t)((committed[b] - 1) & 1)))
-      drained = false;
-  const bool ok = !timed_out && drained;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && nstages > 0) {
-    fold_fast_into_slow(t_fast, t_slow, NT, slow_empty);    // the last sub-slice
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  }
-
-  if (ok && nstages > 0 && warp < 8) {
-    const int q = warp & 3, half = warp >> 2;
-    const int row = a_base + 32 * q + lane;
-    const int cols_per = NT / 2;
-    for (int c0 = half * cols_per; c0 < (half + 1) * cols_per; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(t_slow + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
-      if (row < g.nA) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = b_base + c0 + j;
-          if (col < g.nB) atomicAdd(&g.acc[(size_t)row * g.ldacc + col], (double)__uint_as_float(r[j]));
+          for (int j = 0; j < 32; ++j) {
+            const int col = b0 + c0 + j;
+            if (col < g.nB) {
+              float v = __uint_as_float(r[j]);
+              if (col == g.v_col) v *= vmul;
+              atomicAdd(&g.acc[(size_t)row * g.ldacc + col], (double)v);
+            }
+          }
         }
       }
     }
   }
-  if (!ok && tid == 0) atomicExch(g.err, 1);
+  // On abort every copy and MMA already issued must finish before the CTA
+  // exits: bounded waits on the "full" phases of the stages copied but not
+  // consumed, and on the last MMA commit.
+  __syncthreads();
+  if (s_abort && tid == 0) {
+    volatile int no_abort = 0;
+    for (int i = s_consumed; i < s_issued; ++i)
+      mbar_wait(smem_u32(&full_bar[i % GB_NBUF]), (uint32_t)((i / GB_NBUF) & 1), &no_abort);
+    if (s_last >= 0)
+      mbar_wait(smem_u32(&empty_bar[s_last % GB_NBUF]), (uint32_t)((s_last / GB_NBUF) & 1), &no_abort);
+    atomicExch(g.err, 1);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  __syncwarp();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
 }  // namespace
 
-// acc[a][c] += G rows of atomsA against atomsB on the tensor cores (acc must be
-// cleared by the caller); err_dev (int) is set to 1 if a bounded wait expired.
-int launch_gram_tc(const int4* vis_fx, int64_t M, const float4* atomsA, int nA,
-                   const float4* atomsB, int nB, double* acc, int ldacc, int* err_dev,
-                   cudaStream_t st, bool withhold) {
+// acc[r][c] += Re(Phi_A^H [Phi_atoms | V])[r][c] for the nA first rows of the
+// atom list (A) against all n_atoms atoms plus, when V is given, the V column
+// (index n_atoms). acc must be cleared by the caller. err_dev (int) is set to
+// 1 if a bounded wait expired. pbuf is the phase buffer (grown here).
+int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int n_atoms,
+                   int nA, double* acc, int ldacc, int* err_dev, cudaStream_t st, bool withhold,
+                   DevBuf& pbuf, float* vscale_dev, unsigned* vbits_dev) {
   ProfScope prof_scope_(PROF_GRAM_TC, st);
-  if (M <= 0 || nA <= 0 || nB <= 0) return PC_OK;
-  const int NT = nB > 128 ? 256 : (nB > 64 ? 128 : 64);
-  const size_t stage_bytes = (size_t)2 * TC_M * TC_ROW_BYTES + (size_t)2 * NT * TC_ROW_BYTES;
-  const size_t smem = 2 * stage_bytes + (size_t)(TC_M + NT) * sizeof(float4) +
-                      2 * TC_KV * sizeof(int4) + 2 * sizeof(uint64_t) + 16;
+  if (M <= 0 || nA <= 0 || n_atoms <= 0) return PC_OK;
+  const int rows = n_atoms + (V ? 1 : 0);
+  const int rows_pad = ceil_div(rows, 256) * 256;
+  const int NT = rows > 128 ? 256 : (rows > 64 ? 128 : 64);
+  // chunk of visibilities: the phase buffer (hi + lo) stays within ~2 GB
+  const int64_t per_vis = (int64_t)rows_pad * 8;
+  int64_t KC = (2ll << 30) / per_vis;
+  KC = std::max<int64_t>(GB_SLICE, (KC / GB_SLICE) * GB_SLICE);
+  const int64_t Mpad = ((M + GB_KV - 1) / GB_KV) * GB_KV;
+  KC = std::min(KC, Mpad);
+  const size_t half = (size_t)rows_pad * KC * 4;
+  PC_TRY(pbuf.ensure(2 * half));
+  uint4* hi = pbuf.as<uint4>();
+  uint4* lo = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(pbuf.p) + half);
+  const size_t smem = (size_t)GB_NBUF * (2 * GB_M * GB_ROW_BYTES + 2 * NT * GB_ROW_BYTES);
   static bool attr_set = false;
   if (!attr_set) {
-    PC_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    PC_CUDA(cudaFuncSetAttribute(k_gram_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  TcArgs a{vis_fx, M, atomsA, nA, atomsB, nB, NT, acc, ldacc, err_dev, withhold ? 1 : 0};
-  dim3 grid(ceil_div(nB, NT), ceil_div(nA, TC_M), ceil_div(M, TC_SLICE));
-  prof_scope_.kernels = 1;
-  k_gram_tc<<<grid, TC_THREADS, smem, st>>>(a);
-  PC_LAUNCH_CHECK();
+  int nk = 0;
+  if (V) {
+    PC_CUDA(cudaMemsetAsync(vbits_dev, 0, sizeof(unsigned), st));
+    k_vmax<<<(int)std::min<int64_t>(1024, ceil_div(M, 256)), 256, 0, st>>>(V, M, vbits_dev);
+    k_vscale<<<1, 1, 0, st>>>(vbits_dev, vscale_dev);
+    PC_LAUNCH_CHECK();
+    nk += 3;
+  }
+  for (int64_t k0 = 0; k0 < M; k0 += KC) {
+    const int64_t kc = std::min(KC, M - k0);
+    const int n_stages = (int)((kc + GB_KV - 1) / GB_KV);
+    const int64_t items = (int64_t)n_stages * rows_pad * GB_KG;
+    const int gblocks = (int)std::min<int64_t>(ceil_div(items, 256), 152 * 16);
+    k_phase_gen<<<gblocks, 256, 0, st>>>(vis_fx, V, k0, k0 + kc, atoms, n_atoms, V ? n_atoms : -1,
+                                         rows_pad, n_stages, vscale_dev, hi, lo);
+    PC_LAUNCH_CHECK();
+    GbArgs a{reinterpret_cast<const unsigned char*>(hi), reinterpret_cast<const unsigned char*>(lo),
+             rows_pad, n_stages, nA, rows, V ? n_atoms : -1, V ? vscale_dev : nullptr, NT, acc, ldacc,
+             err_dev, withhold ? 1 : 0};
+    dim3 grid(ceil_div(rows, NT), ceil_div(nA, GB_M), ceil_div(n_stages, GB_SLICE / GB_KV));
+    k_gram_bulk<<<grid, GB_THREADS, smem, st>>>(a);
+    PC_LAUNCH_CHECK();
+    nk += 2;
+  }
+  prof_scope_.kernels = nk;
   return PC_OK;
 }
 

@@ -115,9 +115,10 @@ int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* at
                 const float4* atomsB, int nB, bool with_v, double* acc, int ldacc,
                 cudaStream_t st, bool clear = true);
 // gram_tc.cu: tensor-core rows of the Gram (acc cleared by the caller)
-int launch_gram_tc(const int4* vis_fx, int64_t M, const float4* atomsA, int nA,
-                   const float4* atomsB, int nB, double* acc, int ldacc, int* err_dev,
-                   cudaStream_t st, bool withhold = false);
+struct DevBuf;
+int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int n_atoms,
+                   int nA, double* acc, int ldacc, int* err_dev, cudaStream_t st, bool withhold,
+                   DevBuf& pbuf, float* vscale_dev, unsigned* vbits_dev);
 int launch_gram_finalize(const double* acc, int ldacc, const int32_t* rows, int nrows, int ncols,
                          const int32_t* oldpos, float* G, int ldg, cudaStream_t st);
 // thin contraction: rows = nA atoms (+ the V row when V != null), see sparse.cu
@@ -125,6 +126,8 @@ int launch_gram_thin(const int4* vis_fx, const float2* V, int64_t M, const float
                      const float4* atomsB, int nB, double* acc, int ldacc, double* b64,
                      cudaStream_t st);
 int launch_d2f(const double* in, int n, float* out, cudaStream_t st);
+int launch_gram_finalize_perm(const double* acc, int ldacc, int n_new, int n_act, const int32_t* perm,
+                              float* G, int ldg, float* b, cudaStream_t st);
 int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double dl,
                        float4* atoms, int* dflag, cudaStream_t st);
 
@@ -137,6 +140,8 @@ int launch_old_positions(const int32_t* newidx, int n_new, const int32_t* oldidx
 int launch_compact_nonzero(const float* x, int n, int32_t* keep, int32_t* count_dev,
                            cudaStream_t st);
 int launch_compact_new(const int32_t* oldpos, int n, int32_t* rows, int32_t* count_dev,
+                       cudaStream_t st);
+int launch_compact_old(const int32_t* oldpos, int n, int32_t* rows, int32_t* count_dev,
                        cudaStream_t st);
 
 // apgd.cu
@@ -196,6 +201,7 @@ struct pc_plan_s {
 
   // solver workspace (grown on demand)
   pc::DevBuf atomsA, atomsB, idxA, idxB, xA, xB, oldpos, newrows, keep, GA, GB, bA, bB, acc;
+  pc::DevBuf perm, atomsP, pbuf;   // tensor-core Gram: atom order (new first), atoms, phase buffer
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
 };

@@ -122,10 +122,12 @@ __global__ void k_old_positions(const int32_t* __restrict__ newidx, int n_new,
   oldpos[i] = (lo < n_old && oldidx[lo] == v) ? lo : -1;
 }
 
-// keep = positions i with x[i] != 0 (ascending); count_dev[0] = their number.
-// Also lists the positions with pred (oldpos[i] < 0) when newrows != null.
+// Ascending positions i that satisfy the predicate (mode 0: x[i] != 0;
+// 1: oldpos[i] < 0, a new atom; 2: oldpos[i] >= 0, an old atom);
+// count_dev[0] = their number. One block.
 __global__ void k_compact_single(const float* __restrict__ x, const int32_t* __restrict__ oldpos,
-                                 int n, int32_t* __restrict__ out, int32_t* __restrict__ count_dev) {
+                                 int n, int32_t* __restrict__ out, int32_t* __restrict__ count_dev,
+                                 int mode) {
   __shared__ int wcount[32];
   __shared__ int run_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -134,7 +136,7 @@ __global__ void k_compact_single(const float* __restrict__ x, const int32_t* __r
   for (int base = 0; base < n; base += blockDim.x) {
     const int i = base + threadIdx.x;
     bool f = false;
-    if (i < n) f = x ? (x[i] != 0.0f) : (oldpos[i] < 0);
+    if (i < n) f = mode == 0 ? (x[i] != 0.0f) : (mode == 1 ? oldpos[i] < 0 : oldpos[i] >= 0);
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wcount[warp] = __popc(bal);
     __syncthreads();
@@ -191,7 +193,7 @@ int launch_compact_nonzero(const float* x, int n, int32_t* keep, int32_t* count_
                            cudaStream_t st) {
   ProfScope prof_scope_(PROF_MISC, st);
   prof_scope_.kernels = 1;
-  k_compact_single<<<1, 1024, 0, st>>>(x, nullptr, n, keep, count_dev);
+  k_compact_single<<<1, 1024, 0, st>>>(x, nullptr, n, keep, count_dev, 0);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
@@ -200,7 +202,16 @@ int launch_compact_new(const int32_t* oldpos, int n, int32_t* rows, int32_t* cou
                        cudaStream_t st) {
   ProfScope prof_scope_(PROF_MISC, st);
   prof_scope_.kernels = 1;
-  k_compact_single<<<1, 1024, 0, st>>>(nullptr, oldpos, n, rows, count_dev);
+  k_compact_single<<<1, 1024, 0, st>>>(nullptr, oldpos, n, rows, count_dev, 1);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+int launch_compact_old(const int32_t* oldpos, int n, int32_t* rows, int32_t* count_dev,
+                       cudaStream_t st) {
+  ProfScope prof_scope_(PROF_MISC, st);
+  prof_scope_.kernels = 1;
+  k_compact_single<<<1, 1024, 0, st>>>(nullptr, oldpos, n, rows, count_dev, 2);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

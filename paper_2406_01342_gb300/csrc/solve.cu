@@ -72,26 +72,63 @@ int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStre
 
 inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
 
-// Gram rows of nA atoms against nB atoms into acc (nA x ldacc float64) and,
-// when V is given, b64[c] = Re(Phi_B^H V)[c] for the nB column atoms; both are
-// cleared here. Up to 15 rows (16 with the V row) take the thin kernel (no
-// tile padding); larger blocks take the tensor cores (mode 0 when the block
-// has >= 4096 entries, or mode 2) or the FP32 CUDA-core tile kernel (mode 1),
-// and b comes from the thin kernel's V row. err_dev receives the tensor-core
-// kernel's timeout flag.
-int gram_rows(pc_plan_s* p, const float2* V, const float4* atomsA, int nA, const float4* atomsB,
-              int nB, double* acc, int ldacc, double* b64, int mode, int* err_dev, cudaStream_t st) {
-  if (nA > 0) PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nA * ldacc, st));
-  if (V) PC_CUDA(cudaMemsetAsync(b64, 0, sizeof(double) * (size_t)nB, st));
-  if (nA + (V ? 1 : 0) <= 16 && mode < 2)
-    return launch_gram_thin(p->vis_fx, V, p->M, atomsA, nA, atomsB, nB, acc, ldacc, b64, st);
-  const bool tc = mode >= 2 || (mode == 0 && (int64_t)nA * nB >= 64 * 64);
-  if (tc)
-    PC_TRY(launch_gram_tc(p->vis_fx, p->M, atomsA, nA, atomsB, nB, acc, ldacc, err_dev, st,
-                          mode == 3));
-  else
-    PC_TRY(launch_gram(p->vis_fx, nullptr, p->M, atomsA, nA, atomsB, nB, false, acc, ldacc, st, false));
-  if (V) PC_TRY(launch_gram_thin(p->vis_fx, V, p->M, nullptr, 0, atomsB, nB, nullptr, 0, b64, st));
+__global__ void k_iota(int32_t* __restrict__ a, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = i;
+}
+
+// Gram rows of the n_new new atoms against all n_act active atoms, written
+// into G (leading dimension ldg, both triangles) and b = Re(Phi^H V).
+// atomsB: the active atoms in position order; newrows: ascending positions of
+// the new atoms; oldpos: per position the old index or -1 (null: all new).
+// Up to 15 new atoms take the thin kernel, mode 1 the FP32 tile kernel (both
+// then write b for every atom); otherwise the tensor cores (mode 0 when the
+// block has >= 4096 entries, mode 2, or the self-test mode 3) take the atoms
+// in the order new-first and write the G rows and b of the new atoms (b of
+// the old atoms is the caller's). err_dev receives the tensor-core timeout flag.
+int gram_update(pc_plan_s* p, const float2* V, const float4* atomsB, int n_act,
+                const int32_t* newrows, int n_new, const int32_t* oldpos, float* G, int ldg,
+                float* b, int mode, int* err_dev, cudaStream_t st) {
+  if (n_new <= 0) return PC_OK;
+  const bool thin = n_new + 1 <= 16 && mode < 2;
+  const bool tc = !thin && (mode >= 2 || (mode == 0 && (int64_t)n_new * n_act >= 64 * 64));
+  if (!tc) {
+    const int ldacc = n_act;
+    PC_TRY(p->acc.ensure(sizeof(double) * ((size_t)n_new * ldacc + n_act)));
+    double* acc = p->acc.as<double>();
+    double* b64 = acc + (size_t)n_new * ldacc;
+    PC_TRY(p->atomsA.ensure(sizeof(float4) * n_new));
+    PC_TRY(gather_vec<float4>(atomsB, newrows, n_new, p->atomsA.as<float4>(),
+                              make_float4(0.f, 0.f, 0.f, 0.f), st));
+    PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * ((size_t)n_new * ldacc + n_act), st));
+    if (thin) {
+      PC_TRY(launch_gram_thin(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_new, atomsB, n_act, acc,
+                              ldacc, b64, st));
+    } else {
+      PC_TRY(launch_gram(p->vis_fx, nullptr, p->M, p->atomsA.as<float4>(), n_new, atomsB, n_act,
+                         false, acc, ldacc, st, false));
+      if (V) PC_TRY(launch_gram_thin(p->vis_fx, V, p->M, nullptr, 0, atomsB, n_act, nullptr, 0, b64, st));
+    }
+    PC_TRY(launch_gram_finalize(acc, ldacc, newrows, n_new, n_act, oldpos, G, ldg, st));
+    if (V && b) PC_TRY(launch_d2f(b64, n_act, b, st));
+    return PC_OK;
+  }
+  // tensor cores: atoms in the order new-first
+  PC_TRY(p->perm.ensure(sizeof(int32_t) * n_act));
+  PC_TRY(p->atomsP.ensure(sizeof(float4) * n_act));
+  int32_t* perm = p->perm.as<int32_t>();
+  PC_CUDA(cudaMemcpyAsync(perm, newrows, sizeof(int32_t) * n_new, cudaMemcpyDeviceToDevice, st));
+  if (oldpos && n_act > n_new)
+    PC_TRY(launch_compact_old(oldpos, n_act, perm + n_new, p->iscal + 6, st));
+  PC_TRY(gather_vec<float4>(atomsB, perm, n_act, p->atomsP.as<float4>(),
+                            make_float4(0.f, 0.f, 0.f, 0.f), st));
+  const int ldacc = n_act + 1;
+  PC_TRY(p->acc.ensure(sizeof(double) * (size_t)n_new * ldacc));
+  double* acc = p->acc.as<double>();
+  PC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)n_new * ldacc, st));
+  PC_TRY(launch_gram_tc(p->vis_fx, V, p->M, p->atomsP.as<float4>(), n_act, n_new, acc, ldacc, err_dev,
+                        st, mode == 3, p->pbuf, reinterpret_cast<float*>(p->dscal + 6), p->uscal + 7));
+  PC_TRY(launch_gram_finalize_perm(acc, ldacc, n_new, n_act, perm, G, ldg, V ? b : nullptr, st));
   return PC_OK;
 }
 
@@ -282,16 +319,14 @@ extern "C" int pc_gram(pc_plan_t p, const pc_c32* V, const int32_t* idx, int32_t
   PC_TRY(check_dev(V, with_v && p->M > 0, "pc_gram", "V_dev"));
   PC_TRY(check_dev(b, with_v, "pc_gram", "b_dev"));
   cudaStream_t st = SS(stream);
-  PC_TRY(p->atomsA.ensure(sizeof(float4) * S));
-  PC_TRY(make_atoms_checked(idx, nullptr, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
-  const int ldacc = S;
-  PC_TRY(p->acc.ensure(sizeof(double) * ((size_t)S * ldacc + S)));
-  double* b64 = p->acc.as<double>() + (size_t)S * ldacc;
+  PC_TRY(p->atomsB.ensure(sizeof(float4) * S));
+  PC_TRY(p->newrows.ensure(sizeof(int32_t) * S));
+  PC_TRY(make_atoms_checked(idx, nullptr, S, p->N, p->dl, p->atomsB.as<float4>(), p->iscal, st));
+  k_iota<<<ceil_div(S, 256), 256, 0, st>>>(p->newrows.as<int32_t>(), S);   // every atom is new
+  PC_LAUNCH_CHECK();
   PC_CUDA(cudaMemsetAsync(p->iscal + 4, 0, sizeof(int32_t), st));
-  PC_TRY(gram_rows(p, reinterpret_cast<const float2*>(V), p->atomsA.as<float4>(), S,
-                   p->atomsA.as<float4>(), S, p->acc.as<double>(), ldacc, b64, mode, p->iscal + 4, st));
-  PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, nullptr, S, S, nullptr, G, ldg, st));
-  if (with_v) PC_TRY(launch_d2f(b64, S, b, st));
+  PC_TRY(gram_update(p, reinterpret_cast<const float2*>(V), p->atomsB.as<float4>(), S,
+                     p->newrows.as<int32_t>(), S, nullptr, G, ldg, b, mode, p->iscal + 4, st));
   int32_t err = 0;
   PC_TRY(sync_read(&err, p->iscal + 4, sizeof(err), st));
   if (err) return fail(PC_ERR_TIMEOUT, "pc_gram: a bounded tensor-core wait expired");
@@ -506,24 +541,17 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       int32_t* oldpos = p->oldpos.as<int32_t>();
       PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
       PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
-      // old-old block and warm start (b of old atoms kept when no atom is new)
+      // old-old block, warm start and b of the old atoms
       PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
       PC_TRY(gather_vec<float>(p->xA.as<float>(), oldpos, n_act, p->xB.as<float>(), 0.f, st));
-      if (n_new == 0) PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
-      // Gram rows of the new atoms against every active atom; b for every active atom
+      PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
+      // Gram rows of the new atoms against every active atom, and b
       if (n_new > 0) {
         PC_TRY(launch_make_atoms(p->idxB.as<int32_t>(), nullptr, n_act, p->N, p->dl,
                                  p->atomsB.as<float4>(), st));
-        PC_TRY(gather_vec<float4>(p->atomsB.as<float4>(), p->newrows.as<int32_t>(), n_new,
-                                  p->atomsA.as<float4>(), make_float4(0.f, 0.f, 0.f, 0.f), st));
-        const int ldacc = n_act;
-        PC_TRY(p->acc.ensure(sizeof(double) * ((size_t)n_new * ldacc + n_act)));
-        double* b64 = p->acc.as<double>() + (size_t)n_new * ldacc;
-        PC_TRY(gram_rows(p, V, p->atomsA.as<float4>(), n_new, p->atomsB.as<float4>(), n_act,
-                         p->acc.as<double>(), ldacc, b64, c.gram_mode, p->iscal + 4, st));
-        PC_TRY(launch_gram_finalize(p->acc.as<double>(), ldacc, p->newrows.as<int32_t>(), n_new,
-                                    n_act, oldpos, p->GB.as<float>(), ldB, st));
-        PC_TRY(launch_d2f(b64, n_act, p->bB.as<float>(), st));
+        PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_new,
+                           oldpos, p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode,
+                           p->iscal + 4, st));
       }
       // reweighting: restricted LASSO by APGD
       const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));

@@ -287,6 +287,26 @@ k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
   }
 }
 
+// Tensor-core path: rows r < n_new and columns c < n_act of acc are in the
+// permuted atom order perm (new atoms first); column n_act is b. Writes
+// G[perm[r]][perm[c]] and its mirror (a new-new pair only from r <= c, so G
+// stays exactly symmetric) and b[perm[r]].
+__global__ void k_gram_finalize_perm(const double* __restrict__ acc, int ldacc, int n_new, int n_act,
+                                     const int32_t* __restrict__ perm, float* __restrict__ G, int ldg,
+                                     float* __restrict__ b) {
+  const int r = blockIdx.y;
+  if (r >= n_new) return;
+  const int pr = perm ? perm[r] : r;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_act; c += gridDim.x * blockDim.x) {
+    if (c < n_new && c < r) continue;
+    const int pc = perm ? perm[c] : c;
+    const float v = (float)acc[(size_t)r * ldacc + c];
+    G[(size_t)pr * ldg + pc] = v;
+    G[(size_t)pc * ldg + pr] = v;
+  }
+  if (b && blockIdx.x == 0 && threadIdx.x == 0) b[pr] = (float)acc[(size_t)r * ldacc + n_act];
+}
+
 __global__ void k_d2f(const double* __restrict__ in, int n, float* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -382,6 +402,17 @@ int launch_gram_thin(const int4* vis_fx, const float2* V, int64_t M, const float
   prof_scope_.kernels = 1;
   dim3 grid(ceil_div(nB, THIN_COLS), ceil_div(M, THIN_SLICE));
   k_gram_thin<<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+int launch_gram_finalize_perm(const double* acc, int ldacc, int n_new, int n_act, const int32_t* perm,
+                              float* G, int ldg, float* b, cudaStream_t st) {
+  ProfScope prof_scope_(PROF_GRAM_FINALIZE, st);
+  if (n_new <= 0) return PC_OK;
+  prof_scope_.kernels = 1;
+  dim3 grid(std::max(1, std::min(ceil_div(n_act, 256), 64)), n_new);
+  k_gram_finalize_perm<<<grid, 256, 0, st>>>(acc, ldacc, n_new, n_act, perm, G, ldg, b);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
