@@ -444,6 +444,254 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
+// ---------------------------------------------------------------------------
+// Full-vector variant (used whenever its vectors fit): every CTA keeps all n
+// entries of x, y, z, Gx, Gy, Gz and b, and owns rows [r0, r0 + nr) of G.
+// An iteration multiplies the own rows by the (local) full z, publishes the
+// slice of G z in one of two buffers, passes ONE cluster barrier, gathers the
+// whole G z over distributed shared memory, and then does every reduction and
+// update redundantly over all n entries -- identical data and order in every
+// CTA, so identical decisions without a second cluster round trip. The
+// published buffers alternate, so a CTA may write the next slice while others
+// still read the previous one (they have all passed the barrier in between).
+
+struct SmemF {
+  float* pub;     // 2 x pub_stride: published slices of a matrix-vector product
+  float* x;       // n_pad each, full vectors
+  float* Gx;
+  float* y;
+  float* Gy;
+  float* z;
+  float* Gz;
+  float* bb;
+  float* Gc;      // rows_per x n_pad (optional)
+};
+
+__device__ __forceinline__ int pub_stride(const ApgdArgs& a) { return (a.rows_per + 3) & ~3; }
+
+__device__ SmemF carve_full(float* base, const ApgdArgs& a) {
+  SmemF s;
+  float* p = base;
+  s.pub = p; p += 2 * pub_stride(a);
+  s.x = p; p += a.n_pad;
+  s.Gx = p; p += a.n_pad;
+  s.y = p; p += a.n_pad;
+  s.Gy = p; p += a.n_pad;
+  s.z = p; p += a.n_pad;
+  s.Gz = p; p += a.n_pad;
+  s.bb = p; p += a.n_pad;
+  s.Gc = p;
+  return s;
+}
+
+// out[r] = G[r0 + r, :] . vec (full vector in shared memory) for the nr own rows.
+__device__ void gemv_own(const ApgdArgs& a, const float* Gc, const float* vec, int r0, int nr,
+                         float* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool vecld = a.cache || a.vec_ok;
+  const int n4 = a.n >> 2;
+  const float4* v4 = reinterpret_cast<const float4*>(vec);
+  for (int rb = 4 * warp; rb < nr; rb += 4 * nw) {
+    const float* rows[4];
+    float acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = min(rb + q, nr - 1);
+      rows[q] = a.cache ? Gc + (size_t)r * a.n_pad : a.G + (size_t)(r0 + r) * a.ldg;
+      acc[q] = 0.f;
+    }
+    if (vecld) {
+      for (int c = lane; c < n4; c += 32) {
+        const float4 z = v4[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 g = reinterpret_cast<const float4*>(rows[q])[c];
+          acc[q] = fmaf(g.x, z.x, acc[q]);
+          acc[q] = fmaf(g.y, z.y, acc[q]);
+          acc[q] = fmaf(g.z, z.z, acc[q]);
+          acc[q] = fmaf(g.w, z.w, acc[q]);
+        }
+      }
+      for (int c = 4 * n4 + lane; c < a.n; c += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(rows[q][c], vec[c], acc[q]);
+    } else {
+      for (int c = lane; c < a.n; c += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(rows[q][c], vec[c], acc[q]);
+    }
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if (lane < 4 && rb + lane < nr) {
+      float v = acc[0];
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+        if (lane == q) v = acc[q];
+      out[rb + lane] = v;
+    }
+  }
+}
+
+// G vec for all n rows, in every CTA: own rows, publish, one cluster barrier,
+// gather the slices of all CTAs. Ends with the block synchronised.
+__device__ void cluster_gemv(cg::cluster_group& cl, const ApgdArgs& a, const SmemF& s, const float* vec,
+                             int r0, int nr, int& buf, float* out) {
+  float* mine = s.pub + buf * pub_stride(a);
+  gemv_own(a, s.Gc, vec, r0, nr, mine);
+  cl.sync();
+  for (int idx = threadIdx.x; idx < a.n; idx += blockDim.x) {
+    const int rr = idx / a.rows_per;
+    const int off = idx - rr * a.rows_per;
+    const float* remote = cl.map_shared_rank(mine, rr);
+    out[idx] = remote[off];
+  }
+  buf ^= 1;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
+  extern __shared__ __align__(16) float apgdf_sm[];
+  __shared__ Df scratch[(APGD_THREADS / 32) * NPART];
+  __shared__ Df s_part[NPART];
+  __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const SmemF s = carve_full(apgdf_sm, a);
+  const int r0 = rank * a.rows_per;
+  const int nr = max(0, min(a.n, r0 + a.rows_per) - r0);
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  int buf = 0;
+
+  if (a.cache) {
+    for (int e = tid; e < nr * a.n_pad; e += nt) {
+      const int r = e / a.n_pad, c = e - r * a.n_pad;
+      s.Gc[e] = c < n ? a.G[(size_t)(r0 + r) * a.ldg + c] : 0.f;
+    }
+  }
+  const float v0 = rsqrtf((float)n);        // Lanczos start: all ones / sqrt(n)
+  for (int i = tid; i < a.n_pad; i += nt) {
+    const bool in = i < n;
+    s.bb[i] = in ? a.b[i] : 0.f;
+    s.x[i] = in ? a.x[i] : 0.f;
+    s.y[i] = in ? v0 : 0.f;   // v_j
+    s.z[i] = 0.f;             // v_{j-1}
+  }
+  __syncthreads();
+
+  // ---- Lipschitz constant: Lanczos (alpha = v^T G v, then beta = ||w||)
+  float theta = 0.f, theta_prev = 0.f, beta_prev = 0.f;
+  int m = 0;
+  for (int j = 0; j < LZ_MAX; ++j) {
+    cluster_gemv(cl, a, s, s.y, r0, nr, buf, s.Gz);           // G v_j
+    Df v[NPART] = {};
+    for (int i = tid; i < n; i += nt) v[0] = df_add(v[0], df_prod(s.y[i], s.Gz[i]));
+    block_sums(v, s_part, scratch);
+    const float alpha = s_part[0].hi + s_part[0].lo;
+    Df v2[NPART] = {};
+    for (int i = tid; i < n; i += nt) {
+      const float w = s.Gz[i] - alpha * s.y[i] - beta_prev * s.z[i];
+      s.Gz[i] = w;
+      v2[0] = df_add(v2[0], df_prod(w, w));
+    }
+    block_sums(v2, s_part, scratch);
+    const float beta = sqrtf(fmaxf(s_part[0].hi + s_part[0].lo, 0.f));
+    if (tid == 0) {
+      s_al[j] = alpha;
+      s_be[j] = beta;
+    }
+    m = j + 1;
+    __syncthreads();
+    const bool last = (m == n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
+    if (last || (m % 8) == 0) {
+      theta = tridiag_top(s_al, s_be, m, &s_theta);
+      if (last || fabsf(theta - theta_prev) <= 1e-6f * fabsf(theta)) break;
+      theta_prev = theta;
+    }
+    const float inv = 1.f / beta;
+    for (int i = tid; i < n; i += nt) {
+      const float vn = s.Gz[i] * inv;
+      s.z[i] = s.y[i];
+      s.y[i] = vn;
+    }
+    beta_prev = beta;
+    __syncthreads();
+  }
+  const float L = 1.01f * (theta > 0.f ? theta : 1.f);
+  const float invL = 1.f / L;
+  const float thr = a.lam * invL;
+
+  // ---- initial G x and F(x)
+  cluster_gemv(cl, a, s, s.x, r0, nr, buf, s.Gx);
+  Df Fx;
+  {
+    Df v[NPART] = {};
+    for (int i = tid; i < n; i += nt) {
+      v[0] = df_add(v[0], df_prod(s.x[i], s.Gx[i]));
+      v[1] = df_add(v[1], df_prod(s.bb[i], s.x[i]));
+      v[2] = df_add(v[2], Df{fabsf(s.x[i]), 0.f});
+    }
+    block_sums(v, s_part, scratch);
+    Fx = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
+  }
+  for (int i = tid; i < n; i += nt) {
+    s.y[i] = s.x[i];
+    s.Gy[i] = s.Gx[i];
+  }
+  __syncthreads();
+
+  // ---- monotone FISTA
+  float t = 1.f;
+  int it = 0;
+  for (it = 1; it <= a.max_iter; ++it) {
+    for (int i = tid; i < n; i += nt) {
+      const float u = s.y[i] - (s.Gy[i] - s.bb[i]) * invL;
+      s.z[i] = copysignf(fmaxf(fabsf(u) - thr, 0.f), u);
+    }
+    __syncthreads();
+    cluster_gemv(cl, a, s, s.z, r0, nr, buf, s.Gz);
+    Df v[NPART] = {};
+    for (int i = tid; i < n; i += nt) {
+      const float zr = s.z[i];
+      v[0] = df_add(v[0], df_prod(zr, s.Gz[i]));
+      v[1] = df_add(v[1], df_prod(s.bb[i], zr));
+      v[2] = df_add(v[2], Df{fabsf(zr), 0.f});
+      const float d = zr - s.y[i];
+      v[3] = df_add(v[3], df_prod(d, d));
+      v[4] = df_add(v[4], df_prod(zr, zr));
+    }
+    block_sums(v, s_part, scratch);
+    const Df Fz = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
+    const float step = sqrtf(s_part[3].hi + s_part[3].lo);
+    const float nz = sqrtf(s_part[4].hi + s_part[4].lo);
+    const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+    const bool accept = df_le(Fz, Fx);
+    const float c1 = t / t1, c2 = (t - 1.f) / t1;
+    for (int i = tid; i < n; i += nt) {
+      const float xo = s.x[i], Gxo = s.Gx[i];
+      const float xn = accept ? s.z[i] : xo;
+      const float Gxn = accept ? s.Gz[i] : Gxo;
+      s.y[i] = xn + c1 * (s.z[i] - xn) + c2 * (xn - xo);
+      s.Gy[i] = Gxn + c1 * (s.Gz[i] - Gxn) + c2 * (Gxn - Gxo);
+      s.x[i] = xn;
+      s.Gx[i] = Gxn;
+    }
+    if (accept) Fx = Fz;
+    t = t1;
+    __syncthreads();
+    if (step <= a.eps * nz) break;
+  }
+  if (it > a.max_iter) it = a.max_iter;
+  for (int r = tid; r < nr; r += nt) a.x[r0 + r] = s.x[r0 + r];
+  if (rank == 0 && tid == 0) {
+    if (a.out_iters) *a.out_iters = it;
+    if (a.out_L) *a.out_L = (double)L;
+    if (a.out_F) *a.out_F = (double)Fx.hi + (double)Fx.lo;
+    if (a.out_lanczos) *a.out_lanczos = m;
+  }
+  cl.sync();   // no CTA leaves while others may still read its shared memory
+}
+
 }  // namespace
 
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
@@ -451,34 +699,52 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
              int* lanczos) {
   if (S <= 0) return PC_OK;
   static int cs_max = 0;
-  static size_t smem_set = 0;
+  static bool attrs_set = false;
+  // dynamic shared memory ceilings: 227 KB per CTA minus the kernels' static arrays
+  const size_t limit_rows = 200 * 1024;
+  const size_t limit_full = 226 * 1024;
   if (cs_max == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_apgd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cs_max = (e == cudaSuccess) ? 16 : 8;
-    if (e != cudaSuccess) cudaGetLastError();
+    cudaError_t e1 = cudaFuncSetAttribute(k_apgd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e2 = cudaFuncSetAttribute(k_apgd_full, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cs_max = (e1 == cudaSuccess && e2 == cudaSuccess) ? 16 : 8;
+    cudaGetLastError();
   }
-  // cluster size: the smallest power of two whose CTAs can each cache their
-  // rows of G in shared memory (fewer CTAs = cheaper barriers), else cs_max
+  if (!attrs_set) {
+    PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit_rows));
+    PC_CUDA(cudaFuncSetAttribute(k_apgd_full, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)limit_full));
+    attrs_set = true;
+  }
   const int n_pad = (S + 3) & ~3;
-  const size_t limit = 200 * 1024;
-  auto bytes_for = [&](int cs, bool cached) {
+  // full-vector kernel: 2 published slices + 7 full vectors (+ cached rows of G)
+  auto bytes_full = [&](int cs, bool cached) {
+    const size_t rp = (size_t)ceil_div(S, cs);
+    const size_t ps = (rp + 3) & ~size_t(3);
+    return sizeof(float) * (2 * ps + 7 * (size_t)n_pad) + (cached ? sizeof(float) * rp * n_pad : 0);
+  };
+  // row-slice kernel (larger supports): one full vector + 8 row slices
+  auto bytes_rows = [&](int cs, bool cached) {
     const size_t rp = (size_t)ceil_div(S, cs);
     return sizeof(float) * ((size_t)n_pad + 8 * rp) + 16 + 16 * sizeof(Df) +
            (cached ? sizeof(float) * rp * n_pad : 0);
   };
+  // cluster size: the smallest power of two whose CTAs can each cache their
+  // rows of G in shared memory (fewer CTAs = cheaper barriers), else cs_max
+  bool full = true;
   int CS = 1;
-  while (CS < cs_max && bytes_for(CS, true) > limit) CS *= 2;
-  int rows_per = ceil_div(S, CS);
-  size_t base_bytes = bytes_for(CS, false);
-  if (base_bytes > limit)
-    return fail(PC_ERR_CAPACITY, "apgd: support of %d atoms exceeds the cluster solver", S);
-  const size_t cache_bytes = sizeof(float) * (size_t)rows_per * n_pad;
-  const int cache = (base_bytes + cache_bytes <= limit) ? 1 : 0;
-  const size_t smem = base_bytes + (cache ? cache_bytes : 0);
-  if (smem_set == 0) {   // the largest size any launch may ask for, set once
-    PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
-    smem_set = limit;
+  while (CS < cs_max && bytes_full(CS, true) > limit_full) CS *= 2;
+  int cache = bytes_full(CS, true) <= limit_full ? 1 : 0;
+  size_t smem = bytes_full(CS, cache != 0);
+  if (smem > limit_full) {
+    full = false;
+    CS = 1;
+    while (CS < cs_max && bytes_rows(CS, true) > limit_rows) CS *= 2;
+    if (bytes_rows(CS, false) > limit_rows)
+      return fail(PC_ERR_CAPACITY, "apgd: support of %d atoms exceeds the cluster solver", S);
+    cache = bytes_rows(CS, true) <= limit_rows ? 1 : 0;
+    smem = bytes_rows(CS, cache != 0);
   }
+  const int rows_per = ceil_div(S, CS);
 
   ApgdArgs a;
   a.G = G;
@@ -514,7 +780,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
   {
     ProfScope prof_scope_(PROF_APGD, st);
     prof_scope_.kernels = 1;
-    e = cudaLaunchKernelEx(&cfg, k_apgd, a);
+    e = full ? cudaLaunchKernelEx(&cfg, k_apgd_full, a) : cudaLaunchKernelEx(&cfg, k_apgd, a);
   }
   if (e != cudaSuccess && CS == 16) {
     // fall back to a portable cluster size

@@ -38,6 +38,7 @@
 #include <cuda_fp16.h>
 
 #include "pc_internal.cuh"
+#include "tcgen05.cuh"
 
 namespace pc {
 namespace {
@@ -54,88 +55,16 @@ constexpr int GB_SUB = 8;               // stages per fast-accumulator sub-slice
 constexpr int GB_THREADS = 160;         // warps 0-3: MMA group; warp 4: producer
 constexpr long long GB_WAIT_CYCLES = 4000000000ll;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+using tc::mma_commit;
+using tc::mma_f16;
+using tc::smem_u32;
+using tc::tmem_ld32;
+using tc::tmem_st32;
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((GB_LBO >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((GB_SBO >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;              // descriptor version of tcgen05; no swizzle
-  return d;
-}
-
-// kind::f16 instruction descriptor: FP32 accumulator, FP16 A and B, both K-major.
-__device__ __forceinline__ uint32_t instr_desc(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(done)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait for the completion of the phase with the given parity; gives up
-// early when another thread has raised the abort flag.
-__device__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-  const long long t0 = clock64();
-  while (!mbar_try(mbar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > GB_WAIT_CYCLES) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
-      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
-      "r"(r[29]), "r"(r[30]), "r"(r[31])
-      : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) { return tc::smem_desc(saddr, GB_LBO, GB_SBO); }
+__device__ __forceinline__ uint32_t instr_desc(int M, int N) { return tc::instr_desc_f16(M, N); }
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  return tc::mbar_wait(mbar, parity, abort_flag, GB_WAIT_CYCLES);
 }
 
 // slow += fast (slow = fast when first) for this warp's 32 accumulator lanes
@@ -266,6 +195,10 @@ __global__ void __launch_bounds__(GB_THREADS, 1) k_gram_bulk(GbArgs g) {
   __shared__ int s_go[2], s_go_end;              // MMA-group decisions published by its thread 0
 
   const int NT = g.NT;
+  // Rows and the first nA columns are the same (new) atoms: a tile whose
+  // columns all lie below its first row holds only entries that symmetry
+  // gives (the caller reads G[r][c] of two new atoms for c >= r only).
+  if ((int)(blockIdx.x + 1) * NT <= (int)blockIdx.y * GB_M) return;
   const int a_bytes = GB_M * GB_ROW_BYTES;            // 8 KB
   const int b_bytes = NT * GB_ROW_BYTES;              // NT * 64
   const int buf_bytes = 2 * a_bytes + 2 * b_bytes;
@@ -443,7 +376,8 @@ __global__ void __launch_bounds__(GB_THREADS, 1) k_gram_bulk(GbArgs g) {
 
 // acc[r][c] += Re(Phi_A^H [Phi_atoms | V])[r][c] for the nA first rows of the
 // atom list (A) against all n_atoms atoms plus, when V is given, the V column
-// (index n_atoms). acc must be cleared by the caller. err_dev (int) is set to
+// (index n_atoms), except entries c < r with c < nA (tiles wholly below the
+// diagonal are skipped; they mirror computed ones). acc must be cleared by the caller. err_dev (int) is set to
 // 1 if a bounded wait expired. pbuf is the phase buffer (grown here).
 int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int n_atoms,
                    int nA, double* acc, int ldacc, int* err_dev, cudaStream_t st, bool withhold,
