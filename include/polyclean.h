@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PC_ABI_VERSION 1
+#define PC_ABI_VERSION 2
 
 typedef enum {
   PC_OK = 0,
@@ -65,6 +65,8 @@ typedef struct {
   int32_t kernel_width;   /* ES kernel width W in grid cells (default 7; 4..8)         */
   int32_t tile;           /* gridding tile side in cells (32, the only supported value) */
   int32_t max_planes;     /* cap on the number of w-planes (default 256)                */
+  int32_t grid_mode;      /* gridding: 0 (default) tensor cores when w-stacking, else CUDA
+                             cores; 1: FP32 CUDA cores; 2: tensor cores whenever w-stacking */
 } pc_plan_opts;
 
 /* Solver options (Algorithm 2 and its sub-solver). Zero fields take defaults. */
@@ -179,9 +181,11 @@ int pc_gram(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev, int32_t
 
 /* Restricted LASSO by monotone FISTA on the Gram form (Sect. 3.4 / 4.1):
  * min_x 1/2 x^T G x - b^T x + lambda ||x||_1, warm start x_dev (in/out),
- * step 1/L with L = 1.01 x power-iteration estimate of the top eigenvalue of G,
- * stop when ||z - y|| <= eps ||z|| or after max_iter iterations.
- * iters_host / lipschitz_host (may be NULL) receive the iteration count and L. */
+ * step 1/L with L = 1.01 x the top eigenvalue of G (Lanczos, ~1e-6 relative),
+ * stop when ||z - y|| <= eps ||z|| or after max_iter iterations. Synchronises
+ * the stream. iters_host / lipschitz_host (may be NULL) receive the iteration
+ * count and L. PC_ERR_TIMEOUT if a bounded wait between the CTAs of the
+ * solver's thread-block cluster expired (x_dev is then unchanged). */
 int pc_apgd(const float* G_dev, int32_t ldg, const float* b_dev, int32_t S, double lambda,
             double eps, int32_t max_iter, float* x_dev, int32_t* iters_host,
             double* lipschitz_host, void* stream);

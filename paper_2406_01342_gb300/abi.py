@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-PC_ABI_VERSION = 1
+PC_ABI_VERSION = 2
 PC_OK = 0
 PC_ERR_INVALID_ARG = -1
 PC_ERR_OOM = -2
@@ -41,7 +41,8 @@ class PcError(RuntimeError):
 
 class pc_plan_opts(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("max_planes", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("max_planes", ctypes.c_int32),
+                ("grid_mode", ctypes.c_int32)]
 
 
 class pc_solve_opts(ctypes.Structure):
@@ -169,9 +170,9 @@ class Plan:
 
 
 def pc_plan_create(uvw: torch.Tensor, N: int, fov: float, kernel_width: int = 0, tile: int = 0,
-                   max_planes: int = 0, stream=None) -> Plan:
+                   max_planes: int = 0, stream=None, grid_mode: int = 0) -> Plan:
     lib = load()
-    opts = pc_plan_opts(PC_ABI_VERSION, kernel_width, tile, max_planes)
+    opts = pc_plan_opts(PC_ABI_VERSION, kernel_width, tile, max_planes, grid_mode)
     h = _P()
     M = int(uvw.shape[0])
     _check(lib.pc_plan_create(_dev(uvw, torch.float64, "uvw") if M else None, M, N, float(fov),

@@ -87,6 +87,7 @@ struct ApgdArgs {
   double* out_L;
   double* out_F;
   int* out_lanczos;
+  int* err;       // set to 1 if a bounded wait expired (may be null)
   int rows_per;
   int n_pad;
   int cache;      // 1: rows of G cached in shared memory
@@ -446,48 +447,97 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
 
 // ---------------------------------------------------------------------------
 // Full-vector variant (used whenever its vectors fit): every CTA keeps all n
-// entries of x, y, z, Gx, Gy, Gz and b, and owns rows [r0, r0 + nr) of G.
-// An iteration multiplies the own rows by the (local) full z, publishes the
-// slice of G z in one of two buffers, passes ONE cluster barrier, gathers the
-// whole G z over distributed shared memory, and then does every reduction and
-// update redundantly over all n entries -- identical data and order in every
-// CTA, so identical decisions without a second cluster round trip. The
-// published buffers alternate, so a CTA may write the next slice while others
-// still read the previous one (they have all passed the barrier in between).
+// entries of x, y, z, Gx, Gy and b, and owns rows [r0, r0 + nr) of G. A
+// matrix-vector product multiplies the own rows by the (local) full vector and
+// PUSHES each result to every CTA of the cluster with st.async, whose bytes
+// complete on the receiver's mbarrier; each CTA then waits (bounded) on its own
+// mbarrier until all n entries have landed. No cluster barrier and no remote
+// loads sit on the iteration path, only the one-way latency of the pushes.
+// The reductions and updates are then done redundantly over all n entries --
+// identical data and order in every CTA, hence identical decisions.
+//
+// Two receive buffers alternate. A CTA pushes product i + 2 into buffer
+// i mod 2 only after it has received every CTA's product i + 1, which each CTA
+// sends only after it has consumed product i and re-armed that buffer's
+// mbarrier, so a buffer is never overwritten while it is read and bytes never
+// arrive before the phase that counts them is armed.
+
+constexpr long long APGD_WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
 struct SmemF {
-  float* pub;     // 2 x pub_stride: published slices of a matrix-vector product
+  float* rx0;     // n_pad each: the two receive buffers of the products
+  float* rx1;
   float* x;       // n_pad each, full vectors
   float* Gx;
   float* y;
   float* Gy;
   float* z;
-  float* Gz;
   float* bb;
   float* Gc;      // rows_per x n_pad (optional)
 };
 
-__device__ __forceinline__ int pub_stride(const ApgdArgs& a) { return (a.rows_per + 3) & ~3; }
-
 __device__ SmemF carve_full(float* base, const ApgdArgs& a) {
   SmemF s;
   float* p = base;
-  s.pub = p; p += 2 * pub_stride(a);
+  s.rx0 = p; p += a.n_pad;
+  s.rx1 = p; p += a.n_pad;
   s.x = p; p += a.n_pad;
   s.Gx = p; p += a.n_pad;
   s.y = p; p += a.n_pad;
   s.Gy = p; p += a.n_pad;
   s.z = p; p += a.n_pad;
-  s.Gz = p; p += a.n_pad;
   s.bb = p; p += a.n_pad;
   s.Gc = p;
   return s;
 }
 
-// out[r] = G[r0 + r, :] . vec (full vector in shared memory) for the nr own rows.
-__device__ void gemv_own(const ApgdArgs& a, const float* Gc, const float* vec, int r0, int nr,
-                         float* out) {
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t saddr, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void push_f32(uint32_t raddr, float v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr),
+               "r"(__float_as_uint(v)), "r"(rbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arm(uint32_t mbar, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ bool mbar_wait_cluster(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_cluster(mbar, parity))
+    if (clock64() - t0 > APGD_WAIT_CYCLES) return false;
+  return true;
+}
+
+struct Exchange {
+  uint32_t rx0, rx1;     // shared::cta addresses of the receive buffers
+  uint32_t bar0, bar1;   // ... and of their mbarriers
+  uint32_t phase;        // parity bit per buffer
+  int buf;
+  int CS;
+  __device__ uint32_t rx(int b) const { return b ? rx1 : rx0; }
+  __device__ uint32_t bar(int b) const { return b ? bar1 : bar0; }
+};
+
+// G vec for all n rows, in every CTA; returns the receive buffer holding it.
+// *ok becomes false (in every thread of the CTA) if the bounded wait expired.
+__device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* vec, int r0, int nr,
+                               Exchange& ex, bool& ok) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int b = ex.buf;
   const bool vecld = a.cache || a.vec_ok;
   const int n4 = a.n >> 2;
   const float4* v4 = reinterpret_cast<const float4*>(vec);
@@ -497,7 +547,7 @@ __device__ void gemv_own(const ApgdArgs& a, const float* Gc, const float* vec, i
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = min(rb + q, nr - 1);
-      rows[q] = a.cache ? Gc + (size_t)r * a.n_pad : a.G + (size_t)(r0 + r) * a.ldg;
+      rows[q] = a.cache ? s.Gc + (size_t)r * a.n_pad : a.G + (size_t)(r0 + r) * a.ldg;
       acc[q] = 0.f;
     }
     if (vecld) {
@@ -523,31 +573,27 @@ __device__ void gemv_own(const ApgdArgs& a, const float* Gc, const float* vec, i
     for (int off = 16; off; off >>= 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
-    if (lane < 4 && rb + lane < nr) {
+    // every lane holds the 4 sums: lane L pushes row L / 8 to CTAs L % 8, L % 8 + 8
+    const int q = lane >> 3;
+    if (rb + q < nr) {
       float v = acc[0];
 #pragma unroll
-      for (int q = 1; q < 4; ++q)
-        if (lane == q) v = acc[q];
-      out[rb + lane] = v;
+      for (int qq = 1; qq < 4; ++qq)
+        if (q == qq) v = acc[qq];
+      const uint32_t off = (uint32_t)(r0 + rb + q) * 4u;
+      for (int d = lane & 7; d < ex.CS; d += 8)
+        push_f32(cluster_addr(ex.rx(b) + off, d), v, cluster_addr(ex.bar(b), d));
     }
   }
-}
-
-// G vec for all n rows, in every CTA: own rows, publish, one cluster barrier,
-// gather the slices of all CTAs. Ends with the block synchronised.
-__device__ void cluster_gemv(cg::cluster_group& cl, const ApgdArgs& a, const SmemF& s, const float* vec,
-                             int r0, int nr, int& buf, float* out) {
-  float* mine = s.pub + buf * pub_stride(a);
-  gemv_own(a, s.Gc, vec, r0, nr, mine);
-  cl.sync();
-  for (int idx = threadIdx.x; idx < a.n; idx += blockDim.x) {
-    const int rr = idx / a.rows_per;
-    const int off = idx - rr * a.rows_per;
-    const float* remote = cl.map_shared_rank(mine, rr);
-    out[idx] = remote[off];
+  const bool mine = mbar_wait_cluster(ex.bar(b), (ex.phase >> b) & 1u);
+  ok = !__syncthreads_or(!mine);
+  if (ok) {
+    ex.phase ^= 1u << b;
+    ex.buf ^= 1;
+    // re-arm for this buffer's next use (two products from now)
+    if (threadIdx.x == 0) mbar_arm(ex.bar(b), (uint32_t)a.n * 4u);
   }
-  buf ^= 1;
-  __syncthreads();
+  return b ? s.rx1 : s.rx0;
 }
 
 __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
@@ -555,13 +601,30 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   __shared__ Df scratch[(APGD_THREADS / 32) * NPART];
   __shared__ Df s_part[NPART];
   __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
+  __shared__ __align__(8) uint64_t s_rxbar[2];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const SmemF s = carve_full(apgdf_sm, a);
   const int r0 = rank * a.rows_per;
   const int nr = max(0, min(a.n, r0 + a.rows_per) - r0);
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
-  int buf = 0;
+  bool ok = true;
+
+  Exchange ex;
+  ex.rx0 = (uint32_t)__cvta_generic_to_shared(s.rx0);
+  ex.rx1 = (uint32_t)__cvta_generic_to_shared(s.rx1);
+  ex.bar0 = (uint32_t)__cvta_generic_to_shared(&s_rxbar[0]);
+  ex.bar1 = (uint32_t)__cvta_generic_to_shared(&s_rxbar[1]);
+  ex.phase = 0;
+  ex.buf = 0;
+  ex.CS = (int)cl.num_blocks();
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ex.bar(b)));
+      mbar_arm(ex.bar(b), (uint32_t)n * 4u);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 
   if (a.cache) {
     for (int e = tid; e < nr * a.n_pad; e += nt) {
@@ -577,21 +640,22 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
     s.y[i] = in ? v0 : 0.f;   // v_j
     s.z[i] = 0.f;             // v_{j-1}
   }
-  __syncthreads();
+  cl.sync();   // every CTA's mbarriers are initialised and armed before any push
 
   // ---- Lipschitz constant: Lanczos (alpha = v^T G v, then beta = ||w||)
   float theta = 0.f, theta_prev = 0.f, beta_prev = 0.f;
   int m = 0;
-  for (int j = 0; j < LZ_MAX; ++j) {
-    cluster_gemv(cl, a, s, s.y, r0, nr, buf, s.Gz);           // G v_j
+  for (int j = 0; j < LZ_MAX && ok; ++j) {
+    float* Gv = cluster_gemv(a, s, s.y, r0, nr, ex, ok);       // G v_j
+    if (!ok) break;
     Df v[NPART] = {};
-    for (int i = tid; i < n; i += nt) v[0] = df_add(v[0], df_prod(s.y[i], s.Gz[i]));
+    for (int i = tid; i < n; i += nt) v[0] = df_add(v[0], df_prod(s.y[i], Gv[i]));
     block_sums(v, s_part, scratch);
     const float alpha = s_part[0].hi + s_part[0].lo;
     Df v2[NPART] = {};
     for (int i = tid; i < n; i += nt) {
-      const float w = s.Gz[i] - alpha * s.y[i] - beta_prev * s.z[i];
-      s.Gz[i] = w;
+      const float w = Gv[i] - alpha * s.y[i] - beta_prev * s.z[i];
+      Gv[i] = w;
       v2[0] = df_add(v2[0], df_prod(w, w));
     }
     block_sums(v2, s_part, scratch);
@@ -610,7 +674,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
     }
     const float inv = 1.f / beta;
     for (int i = tid; i < n; i += nt) {
-      const float vn = s.Gz[i] * inv;
+      const float vn = Gv[i] * inv;
       s.z[i] = s.y[i];
       s.y[i] = vn;
     }
@@ -622,38 +686,40 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   const float thr = a.lam * invL;
 
   // ---- initial G x and F(x)
-  cluster_gemv(cl, a, s, s.x, r0, nr, buf, s.Gx);
-  Df Fx;
-  {
-    Df v[NPART] = {};
-    for (int i = tid; i < n; i += nt) {
-      v[0] = df_add(v[0], df_prod(s.x[i], s.Gx[i]));
-      v[1] = df_add(v[1], df_prod(s.bb[i], s.x[i]));
-      v[2] = df_add(v[2], Df{fabsf(s.x[i]), 0.f});
+  Df Fx = {0.f, 0.f};
+  if (ok) {
+    const float* Gxr = cluster_gemv(a, s, s.x, r0, nr, ex, ok);
+    if (ok) {
+      Df v[NPART] = {};
+      for (int i = tid; i < n; i += nt) {
+        const float gx = Gxr[i];
+        s.Gx[i] = gx;
+        s.y[i] = s.x[i];
+        s.Gy[i] = gx;
+        v[0] = df_add(v[0], df_prod(s.x[i], gx));
+        v[1] = df_add(v[1], df_prod(s.bb[i], s.x[i]));
+        v[2] = df_add(v[2], Df{fabsf(s.x[i]), 0.f});
+      }
+      block_sums(v, s_part, scratch);
+      Fx = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
     }
-    block_sums(v, s_part, scratch);
-    Fx = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
   }
-  for (int i = tid; i < n; i += nt) {
-    s.y[i] = s.x[i];
-    s.Gy[i] = s.Gx[i];
-  }
-  __syncthreads();
 
   // ---- monotone FISTA
   float t = 1.f;
   int it = 0;
-  for (it = 1; it <= a.max_iter; ++it) {
+  for (it = 1; it <= a.max_iter && ok; ++it) {
     for (int i = tid; i < n; i += nt) {
       const float u = s.y[i] - (s.Gy[i] - s.bb[i]) * invL;
       s.z[i] = copysignf(fmaxf(fabsf(u) - thr, 0.f), u);
     }
     __syncthreads();
-    cluster_gemv(cl, a, s, s.z, r0, nr, buf, s.Gz);
+    const float* Gz = cluster_gemv(a, s, s.z, r0, nr, ex, ok);
+    if (!ok) break;
     Df v[NPART] = {};
     for (int i = tid; i < n; i += nt) {
       const float zr = s.z[i];
-      v[0] = df_add(v[0], df_prod(zr, s.Gz[i]));
+      v[0] = df_add(v[0], df_prod(zr, Gz[i]));
       v[1] = df_add(v[1], df_prod(s.bb[i], zr));
       v[2] = df_add(v[2], Df{fabsf(zr), 0.f});
       const float d = zr - s.y[i];
@@ -670,9 +736,9 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
     for (int i = tid; i < n; i += nt) {
       const float xo = s.x[i], Gxo = s.Gx[i];
       const float xn = accept ? s.z[i] : xo;
-      const float Gxn = accept ? s.Gz[i] : Gxo;
+      const float Gxn = accept ? Gz[i] : Gxo;
       s.y[i] = xn + c1 * (s.z[i] - xn) + c2 * (xn - xo);
-      s.Gy[i] = Gxn + c1 * (s.Gz[i] - Gxn) + c2 * (Gxn - Gxo);
+      s.Gy[i] = Gxn + c1 * (Gz[i] - Gxn) + c2 * (Gxn - Gxo);
       s.x[i] = xn;
       s.Gx[i] = Gxn;
     }
@@ -682,21 +748,31 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
     if (step <= a.eps * nz) break;
   }
   if (it > a.max_iter) it = a.max_iter;
-  for (int r = tid; r < nr; r += nt) a.x[r0 + r] = s.x[r0 + r];
-  if (rank == 0 && tid == 0) {
-    if (a.out_iters) *a.out_iters = it;
-    if (a.out_L) *a.out_L = (double)L;
-    if (a.out_F) *a.out_F = (double)Fx.hi + (double)Fx.lo;
-    if (a.out_lanczos) *a.out_lanczos = m;
+  if (ok) {
+    for (int r = tid; r < nr; r += nt) a.x[r0 + r] = s.x[r0 + r];
+    if (rank == 0 && tid == 0) {
+      if (a.out_iters) *a.out_iters = it;
+      if (a.out_L) *a.out_L = (double)L;
+      if (a.out_F) *a.out_F = (double)Fx.hi + (double)Fx.lo;
+      if (a.out_lanczos) *a.out_lanczos = m;
+    }
+  } else {
+    // a wait expired: report it, and give pushes still addressed to this CTA
+    // (bounded) time to land before it leaves
+    if (tid == 0) {
+      if (a.err) atomicExch(a.err, 1);
+      mbar_wait_cluster(ex.bar(ex.buf), (ex.phase >> ex.buf) & 1u);
+    }
+    __syncthreads();
   }
-  cl.sync();   // no CTA leaves while others may still read its shared memory
+  cl.sync();   // no CTA leaves while others may still address its shared memory
 }
 
 }  // namespace
 
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
              int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
-             int* lanczos) {
+             int* lanczos, int* err) {
   if (S <= 0) return PC_OK;
   static int cs_max = 0;
   static bool attrs_set = false;
@@ -716,11 +792,10 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     attrs_set = true;
   }
   const int n_pad = (S + 3) & ~3;
-  // full-vector kernel: 2 published slices + 7 full vectors (+ cached rows of G)
+  // full-vector kernel: 2 receive buffers + 6 full vectors (+ cached rows of G)
   auto bytes_full = [&](int cs, bool cached) {
     const size_t rp = (size_t)ceil_div(S, cs);
-    const size_t ps = (rp + 3) & ~size_t(3);
-    return sizeof(float) * (2 * ps + 7 * (size_t)n_pad) + (cached ? sizeof(float) * rp * n_pad : 0);
+    return sizeof(float) * (8 * (size_t)n_pad) + (cached ? sizeof(float) * rp * n_pad : 0);
   };
   // row-slice kernel (larger supports): one full vector + 8 row slices
   auto bytes_rows = [&](int cs, bool cached) {
@@ -759,6 +834,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
   a.out_L = L;
   a.out_F = Fx;
   a.out_lanczos = lanczos;
+  a.err = err;
   a.rows_per = rows_per;
   a.n_pad = n_pad;
   a.cache = cache;
@@ -786,7 +862,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     // fall back to a portable cluster size
     cudaGetLastError();
     cs_max = 8;
-    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st, lanczos);
+    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st, lanczos, err);
   }
   PC_CUDA(e);
   return PC_OK;

@@ -153,6 +153,9 @@ int launch_grid(pc_plan_s* p, const float2* h, cudaStream_t st) {
   if (p->T != GRID_T || p->Qg > 8)
     return fail(PC_ERR_INVALID_ARG, "gridding: needs 32-cell tiles and <= 8 planes per group");
   prof_scope_.kernels = 2;
+  // tensor cores for w-stacked plans (the coplanar case has one plane and
+  // would leave 7/8 of the tensor-core tile empty); iscal[7] = timeout flag
+  if (p->wstack && p->grid_mode != 1) return launch_grid_tc(p, h, p->iscal + 7, st);
   const float beta = (float)p->beta;
   const int ws = p->wstack ? 1 : 0;
 #define PC_GRID_CASE(WW)                                                                      \

@@ -147,10 +147,12 @@ int launch_compact_old(const int32_t* oldpos, int n, int32_t* rows, int32_t* cou
 // apgd.cu
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
              int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
-             int* lanczos = nullptr);
+             int* lanczos = nullptr, int* err = nullptr);
 
 // grid.cu / fft.cu
 int launch_grid(pc_plan_s* p, const float2* r, cudaStream_t st);
+// grid_tc.cu: tensor-core gridding (w-stacking plans); err_dev set to 1 if a bounded wait expired
+int launch_grid_tc(pc_plan_s* p, const float2* h, int* err_dev, cudaStream_t st);
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st);
@@ -173,6 +175,7 @@ struct pc_plan_s {
   double fov = 0, dl = 0, beta = 0;
   double w0 = 0, dw = 1, s_c = 0, w_min = 0, w_max = 0;
   bool wstack = false;
+  int grid_mode = 0;  // 0 auto, 1 CUDA cores, 2 tensor cores (w-stacking only)
   int64_t n_slots = 0;
   int n_sub = 0;
 

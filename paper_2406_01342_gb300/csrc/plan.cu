@@ -482,6 +482,7 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   PC_TRY(dev_alloc_t(p, &p->dscal, 8));
   PC_TRY(dev_alloc_t(p, &p->uscal, 8));
   PC_TRY(dev_alloc_t(p, &p->iscal, 8));
+  PC_CUDA(cudaMemsetAsync(p->iscal, 0, 8 * sizeof(int32_t), st));
   p->sel_blocks_n = ceil_div(NN, 4096);
   PC_TRY(dev_alloc_t(p, &p->sel_blocks, (size_t)p->sel_blocks_n + 1));
   PC_TRY(dev_alloc_t(p, &p->vis_fx, (size_t)std::max<int64_t>(M, 1)));
@@ -610,6 +611,9 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   if (W < 4 || W > kMaxW) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: kernel_width %d not in [4, 8]", W);
   if (T != 32) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: tile %d must be 32", T);
   if (maxP < 1 || maxP > 4096) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: max_planes %d", maxP);
+  const int grid_mode = opts ? opts->grid_mode : 0;
+  if (grid_mode < 0 || grid_mode > 2)
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: grid_mode %d not in [0, 2]", grid_mode);
 
   pc_plan_s* p = new pc_plan_s();
   cudaGetDevice(&p->device);
@@ -618,6 +622,7 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   p->fov = fov_rad;
   p->W = W;
   p->T = T;
+  p->grid_mode = grid_mode;
   int rc = build_plan(p, uvw_dev, (cudaStream_t)stream, maxP);
   if (rc != PC_OK) {
     pc_plan_destroy(p);

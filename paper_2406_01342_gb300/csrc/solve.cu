@@ -162,6 +162,19 @@ int sync_read(void* host, const void* dev, size_t bytes, cudaStream_t st) {
   return PC_OK;
 }
 
+// Synchronise the stream (after any reads the caller queued) and report an
+// expired bounded wait of the tensor-core gridding (flag iscal[7], cleared here).
+int grid_flag_sync(pc_plan_s* p, cudaStream_t st, const char* fn) {
+  int32_t flag = 0;
+  PC_CUDA(cudaMemcpyAsync(&flag, p->iscal + 7, sizeof(flag), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    PC_CUDA(cudaMemsetAsync(p->iscal + 7, 0, sizeof(int32_t), st));
+    return fail(PC_ERR_TIMEOUT, "%s: a bounded tensor-core gridding wait expired", fn);
+  }
+  return PC_OK;
+}
+
 float bits_to_float(unsigned b) {
   float f;
   std::memcpy(&f, &b, sizeof(f));
@@ -243,7 +256,8 @@ extern "C" int pc_lambda_max(pc_plan_t p, const pc_c32* V, double* out, void* st
   PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
   PC_TRY(adjoint_grid_impl(p, reinterpret_cast<const float2*>(V), p->mu, 1.0f, p->uscal, st));
   unsigned b = 0;
-  PC_TRY(sync_read(&b, p->uscal, sizeof(b), st));
+  PC_CUDA(cudaMemcpyAsync(&b, p->uscal, sizeof(b), cudaMemcpyDeviceToHost, st));
+  PC_TRY(grid_flag_sync(p, st, "pc_lambda_max"));
   const float f = bits_to_float(b);
   if (!std::isfinite(f)) return fail(PC_ERR_NUMERIC, "pc_lambda_max: non-finite dirty image");
   *out = (double)f;
@@ -275,7 +289,7 @@ extern "C" int pc_certificate(pc_plan_t p, const pc_c32* V, const int32_t* idx, 
     double ss = 0.0;
     PC_CUDA(cudaMemcpyAsync(&b, p->uscal, sizeof(b), cudaMemcpyDeviceToHost, st));
     PC_CUDA(cudaMemcpyAsync(&ss, p->dscal, sizeof(ss), cudaMemcpyDeviceToHost, st));
-    PC_CUDA(cudaStreamSynchronize(st));
+    PC_TRY(grid_flag_sync(p, st, "pc_certificate"));
     if (mu_inf_host) *mu_inf_host = (double)bits_to_float(b);
     if (sumsq_host) *sumsq_host = ss;
   }
@@ -348,16 +362,16 @@ extern "C" int pc_apgd(const float* G, int32_t ldg, const float* b, int32_t S, d
   PC_TRY(apgd_scratch(&scr));
   int* d_it = static_cast<int*>(scr);
   double* d_d = reinterpret_cast<double*>(static_cast<char*>(scr) + 16);
-  PC_TRY(run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, d_it, d_d, d_d + 1, st));
-  if (iters_host || lipschitz_host) {
-    int it = 0;
-    double L = 0.0;
-    PC_CUDA(cudaMemcpyAsync(&it, d_it, sizeof(it), cudaMemcpyDeviceToHost, st));
-    PC_CUDA(cudaMemcpyAsync(&L, d_d, sizeof(L), cudaMemcpyDeviceToHost, st));
-    PC_CUDA(cudaStreamSynchronize(st));
-    if (iters_host) *iters_host = it;
-    if (lipschitz_host) *lipschitz_host = L;
-  }
+  PC_CUDA(cudaMemsetAsync(d_it + 1, 0, sizeof(int), st));
+  PC_TRY(run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, d_it, d_d, d_d + 1, st, nullptr, d_it + 1));
+  int hi[2] = {0, 0};
+  double L = 0.0;
+  PC_CUDA(cudaMemcpyAsync(hi, d_it, sizeof(hi), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaMemcpyAsync(&L, d_d, sizeof(L), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  if (hi[1]) return fail(PC_ERR_TIMEOUT, "pc_apgd: a bounded device wait expired");
+  if (iters_host) *iters_host = hi[0];
+  if (lipschitz_host) *lipschitz_host = L;
   return PC_OK;
 }
 
@@ -479,7 +493,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
     PC_TRY(adjoint_grid_impl(p, p->resid, p->mu, inv_lam, p->uscal, st));
     unsigned mb = 0;
-    PC_TRY(sync_read(&mb, p->uscal, sizeof(mb), st));
+    PC_CUDA(cudaMemcpyAsync(&mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
+    PC_TRY(grid_flag_sync(p, st, "pc_solve"));
     mu_inf = (double)bits_to_float(mb);
     if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
     float thr;
@@ -557,7 +572,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
       int32_t* d_it = p->iscal + 2;
       PC_TRY(run_apgd(p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
-                      p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st, p->iscal + 5));
+                      p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st, p->iscal + 5,
+                      p->iscal + 4));
       // pruning
       PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
       int32_t hi[6];
@@ -565,7 +581,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
       PC_CUDA(cudaMemcpyAsync(hd, p->dscal + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
       PC_CUDA(cudaStreamSynchronize(st));
-      if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded tensor-core wait expired");
+      if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded device wait expired");
       n_sup = hi[3];
       cur.apgd_iterations = hi[2];
       cur.lanczos_steps = hi[5];
@@ -587,7 +603,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
   PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
   PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, inv_lam, p->uscal, st));
   unsigned mb = 0;
-  PC_TRY(sync_read(&mb, p->uscal, sizeof(mb), st));
+  PC_CUDA(cudaMemcpyAsync(&mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
+  PC_TRY(grid_flag_sync(p, st, "pc_solve"));
   if (stats) {
     stats->status = status;
     stats->iterations = k;

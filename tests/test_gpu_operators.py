@@ -58,10 +58,13 @@ def test_forward_sparse(abi, name, kw):
     assert rel_l2(y, ref) <= TOL
 
 
+@pytest.mark.parametrize("grid_mode", [1, 2])
 @pytest.mark.parametrize("name,kw", CASES)
-def test_adjoint_grid(abi, name, kw):
+def test_adjoint_grid(abi, name, kw, grid_mode):
+    """Gridding on FP32 CUDA cores (1) and on the tensor cores with split-FP16
+    operands (2; w-stacked plans), then FFT and epilogue, against the direct sum."""
     wl, V = workload(name, **kw)
-    plan = _plan(abi, wl)
+    plan = _plan(abi, wl, grid_mode=grid_mode)
     img = abi.pc_adjoint_grid(plan, to_dev(V.astype(np.complex64))).cpu().numpy().ravel()
     if wl.N <= 64:
         pix = np.arange(wl.N * wl.N)
@@ -162,11 +165,12 @@ def test_empty_and_degenerate(abi):
         abi.pc_plan_create(to_dev(wl.uvw), 63, wl.fov)
 
 
-def test_full_size_medium_sampled(abi):
+@pytest.mark.parametrize("grid_mode", [1, 2])
+def test_full_size_medium_sampled(abi, grid_mode):
     """The 512 x 512, M = 200k workload timed by the benchmark: operators on
     seeded samples of pixels and visibilities."""
     wl, V = workload("medium_512_w")
-    plan = _plan(abi, wl)
+    plan = _plan(abi, wl, grid_mode=grid_mode)
     Vs = V.astype(np.complex64)
     img = abi.pc_adjoint_grid(plan, to_dev(Vs)).cpu().numpy().ravel()
     rng = np.random.default_rng(8)
