@@ -544,9 +544,14 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
     PC_LAUNCH_CHECK();
   }
 
-  // ---- gridding sub-problems: (tile, plane group) ranges split into chunks
+  // ---- gridding sub-problems: the slot range of each (tile, plane group),
+  // split into equal pieces of at most kMaxSlotsPerSub slots (multiples of 64,
+  // the tensor-core stage) sized so that the pieces fill the GPU in about two
+  // even waves of two CTAs per SM -- a few long sub-problems left over for a
+  // second wave would otherwise double the gridding time.
   const int kMaxSlotsPerSub = 1024;
-  std::vector<int4> subs;
+  std::vector<int4> ranges;
+  int64_t total_slots = 0;
   const int ngroups = ceil_div(p->P, p->Qg);
   for (int t = 0; t < p->nT * p->nT; ++t) {
     for (int gq = 0; gq < ngroups; ++gq) {
@@ -558,9 +563,23 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
       }
       int s0 = hoff[(size_t)t * p->P + ps_lo];
       int s1 = hoff[(size_t)t * p->P + ps_hi + 1];
-      for (int s = s0; s < s1; s += kMaxSlotsPerSub)
-        subs.push_back(make_int4(t, gq, s, std::min(s1, s + kMaxSlotsPerSub)));
+      if (s1 > s0) {
+        ranges.push_back(make_int4(t, gq, s0, s1));
+        total_slots += s1 - s0;
+      }
     }
+  }
+  int n_sm = 152;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
+  const int64_t want = 4ll * n_sm;
+  int piece = (int)std::min<int64_t>(kMaxSlotsPerSub, std::max<int64_t>(128, (total_slots + want - 1) / want));
+  piece = ceil_div(piece, 64) * 64;
+  std::vector<int4> subs;
+  for (const int4& r : ranges) {
+    const int len = r.w - r.z;
+    const int n_pieces = ceil_div(len, piece);
+    const int sz = ceil_div(ceil_div(len, n_pieces), 64) * 64;
+    for (int s = r.z; s < r.w; s += sz) subs.push_back(make_int4(r.x, r.y, s, std::min(r.w, s + sz)));
   }
   p->n_sub = (int)subs.size();
   PC_TRY(dev_alloc_t(p, &p->subs, std::max<size_t>(subs.size(), 1)));

@@ -214,25 +214,26 @@ constexpr int THIN_SLICE = 1024;  // visibilities per CTA
 // column atom for every other visibility of a chunk; the row phases of the
 // chunk are generated once into shared memory. No tile padding: the cost is
 // one phase per (visibility, column) plus 2 FMAs per row.
+template <int R>
 __global__ void __launch_bounds__(256)
 k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
             const float4* __restrict__ atomsA, int nA, const float4* __restrict__ atomsB, int nB,
             double* __restrict__ acc, int ldacc, double* __restrict__ b64) {
-  __shared__ float sRe[THIN_RMAX][THIN_CHUNK];
-  __shared__ float sIm[THIN_RMAX][THIN_CHUNK];
+  __shared__ float sRe[R][THIN_CHUNK];
+  __shared__ float sIm[R][THIN_CHUNK];
   __shared__ int4 sVis[THIN_CHUNK];
-  __shared__ float4 sA[THIN_RMAX];
-  __shared__ float sRed[THIN_RMAX][THIN_COLS];
+  __shared__ float4 sA[R];
+  __shared__ float sRed[R][THIN_COLS];
   const int rows = nA + (V ? 1 : 0);
   const int tid = threadIdx.x, col = tid % THIN_COLS, half = tid / THIN_COLS;
   const int c_glob = blockIdx.x * THIN_COLS + col;
   const float4 bt = c_glob < nB ? atomsB[c_glob] : make_float4(0.f, 0.f, 0.f, 0.f);
-  if (tid < THIN_RMAX) sA[tid] = tid < nA ? atomsA[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid < R) sA[tid] = tid < nA ? atomsA[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
   const int64_t k_lo = (int64_t)blockIdx.y * THIN_SLICE;
   const int64_t k_hi = min(M, k_lo + THIN_SLICE);
-  float outer[THIN_RMAX];
+  float outer[R];
 #pragma unroll
-  for (int r = 0; r < THIN_RMAX; ++r) outer[r] = 0.f;
+  for (int r = 0; r < R; ++r) outer[r] = 0.f;
   for (int64_t k0 = k_lo; k0 < k_hi; k0 += THIN_CHUNK) {
     const int cnt = (int)min((int64_t)THIN_CHUNK, k_hi - k0);
     __syncthreads();
@@ -257,28 +258,28 @@ k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
       sIm[r][t] = im;
     }
     __syncthreads();
-    float inner[THIN_RMAX];
+    float inner[R];
 #pragma unroll
-    for (int r = 0; r < THIN_RMAX; ++r) inner[r] = 0.f;
+    for (int r = 0; r < R; ++r) inner[r] = 0.f;
     for (int t = half; t < cnt; t += 2) {
       float sn, cs;
       __sincosf(6.283185307179586f * phase_turns(sVis[t], bt), &sn, &cs);
       const float br = cs * bt.w, bi = sn * bt.w;
 #pragma unroll
-      for (int r = 0; r < THIN_RMAX; ++r)
+      for (int r = 0; r < R; ++r)
         if (r < rows) inner[r] = fmaf(sRe[r][t], br, fmaf(sIm[r][t], bi, inner[r]));
     }
 #pragma unroll
-    for (int r = 0; r < THIN_RMAX; ++r) outer[r] += inner[r];
+    for (int r = 0; r < R; ++r) outer[r] += inner[r];
   }
   __syncthreads();
   if (half == 1)
 #pragma unroll
-    for (int r = 0; r < THIN_RMAX; ++r) sRed[r][col] = outer[r];
+    for (int r = 0; r < R; ++r) sRed[r][col] = outer[r];
   __syncthreads();
   if (half == 0 && c_glob < nB) {
 #pragma unroll
-    for (int r = 0; r < THIN_RMAX; ++r) {
+    for (int r = 0; r < R; ++r) {
       if (r >= rows) break;
       const double v = (double)outer[r] + (double)sRed[r][col];
       if (r < nA) atomicAdd(&acc[(size_t)r * ldacc + c_glob], v);
@@ -401,7 +402,18 @@ int launch_gram_thin(const int4* vis_fx, const float2* V, int64_t M, const float
   if (nA + (V ? 1 : 0) > THIN_RMAX) return fail(PC_ERR_INVALID_ARG, "thin Gram: too many rows");
   prof_scope_.kernels = 1;
   dim3 grid(ceil_div(nB, THIN_COLS), ceil_div(M, THIN_SLICE));
-  k_gram_thin<<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  // rows padded to a power of two: the per-row loops are unrolled at that size
+  const int rows = nA + (V ? 1 : 0);
+  if (rows <= 1)
+    k_gram_thin<1><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  else if (rows <= 2)
+    k_gram_thin<2><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  else if (rows <= 4)
+    k_gram_thin<4><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  else if (rows <= 8)
+    k_gram_thin<8><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+  else
+    k_gram_thin<16><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
