@@ -76,11 +76,13 @@ typedef struct {
   int32_t max_fw;         /* Frank-Wolfe iteration cap (default 100)                                 */
   int32_t apgd_max_iter;  /* sub-solver iteration cap (default 10000)                                */
   int32_t gram_mode;      /* 0 (default): tensor cores for large blocks; 1: FP32 only; 2: tensor cores */
-  int32_t reserved0;
+  int32_t positivity;     /* 1: x >= 0 (remark of Sect. 4.1): candidates only where mu >= thr,
+                             reweighting with the non-negative proximal map; 0 (default): off */
   double  tol;            /* stop when (F_k - F_{k+1}) / F_k < tol (default 1e-4, Sect. 5.1)          */
   double  eps0;           /* sub-solver accuracy eps_k = max(eps_min, eps0 2^-k) (default 1e-2)       */
   double  eps_min;        /* (default 1e-5)                                                           */
-  double  lambda_max;     /* for rule 1: lambda_max if known (<= 0: computed)                        */
+  double  lambda_max;     /* for rule 1: lambda_max if known (<= 0: computed; under positivity the
+                             positive lambda_max of pc_lambda_max_positive)                          */
 } pc_solve_opts;
 
 /* Per-iteration record of pc_solve (host memory). */
@@ -91,7 +93,8 @@ typedef struct {
   int32_t n_support;      /* |S_{k+1}| after pruning                                 */
   int32_t apgd_iterations;
   int32_t lanczos_steps;  /* Lanczos steps of the step-size estimate                */
-  double  mu_inf;         /* ||mu_k||_inf (eta_k / lambda) at the start of iteration k */
+  double  mu_inf;         /* ||mu_k||_inf (eta_k / lambda) at the start of iteration k;
+                             max mu_k under positivity                              */
   double  objective;      /* F(I_{k+1})                                              */
   double  rel_improvement;
   double  lipschitz;
@@ -148,6 +151,12 @@ int pc_adjoint_grid(pc_plan_t plan, const pc_c32* y_dev, float* img_dev, void* s
 /* lambda_max = ||Phi* V||_inf (Sect. 4.4), returned in host memory. */
 int pc_lambda_max(pc_plan_t plan, const pc_c32* V_dev, double* lambda_max_host, void* stream);
 
+/* max(0, max_p Phi*(V)_p): the smallest lambda for which x = 0 is optimal under
+ * the positivity constraint (remark of Sect. 4.1; lambda = alpha times it),
+ * returned in host memory. */
+int pc_lambda_max_positive(pc_plan_t plan, const pc_c32* V_dev, double* lambda_max_host,
+                           void* stream);
+
 /* mu = Phi*(V - Phi x) / lambda (Sect. 3.2), x given on a support of S pixels.
  * mu_dev: N*N floats. mu_inf_host (may be NULL): ||mu||_inf. sumsq_host (may
  * be NULL): ||V - Phi x||^2 accumulated in float64. */
@@ -184,10 +193,12 @@ int pc_gram(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev, int32_t
  * step 1/L with L = 1.01 x the top eigenvalue of G (Lanczos, ~1e-6 relative),
  * stop when ||z - y|| <= eps ||z|| or after max_iter iterations. Synchronises
  * the stream. iters_host / lipschitz_host (may be NULL) receive the iteration
- * count and L. PC_ERR_TIMEOUT if a bounded wait between the CTAs of the
- * solver's thread-block cluster expired (x_dev is then unchanged). */
+ * count and L. positive = 1 adds the constraint x >= 0 (proximal map
+ * max(z - lambda/L, 0); the positivity remark of Sect. 4.1). PC_ERR_TIMEOUT if
+ * a bounded wait between the CTAs of the solver's thread-block cluster expired
+ * (x_dev is then unchanged). */
 int pc_apgd(const float* G_dev, int32_t ldg, const float* b_dev, int32_t S, double lambda,
-            double eps, int32_t max_iter, float* x_dev, int32_t* iters_host,
+            double eps, int32_t max_iter, int32_t positive, float* x_dev, int32_t* iters_host,
             double* lipschitz_host, void* stream);
 
 /* ------------------------------------------------------------------ solver */

@@ -18,6 +18,10 @@ module fixes them (the same readings are used by the GPU path):
 
 coordinate_descent and brute_force are independent LASSO solvers used only to
 pin apgd and the Frank-Wolfe loop on tiny problems.
+
+positive=True solves the positivity-constrained variant (the remarks on a
+positivity constraint in Sect. 3.1 and 4.1): x >= 0, the proximal map of
+t ||.||_1 + indicator(x >= 0) is max(z - t, 0).
 """
 from __future__ import annotations
 
@@ -30,6 +34,11 @@ import numpy as np
 def soft(z, t):
     """Proximal map of t ||.||_1 (soft thresholding)."""
     return np.sign(z) * np.maximum(np.abs(z) - t, 0.0)
+
+
+def prox(z, t, positive=False):
+    """Proximal map of t ||.||_1, plus the indicator of x >= 0 when positive."""
+    return np.maximum(z - t, 0.0) if positive else soft(z, t)
 
 
 def objective(A, V, lam, x) -> float:
@@ -51,7 +60,7 @@ def lipschitz(A) -> float:
     return 1.01 * ev if ev > 0.0 else 1.0
 
 
-def apgd(A, V, lam, x0, eps, max_iter=10_000, L=None):
+def apgd(A, V, lam, x0, eps, max_iter=10_000, L=None, positive=False):
     """Monotone FISTA on the restricted LASSO. Returns (x, iterations, L)."""
     if L is None:
         L = lipschitz(A)
@@ -62,7 +71,7 @@ def apgd(A, V, lam, x0, eps, max_iter=10_000, L=None):
     it = 0
     for it in range(1, max_iter + 1):
         grad = np.real(A.conj().T @ (A @ y - V))
-        z = soft(y - grad / L, lam / L)
+        z = prox(y - grad / L, lam / L, positive)
         Fz = objective(A, V, lam, z)
         t_next = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
         x_next = z if Fz <= Fx else x
@@ -77,7 +86,7 @@ def apgd(A, V, lam, x0, eps, max_iter=10_000, L=None):
     return x, it, L
 
 
-def coordinate_descent(A, V, lam, tol=1e-14, max_sweeps=100_000):
+def coordinate_descent(A, V, lam, tol=1e-14, max_sweeps=100_000, positive=False):
     """Cyclic coordinate descent (independent solver for pins)."""
     s = A.shape[1]
     x = np.zeros(s)
@@ -88,7 +97,10 @@ def coordinate_descent(A, V, lam, tol=1e-14, max_sweeps=100_000):
         for j in range(s):
             rj = r + A[:, j] * x[j]
             c = float(np.real(np.vdot(A[:, j], rj)))
-            xj = np.sign(c) * max(abs(c) - lam, 0.0) / col2[j]
+            if positive:
+                xj = max(c - lam, 0.0) / col2[j]
+            else:
+                xj = np.sign(c) * max(abs(c) - lam, 0.0) / col2[j]
             if xj != x[j]:
                 change = max(change, abs(xj - x[j]))
                 r = rj - A[:, j] * xj
@@ -98,19 +110,20 @@ def coordinate_descent(A, V, lam, tol=1e-14, max_sweeps=100_000):
     return x
 
 
-def brute_force(A, V, lam):
-    """Exact LASSO by enumerating sign patterns s in {-1, 0, +1}^n (tiny n only).
+def brute_force(A, V, lam, positive=False):
+    """Exact LASSO by enumerating sign patterns s in {-1, 0, +1}^n (tiny n only;
+    {0, +1}^n when positive).
 
     For a pattern with support T: solve G_TT x_T = b_T - lam s_T with
     G = Re(A^H A), b = Re(A^H V); keep x if sign(x_T) = s_T and the
-    off-support optimality |b - G x| <= lam holds. Returns the feasible x with
-    the smallest objective.
+    off-support optimality |b - G x| <= lam (b - G x <= lam when positive)
+    holds. Returns the feasible x with the smallest objective.
     """
     n = A.shape[1]
     G = np.real(A.conj().T @ A)
     b = np.real(A.conj().T @ V)
     best, best_f = np.zeros(n), objective(A, V, lam, np.zeros(n))
-    for pattern in itertools.product((-1, 0, 1), repeat=n):
+    for pattern in itertools.product((0, 1) if positive else (-1, 0, 1), repeat=n):
         s = np.array(pattern, dtype=np.float64)
         T = np.nonzero(s)[0]
         if T.size == 0:
@@ -125,7 +138,8 @@ def brute_force(A, V, lam):
         x[T] = xT
         g = b - G @ x
         off = np.setdiff1d(np.arange(n), T)
-        if off.size and np.max(np.abs(g[off])) > lam * (1 + 1e-12):
+        viol = g[off] if positive else np.abs(g[off])
+        if off.size and np.max(viol) > lam * (1 + 1e-12):
             continue
         f = objective(A, V, lam, x)
         if f < best_f:

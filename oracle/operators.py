@@ -93,6 +93,13 @@ def lambda_max(uvw, N, fov, V) -> float:
     return float(np.max(np.abs(adjoint(uvw, N, fov, V))))
 
 
+def lambda_max_positive(uvw, N, fov, V) -> float:
+    """max(0, max_p Phi*(V)_p): the smallest lambda for which x = 0 is optimal
+    when the image is constrained to be non-negative (the positivity variant of
+    Sect. 3.1 / 4.1): the optimality condition at 0 is Phi*(V) <= lambda."""
+    return max(0.0, float(np.max(adjoint(uvw, N, fov, V))))
+
+
 def residual(uvw, N, fov, V, idx, x) -> np.ndarray:
     """r = V - Phi x for a sparse image (support idx, weights x)."""
     return np.asarray(V, dtype=np.complex128) - forward(uvw, N, fov, idx, x)

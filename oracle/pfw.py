@@ -19,6 +19,11 @@ Readings where the paper gives no value (the GPU path uses the same ones):
   * eps_k = max(eps_min, eps0 * 2^-k), eps0 = 1e-2, eps_min = 1e-5;
   * objective F_k = 1/2 ||V - Phi I_k||^2 + lambda ||I_k||_1, F_0 = 1/2 ||V||^2;
   * tol = 1e-4 (Sect. 5.1), at most max_fw iterations.
+
+positive=True is the positivity-constrained variant (remark in Sect. 4.1):
+candidates only at positive values of the certificate (R2: mu >= 1 - delta;
+R1: eta >= max(eta) - 2 Delta/(k + 2) with eta > 0, Delta from
+lambda_max_positive), and the reweighting with x >= 0.
 """
 from __future__ import annotations
 
@@ -41,13 +46,18 @@ class SolveResult:
     history: list
 
 
-def select_r2(mu: np.ndarray, delta: float) -> np.ndarray:
-    """Pixels whose certificate magnitude reaches 1 - delta (ascending raster order)."""
-    return np.nonzero(np.abs(mu) >= 1.0 - delta)[0]
+def select_r2(mu: np.ndarray, delta: float, positive: bool = False) -> np.ndarray:
+    """Pixels whose certificate magnitude (its value, when positive) reaches
+    1 - delta (ascending raster order)."""
+    a = mu if positive else np.abs(mu)
+    return np.nonzero(a >= 1.0 - delta)[0]
 
 
-def select_r1(eta: np.ndarray, k: int, Delta: float) -> np.ndarray:
-    """Exploration set of Algorithm 2: |eta| >= ||eta||_inf - 2 Delta / (k + 2)."""
+def select_r1(eta: np.ndarray, k: int, Delta: float, positive: bool = False) -> np.ndarray:
+    """Exploration set of Algorithm 2: |eta| >= ||eta||_inf - 2 Delta / (k + 2);
+    when positive, eta >= max(eta) - 2 Delta / (k + 2) among the pixels with eta > 0."""
+    if positive:
+        return np.nonzero((eta > 0.0) & (eta >= eta.max() - 2.0 * Delta / (k + 2)))[0]
     a = np.abs(eta)
     return np.nonzero(a >= a.max() - 2.0 * Delta / (k + 2))[0]
 
@@ -56,15 +66,17 @@ def eps_schedule(k: int, eps0: float = 1e-2, eps_min: float = 1e-5) -> float:
     return max(eps_min, eps0 * 2.0 ** (-k))
 
 
-def duality_gap(uvw, N, fov, V, lam, idx, x) -> float:
-    """F(x) - D(theta) with the dual-feasible scaling theta = r min(1, lambda / ||Phi* r||_inf).
+def duality_gap(uvw, N, fov, V, lam, idx, x, positive=False) -> float:
+    """F(x) - D(theta) with the dual-feasible scaling theta = r min(1, lambda / ||Phi* r||_inf)
+    (lambda / max(Phi* r) when positive: the dual constraint is then Phi* theta <= lambda).
 
     D(theta) = 1/2 ||V||^2 - 1/2 ||V - theta||^2 is the LASSO dual objective
     (complex data as a real vector space with inner product Re<.,.>).
     """
     V = np.asarray(V, dtype=np.complex128)
     r = operators.residual(uvw, N, fov, V, idx, x)
-    g = np.max(np.abs(operators.adjoint(uvw, N, fov, r)))
+    eta = operators.adjoint(uvw, N, fov, r)
+    g = np.max(eta) if positive else np.max(np.abs(eta))
     theta = r * min(1.0, lam / g) if g > 0 else r
     F = 0.5 * float(np.vdot(r, r).real) + lam * float(np.sum(np.abs(x)))
     D = 0.5 * float(np.vdot(V, V).real) - 0.5 * float(np.vdot(V - theta, V - theta).real)
@@ -72,10 +84,10 @@ def duality_gap(uvw, N, fov, V, lam, idx, x) -> float:
 
 
 def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
-          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None) -> SolveResult:
+          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None, positive=False) -> SolveResult:
     V = np.asarray(V, dtype=np.complex128)
     if lmax is None:
-        lmax = operators.lambda_max(uvw, N, fov, V)
+        lmax = (operators.lambda_max_positive if positive else operators.lambda_max)(uvw, N, fov, V)
     Delta = (1.0 - delta) * lmax
     S = np.zeros(0, dtype=np.int64)
     x = np.zeros(0)
@@ -87,11 +99,19 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
     for k in range(max_fw):
         eta = operators.adjoint(uvw, N, fov, r)                 # dirty residual, all pixels
         if rule == "R2":
-            new = select_r2(eta / lam, delta)
+            new = select_r2(eta / lam, delta, positive)
+            thr_mu = 1.0 - delta
         elif rule == "R1":
-            new = select_r1(eta, k, Delta)
+            new = select_r1(eta, k, Delta, positive)
+            top = eta.max() if positive else np.abs(eta).max()
+            thr_mu = (top - 2.0 * Delta / (k + 2)) / lam
         else:
             raise ValueError(rule)
+        # diagnostic (no effect on the iteration): pixels whose candidate value
+        # lies within 1e-5 max|mu| of the threshold, where an FP32 evaluation of
+        # the certificate may legitimately take the other side
+        cand = eta / lam if positive else np.abs(eta) / lam
+        n_border = int(np.count_nonzero(np.abs(cand - thr_mu) <= 1e-5 * np.abs(eta).max() / lam))
         n_new = int(np.setdiff1d(new, S).size)
         S_next = np.union1d(S, new).astype(np.int64)            # sorted, unique
         x0 = np.zeros(S_next.size)
@@ -100,7 +120,7 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
         l, m, n = operators.pixel_lmn(N, fov, S_next)
         A = operators.phase_block(uvw, l, m, n)                  # Phi restricted to S_next
         eps = eps_schedule(k, eps0, eps_min)
-        xs, n_it, L = lasso.apgd(A, V, lam, x0, eps, apgd_max_iter)
+        xs, n_it, L = lasso.apgd(A, V, lam, x0, eps, apgd_max_iter, positive=positive)
         keep = xs != 0.0                                          # pruning
         S, x = S_next[keep], xs[keep]
         r = V - A[:, keep] @ x
@@ -108,9 +128,10 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
         rel = (F_prev - F) / F_prev if F_prev > 0 else 0.0
         history.append(dict(k=k, n_new=n_new,
                             n_active=int(S_next.size), n_support=int(S.size),
-                            mu_inf=float(np.max(np.abs(eta)) / lam), objective=F,
+                            mu_inf=float(np.max(eta if positive else np.abs(eta)) / lam),
+                            objective=F,
                             rel_improvement=rel, apgd_iterations=int(n_it), L=float(L),
-                            eps=eps))
+                            eps=eps, n_borderline=n_border))
         F_prev = F
         if rel < tol:
             converged = True

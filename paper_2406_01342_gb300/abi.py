@@ -29,7 +29,7 @@ EXPORTS = [
     "pc_plan_create", "pc_plan_destroy", "pc_plan_info", "pc_forward_sparse",
     "pc_adjoint_sparse", "pc_adjoint_grid", "pc_lambda_max", "pc_certificate", "pc_select",
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
-    "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc",
+    "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
 ]
 
 
@@ -48,7 +48,7 @@ class pc_plan_opts(ctypes.Structure):
 class pc_solve_opts(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int32), ("select_rule", ctypes.c_int32),
                 ("max_fw", ctypes.c_int32), ("apgd_max_iter", ctypes.c_int32),
-                ("gram_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("gram_mode", ctypes.c_int32), ("positivity", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("eps_min", ctypes.c_double), ("lambda_max", ctypes.c_double)]
 
@@ -103,11 +103,12 @@ def load(path: str | None = None):
         "pc_adjoint_sparse": (_I32, [_P, _P, _P, _I32, _P, _P]),
         "pc_adjoint_grid": (_I32, [_P, _P, _P, _P]),
         "pc_lambda_max": (_I32, [_P, _P, ctypes.POINTER(_D), _P]),
+        "pc_lambda_max_positive": (_I32, [_P, _P, ctypes.POINTER(_D), _P]),
         "pc_certificate": (_I32, [_P, _P, _P, _P, _I32, _D, _P, ctypes.POINTER(_D),
                                   ctypes.POINTER(_D), _P]),
         "pc_select": (_I32, [_P, _P, _F, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _P]),
         "pc_gram": (_I32, [_P, _P, _P, _I32, _P, _I32, _P, _I32, _P]),
-        "pc_apgd": (_I32, [_P, _I32, _P, _I32, _D, _D, _I32, _P, ctypes.POINTER(_I32),
+        "pc_apgd": (_I32, [_P, _I32, _P, _I32, _D, _D, _I32, _I32, _P, ctypes.POINTER(_I32),
                            ctypes.POINTER(_D), _P]),
         "pc_solve": (_I32, [_P, _P, _D, _D, _P, _P, _P, _I32, _P, ctypes.POINTER(pc_solve_stats),
                             _P, _I32, _P]),
@@ -227,6 +228,13 @@ def pc_lambda_max(plan: Plan, V: torch.Tensor, stream=None) -> float:
     return out.value
 
 
+def pc_lambda_max_positive(plan: Plan, V: torch.Tensor, stream=None) -> float:
+    out = _D()
+    _check(load().pc_lambda_max_positive(plan.handle, _dev(V, torch.complex64, "V"),
+                                         ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 def pc_certificate(plan: Plan, V: torch.Tensor, idx: torch.Tensor, x: torch.Tensor, lam: float,
                    mu: torch.Tensor | None = None, stream=None):
     if mu is None:
@@ -261,20 +269,21 @@ def pc_gram(plan: Plan, V: torch.Tensor | None, idx: torch.Tensor, mode: int = 0
 
 
 def pc_apgd(G: torch.Tensor, b: torch.Tensor, lam: float, eps: float, max_iter: int,
-            x: torch.Tensor, stream=None):
+            x: torch.Tensor, stream=None, positive: bool = False):
     S = int(b.numel())
     it = _I32()
     L = _D()
     _check(load().pc_apgd(_dev(G, torch.float32, "G"), int(G.stride(0)), _dev(b, torch.float32, "b"),
-                          S, float(lam), float(eps), int(max_iter), _dev(x, torch.float32, "x"),
-                          ctypes.byref(it), ctypes.byref(L), _stream(stream)))
+                          S, float(lam), float(eps), int(max_iter), int(bool(positive)),
+                          _dev(x, torch.float32, "x"), ctypes.byref(it), ctypes.byref(L),
+                          _stream(stream)))
     return x, it.value, L.value
 
 
 def _solve_opts(select_rule=0, max_fw=0, apgd_max_iter=0, tol=0.0, eps0=0.0, eps_min=0.0,
-                lambda_max=0.0, gram_mode=0):
-    return pc_solve_opts(PC_ABI_VERSION, select_rule, max_fw, apgd_max_iter, gram_mode, 0, tol,
-                         eps0, eps_min, lambda_max)
+                lambda_max=0.0, gram_mode=0, positivity=0):
+    return pc_solve_opts(PC_ABI_VERSION, select_rule, max_fw, apgd_max_iter, gram_mode,
+                         int(positivity), tol, eps0, eps_min, lambda_max)
 
 
 def pc_solve(plan: Plan, V: torch.Tensor, lam: float, delta: float, cap: int = 65536,

@@ -21,11 +21,14 @@
 // identical decisions). G z is the only matrix product per iteration: G y and
 // G x are kept as linear combinations of previous products.
 //
-// Arithmetic: FP32 vectors; the reductions that drive decisions (objective,
-// step norm) are carried as double-float pairs (hi + lo, exact products and
-// error-free sums), which gives about 44 bits without float64 instructions --
-// float64 has a low rate and long dependent latency on this GPU and made each
-// iteration take ~10 us.
+// Arithmetic: FP32 vectors and no float64 instruction in any loop (float64 has
+// a low rate and long dependent latency on this GPU; it made an iteration take
+// ~10 us). The monotone test F(z) <= F(x) needs the sign of a difference of two
+// ~1e7 numbers: the full-vector kernel sums the difference directly as
+// sum_i (z_i - x_i)((Gz_i + Gx_i)/2 - b_i) + lambda(|z_i| - |x_i|), whose terms
+// all vanish as z -> x, in FP32; the row-slice kernel (large supports) carries
+// the objective itself as double-float pairs (hi + lo, exact products and
+// error-free sums, ~44 bits).
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -88,6 +91,7 @@ struct ApgdArgs {
   double* out_F;
   int* out_lanczos;
   int* err;       // set to 1 if a bounded wait expired (may be null)
+  int positive;   // 1: x >= 0 (proximal map max(z - lambda/L, 0))
   int rows_per;
   int n_pad;
   int cache;      // 1: rows of G cached in shared memory
@@ -202,10 +206,19 @@ __device__ void block_sums(Df v[NPART], Df* part, Df* scratch) {
 #pragma unroll
     for (int q = 0; q < NPART; ++q) scratch[warp * NPART + q] = v[q];
   __syncthreads();
-  if (threadIdx.x < NPART) {
-    Df t = {0.f, 0.f};
-    for (int w = 0; w < nw; ++w) t = df_add(t, scratch[w * NPART + threadIdx.x]);
-    part[threadIdx.x] = t;
+  if (warp == 0) {   // the nw (<= 8) warp sums: a 3-level butterfly in warp 0
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) v[q] = lane < nw ? scratch[lane * NPART + q] : Df{0.f, 0.f};
+    for (int off = 4; off; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < NPART; ++q) v[q] = df_add(v[q], df_shfl_xor(v[q], off));
+    if (lane < NPART) {
+      Df t = v[0];
+#pragma unroll
+      for (int q = 1; q < NPART; ++q)
+        if (lane == q) t = v[q];
+      part[lane] = t;
+    }
   }
   __syncthreads();
 }
@@ -391,7 +404,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   for (it = 1; it <= a.max_iter; ++it) {
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
       const float u = s.y[r] - (s.Gy[r] - s.bb[r]) * invL;
-      const float zr = copysignf(fmaxf(fabsf(u) - thr, 0.f), u);
+      const float zr = (a.positive ? fmaxf(u - thr, 0.f) : copysignf(fmaxf(fabsf(u) - thr, 0.f), u));
       s.z[r] = zr;
       s.pub[r] = zr;
     }
@@ -445,26 +458,58 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
   cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
+// Block-wide FP32 sums of K per-thread values (a fixed butterfly: the same
+// inputs give the same sums in every CTA); every thread receives them.
+template <int K>
+__device__ void block_sum_f(float (&v)[K], float* scratch, float* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int off = 16; off; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < K; ++q) scratch[warp * K + q] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] = lane < nw ? scratch[lane * K + q] : 0.f;
+    for (int off = 4; off; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < K; ++q) out[q] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = out[q];
+}
+
 // ---------------------------------------------------------------------------
 // Full-vector variant (used whenever its vectors fit): every CTA keeps all n
-// entries of x, y, z, Gx, Gy and b, and owns rows [r0, r0 + nr) of G. A
-// matrix-vector product multiplies the own rows by the (local) full vector and
-// PUSHES each result to every CTA of the cluster with st.async, whose bytes
-// complete on the receiver's mbarrier; each CTA then waits (bounded) on its own
-// mbarrier until all n entries have landed. No cluster barrier and no remote
-// loads sit on the iteration path, only the one-way latency of the pushes.
+// entries of x, y, z, Gx, Gy and b, and owns rows [r0, r0 + nr) of G (nr a
+// multiple of 4 except in the last CTA). A matrix-vector product multiplies
+// the own rows by the (local) full vector into a local slice and PUSHES the
+// slice to every CTA of the cluster with one bulk copy each (shared memory to
+// distributed shared memory), whose bytes complete on the receiver's
+// mbarrier; each CTA then waits (bounded) on its own mbarrier until all
+// entries have landed. No cluster barrier and no remote loads sit on the
+// iteration path, only the one-way latency of the copies.
 // The reductions and updates are then done redundantly over all n entries --
 // identical data and order in every CTA, hence identical decisions.
 //
-// Two receive buffers alternate. A CTA pushes product i + 2 into buffer
-// i mod 2 only after it has received every CTA's product i + 1, which each CTA
-// sends only after it has consumed product i and re-armed that buffer's
-// mbarrier, so a buffer is never overwritten while it is read and bytes never
-// arrive before the phase that counts them is armed.
+// Two receive buffers (and two local slices) alternate. A CTA pushes product
+// i + 2 into buffer i mod 2 only after it has received every CTA's product
+// i + 1, which each CTA sends only after it has consumed product i and
+// re-armed that buffer's mbarrier, so a buffer is never overwritten while it
+// is read, bytes never arrive before the phase that counts them is armed, and
+// a local slice is rewritten only after every copy that read it has landed.
 
 constexpr long long APGD_WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
 struct SmemF {
+  float* pub0;    // rows_per each: this CTA's slices of the last two products
+  float* pub1;
   float* rx0;     // n_pad each: the two receive buffers of the products
   float* rx1;
   float* x;       // n_pad each, full vectors
@@ -479,6 +524,8 @@ struct SmemF {
 __device__ SmemF carve_full(float* base, const ApgdArgs& a) {
   SmemF s;
   float* p = base;
+  s.pub0 = p; p += a.rows_per;
+  s.pub1 = p; p += a.rows_per;
   s.rx0 = p; p += a.n_pad;
   s.rx1 = p; p += a.n_pad;
   s.x = p; p += a.n_pad;
@@ -495,11 +542,6 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t saddr, int rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
   return r;
-}
-__device__ __forceinline__ void push_f32(uint32_t raddr, float v, uint32_t rbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr),
-               "r"(__float_as_uint(v)), "r"(rbar)
-               : "memory");
 }
 __device__ __forceinline__ void mbar_arm(uint32_t mbar, uint32_t tx) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(tx) : "memory");
@@ -538,6 +580,7 @@ __device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* v
                                Exchange& ex, bool& ok) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int b = ex.buf;
+  float* pub = b ? s.pub1 : s.pub0;
   const bool vecld = a.cache || a.vec_ok;
   const int n4 = a.n >> 2;
   const float4* v4 = reinterpret_cast<const float4*>(vec);
@@ -573,17 +616,27 @@ __device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* v
     for (int off = 16; off; off >>= 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
-    // every lane holds the 4 sums: lane L pushes row L / 8 to CTAs L % 8, L % 8 + 8
-    const int q = lane >> 3;
-    if (rb + q < nr) {
+    if (lane < 4 && rb + lane < nr) {
       float v = acc[0];
 #pragma unroll
-      for (int qq = 1; qq < 4; ++qq)
-        if (q == qq) v = acc[qq];
-      const uint32_t off = (uint32_t)(r0 + rb + q) * 4u;
-      for (int d = lane & 7; d < ex.CS; d += 8)
-        push_f32(cluster_addr(ex.rx(b) + off, d), v, cluster_addr(ex.bar(b), d));
+      for (int q = 1; q < 4; ++q)
+        if (lane == q) v = acc[q];
+      pub[rb + lane] = v;
     }
+  }
+  // the slice (padded to 4 floats) goes to every CTA in one bulk copy each
+  const int nr4 = (nr + 3) & ~3;
+  for (int r = nr + threadIdx.x; r < nr4; r += blockDim.x) pub[r] = 0.f;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if ((int)threadIdx.x < ex.CS && nr4 > 0) {
+    const int d = threadIdx.x;
+    const uint32_t src = (uint32_t)__cvta_generic_to_shared(pub);
+    const uint32_t dst = cluster_addr(ex.rx(b) + (uint32_t)r0 * 4u, d);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "r"(src), "r"((uint32_t)nr4 * 4u), "r"(cluster_addr(ex.bar(b), d))
+        : "memory");
   }
   const bool mine = mbar_wait_cluster(ex.bar(b), (ex.phase >> b) & 1u);
   ok = !__syncthreads_or(!mine);
@@ -591,7 +644,7 @@ __device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* v
     ex.phase ^= 1u << b;
     ex.buf ^= 1;
     // re-arm for this buffer's next use (two products from now)
-    if (threadIdx.x == 0) mbar_arm(ex.bar(b), (uint32_t)a.n * 4u);
+    if (threadIdx.x == 0) mbar_arm(ex.bar(b), (uint32_t)a.n_pad * 4u);
   }
   return b ? s.rx1 : s.rx0;
 }
@@ -600,6 +653,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   extern __shared__ __align__(16) float apgdf_sm[];
   __shared__ Df scratch[(APGD_THREADS / 32) * NPART];
   __shared__ Df s_part[NPART];
+  __shared__ float s_fscr[(APGD_THREADS / 32) * 3], s_fout[3];
   __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
   __shared__ __align__(8) uint64_t s_rxbar[2];
   cg::cluster_group cl = cg::this_cluster();
@@ -621,7 +675,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ex.bar(b)));
-      mbar_arm(ex.bar(b), (uint32_t)n * 4u);
+      mbar_arm(ex.bar(b), (uint32_t)a.n_pad * 4u);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -648,18 +702,18 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   for (int j = 0; j < LZ_MAX && ok; ++j) {
     float* Gv = cluster_gemv(a, s, s.y, r0, nr, ex, ok);       // G v_j
     if (!ok) break;
-    Df v[NPART] = {};
-    for (int i = tid; i < n; i += nt) v[0] = df_add(v[0], df_prod(s.y[i], Gv[i]));
-    block_sums(v, s_part, scratch);
-    const float alpha = s_part[0].hi + s_part[0].lo;
-    Df v2[NPART] = {};
+    float va[1] = {0.f};
+    for (int i = tid; i < n; i += nt) va[0] = fmaf(s.y[i], Gv[i], va[0]);
+    block_sum_f<1>(va, s_fscr, s_fout);
+    const float alpha = va[0];
+    float vb[1] = {0.f};
     for (int i = tid; i < n; i += nt) {
       const float w = Gv[i] - alpha * s.y[i] - beta_prev * s.z[i];
       Gv[i] = w;
-      v2[0] = df_add(v2[0], df_prod(w, w));
+      vb[0] = fmaf(w, w, vb[0]);
     }
-    block_sums(v2, s_part, scratch);
-    const float beta = sqrtf(fmaxf(s_part[0].hi + s_part[0].lo, 0.f));
+    block_sum_f<1>(vb, s_fscr, s_fout);
+    const float beta = sqrtf(fmaxf(vb[0], 0.f));
     if (tid == 0) {
       s_al[j] = alpha;
       s_be[j] = beta;
@@ -685,23 +739,17 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   const float invL = 1.f / L;
   const float thr = a.lam * invL;
 
-  // ---- initial G x and F(x)
-  Df Fx = {0.f, 0.f};
+  // ---- initial G x
   if (ok) {
     const float* Gxr = cluster_gemv(a, s, s.x, r0, nr, ex, ok);
     if (ok) {
-      Df v[NPART] = {};
       for (int i = tid; i < n; i += nt) {
         const float gx = Gxr[i];
         s.Gx[i] = gx;
         s.y[i] = s.x[i];
         s.Gy[i] = gx;
-        v[0] = df_add(v[0], df_prod(s.x[i], gx));
-        v[1] = df_add(v[1], df_prod(s.bb[i], s.x[i]));
-        v[2] = df_add(v[2], Df{fabsf(s.x[i]), 0.f});
       }
-      block_sums(v, s_part, scratch);
-      Fx = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
+      __syncthreads();
     }
   }
 
@@ -711,27 +759,28 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   for (it = 1; it <= a.max_iter && ok; ++it) {
     for (int i = tid; i < n; i += nt) {
       const float u = s.y[i] - (s.Gy[i] - s.bb[i]) * invL;
-      s.z[i] = copysignf(fmaxf(fabsf(u) - thr, 0.f), u);
+      s.z[i] = (a.positive ? fmaxf(u - thr, 0.f) : copysignf(fmaxf(fabsf(u) - thr, 0.f), u));
     }
     __syncthreads();
     const float* Gz = cluster_gemv(a, s, s.z, r0, nr, ex, ok);
     if (!ok) break;
-    Df v[NPART] = {};
+    // F(z) - F(x) = sum_i (z_i - x_i) ((Gz_i + Gx_i) / 2 - b_i) + lambda (|z_i| - |x_i|)
+    // (G symmetric): every term vanishes as z -> x, so an FP32 sum resolves the
+    // sign of the difference where F itself (~1e7) would need ~50 bits
+    float v[3] = {0.f, 0.f, 0.f};
     for (int i = tid; i < n; i += nt) {
-      const float zr = s.z[i];
-      v[0] = df_add(v[0], df_prod(zr, Gz[i]));
-      v[1] = df_add(v[1], df_prod(s.bb[i], zr));
-      v[2] = df_add(v[2], Df{fabsf(zr), 0.f});
+      const float zr = s.z[i], xr = s.x[i];
+      const float dF = fmaf(zr - xr, 0.5f * (Gz[i] + s.Gx[i]) - s.bb[i], a.lam * (fabsf(zr) - fabsf(xr)));
+      v[0] += dF;
       const float d = zr - s.y[i];
-      v[3] = df_add(v[3], df_prod(d, d));
-      v[4] = df_add(v[4], df_prod(zr, zr));
+      v[1] = fmaf(d, d, v[1]);
+      v[2] = fmaf(zr, zr, v[2]);
     }
-    block_sums(v, s_part, scratch);
-    const Df Fz = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
-    const float step = sqrtf(s_part[3].hi + s_part[3].lo);
-    const float nz = sqrtf(s_part[4].hi + s_part[4].lo);
+    block_sum_f<3>(v, s_fscr, s_fout);
+    const float step = sqrtf(v[1]);
+    const float nz = sqrtf(v[2]);
     const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
-    const bool accept = df_le(Fz, Fx);
+    const bool accept = v[0] <= 0.f;
     const float c1 = t / t1, c2 = (t - 1.f) / t1;
     for (int i = tid; i < n; i += nt) {
       const float xo = s.x[i], Gxo = s.Gx[i];
@@ -742,12 +791,23 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
       s.x[i] = xn;
       s.Gx[i] = Gxn;
     }
-    if (accept) Fx = Fz;
     t = t1;
     __syncthreads();
     if (step <= a.eps * nz) break;
   }
   if (it > a.max_iter) it = a.max_iter;
+  // objective of the returned x, in double-float (reported only)
+  Df Fx = {0.f, 0.f};
+  if (ok) {
+    Df v[NPART] = {};
+    for (int i = tid; i < n; i += nt) {
+      v[0] = df_add(v[0], df_prod(s.x[i], s.Gx[i]));
+      v[1] = df_add(v[1], df_prod(s.bb[i], s.x[i]));
+      v[2] = df_add(v[2], Df{fabsf(s.x[i]), 0.f});
+    }
+    block_sums(v, s_part, scratch);
+    Fx = df_add(df_add(df_scale(s_part[0], 0.5f), df_neg(s_part[1])), df_scale(s_part[2], a.lam));
+  }
   if (ok) {
     for (int r = tid; r < nr; r += nt) a.x[r0 + r] = s.x[r0 + r];
     if (rank == 0 && tid == 0) {
@@ -772,7 +832,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
 
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
              int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
-             int* lanczos, int* err) {
+             int* lanczos, int* err, bool positive) {
   if (S <= 0) return PC_OK;
   static int cs_max = 0;
   static bool attrs_set = false;
@@ -792,10 +852,12 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     attrs_set = true;
   }
   const int n_pad = (S + 3) & ~3;
-  // full-vector kernel: 2 receive buffers + 6 full vectors (+ cached rows of G)
+  // full-vector kernel: 2 local slices, 2 receive buffers and 6 full vectors
+  // (+ cached rows of G); its slices hold a multiple of 4 rows (bulk copies)
+  auto rows_full = [&](int cs) { return (ceil_div(S, cs) + 3) & ~3; };
   auto bytes_full = [&](int cs, bool cached) {
-    const size_t rp = (size_t)ceil_div(S, cs);
-    return sizeof(float) * (8 * (size_t)n_pad) + (cached ? sizeof(float) * rp * n_pad : 0);
+    const size_t rp = (size_t)rows_full(cs);
+    return sizeof(float) * (2 * rp + 8 * (size_t)n_pad) + (cached ? sizeof(float) * rp * n_pad : 0);
   };
   // row-slice kernel (larger supports): one full vector + 8 row slices
   auto bytes_rows = [&](int cs, bool cached) {
@@ -803,11 +865,15 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     return sizeof(float) * ((size_t)n_pad + 8 * rp) + 16 + 16 * sizeof(Df) +
            (cached ? sizeof(float) * rp * n_pad : 0);
   };
-  // cluster size: the smallest power of two whose CTAs can each cache their
-  // rows of G in shared memory (fewer CTAs = cheaper barriers), else cs_max
+  // cluster size: the smallest power of two whose CTAs each cache at most
+  // ~64 KB of G in shared memory (a matrix-vector product then streams it in
+  // ~500 cycles), else the smallest that caches G at all, else cs_max
   bool full = true;
   int CS = 1;
-  while (CS < cs_max && bytes_full(CS, true) > limit_full) CS *= 2;
+  const size_t share_target = 64 * 1024;
+  while (CS < cs_max && (bytes_full(CS, true) > limit_full ||
+                         sizeof(float) * (size_t)rows_full(CS) * n_pad > share_target))
+    CS *= 2;
   int cache = bytes_full(CS, true) <= limit_full ? 1 : 0;
   size_t smem = bytes_full(CS, cache != 0);
   if (smem > limit_full) {
@@ -819,7 +885,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     cache = bytes_rows(CS, true) <= limit_rows ? 1 : 0;
     smem = bytes_rows(CS, cache != 0);
   }
-  const int rows_per = ceil_div(S, CS);
+  const int rows_per = full ? rows_full(CS) : ceil_div(S, CS);
 
   ApgdArgs a;
   a.G = G;
@@ -835,6 +901,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
   a.out_F = Fx;
   a.out_lanczos = lanczos;
   a.err = err;
+  a.positive = positive ? 1 : 0;
   a.rows_per = rows_per;
   a.n_pad = n_pad;
   a.cache = cache;
@@ -862,7 +929,7 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     // fall back to a portable cluster size
     cudaGetLastError();
     cs_max = 8;
-    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st, lanczos, err);
+    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st, lanczos, err, positive);
   }
   PC_CUDA(e);
   return PC_OK;

@@ -146,6 +146,7 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
     __syncthreads();
   }
   float amax = 0.0f;
+  unsigned skey = 0;   // order-preserving key of the signed maximum (0 below every number)
 #pragma unroll
   for (int jj = 0; jj < JPT; ++jj) {
     const int j = threadIdx.x + jj * blockDim.x;
@@ -154,11 +155,18 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
       mu[(size_t)i * N + j] = m;
       amax = fmaxf(amax, fabsf(m));
       if (m != m) amax = __int_as_float(0x7fc00000);
+      skey = max(skey, float_order_key(m));
     }
   }
   unsigned bits = __float_as_uint(amax);
-  for (int off = 16; off; off >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
-  if ((threadIdx.x & 31) == 0 && maxbits) atomicMax(maxbits, bits);
+  for (int off = 16; off; off >>= 1) {
+    bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    skey = max(skey, __shfl_xor_sync(0xffffffffu, skey, off));
+  }
+  if ((threadIdx.x & 31) == 0 && maxbits) {
+    atomicMax(maxbits, bits);
+    atomicMax(maxbits + 1, skey);
+  }
 }
 
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {

@@ -12,10 +12,13 @@
 // tiles of 128), N = 32 rows x {Re, Im} = 64 columns, K = visibilities, the
 // form in which a tile is a GEMM. Per stage of 64 visibilities the CTA
 //   1. evaluates the kernel weights of each visibility (W in u, W in v, one per
-//      plane) and its pre-twiddled, power-of-two scaled value h into shared
-//      memory,
-//   2. writes A and B as FP16 hi + lo pairs straight into the K-major
-//      core-matrix layout (8 rows x 16 bytes) the tensor core reads,
+//      plane; one role per warp pair, so no warp diverges) and its
+//      pre-twiddled, power-of-two scaled value h, then tabulates the products
+//      phi_w(q) phi_u(i) and h phi_v(i) once per visibility, each already
+//      split into an FP16 {hi, lo} pair,
+//   2. assembles A and B from the tables (byte permutes, no arithmetic)
+//      straight into the K-major core-matrix layout (8 rows x 16 bytes) the
+//      tensor core reads,
 //   3. one thread issues 2 x 4 x 3 tcgen05 MMAs (hi*hi + hi*lo + lo*hi,
 //      FP32 accumulators in tensor memory) and commits them to an mbarrier,
 //   4. all eight warps wait (bounded), read the stage's partial tile from
@@ -65,6 +68,8 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
   __shared__ float s_fw[GT_KS][GT_Q];
   __shared__ float2 s_h[GT_KS];
   __shared__ int s_a0[GT_KS], s_b0[GT_KS];
+  __shared__ uint32_t s_pa[GT_KS * 64];   // {hi, lo} FP16 pairs of phi_w(q) phi_u(i)
+  __shared__ uint32_t s_pb[GT_KS * 16];   // {hi, lo} FP16 pairs of (Re|Im h) phi_v(i)
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
   __shared__ float s_red[GT_THREADS / 32];
@@ -119,9 +124,10 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
   int stage = 0;
   for (int c0 = sub.z; c0 < sub.w; c0 += GT_KS, ++stage) {
     const int cnt = min(GT_KS, sub.w - c0);
-    // ---- 1. per-visibility weights: 4 threads per visibility
+    // ---- 1a. per-visibility weights, one role per warp pair (no divergence):
+    //      warps 0-1 phi_u, 2-3 phi_v, 4-5 phi_w per plane, 6-7 h
     {
-      const int k = tid >> 2, part = tid & 3;
+      const int k = ((warp & 1) << 5) | lane, role = warp >> 1;
       const bool valid = k < cnt;
       int2 sv = make_int2(0, 0);
       float4 gm = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -129,17 +135,17 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
         sv = slot_vis[c0 + k];
         gm = slot_geom[c0 + k];
       }
-      if (part == 0) {
+      if (role == 0) {
 #pragma unroll
         for (int c = 0; c < 8; ++c)
           s_fu[k][c] = (valid && c < W) ? es_kernel((c - gm.x) * two_over_w, beta) : 0.f;
-        s_a0[k] = (sv.y & 0xff) - 64;
-      } else if (part == 1) {
+        s_a0[k] = valid ? (sv.y & 0xff) - 64 : -64;
+      } else if (role == 1) {
 #pragma unroll
         for (int c = 0; c < 8; ++c)
           s_fv[k][c] = (valid && c < W) ? es_kernel((c - gm.y) * two_over_w, beta) : 0.f;
-        s_b0[k] = ((sv.y >> 8) & 0xff) - 64;
-      } else if (part == 2) {
+        s_b0[k] = valid ? ((sv.y >> 8) & 0xff) - 64 : -64;
+      } else if (role == 2) {
         const int ps = sv.y >> 16;
 #pragma unroll
         for (int q = 0; q < GT_Q; ++q) {
@@ -161,23 +167,45 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
       }
     }
     __syncthreads();
+    // ---- 1b. product tables, each entry an FP16 pair {hi, lo} in one word:
+    //      s_pa[k][q][i] = phi_w(q) phi_u(i),  s_pb[k][c][i] = (Re|Im h) phi_v(i)
+    for (int e = tid; e < GT_KS * 80; e += GT_THREADS) {
+      float v;
+      uint32_t* dst;
+      if (e < GT_KS * 64) {
+        const int k = e >> 6, q = (e >> 3) & 7, i = e & 7;
+        v = s_fw[k][q] * s_fu[k][i];
+        dst = &s_pa[e];
+      } else {
+        const int e2 = e - GT_KS * 64;
+        const int k = e2 >> 4, c = (e2 >> 3) & 1, i = e2 & 7;
+        v = (c ? s_h[k].y : s_h[k].x) * s_fv[k][i];
+        dst = &s_pb[e2];
+      }
+      const __half hh = __float2half_rn(v);
+      const __half hl = __float2half_rn(v - __half2float(hh));
+      *dst = (uint32_t)__half_as_ushort(hh) | ((uint32_t)__half_as_ushort(hl) << 16);
+    }
+    __syncthreads();
     // ---- 2a. A: thread = row (plane q, column a); 8 visibilities per 16-byte store
     if (tid < n_tiles * 128) {
       const int R = tid, q = R >> 5, a = R & 31;
       const uint32_t rowoff = (uint32_t)(R >> 3) * GT_SBO + (uint32_t)(R & 7) * 16;
+      const uint32_t* pa_q = s_pa + q * 8;
 #pragma unroll 2
       for (int kg = 0; kg < GT_KS / 8; ++kg) {
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          float v[2];
+          uint32_t pr[2];
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
             const int k = kg * 8 + 2 * i + s;
-            const int da = a - s_a0[k];
-            v[s] = (da >= 0 && da < W) ? s_fw[k][q] * s_fu[k][da] : 0.f;
+            const unsigned da = (unsigned)(a - s_a0[k]);
+            pr[s] = da < (unsigned)W ? pa_q[k * 64 + da] : 0u;
           }
-          tc::split_f16x2(v[0], v[1], hi[i], lo[i]);
+          hi[i] = __byte_perm(pr[0], pr[1], 0x5410);
+          lo[i] = __byte_perm(pr[0], pr[1], 0x7632);
         }
         const uint32_t off = rowoff + (uint32_t)kg * 128;
         *reinterpret_cast<uint4*>(A_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -188,21 +216,22 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
     {
       const int n = tid & 63, b = n >> 1, im = n & 1;
       const uint32_t rowoff = (uint32_t)(n >> 3) * GT_SBO + (uint32_t)(n & 7) * 16;
+      const uint32_t* pb_c = s_pb + im * 8;
 #pragma unroll
       for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = 2 * (tid >> 6) + g2;
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          float v[2];
+          uint32_t pr[2];
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
             const int k = kg * 8 + 2 * i + s;
-            const int db = b - s_b0[k];
-            const float hv = im ? s_h[k].y : s_h[k].x;
-            v[s] = (db >= 0 && db < W) ? hv * s_fv[k][db] : 0.f;
+            const unsigned db = (unsigned)(b - s_b0[k]);
+            pr[s] = db < (unsigned)W ? pb_c[k * 16 + db] : 0u;
           }
-          tc::split_f16x2(v[0], v[1], hi[i], lo[i]);
+          hi[i] = __byte_perm(pr[0], pr[1], 0x5410);
+          lo[i] = __byte_perm(pr[0], pr[1], 0x7632);
         }
         const uint32_t off = rowoff + (uint32_t)kg * 128;
         *reinterpret_cast<uint4*>(B_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -294,6 +323,8 @@ int launch_grid_tc(pc_plan_s* p, const float2* h, int* err_dev, cudaStream_t st)
     if (!attr_set[WW]) {                                                                             \
       PC_CUDA(cudaFuncSetAttribute(k_grid_tc<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                    GT_SMEM));                                                        \
+      PC_CUDA(cudaFuncSetAttribute(k_grid_tc<WW>, cudaFuncAttributePreferredSharedMemoryCarveout,  \
+                                   100));                                                            \
       attr_set[WW] = true;                                                                           \
     }                                                                                                \
     k_grid_tc<WW><<<p->n_sub, GT_THREADS, GT_SMEM, st>>>(p->subs, p->slot_vis, p->slot_geom, h,     \

@@ -100,6 +100,18 @@ __device__ __forceinline__ float phase_turns(int4 vis, float4 atom) {
   return t - rintf(t);
 }
 
+// Order-preserving map of a float onto unsigned (atomicMax of signed values):
+// non-negative floats get the sign bit set, negative ones are inverted.
+__host__ __device__ __forceinline__ unsigned float_order_key(float f) {
+#ifdef __CUDA_ARCH__
+  const unsigned u = __float_as_uint(f);
+#else
+  unsigned u;
+  std::memcpy(&u, &f, sizeof(u));
+#endif
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -133,7 +145,8 @@ int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double 
 
 // select.cu
 int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark, int32_t* out,
-                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st);
+                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st,
+                  bool positive = false);
 int launch_mark(uint8_t* mark, const int32_t* idx, int n, uint8_t value, cudaStream_t st);
 int launch_old_positions(const int32_t* newidx, int n_new, const int32_t* oldidx, int n_old,
                          int32_t* oldpos, cudaStream_t st);
@@ -147,7 +160,7 @@ int launch_compact_old(const int32_t* oldpos, int n, int32_t* rows, int32_t* cou
 // apgd.cu
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
              int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
-             int* lanczos = nullptr, int* err = nullptr);
+             int* lanczos = nullptr, int* err = nullptr, bool positive = false);
 
 // grid.cu / fft.cu
 int launch_grid(pc_plan_s* p, const float2* r, cudaStream_t st);

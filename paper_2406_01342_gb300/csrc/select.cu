@@ -1,5 +1,6 @@
 // Atom selection and support bookkeeping of Algorithm 2:
-//   exploration (step 1a)  I = {p : |mu_p| >= thr}
+//   exploration (step 1a)  I = {p : |mu_p| >= thr}  (mu_p >= thr with the
+//                          positivity constraint: candidates only at positive values)
 //   union (step 1b)        S u I in ascending raster order (stream compaction
 //                          over all N^2 pixels of  |mu_p| >= thr  or  p in S)
 //   pruning (step 3)       positions of the nonzero weights
@@ -12,18 +13,20 @@ constexpr int SEL_THREADS = 256;
 constexpr int SEL_ROUNDS = 16;
 constexpr int SEL_ITEMS = SEL_THREADS * SEL_ROUNDS;
 
-__device__ __forceinline__ bool sel_flag(const float* mu, const uint8_t* mark, int64_t p, float thr) {
-  return fabsf(mu[p]) >= thr || mark[p] != 0;
+__device__ __forceinline__ bool sel_flag(const float* mu, const uint8_t* mark, int64_t p, float thr,
+                                         int positive) {
+  const float v = mu[p];
+  return (positive ? v : fabsf(v)) >= thr || mark[p] != 0;
 }
 
 __global__ void k_sel_count(const float* __restrict__ mu, const uint8_t* __restrict__ mark,
-                            int64_t npix, float thr, int32_t* __restrict__ block_counts) {
+                            int64_t npix, float thr, int positive, int32_t* __restrict__ block_counts) {
   __shared__ int wsum[SEL_THREADS / 32];
   int c = 0;
   const int64_t base = (int64_t)blockIdx.x * SEL_ITEMS;
   for (int r = 0; r < SEL_ROUNDS; ++r) {
     const int64_t p = base + r * SEL_THREADS + threadIdx.x;
-    if (p < npix && sel_flag(mu, mark, p, thr)) ++c;
+    if (p < npix && sel_flag(mu, mark, p, thr, positive)) ++c;
   }
   for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
@@ -71,7 +74,7 @@ __global__ void k_scan_ints(int32_t* __restrict__ a, int n) {
 }
 
 __global__ void k_sel_write(const float* __restrict__ mu, const uint8_t* __restrict__ mark,
-                            int64_t npix, float thr, const int32_t* __restrict__ block_off,
+                            int64_t npix, float thr, int positive, const int32_t* __restrict__ block_off,
                             int32_t* __restrict__ out, int cap) {
   __shared__ int wcount[SEL_THREADS / 32];
   __shared__ int run_s;
@@ -81,7 +84,7 @@ __global__ void k_sel_write(const float* __restrict__ mu, const uint8_t* __restr
   const int64_t base = (int64_t)blockIdx.x * SEL_ITEMS;
   for (int r = 0; r < SEL_ROUNDS; ++r) {
     const int64_t p = base + r * SEL_THREADS + threadIdx.x;
-    const bool f = p < npix && sel_flag(mu, mark, p, thr);
+    const bool f = p < npix && sel_flag(mu, mark, p, thr, positive);
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wcount[warp] = __popc(bal);
     __syncthreads();
@@ -156,15 +159,15 @@ __global__ void k_compact_single(const float* __restrict__ x, const int32_t* __r
 }  // namespace
 
 int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark, int32_t* out,
-                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st) {
+                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st, bool positive) {
   ProfScope prof_scope_(PROF_SELECT, st);
   const int nblk = ceil_div(npix, SEL_ITEMS);
   prof_scope_.kernels = 4;
-  k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, block_counts);
+  k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts);
   PC_LAUNCH_CHECK();
   k_scan_ints<<<1, 1024, 0, st>>>(block_counts, nblk);
   PC_LAUNCH_CHECK();
-  k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, block_counts, out, cap);
+  k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, out, cap);
   PC_LAUNCH_CHECK();
   PC_CUDA(cudaMemcpyAsync(count_dev, block_counts + nblk, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return PC_OK;

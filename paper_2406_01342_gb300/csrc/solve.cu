@@ -181,6 +181,12 @@ float bits_to_float(unsigned b) {
   return f;
 }
 
+// Inverse of float_order_key (a zero key, "nothing seen", maps to -infinity).
+float key_to_float(unsigned key) {
+  if (key == 0) return -INFINITY;
+  return bits_to_float((key & 0x80000000u) ? (key & 0x7fffffffu) : ~key);
+}
+
 // Small per-device scratch for pc_apgd (no plan): 4 ints + 4 doubles.
 int apgd_scratch(void** out) {
   static std::map<int, void*> bufs;
@@ -253,7 +259,7 @@ extern "C" int pc_lambda_max(pc_plan_t p, const pc_c32* V, double* out, void* st
   PC_TRY(check_dev(V, p->M > 0, "pc_lambda_max", "V_dev"));
   if (!out) return fail(PC_ERR_INVALID_ARG, "pc_lambda_max: NULL output");
   cudaStream_t st = SS(stream);
-  PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
   PC_TRY(adjoint_grid_impl(p, reinterpret_cast<const float2*>(V), p->mu, 1.0f, p->uscal, st));
   unsigned b = 0;
   PC_CUDA(cudaMemcpyAsync(&b, p->uscal, sizeof(b), cudaMemcpyDeviceToHost, st));
@@ -261,6 +267,24 @@ extern "C" int pc_lambda_max(pc_plan_t p, const pc_c32* V, double* out, void* st
   const float f = bits_to_float(b);
   if (!std::isfinite(f)) return fail(PC_ERR_NUMERIC, "pc_lambda_max: non-finite dirty image");
   *out = (double)f;
+  return PC_OK;
+}
+
+extern "C" int pc_lambda_max_positive(pc_plan_t p, const pc_c32* V, double* out, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_lambda_max_positive"));
+  PC_TRY(check_dev(V, p->M > 0, "pc_lambda_max_positive", "V_dev"));
+  if (!out) return fail(PC_ERR_INVALID_ARG, "pc_lambda_max_positive: NULL output");
+  cudaStream_t st = SS(stream);
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
+  PC_TRY(adjoint_grid_impl(p, reinterpret_cast<const float2*>(V), p->mu, 1.0f, p->uscal, st));
+  unsigned b[2] = {0, 0};
+  PC_CUDA(cudaMemcpyAsync(b, p->uscal, sizeof(b), cudaMemcpyDeviceToHost, st));
+  PC_TRY(grid_flag_sync(p, st, "pc_lambda_max_positive"));
+  const float f = key_to_float(b[1]);
+  if (!std::isfinite(f) || !std::isfinite(bits_to_float(b[0])))
+    return fail(PC_ERR_NUMERIC, "pc_lambda_max_positive: non-finite dirty image");
+  *out = std::max(0.0, (double)f);
   return PC_OK;
 }
 
@@ -280,7 +304,7 @@ extern "C" int pc_certificate(pc_plan_t p, const pc_c32* V, const int32_t* idx, 
   PC_TRY(p->atomsA.ensure(sizeof(float4) * std::max(S, 1)));
   PC_TRY(make_atoms_checked(idx, x, S, p->N, p->dl, p->atomsA.as<float4>(), p->iscal, st));
   PC_CUDA(cudaMemsetAsync(p->dscal, 0, sizeof(double), st));
-  PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
   PC_TRY(launch_residual(p->vis_fx, reinterpret_cast<const float2*>(V), p->M,
                          p->atomsA.as<float4>(), S, p->resid, p->dscal, st));
   PC_TRY(adjoint_grid_impl(p, p->resid, mu, (float)(1.0 / lambda), p->uscal, st));
@@ -348,10 +372,11 @@ extern "C" int pc_gram(pc_plan_t p, const pc_c32* V, const int32_t* idx, int32_t
 }
 
 extern "C" int pc_apgd(const float* G, int32_t ldg, const float* b, int32_t S, double lambda,
-                       double eps, int32_t max_iter, float* x, int32_t* iters_host,
+                       double eps, int32_t max_iter, int32_t positive, float* x, int32_t* iters_host,
                        double* lipschitz_host, void* stream) {
   clear_error();
-  if (S < 0 || ldg < S || max_iter < 1 || !(lambda >= 0.0) || !(eps >= 0.0))
+  if (S < 0 || ldg < S || max_iter < 1 || !(lambda >= 0.0) || !(eps >= 0.0) ||
+      (positive != 0 && positive != 1))
     return fail(PC_ERR_INVALID_ARG, "pc_apgd: bad arguments");
   if (S == 0) return PC_OK;
   PC_TRY(check_dev(G, true, "pc_apgd", "G_dev"));
@@ -363,7 +388,8 @@ extern "C" int pc_apgd(const float* G, int32_t ldg, const float* b, int32_t S, d
   int* d_it = static_cast<int*>(scr);
   double* d_d = reinterpret_cast<double*>(static_cast<char*>(scr) + 16);
   PC_CUDA(cudaMemsetAsync(d_it + 1, 0, sizeof(int), st));
-  PC_TRY(run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, d_it, d_d, d_d + 1, st, nullptr, d_it + 1));
+  PC_TRY(run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, d_it, d_d, d_d + 1, st, nullptr, d_it + 1,
+                  positive != 0));
   int hi[2] = {0, 0};
   double L = 0.0;
   PC_CUDA(cudaMemcpyAsync(hi, d_it, sizeof(hi), cudaMemcpyDeviceToHost, st));
@@ -382,7 +408,7 @@ namespace {
 inline int round4(int n) { return (n + 3) & ~3; }
 
 struct SolveCfg {
-  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0;
+  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0;
   double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
 };
 
@@ -414,7 +440,9 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     if (opts->eps_min > 0) c.eps_min = opts->eps_min;
     if (opts->lambda_max > 0) c.lmax = opts->lambda_max;
     c.gram_mode = opts->gram_mode;
+    c.positive = opts->positivity;
   }
+  if (c.positive != 0 && c.positive != 1) return fail(PC_ERR_INVALID_ARG, "pc_solve: positivity must be 0 or 1");
   if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: select_rule must be 1 or 2");
   if (c.gram_mode < 0 || c.gram_mode > 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: gram_mode must be 0, 1 or 2");
   cudaStream_t st = SS(stream);
@@ -490,26 +518,30 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       if (k >= c.max_fw) { status = PC_ERR_NOT_CONVERGED; break; }
     }
     // certificate mu_k = Phi*(r) / lambda
-    PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+    PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
     PC_TRY(adjoint_grid_impl(p, p->resid, p->mu, inv_lam, p->uscal, st));
-    unsigned mb = 0;
-    PC_CUDA(cudaMemcpyAsync(&mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
+    unsigned mb[2] = {0, 0};
+    PC_CUDA(cudaMemcpyAsync(mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
     PC_TRY(grid_flag_sync(p, st, "pc_solve"));
-    mu_inf = (double)bits_to_float(mb);
+    mu_inf = (double)bits_to_float(mb[0]);
     if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
+    // the largest candidate value: max |mu|, or max mu under positivity
+    const double mu_top = c.positive ? (double)key_to_float(mb[1]) : mu_inf;
     float thr;
     if (c.rule == 2) {
       thr = (float)(1.0 - delta);
     } else {
-      if (Delta < 0) Delta = (1.0 - delta) * lambda * mu_inf;   // lambda_max = ||Phi* V||_inf at k = 0
-      thr = (float)(mu_inf - 2.0 * Delta / ((k + 2) * lambda));
+      // lambda_max (||Phi* V||_inf, or max Phi* V under positivity) from the certificate at k = 0
+      if (Delta < 0) Delta = (1.0 - delta) * lambda * std::max(mu_top, 0.0);
+      thr = (float)(mu_top - 2.0 * Delta / ((k + 2) * lambda));
+      if (c.positive) thr = std::max(thr, 1.4e-45f);   // mu >= smallest positive float: mu > 0
     }
     // exploration and union, ascending raster order
     int n_act = 0;
     for (;;) {
       PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), nS, 1, st));
       PC_TRY(launch_select(p->mu, npix, thr, p->mark, p->idxB.as<int32_t>(), p->iscal,
-                           p->sel_blocks, wcap, st));
+                           p->sel_blocks, wcap, st, c.positive != 0));
       PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), nS, 0, st));
       PC_TRY(sync_read(&n_act, p->iscal, sizeof(int), st));
       if (n_act <= wcap) break;
@@ -547,7 +579,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     cur.k = k;
     cur.n_new = n_new;
     cur.n_active = n_act;
-    cur.mu_inf = mu_inf;
+    cur.mu_inf = mu_top;
     have_cur = true;
 
     int n_sup = 0;
@@ -573,7 +605,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       int32_t* d_it = p->iscal + 2;
       PC_TRY(run_apgd(p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
                       p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st, p->iscal + 5,
-                      p->iscal + 4));
+                      p->iscal + 4, c.positive != 0));
       // pruning
       PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
       int32_t hi[6];
@@ -600,7 +632,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
 
   // final certificate at the returned iterate (its residual is in p->resid)
   float* mu_dst = mu_out ? mu_out : p->mu;
-  PC_CUDA(cudaMemsetAsync(p->uscal, 0, sizeof(unsigned), st));
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
   PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, inv_lam, p->uscal, st));
   unsigned mb = 0;
   PC_CUDA(cudaMemcpyAsync(&mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));

@@ -20,20 +20,24 @@ def abi():
     return _abi
 
 
-def _compare(abi, wl, V, lam, delta, rule="R2", **opts):
+def _compare(abi, wl, V, lam, delta, rule="R2", positive=False, **opts):
     Vs = V.astype(np.complex64).astype(np.complex128)
-    ref = pfw.solve(wl.uvw, wl.N, wl.fov, Vs, lam, delta, rule=rule)
+    ref = pfw.solve(wl.uvw, wl.N, wl.fov, Vs, lam, delta, rule=rule, positive=positive)
     plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
     res = abi.pc_solve(plan, to_dev(V.astype(np.complex64)), lam, delta,
-                       select_rule=1 if rule == "R1" else 2, **opts)
+                       select_rule=1 if rule == "R1" else 2, positivity=int(positive), **opts)
     idx = res["idx"].cpu().numpy()
     x = res["x"].cpu().numpy().astype(np.float64)
     assert idx.tolist() == ref.idx.tolist(), (idx, ref.idx)
     assert abs(res["objective"] - ref.objective) <= 1e-4 * ref.objective
     assert res["converged"] and ref.converged
-    # per-iteration active sets follow the oracle's
-    assert [h["n_active"] for h in res["history"]] == [h["n_active"] for h in ref.history]
-    assert [h["n_support"] for h in res["history"]] == [h["n_support"] for h in ref.history]
+    # per-iteration active sets follow the oracle's, up to the pixels whose
+    # certificate lies within the FP32 operator error (1e-5 max|mu|) of the
+    # selection threshold (the oracle counts them)
+    assert len(res["history"]) == len(ref.history)
+    for g, o in zip(res["history"], ref.history):
+        assert abs(g["n_active"] - o["n_active"]) <= o["n_borderline"], (g, o)
+        assert abs(g["n_support"] - o["n_support"]) <= o["n_borderline"], (g, o)
     # the final certificate is the certificate of the returned image
     mu_ref = operators.certificate(wl.uvw, wl.N, wl.fov, Vs, lam, idx, x)
     assert rel_l2(res["mu"].cpu().numpy().ravel(), mu_ref) <= 1e-5
@@ -113,3 +117,59 @@ def test_tensor_core_and_fp32_gram_give_the_same_solve(abi):
     assert a["idx"].cpu().numpy().tolist() == b["idx"].cpu().numpy().tolist()
     assert abs(a["objective"] - b["objective"]) <= 1e-6 * a["objective"]
     assert a["converged"] and b["converged"]
+
+
+# ---------------------------------------------------------------- positivity (remark of Sect. 4.1)
+
+def _signed_workload(name):
+    """The workload with its brightest source made negative (so the constraint binds)."""
+    from oracle import operators as ops
+    wl, _ = workload(name)
+    flux = wl.sky_flux.copy()
+    flux[int(np.argmax(flux))] *= -1.0
+    V = ops.forward(wl.uvw, wl.N, wl.fov, wl.sky_idx, flux) + wl.noise
+    return wl, V
+
+
+@pytest.mark.parametrize("name,frac", [("tiny_64_coplanar", None), ("small_wide_w", 0.05)])
+def test_solve_positivity(abi, name, frac):
+    """Non-negative solve: candidates only at positive certificate values, the
+    reweighting with x >= 0; same support, objective and certificate as the
+    oracle's positive solve; every weight positive."""
+    wl, V = _signed_workload(name)
+    Vs = V.astype(np.complex64).astype(np.complex128)
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    lmax_pos = abi.pc_lambda_max_positive(plan, to_dev(V.astype(np.complex64)))
+    ref_lmax = operators.lambda_max_positive(wl.uvw, wl.N, wl.fov, Vs)
+    assert abs(lmax_pos - ref_lmax) <= 1e-5 * ref_lmax
+    assert ref_lmax < operators.lambda_max(wl.uvw, wl.N, wl.fov, Vs)
+    lam = (frac if frac else wl.alpha) * ref_lmax
+    res, ref = _compare(abi, wl, V, lam, wl.delta, positive=True)
+    assert (res["x"].cpu().numpy() > 0).all() and (ref.x > 0).all()
+
+
+def test_solve_positivity_rule_r1(abi):
+    wl, V = _signed_workload("tiny_64_coplanar")
+    Vs = V.astype(np.complex64).astype(np.complex128)
+    lam = wl.alpha * operators.lambda_max_positive(wl.uvw, wl.N, wl.fov, Vs)
+    _compare(abi, wl, V, lam, 0.9, rule="R1", positive=True)
+
+
+def test_apgd_positive_matches_oracle_subsolver(abi):
+    wl, V = _signed_workload("small_wide_w")
+    Vs = V.astype(np.complex64).astype(np.complex128)
+    lam = 0.05 * operators.lambda_max_positive(wl.uvw, wl.N, wl.fov, Vs)
+    idx = np.sort(np.random.default_rng(9).choice(wl.N * wl.N, 60, replace=False))
+    idx = np.union1d(idx, wl.sky_idx)
+    l, m, n = operators.pixel_lmn(wl.N, wl.fov, idx)
+    A = operators.phase_block(wl.uvw, l, m, n)
+    G = np.real(A.conj().T @ A).astype(np.float32)
+    b = np.real(A.conj().T @ Vs).astype(np.float32)
+    x_ref, it_ref, L_ref = lasso.apgd(A, Vs, lam, np.zeros(idx.size), 1e-7, 50_000, positive=True)
+    x = torch.zeros(idx.size, dtype=torch.float32, device="cuda")
+    x, it, L = abi.pc_apgd(to_dev(G), to_dev(b), lam, 1e-7, 50_000, x, positive=True)
+    xg = x.cpu().numpy()
+    assert (xg >= 0).all()
+    assert abs(L - L_ref) <= 1e-4 * L_ref
+    assert rel_l2(xg, x_ref) <= 1e-3
+    assert set(np.nonzero(xg)[0]) == set(np.nonzero(x_ref)[0])
