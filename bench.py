@@ -165,6 +165,30 @@ def flush_l2(buf):
 
 # ------------------------------------------------------------------ roofline
 
+def recorded_traffic(kernel_class: str):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary
+    (`traffic-record:` lines under profiles/), valid only while the kernel
+    sources still hash to the profiled ones; otherwise None."""
+    import glob
+    import hashlib
+    for md in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(md):
+            if not line.startswith("traffic-record:"):
+                continue
+            f = dict(kv.split("=", 1) for kv in line.split()[1:])
+            if f.get("class") != kernel_class:
+                continue
+            ok = True
+            for item in f.get("sources", "").split(","):
+                name, want = item.split(":")
+                path = os.path.join(ROOT, "paper_2406_01342_gb300", "csrc", name)
+                have = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] if os.path.exists(path) else ""
+                ok = ok and have == want
+            if ok:
+                return float(f["bytes_per_launch"])
+    return None
+
+
 def gram_entries(n_new: int, n_act: int) -> float:
     """Distinct entries of the Gram rows of the new atoms plus their b entries."""
     return n_new * (n_act + 1) - n_new * (n_new - 1) / 2.0
@@ -233,7 +257,7 @@ def roofline(prof, info, wl, history, steps, peaks):
         out["frac"] = out["achieved"] / out["peak"]
     else:
         out["frac"] = None
-    out["traffic"] = None
+    out["traffic"] = recorded_traffic(dom)
     return out
 
 

@@ -119,10 +119,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 // ------------------------------------------------------------------ kernels (host launchers)
 
 // sparse.cu
+// S_dev (optional): the count is read on the device, S is its upper bound
 int launch_make_atoms(const int32_t* idx, const float* x, int S, int N, double dl, float4* atoms,
-                      cudaStream_t st);
+                      cudaStream_t st, const int32_t* S_dev = nullptr);
 int launch_residual(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int S,
-                    float2* out, double* sumsq, cudaStream_t st);
+                    float2* out, double* sumsq, cudaStream_t st, const int32_t* S_dev = nullptr);
 int launch_gram(const int4* vis_fx, const float2* V, int64_t M, const float4* atomsA, int nA,
                 const float4* atomsB, int nB, bool with_v, double* acc, int ldacc,
                 cudaStream_t st, bool clear = true);
@@ -144,10 +145,13 @@ int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double 
                        float4* atoms, int* dflag, cudaStream_t st);
 
 // select.cu
+// thr_dev (optional): the threshold is read on the device
 int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark, int32_t* out,
                   int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st,
-                  bool positive = false);
-int launch_mark(uint8_t* mark, const int32_t* idx, int n, uint8_t value, cudaStream_t st);
+                  bool positive = false, const float* thr_dev = nullptr);
+// n_dev (optional): the count is read on the device, n is its upper bound
+int launch_mark(uint8_t* mark, const int32_t* idx, int n, uint8_t value, cudaStream_t st,
+                const int32_t* n_dev = nullptr);
 int launch_old_positions(const int32_t* newidx, int n_new, const int32_t* oldidx, int n_old,
                          int32_t* oldpos, cudaStream_t st);
 int launch_compact_nonzero(const float* x, int n, int32_t* keep, int32_t* count_dev,

@@ -20,8 +20,10 @@ __device__ __forceinline__ bool sel_flag(const float* mu, const uint8_t* mark, i
 }
 
 __global__ void k_sel_count(const float* __restrict__ mu, const uint8_t* __restrict__ mark,
-                            int64_t npix, float thr, int positive, int32_t* __restrict__ block_counts) {
+                            int64_t npix, float thr, int positive, int32_t* __restrict__ block_counts,
+                            const float* __restrict__ thr_dev) {
   __shared__ int wsum[SEL_THREADS / 32];
+  if (thr_dev) thr = *thr_dev;
   int c = 0;
   const int64_t base = (int64_t)blockIdx.x * SEL_ITEMS;
   for (int r = 0; r < SEL_ROUNDS; ++r) {
@@ -75,9 +77,10 @@ __global__ void k_scan_ints(int32_t* __restrict__ a, int n) {
 
 __global__ void k_sel_write(const float* __restrict__ mu, const uint8_t* __restrict__ mark,
                             int64_t npix, float thr, int positive, const int32_t* __restrict__ block_off,
-                            int32_t* __restrict__ out, int cap) {
+                            int32_t* __restrict__ out, int cap, const float* __restrict__ thr_dev) {
   __shared__ int wcount[SEL_THREADS / 32];
   __shared__ int run_s;
+  if (thr_dev) thr = *thr_dev;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) run_s = block_off[blockIdx.x];
   __syncthreads();
@@ -105,8 +108,9 @@ __global__ void k_sel_write(const float* __restrict__ mu, const uint8_t* __restr
 }
 
 __global__ void k_mark(uint8_t* __restrict__ mark, const int32_t* __restrict__ idx, int n,
-                       uint8_t value) {
+                       uint8_t value, const int32_t* __restrict__ n_dev) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_dev) n = min(n, *n_dev);
   if (s < n) mark[idx[s]] = value;
 }
 
@@ -159,25 +163,28 @@ __global__ void k_compact_single(const float* __restrict__ x, const int32_t* __r
 }  // namespace
 
 int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark, int32_t* out,
-                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st, bool positive) {
+                  int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st, bool positive,
+                  const float* thr_dev) {
   ProfScope prof_scope_(PROF_SELECT, st);
   const int nblk = ceil_div(npix, SEL_ITEMS);
   prof_scope_.kernels = 4;
-  k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts);
+  k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, thr_dev);
   PC_LAUNCH_CHECK();
   k_scan_ints<<<1, 1024, 0, st>>>(block_counts, nblk);
   PC_LAUNCH_CHECK();
-  k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, out, cap);
+  k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, out, cap,
+                                             thr_dev);
   PC_LAUNCH_CHECK();
   PC_CUDA(cudaMemcpyAsync(count_dev, block_counts + nblk, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return PC_OK;
 }
 
-int launch_mark(uint8_t* mark, const int32_t* idx, int n, uint8_t value, cudaStream_t st) {
+int launch_mark(uint8_t* mark, const int32_t* idx, int n, uint8_t value, cudaStream_t st,
+                const int32_t* n_dev) {
   ProfScope prof_scope_(PROF_MISC, st);
   if (n <= 0) return PC_OK;
   prof_scope_.kernels = 1;
-  k_mark<<<ceil_div(n, 256), 256, 0, st>>>(mark, idx, n, value);
+  k_mark<<<ceil_div(n, 256), 256, 0, st>>>(mark, idx, n, value, n_dev);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

@@ -14,8 +14,10 @@ namespace {
 
 // Gdst[i][j] = Gsrc[map[i]][map[j]] where both map entries are >= 0.
 __global__ void k_gather_sym(const float* __restrict__ Gsrc, int lds, const int32_t* __restrict__ map,
-                             int n, float* __restrict__ Gdst, int ldd) {
+                             int n, float* __restrict__ Gdst, int ldd, const int32_t* __restrict__ n_dev) {
+  if (n_dev) n = min(n, *n_dev);   // count held on the device (n: its upper bound)
   const int i = blockIdx.y;
+  if (i >= n) return;
   const int mi = map[i];
   if (mi < 0) return;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -27,7 +29,8 @@ __global__ void k_gather_sym(const float* __restrict__ Gsrc, int lds, const int3
 // dst[i] = map[i] >= 0 ? src[map[i]] : fill
 template <class T>
 __global__ void k_gather_vec(const T* __restrict__ src, const int32_t* __restrict__ map, int n,
-                             T* __restrict__ dst, T fill) {
+                             T* __restrict__ dst, T fill, const int32_t* __restrict__ n_dev) {
+  if (n_dev) n = min(n, *n_dev);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int m = map[i];
@@ -35,8 +38,10 @@ __global__ void k_gather_vec(const T* __restrict__ src, const int32_t* __restric
 }
 
 // sum |x| in float64 (one block)
-__global__ void k_l1(const float* __restrict__ x, int n, double* __restrict__ out) {
+__global__ void k_l1(const float* __restrict__ x, int n, double* __restrict__ out,
+                     const int32_t* __restrict__ n_dev) {
   __shared__ double ws[32];
+  if (n_dev) n = min(n, *n_dev);
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs((double)x[i]);
   for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -50,27 +55,48 @@ __global__ void k_l1(const float* __restrict__ x, int n, double* __restrict__ ou
 }
 
 int gather_sym(const float* Gsrc, int lds, const int32_t* map, int n, float* Gdst, int ldd,
-               cudaStream_t st) {
+               cudaStream_t st, const int32_t* n_dev = nullptr) {
   ProfScope prof_scope_(PROF_MISC, st);
   if (n <= 0) return PC_OK;
   dim3 grid(std::max(1, std::min(ceil_div(n, 256), 32)), n);
   prof_scope_.kernels = 1;
-  k_gather_sym<<<grid, 256, 0, st>>>(Gsrc, lds, map, n, Gdst, ldd);
+  k_gather_sym<<<grid, 256, 0, st>>>(Gsrc, lds, map, n, Gdst, ldd, n_dev);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
 
 template <class T>
-int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStream_t st) {
+int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStream_t st,
+               const int32_t* n_dev = nullptr) {
   ProfScope prof_scope_(PROF_MISC, st);
   if (n <= 0) return PC_OK;
   prof_scope_.kernels = 1;
-  k_gather_vec<T><<<ceil_div(n, 256), 256, 0, st>>>(src, map, n, dst, fill);
+  k_gather_vec<T><<<ceil_div(n, 256), 256, 0, st>>>(src, map, n, dst, fill, n_dev);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
 
 inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
+
+// Exploration threshold of rule R1 (Algorithm 2) from the certificate maxima
+// on the device: thr = top - 2 Delta / ((k + 2) lambda) with top = max |mu|
+// (max mu under positivity); at k = 0 without a given lambda_max, Delta =
+// (1 - delta) lambda max(top, 0) is stored in *Delta for later iterations.
+__global__ void k_r1_threshold(const unsigned* __restrict__ maxbits, int positive, double lambda,
+                               double delta, int k, double* __restrict__ Delta, float* __restrict__ thr) {
+  const unsigned key = maxbits[1];
+  float top;
+  if (positive) {
+    const unsigned u = key == 0 ? 0xff800000u : ((key & 0x80000000u) ? (key & 0x7fffffffu) : ~key);
+    top = __uint_as_float(u);
+  } else {
+    top = __uint_as_float(maxbits[0]);
+  }
+  if (*Delta < 0.0) *Delta = (1.0 - delta) * lambda * fmax((double)top, 0.0);
+  float t = (float)((double)top - 2.0 * (*Delta) / ((k + 2) * lambda));
+  if (positive) t = fmaxf(t, 1.4e-45f);   // mu >= smallest positive float: mu > 0
+  *thr = t;
+}
 
 __global__ void k_iota(int32_t* __restrict__ a, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -473,16 +499,28 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
   };
   PC_TRY(grow(1024));
 
-  // ||V||^2 and r = V; tensor-core timeout flag cleared
-  PC_CUDA(cudaMemsetAsync(p->iscal + 4, 0, sizeof(int32_t), st));
+  // ||V||^2 and r = V; counters, the pruned-support count and the tensor-core
+  // flag cleared (the gridding flag iscal[7] may still report an earlier call)
+  PC_CUDA(cudaMemsetAsync(p->iscal, 0, 7 * sizeof(int32_t), st));
   PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
   PC_TRY(launch_residual(p->vis_fx, V, p->M, nullptr, 0, p->resid, p->dscal, st));
   double sumsqV = 0.0;
   PC_TRY(sync_read(&sumsqV, p->dscal, sizeof(double), st));
+  {
+    const double d0 = (c.rule == 1 && c.lmax > 0) ? (1.0 - delta) * c.lmax : -1.0;
+    PC_CUDA(cudaMemcpyAsync(p->dscal + 4, &d0, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  float* mu_dst = mu_out ? mu_out : p->mu;
+  float* thr_dev = reinterpret_cast<float*>(p->dscal + 5);
+  int32_t* n_sup_dev = p->iscal + 3;      // support count after the last pruning
 
-  int nS = 0, ldA = 4;
-  double F_prev = 0.5 * sumsqV, F = F_prev, Delta = -1.0;
-  if (c.rule == 1 && c.lmax > 0) Delta = (1.0 - delta) * c.lmax;
+  // One host synchronisation per Frank-Wolfe iteration: the pruning of the
+  // previous reweighting, the residual and objective of the iterate, its
+  // certificate and the exploration set are queued with every count kept on
+  // the device; then the host reads the objective, the certificate maxima,
+  // the new active-set size and the sub-solver statistics together.
+  int nS = 0, ldA = 4, n_prev_act = 0, ldB_prev = 4;
+  double F_prev = 0.5 * sumsqV, F = F_prev;
   int n_hist = 0, k = 0, status = PC_ERR_NOT_CONVERGED;
   double mu_inf = 0.0;
   pc_iter_record cur{};
@@ -490,22 +528,74 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
 
   for (k = 0;; ++k) {
     if (k > 0) {
+      // pruning of the previous reweighting: S = {x != 0}, in position order
+      const int32_t* keep = p->keep.as<int32_t>();
+      PC_TRY(gather_vec<int32_t>(p->idxB.as<int32_t>(), keep, n_prev_act, p->idxA.as<int32_t>(), 0, st,
+                                 n_sup_dev));
+      PC_TRY(gather_vec<float>(p->xB.as<float>(), keep, n_prev_act, p->xA.as<float>(), 0.f, st, n_sup_dev));
+      PC_TRY(gather_vec<float>(p->bB.as<float>(), keep, n_prev_act, p->bA.as<float>(), 0.f, st, n_sup_dev));
+      PC_TRY(gather_sym(p->GB.as<float>(), ldB_prev, keep, n_prev_act, p->GA.as<float>(), ldB_prev, st,
+                        n_sup_dev));
+      ldA = ldB_prev;
       // residual and objective of the current iterate
-      double sc[2] = {0.0, 0.0};
       PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
-      PC_TRY(launch_make_atoms(p->idxA.as<int32_t>(), p->xA.as<float>(), nS, p->N, p->dl,
-                               p->atomsA.as<float4>(), st));
-      PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), nS, p->resid, p->dscal, st));
-      if (nS > 0) {
+      if (n_prev_act > 0) {
+        PC_TRY(launch_make_atoms(p->idxA.as<int32_t>(), p->xA.as<float>(), n_prev_act, p->N, p->dl,
+                                 p->atomsA.as<float4>(), st, n_sup_dev));
         ProfScope prof_scope_(PROF_MISC, st);
         prof_scope_.kernels = 1;
-        k_l1<<<1, 256, 0, st>>>(p->xA.as<float>(), nS, p->dscal + 1);
+        k_l1<<<1, 256, 0, st>>>(p->xA.as<float>(), n_prev_act, p->dscal + 1, n_sup_dev);
         PC_LAUNCH_CHECK();
       }
-      PC_TRY(sync_read(sc, p->dscal, sizeof(sc), st));
-      F = 0.5 * sc[0] + lambda * sc[1];
+      PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_prev_act, p->resid, p->dscal,
+                             st, n_sup_dev));
+    }
+    // certificate mu_k = Phi*(r) / lambda (written where the caller wants the final one)
+    PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
+    PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, inv_lam, p->uscal, st));
+    // exploration and union, ascending raster order
+    auto explore = [&]() -> int {
+      const float* thr_d = nullptr;
+      if (c.rule == 1) {
+        ProfScope prof_scope_(PROF_MISC, st);
+        prof_scope_.kernels = 1;
+        k_r1_threshold<<<1, 1, 0, st>>>(p->uscal, c.positive, lambda, delta, k, p->dscal + 4, thr_dev);
+        PC_LAUNCH_CHECK();
+        thr_d = thr_dev;
+      }
+      const int bound = std::max(n_prev_act, 1);
+      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 1, st, n_sup_dev));
+      PC_TRY(launch_select(mu_dst, npix, (float)(1.0 - delta), p->mark, p->idxB.as<int32_t>(), p->iscal,
+                           p->sel_blocks, wcap, st, c.positive != 0, thr_d));
+      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 0, st, n_sup_dev));
+      return PC_OK;
+    };
+    PC_TRY(explore());
+    // the one synchronisation of the iteration
+    int32_t hi[8];
+    double hd[3];
+    unsigned mb[2];
+    PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaMemcpyAsync(hd, p->dscal, sizeof(hd), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaMemcpyAsync(mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    if (hi[7]) {
+      PC_CUDA(cudaMemsetAsync(p->iscal + 7, 0, sizeof(int32_t), st));
+      return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded tensor-core gridding wait expired");
+    }
+    if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded device wait expired");
+    mu_inf = (double)bits_to_float(mb[0]);
+    if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
+    const double mu_top = c.positive ? (double)key_to_float(mb[1]) : mu_inf;
+    if (k > 0) {
+      nS = hi[3];
+      F = 0.5 * hd[0] + lambda * hd[1];
       const double rel = F_prev > 0 ? (F_prev - F) / F_prev : 0.0;
       if (have_cur) {
+        cur.n_support = nS;
+        cur.apgd_iterations = hi[2];
+        cur.lanczos_steps = hi[5];
+        cur.lipschitz = hd[2];
         cur.objective = F;
         cur.rel_improvement = rel;
         if (n_hist < hist_cap && hist) hist[n_hist] = cur;
@@ -517,34 +607,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       if (rel < c.tol) { status = PC_OK; break; }
       if (k >= c.max_fw) { status = PC_ERR_NOT_CONVERGED; break; }
     }
-    // certificate mu_k = Phi*(r) / lambda
-    PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
-    PC_TRY(adjoint_grid_impl(p, p->resid, p->mu, inv_lam, p->uscal, st));
-    unsigned mb[2] = {0, 0};
-    PC_CUDA(cudaMemcpyAsync(mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
-    PC_TRY(grid_flag_sync(p, st, "pc_solve"));
-    mu_inf = (double)bits_to_float(mb[0]);
-    if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
-    // the largest candidate value: max |mu|, or max mu under positivity
-    const double mu_top = c.positive ? (double)key_to_float(mb[1]) : mu_inf;
-    float thr;
-    if (c.rule == 2) {
-      thr = (float)(1.0 - delta);
-    } else {
-      // lambda_max (||Phi* V||_inf, or max Phi* V under positivity) from the certificate at k = 0
-      if (Delta < 0) Delta = (1.0 - delta) * lambda * std::max(mu_top, 0.0);
-      thr = (float)(mu_top - 2.0 * Delta / ((k + 2) * lambda));
-      if (c.positive) thr = std::max(thr, 1.4e-45f);   // mu >= smallest positive float: mu > 0
-    }
-    // exploration and union, ascending raster order
-    int n_act = 0;
-    for (;;) {
-      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), nS, 1, st));
-      PC_TRY(launch_select(p->mu, npix, thr, p->mark, p->idxB.as<int32_t>(), p->iscal,
-                           p->sel_blocks, wcap, st, c.positive != 0));
-      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), nS, 0, st));
-      PC_TRY(sync_read(&n_act, p->iscal, sizeof(int), st));
-      if (n_act <= wcap) break;
+    int n_act = hi[0];
+    while (n_act > wcap) {
       if (n_act > 60000) return fail(PC_ERR_CAPACITY, "pc_solve: active set of %d atoms too large", n_act);
       // grow, keeping the current support and weights
       int32_t* old_idx = nullptr;
@@ -573,6 +637,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       cudaFree(old_idx);
       PC_TRY(rc);
       PC_LAUNCH_CHECK();
+      PC_TRY(explore());
+      PC_TRY(sync_read(&n_act, p->iscal, sizeof(int), st));
     }
     const int n_new = n_act - nS;
     cur = pc_iter_record{};
@@ -582,9 +648,8 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     cur.mu_inf = mu_top;
     have_cur = true;
 
-    int n_sup = 0;
+    const int ldB = round4(std::max(n_act, 1));
     if (n_act > 0) {
-      const int ldB = round4(n_act);
       int32_t* oldpos = p->oldpos.as<int32_t>();
       PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
       PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
@@ -602,41 +667,18 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
       }
       // reweighting: restricted LASSO by APGD
       const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
-      int32_t* d_it = p->iscal + 2;
       PC_TRY(run_apgd(p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
-                      p->xB.as<float>(), d_it, p->dscal + 2, p->dscal + 3, st, p->iscal + 5,
+                      p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->dscal + 3, st, p->iscal + 5,
                       p->iscal + 4, c.positive != 0));
-      // pruning
-      PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
-      int32_t hi[6];
-      double hd[2];
-      PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
-      PC_CUDA(cudaMemcpyAsync(hd, p->dscal + 2, sizeof(hd), cudaMemcpyDeviceToHost, st));
-      PC_CUDA(cudaStreamSynchronize(st));
-      if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded device wait expired");
-      n_sup = hi[3];
-      cur.apgd_iterations = hi[2];
-      cur.lanczos_steps = hi[5];
-      cur.lipschitz = hd[0];
-      const int32_t* keep = p->keep.as<int32_t>();
-      const int ldNew = round4(std::max(n_sup, 1));
-      PC_TRY(gather_vec<int32_t>(p->idxB.as<int32_t>(), keep, n_sup, p->idxA.as<int32_t>(), 0, st));
-      PC_TRY(gather_vec<float>(p->xB.as<float>(), keep, n_sup, p->xA.as<float>(), 0.f, st));
-      PC_TRY(gather_vec<float>(p->bB.as<float>(), keep, n_sup, p->bA.as<float>(), 0.f, st));
-      PC_TRY(gather_sym(p->GB.as<float>(), ldB, keep, n_sup, p->GA.as<float>(), ldNew, st));
-      ldA = ldNew;
+      // the nonzero positions; the gathers run at the start of the next iteration
+      PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), n_sup_dev, st));
+    } else {
+      PC_CUDA(cudaMemsetAsync(n_sup_dev, 0, sizeof(int32_t), st));
     }
-    nS = n_sup;
-    cur.n_support = n_sup;
+    n_prev_act = n_act;
+    ldB_prev = ldB;
   }
 
-  // final certificate at the returned iterate (its residual is in p->resid)
-  float* mu_dst = mu_out ? mu_out : p->mu;
-  PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
-  PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, inv_lam, p->uscal, st));
-  unsigned mb = 0;
-  PC_CUDA(cudaMemcpyAsync(&mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
-  PC_TRY(grid_flag_sync(p, st, "pc_solve"));
   if (stats) {
     stats->status = status;
     stats->iterations = k;
@@ -644,7 +686,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     stats->n_history = std::min(n_hist, hist_cap);
     stats->objective = F;
     stats->lambda = lambda;
-    stats->mu_inf = (double)bits_to_float(mb);
+    stats->mu_inf = mu_inf;
     stats->sumsq_V = sumsqV;
   }
   if (nS > cap) return fail(PC_ERR_CAPACITY, "pc_solve: support of %d atoms exceeds capacity %d", nS, cap);

@@ -16,8 +16,10 @@ namespace pc {
 namespace {
 
 __global__ void k_make_atoms(const int32_t* __restrict__ idx, const float* __restrict__ x, int S,
-                             int N, double dl, float4* __restrict__ atoms, int* __restrict__ bad) {
+                             int N, double dl, float4* __restrict__ atoms, int* __restrict__ bad,
+                             const int32_t* __restrict__ S_dev) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (S_dev) S = min(S, *S_dev);   // count held on the device (S: its upper bound)
   if (s >= S) return;
   int p = idx[s];
   if (bad && (p < 0 || p >= N * N || (s > 0 && idx[s - 1] >= p))) atomicOr(bad, 1);
@@ -41,9 +43,10 @@ constexpr int RES_CHUNK = 1024;
 __global__ void __launch_bounds__(256)
 k_residual(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
            const float4* __restrict__ atoms, int S, float2* __restrict__ out,
-           double* __restrict__ sumsq) {
+           double* __restrict__ sumsq, const int32_t* __restrict__ S_dev) {
   __shared__ float4 sa[RES_CHUNK];
   __shared__ double red[8];
+  if (S_dev) S = min(S, *S_dev);
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = k < M;
   const int4 vk = active ? vis[k] : make_int4(0, 0, 0, 0);
@@ -336,11 +339,11 @@ __global__ void k_gram_finalize(const double* __restrict__ acc, int ldacc,
 }  // namespace
 
 int launch_make_atoms(const int32_t* idx, const float* x, int S, int N, double dl, float4* atoms,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int32_t* S_dev) {
   ProfScope prof_scope_(PROF_MISC, st);
   if (S <= 0) return PC_OK;
   prof_scope_.kernels = 1;
-  k_make_atoms<<<ceil_div(S, 256), 256, 0, st>>>(idx, x, S, N, dl, atoms, nullptr);
+  k_make_atoms<<<ceil_div(S, 256), 256, 0, st>>>(idx, x, S, N, dl, atoms, nullptr, S_dev);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
@@ -351,7 +354,7 @@ int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double 
                        float4* atoms, int* dflag, cudaStream_t st) {
   if (S <= 0) return PC_OK;
   PC_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), st));
-  k_make_atoms<<<ceil_div(S, 256), 256, 0, st>>>(idx, x, S, N, dl, atoms, dflag);
+  k_make_atoms<<<ceil_div(S, 256), 256, 0, st>>>(idx, x, S, N, dl, atoms, dflag, nullptr);
   PC_LAUNCH_CHECK();
   int h = 0;
   PC_CUDA(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -361,11 +364,11 @@ int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double 
 }
 
 int launch_residual(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int S,
-                    float2* out, double* sumsq, cudaStream_t st) {
+                    float2* out, double* sumsq, cudaStream_t st, const int32_t* S_dev) {
   ProfScope prof_scope_(PROF_RESIDUAL, st);
   if (M <= 0) return PC_OK;
   prof_scope_.kernels = 1;
-  k_residual<<<ceil_div(M, 256), 256, 0, st>>>(vis_fx, V, M, atoms, S, out, sumsq);
+  k_residual<<<ceil_div(M, 256), 256, 0, st>>>(vis_fx, V, M, atoms, S, out, sumsq, S_dev);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
