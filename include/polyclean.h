@@ -264,6 +264,11 @@ typedef struct {
 } pc_kernel_time;
 
 int pc_profile_begin(void);
+/* As pc_profile_begin, recording only the comma-separated classes named in
+ * `classes` (e.g. "gram_tc"; NULL or "" = all); PC_ERR_INVALID_ARG for an
+ * unknown name. Recording one class costs two event records per launch of
+ * that class only. */
+int pc_profile_begin_classes(const char* classes);
 int pc_profile_end(pc_kernel_time* out_host, int32_t cap, int32_t* n_out_host);
 
 /* ------------------------------------------------------------------ misc */

@@ -30,6 +30,7 @@ EXPORTS = [
     "pc_adjoint_sparse", "pc_adjoint_grid", "pc_lambda_max", "pc_certificate", "pc_select",
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
+    "pc_profile_begin_classes",
 ]
 
 
@@ -116,6 +117,7 @@ def load(path: str | None = None):
                                  ctypes.POINTER(pc_solve_stats), _P]),
         "pc_adjoint_sparse_noalloc": (_I32, [_P, _I64, _I32, _D, _P, _P, _I32, _P, _P]),
         "pc_profile_begin": (_I32, []),
+        "pc_profile_begin_classes": (_I32, [ctypes.c_char_p]),
         "pc_profile_end": (_I32, [ctypes.POINTER(pc_kernel_time), _I32, ctypes.POINTER(_I32)]),
         "pc_last_error": (ctypes.c_char_p, []),
         "pc_abi_version": (_I32, []),
@@ -332,8 +334,13 @@ def pc_solve_host(uvw, V, N: int, fov: float, alpha: float, delta: float, cap: i
                 objective=st.objective, lam=st.lambda_, mu_inf=st.mu_inf)
 
 
-def pc_profile_begin() -> None:
-    _check(load().pc_profile_begin())
+def pc_profile_begin(classes: str | None = None) -> None:
+    """Start per-kernel-class event timing: every class, or only the
+    comma-separated classes named (e.g. "gram_tc")."""
+    if classes:
+        _check(load().pc_profile_begin_classes(classes.encode()))
+    else:
+        _check(load().pc_profile_begin())
 
 
 def pc_profile_end() -> dict:

@@ -75,6 +75,7 @@ struct ProfRec {
 };
 
 bool g_prof_on = false;
+unsigned g_prof_mask = ~0u;   // classes recorded while profiling is on
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_pool;
 size_t g_pool_used = 0;
@@ -94,7 +95,7 @@ cudaEvent_t pool_event() {
 }  // namespace
 
 int prof_start(int cls, cudaStream_t st) {
-  if (!g_prof_on) return -1;
+  if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return -1;
   cudaEvent_t a = pool_event(), b = pool_event();
   if (!a || !b) return -1;
   cudaEventRecord(a, st);
@@ -113,7 +114,37 @@ void prof_stop(int token, cudaStream_t st, int kernels) {
 extern "C" int pc_profile_begin(void) {
   pc::g_prof.clear();
   pc::g_pool_used = 0;
+  pc::g_prof_mask = ~0u;
   pc::g_prof_on = true;
+  return PC_OK;
+}
+
+extern "C" int pc_profile_begin_classes(const char* classes) {
+  using namespace pc;
+  unsigned mask = 0;
+  if (!classes || !*classes) {
+    mask = ~0u;
+  } else {
+    std::string s(classes);
+    size_t pos = 0;
+    while (pos <= s.size()) {
+      size_t q = s.find(',', pos);
+      if (q == std::string::npos) q = s.size();
+      const std::string name = s.substr(pos, q - pos);
+      bool found = false;
+      for (int c = 0; c < PROF_NCLASSES; ++c)
+        if (name == kProfNames[c]) {
+          mask |= 1u << c;
+          found = true;
+        }
+      if (!found) return fail(PC_ERR_INVALID_ARG, "pc_profile_begin_classes: unknown class '%s'", name.c_str());
+      pos = q + 1;
+    }
+  }
+  g_prof.clear();
+  g_pool_used = 0;
+  g_prof_mask = mask;
+  g_prof_on = true;
   return PC_OK;
 }
 

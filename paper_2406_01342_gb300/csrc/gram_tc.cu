@@ -112,58 +112,58 @@ __global__ void k_vscale(const unsigned* __restrict__ bits, float* __restrict__ 
   scale[1] = ldexpf(1.f, e);
 }
 
-// One uint4 (4 visibilities of one row, FP16 re/im pairs) per item; item order
-// equals memory order: [stage][row group][K-group][row in group].
+// One thread per (row, stage): the 16 visibilities of the stage for one atom
+// (or the V row), as four 16-byte items of FP16 re/im pairs in hi and in lo.
+// Item order equals memory order: [stage][row group][K-group][row in group],
+// so a warp (32 consecutive rows) writes 4 x 128 contiguous bytes per K-group.
+// The atom stays in registers across the stages a thread visits; the stage's
+// visibilities are the same for the whole block (broadcast loads).
 __global__ void __launch_bounds__(256)
 k_phase_gen(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t k0, int64_t k_end,
             const float4* __restrict__ atoms, int n_atoms, int v_row, int rows_pad, int n_stages,
             const float* __restrict__ vscale, uint4* __restrict__ hi, uint4* __restrict__ lo) {
-  const int64_t items = (int64_t)n_stages * rows_pad * GB_KG;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows_pad) return;
   const float sc = V ? vscale[0] : 0.f;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < items;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(idx & 7);
-    const int kg = (int)((idx >> 3) % GB_KG);
-    const int64_t rest = (idx >> 3) / GB_KG;
-    const int g = (int)(rest % (rows_pad / 8));
-    const int64_t stage = rest / (rows_pad / 8);
-    const int row = 8 * g + r;
-    const int64_t kbase = k0 + stage * GB_KV + kg * 4;
-    __half2 h[4], l[4];
-    float4 at = make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool is_atom = row < n_atoms, is_v = row == v_row;
-    if (is_atom) at = atoms[row];
+  const bool is_atom = row < n_atoms, is_v = row == v_row;
+  const float4 at = is_atom ? atoms[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const size_t row_item = (size_t)(row >> 3) * (GB_KG * 8) + (row & 7);
+  const size_t stage_items = (size_t)rows_pad * GB_KG;
+  for (int stage = blockIdx.y; stage < n_stages; stage += gridDim.y) {
+    const int64_t kbase = k0 + (int64_t)stage * GB_KV;
+    const size_t base = (size_t)stage * stage_items + row_item;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t k = kbase + v;
-      float re = 0.f, im = 0.f;
-      if (k < k_end) {
-        if (is_atom) {
-          float sn, cs;
-          __sincosf(6.283185307179586f * phase_turns(vis[k], at), &sn, &cs);
-          re = cs * at.w;
-          im = sn * at.w;
-        } else if (is_v) {
-          const float2 vv = V[k];
-          re = vv.x * sc;
-          im = -vv.y * sc;
+    for (int kg = 0; kg < GB_KG; ++kg) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int v = 0; v < 4; v += 2) {
+        float re[2], im[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int64_t k = kbase + kg * 4 + v + s;
+          re[s] = 0.f;
+          im[s] = 0.f;
+          if (k < k_end) {
+            if (is_atom) {
+              float sn, cs;
+              __sincosf(6.283185307179586f * phase_turns(vis[k], at), &sn, &cs);
+              re[s] = cs * at.w;
+              im[s] = sn * at.w;
+            } else if (is_v) {
+              const float2 vv = V[k];
+              re[s] = vv.x * sc;
+              im[s] = -vv.y * sc;
+            }
+          }
         }
+        // pairs (re, im) of two visibilities: split each into hi + lo
+        tc::split_f16x2(re[0], im[0], h[v], l[v]);
+        tc::split_f16x2(re[1], im[1], h[v + 1], l[v + 1]);
       }
-      h[v] = __floats2half2_rn(re, im);
-      const float2 hf = __half22float2(h[v]);
-      l[v] = __floats2half2_rn(re - hf.x, im - hf.y);
+      const size_t item = base + (size_t)kg * 8;
+      hi[item] = make_uint4(h[0], h[1], h[2], h[3]);
+      lo[item] = make_uint4(l[0], l[1], l[2], l[3]);
     }
-    uint4 hv, lv;
-    hv.x = *reinterpret_cast<uint32_t*>(&h[0]);
-    hv.y = *reinterpret_cast<uint32_t*>(&h[1]);
-    hv.z = *reinterpret_cast<uint32_t*>(&h[2]);
-    hv.w = *reinterpret_cast<uint32_t*>(&h[3]);
-    lv.x = *reinterpret_cast<uint32_t*>(&l[0]);
-    lv.y = *reinterpret_cast<uint32_t*>(&l[1]);
-    lv.z = *reinterpret_cast<uint32_t*>(&l[2]);
-    lv.w = *reinterpret_cast<uint32_t*>(&l[3]);
-    hi[idx] = hv;
-    lo[idx] = lv;
   }
 }
 
@@ -414,10 +414,11 @@ int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4*
   for (int64_t k0 = 0; k0 < M; k0 += KC) {
     const int64_t kc = std::min(KC, M - k0);
     const int n_stages = (int)((kc + GB_KV - 1) / GB_KV);
-    const int64_t items = (int64_t)n_stages * rows_pad * GB_KG;
-    const int gblocks = (int)std::min<int64_t>(ceil_div(items, 256), 152 * 16);
-    k_phase_gen<<<gblocks, 256, 0, st>>>(vis_fx, V, k0, k0 + kc, atoms, n_atoms, V ? n_atoms : -1,
-                                         rows_pad, n_stages, vscale_dev, hi, lo);
+    // ~16 resident 256-thread blocks per SM; each thread walks stages with stride gridDim.y
+    const int bx = rows_pad / 256;
+    const int by = (int)std::min<int64_t>(n_stages, std::max<int64_t>(1, (int64_t)152 * 16 / bx));
+    k_phase_gen<<<dim3(bx, by), 256, 0, st>>>(vis_fx, V, k0, k0 + kc, atoms, n_atoms, V ? n_atoms : -1,
+                                              rows_pad, n_stages, vscale_dev, hi, lo);
     PC_LAUNCH_CHECK();
     GbArgs a{reinterpret_cast<const unsigned char*>(hi), reinterpret_cast<const unsigned char*>(lo),
              rows_pad, n_stages, nA, rows, V ? n_atoms : -1, V ? vscale_dev : nullptr, NT, acc, ldacc,
