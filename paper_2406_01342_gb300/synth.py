@@ -133,6 +133,42 @@ def unit_complex_noise(M: int, rng: np.random.Generator) -> np.ndarray:
 
 # ---------------------------------------------------------------- named workloads
 
+def gaussian_blobs(N: int, n_blobs: int, rng: np.random.Generator, width_px=(5.0, 50.0),
+                   peak=(0.1, 1.0), floor: float = 1e-3):
+    """Elliptical Gaussian blobs: axis FWHMs U[width_px], random orientation,
+    centres in the inner 80 % of the image, peak brightness U[peak] per pixel;
+    pixels below `floor` x peak are dropped. Returns (sorted raster indices,
+    brightness per pixel), overlapping blobs summed."""
+    img = {}
+    for _ in range(n_blobs):
+        fa, fb = rng.uniform(width_px[0], width_px[1], 2)
+        sa, sb = fa / 2.3548200450309493, fb / 2.3548200450309493
+        th = rng.uniform(0.0, np.pi)
+        ci, cj = rng.uniform(0.1 * N, 0.9 * N, 2)
+        pk = rng.uniform(peak[0], peak[1])
+        r = int(math.ceil(max(sa, sb) * math.sqrt(2.0 * math.log(1.0 / floor)))) + 1
+        i0, i1 = max(0, int(ci) - r), min(N, int(ci) + r + 1)
+        j0, j1 = max(0, int(cj) - r), min(N, int(cj) + r + 1)
+        ii, jj = np.meshgrid(np.arange(i0, i1), np.arange(j0, j1), indexing="ij")
+        di, dj = ii - ci, jj - cj
+        u = di * math.cos(th) + dj * math.sin(th)
+        v = -di * math.sin(th) + dj * math.cos(th)
+        val = pk * np.exp(-0.5 * ((u / sa) ** 2 + (v / sb) ** 2))
+        for p, b in zip((ii * N + jj)[val >= floor * pk].ravel(), val[val >= floor * pk].ravel()):
+            img[int(p)] = img.get(int(p), 0.0) + float(b)
+    idx = np.array(sorted(img), dtype=np.int64)
+    return idx, np.array([img[int(p)] for p in idx], dtype=np.float64)
+
+
+def merge_skies(idx_a, f_a, idx_b, f_b):
+    """Union of two sparse skies (sorted indices), values summed where they meet."""
+    idx = np.union1d(idx_a, idx_b)
+    f = np.zeros(idx.size)
+    f[np.searchsorted(idx, idx_a)] += f_a
+    f[np.searchsorted(idx, idx_b)] += f_b
+    return idx, f
+
+
 def _rngs(seed: int):
     ss = np.random.SeedSequence(seed)
     layout, sky, noise, sub = ss.spawn(4)
@@ -181,16 +217,24 @@ def medium_512(seed: int = 1001, M: int = 200_000) -> Workload:
                                    50, 20.0)
 
 
-def large_2048(seed: int = 1002, M: int = 2_000_000) -> Workload:
+def large_2048(seed: int = 1002, M: int = 2_000_000, blobs: bool = False) -> Workload:
     """2048x2048, FOV 5 deg, 60 stations within 5 km (baselines up to 10 km),
-    Earth rotation to M = 2M, 200 log-normal point sources, 15 dB SNR (point part only)."""
-    return earth_rotation_workload("large_2048_w", seed, 2048, 5.0, 60, 5000.0, 3.14, 10.0, M,
-                                   200, 15.0)
+    Earth rotation to M = 2M, 200 log-normal point sources, 15 dB SNR; with
+    blobs=True also 10 elliptical Gaussian blobs (FWHM 5-50 px, peak U[0.1, 1]
+    per pixel), the diffuse part of the configuration."""
+    wl = earth_rotation_workload("large_2048_w", seed, 2048, 5.0, 60, 5000.0, 3.14, 10.0, M,
+                                 200, 15.0)
+    if blobs:
+        rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(5)[4])
+        bi, bf = gaussian_blobs(wl.N, 10, rng)
+        wl.sky_idx, wl.sky_flux = merge_skies(wl.sky_idx, wl.sky_flux, bi, bf)
+        wl.name = "large_2048_blobs"
+    return wl
 
 
 def fine_4096(seed: int = 1003, M: int = 10_000_000) -> Workload:
     """4096x4096, FOV 5 deg, 100 stations within 5.85 km, M = 10M, 500 log-normal sources."""
-    return earth_rotation_workload("fine_4096_w", seed, 4096, 5.0, 100, 5850.0, 5.6, 10.0, M,
+    return earth_rotation_workload("fine_4096_w", seed, 4096, 5.0, 100, 5850.0, 5.62, 10.0, M,
                                    500, 20.0)
 
 
