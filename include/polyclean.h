@@ -3,14 +3,14 @@
  *
  * The library implements, as hand-written CUDA kernels, the operators and the
  * solver loop of PolyCLEAN (Polyatomic Frank-Wolfe for the LASSO imaging
- * problem, Sect. 3.1 and Algorithm 2 of the paper):
+ * problem, Sect. 4.1 and Algorithm 2 of the paper):
  *
  *   Phi  : R^{N x N} -> C^M   Phi(I)[k]  = sum_p I_p / n_p exp(-j2pi(u_k l_p + v_k m_p + w_k (n_p - 1)))
  *                             (the discrete forward equation, Sect. 2.2)
  *   Phi* : C^M -> R^{N x N}   Phi*(h)[p] = Re sum_k h_k / n_p exp(+j2pi(u_k l_p + v_k m_p + w_k (n_p - 1)))
  *                             (the adjoint equation, Sect. 2.2)
- *   mu   = Phi*(V - Phi x) / lambda          (dual certificate, Sect. 3.2)
- *   lambda_max = ||Phi* V||_inf              (Sect. 4.4)
+ *   mu   = Phi*(V - Phi x) / lambda          (dual certificate, Sect. 4.2)
+ *   lambda_max = ||Phi* V||_inf              (Sect. 5.3)
  *   argmin_x 1/2 ||V - Phi x||^2 + lambda ||x||_1 by Polyatomic Frank-Wolfe (Algorithm 2)
  *
  * Conventions shared by every call:
@@ -76,9 +76,9 @@ typedef struct {
   int32_t max_fw;         /* Frank-Wolfe iteration cap (default 100)                                 */
   int32_t apgd_max_iter;  /* sub-solver iteration cap (default 10000)                                */
   int32_t gram_mode;      /* 0 (default): tensor cores for large blocks; 1: FP32 only; 2: tensor cores */
-  int32_t positivity;     /* 1: x >= 0 (remark of Sect. 4.1): candidates only where mu >= thr,
+  int32_t positivity;     /* 1: x >= 0 (remark of Sect. 5.1): candidates only where mu >= thr,
                              reweighting with the non-negative proximal map; 0 (default): off */
-  double  tol;            /* stop when (F_k - F_{k+1}) / F_k < tol (default 1e-4, Sect. 5.1)          */
+  double  tol;            /* stop when (F_k - F_{k+1}) / F_k < tol (default 1e-4, Sect. 6.1)          */
   double  eps0;           /* sub-solver accuracy eps_k = max(eps_min, eps0 2^-k) (default 1e-2)       */
   double  eps_min;        /* (default 1e-5)                                                           */
   double  lambda_max;     /* for rule 1: lambda_max if known (<= 0: computed; under positivity the
@@ -117,7 +117,7 @@ typedef struct {
  * with full field-of-view side fov_rad (direction cosine units). Sorts and bins
  * the visibilities by (gridding tile, w-plane), precomputes the kernel
  * corrections and allocates the gridding / FFT workspace (the plan owns it).
- * Sect. 2.2 (pixel grid, operators) and Sect. 4.2 (the operator is evaluated
+ * Sect. 2.2 (pixel grid, operators) and Sect. 5.2 (the operator is evaluated
  * with a non-uniform FFT: here exponential-of-semicircle gridding on a 2x
  * oversampled grid with w-stacking). N must be even, 16 <= N <= 4096.
  * M may be 0 (all operators then return zeros). */
@@ -134,7 +134,7 @@ int pc_plan_info(pc_plan_t plan, int32_t* grid_side, int32_t* tile, int32_t* n_p
 
 /* y = Phi restricted to the support: y[k] = sum_s x[s]/n_s exp(-j2pi theta_ks),
  * direct sum over the support (the forward equation of Sect. 2.2 for a sparse
- * image; the paper evaluates it as a type-3 NUFFT, Sect. 4.2).
+ * image; the paper evaluates it as a type-3 NUFFT, Sect. 5.2).
  * idx_dev: S ascending raster indices; x_dev: S weights; y_dev: M outputs. */
 int pc_forward_sparse(pc_plan_t plan, const int32_t* idx_dev, const float* x_dev, int32_t S,
                       pc_c32* y_dev, void* stream);
@@ -148,16 +148,16 @@ int pc_adjoint_sparse(pc_plan_t plan, const pc_c32* y_dev, const int32_t* idx_de
  * correction. With y = V this is the dirty image. img_dev: N*N floats. */
 int pc_adjoint_grid(pc_plan_t plan, const pc_c32* y_dev, float* img_dev, void* stream);
 
-/* lambda_max = ||Phi* V||_inf (Sect. 4.4), returned in host memory. */
+/* lambda_max = ||Phi* V||_inf (Sect. 5.3), returned in host memory. */
 int pc_lambda_max(pc_plan_t plan, const pc_c32* V_dev, double* lambda_max_host, void* stream);
 
 /* max(0, max_p Phi*(V)_p): the smallest lambda for which x = 0 is optimal under
- * the positivity constraint (remark of Sect. 4.1; lambda = alpha times it),
+ * the positivity constraint (remark of Sect. 5.1; lambda = alpha times it),
  * returned in host memory. */
 int pc_lambda_max_positive(pc_plan_t plan, const pc_c32* V_dev, double* lambda_max_host,
                            void* stream);
 
-/* mu = Phi*(V - Phi x) / lambda (Sect. 3.2), x given on a support of S pixels.
+/* mu = Phi*(V - Phi x) / lambda (Sect. 4.2), x given on a support of S pixels.
  * mu_dev: N*N floats. mu_inf_host (may be NULL): ||mu||_inf. sumsq_host (may
  * be NULL): ||V - Phi x||^2 accumulated in float64. */
 int pc_certificate(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev,
@@ -188,13 +188,13 @@ int pc_select(pc_plan_t plan, const float* mu_dev, float thr, const int32_t* pre
 int pc_gram(pc_plan_t plan, const pc_c32* V_dev, const int32_t* idx_dev, int32_t S,
             float* G_dev, int32_t ldg, float* b_dev, int32_t mode, void* stream);
 
-/* Restricted LASSO by monotone FISTA on the Gram form (Sect. 3.4 / 4.1):
+/* Restricted LASSO by monotone FISTA on the Gram form (Sect. 4.4 / 4.1):
  * min_x 1/2 x^T G x - b^T x + lambda ||x||_1, warm start x_dev (in/out),
  * step 1/L with L = 1.01 x the top eigenvalue of G (Lanczos, ~1e-6 relative),
  * stop when ||z - y|| <= eps ||z|| or after max_iter iterations. Synchronises
  * the stream. iters_host / lipschitz_host (may be NULL) receive the iteration
  * count and L. positive = 1 adds the constraint x >= 0 (proximal map
- * max(z - lambda/L, 0); the positivity remark of Sect. 4.1). PC_ERR_TIMEOUT if
+ * max(z - lambda/L, 0); the positivity remark of Sect. 5.1). PC_ERR_TIMEOUT if
  * a bounded wait between the CTAs of the solver's thread-block cluster expired
  * (x_dev is then unchanged). */
 int pc_apgd(const float* G_dev, int32_t ldg, const float* b_dev, int32_t S, double lambda,
@@ -217,8 +217,9 @@ int pc_solve(pc_plan_t plan, const pc_c32* V_dev, double lambda, double delta,
 
 /* End-to-end call on HOST buffers: copies uvw (M x 3 float64) and V (M
  * complex) to the device, builds a plan, solves with lambda = alpha *
- * lambda_max, copies the support and weights back (capacity cap), frees
- * everything. The host buffers may be pageable or pinned. */
+ * lambda_max (the positive lambda_max of pc_lambda_max_positive when
+ * opts->positivity is set), copies the support and weights back (capacity
+ * cap), frees everything. The host buffers may be pageable or pinned. */
 int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32_t N,
                   double fov_rad, double alpha, double delta, const pc_solve_opts* opts,
                   int32_t* idx_out_host, float* x_out_host, int32_t cap,
@@ -247,6 +248,52 @@ int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32
 int pc_adjoint_sparse_noalloc(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
                               const pc_c32* y_dev, const int32_t* idx_dev, int32_t S,
                               float* out_dev, void* stream);
+
+/* ------------------------------------------------------------------ serving loop
+ *
+ * Continuous batching of imaging requests (each one the solve of
+ * pc_solve_host: plan, lambda = alpha lambda_max, Algorithm 2). The paper
+ * names parallel processing as future work (Sect. 7); this loop serves many
+ * requests of different grid and visibility sizes on one GPU. A scheduler
+ * thread admits queued requests while fewer than max_jobs are active and their
+ * estimated device bytes fit the memory budget, keeps each job's plan,
+ * binned visibilities and support on the device, advances every active job on
+ * its own stream (their kernels overlap on the GPU) and launches the
+ * reweightings (APGD) of all jobs that reach that step together, several
+ * jobs per launch. Requests that arrive while others run are admitted as slots
+ * and memory free up. */
+
+typedef struct pc_server_s* pc_server_t;
+
+typedef struct {
+  int32_t version;          /* PC_ABI_VERSION                                              */
+  int32_t max_jobs;         /* concurrently active jobs (default 8)                        */
+  int64_t memory_budget;    /* device bytes for active jobs (<= 0: half the free memory)    */
+  int32_t batch_apgd;       /* 1 (default): one launch for all ready reweightings; 2: one per job */
+  int32_t reserved;
+} pc_server_opts;
+
+/* Per-request timing on the server's steady clock (seconds since its creation). */
+typedef struct {
+  double submitted;         /* pc_server_submit returned                                   */
+  double admitted;          /* inputs on the device, plan building starts                  */
+  double finished;          /* result ready (latency = finished - submitted)               */
+} pc_job_times;
+
+int pc_server_create(const pc_server_opts* opts, pc_server_t* server_out);
+/* Queues one request; the host inputs are copied (the caller may free them on
+ * return). uvw: M x 3 float64 wavelengths, V: M complex64; alpha in (0, 1],
+ * delta in (0, 1]; opts as pc_solve (NULL = defaults). *job_id_out > 0. */
+int pc_server_submit(pc_server_t server, const double* uvw_host, const pc_c32* V_host, int64_t M,
+                     int32_t N, double fov_rad, double alpha, double delta,
+                     const pc_solve_opts* opts, int64_t* job_id_out);
+/* Blocks until the job is done; copies its support and weights (host, up to
+ * cap) and statistics, releases the job and returns its status (as pc_solve;
+ * PC_ERR_INVALID_ARG for an unknown or already collected job). times may be NULL. */
+int pc_server_wait(pc_server_t server, int64_t job_id, int32_t* idx_out_host, float* x_out_host,
+                   int32_t cap, pc_solve_stats* stats_host, pc_job_times* times_host);
+/* Finishes every queued and active job, then frees the server. */
+void pc_server_destroy(pc_server_t server);
 
 /* ------------------------------------------------------------------ profiling */
 

@@ -2,10 +2,10 @@
 
 This package is a plain, slow, obviously-correct restatement of what the paper
 defines: the discrete measurement operator and its adjoint (Sect. 2.2, the
-discrete forward equation and its adjoint), the LASSO objective (Sect. 3.1),
-the dual certificate (Sect. 3.2), lambda_max (Sect. 4.4) and the Polyatomic
+discrete forward equation and its adjoint), the LASSO objective (Sect. 4.1),
+the dual certificate (Sect. 4.2), lambda_max (Sect. 5.3) and the Polyatomic
 Frank-Wolfe loop (Algorithm 2) with an accelerated proximal-gradient
-sub-solver (Sect. 3.4 / Sect. 4.1).
+sub-solver (Sect. 4.4 / Sect. 5.1).
 
 It is test infrastructure. Only the test-suite, the smoke check of the
 package entry file and the CPU-baseline leg of the benchmark may import it.

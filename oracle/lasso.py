@@ -1,12 +1,12 @@
 """Restricted LASSO sub-solvers in FP64 (test infrastructure only).
 
-Step 2 of Algorithm 2 solves the LASSO (Sect. 3.1)
+Step 2 of Algorithm 2 solves the LASSO (Sect. 4.1)
 
     min_x  1/2 ||V - A x||^2 + lambda ||x||_1,   x real, A = Phi restricted to a support,
 
 with an accelerated proximal-gradient method (APGD / FISTA, Beck & Teboulle
-2009, cited in Sect. 3.4), stopped early with an accuracy that tightens over
-the Frank-Wolfe iterations (Sect. 4.1). The paper gives no constants, so this
+2009, cited in Sect. 4.4), stopped early with an accuracy that tightens over
+the Frank-Wolfe iterations (Sect. 5.1). The paper gives no constants, so this
 module fixes them (the same readings are used by the GPU path):
 
   * step 1/L with L = 1.01 x the largest eigenvalue of Re(A^H A), the Hessian
@@ -20,7 +20,7 @@ coordinate_descent and brute_force are independent LASSO solvers used only to
 pin apgd and the Frank-Wolfe loop on tiny problems.
 
 positive=True solves the positivity-constrained variant (the remarks on a
-positivity constraint in Sect. 3.1 and 4.1): x >= 0, the proximal map of
+positivity constraint in Sect. 4.1 and 5.1): x >= 0, the proximal map of
 t ||.||_1 + indicator(x >= 0) is max(z - t, 0).
 """
 from __future__ import annotations

@@ -89,14 +89,14 @@ def dirty_image(uvw, N, fov, V) -> np.ndarray:
 
 
 def lambda_max(uvw, N, fov, V) -> float:
-    """lambda_max = ||Phi* V||_inf (Sect. 4.4): the smallest lambda with x = 0 optimal."""
+    """lambda_max = ||Phi* V||_inf (Sect. 5.3): the smallest lambda with x = 0 optimal."""
     return float(np.max(np.abs(adjoint(uvw, N, fov, V))))
 
 
 def lambda_max_positive(uvw, N, fov, V) -> float:
     """max(0, max_p Phi*(V)_p): the smallest lambda for which x = 0 is optimal
     when the image is constrained to be non-negative (the positivity variant of
-    Sect. 3.1 / 4.1): the optimality condition at 0 is Phi*(V) <= lambda."""
+    Sect. 4.1 / 4.1): the optimality condition at 0 is Phi*(V) <= lambda."""
     return max(0.0, float(np.max(adjoint(uvw, N, fov, V))))
 
 
@@ -106,12 +106,12 @@ def residual(uvw, N, fov, V, idx, x) -> np.ndarray:
 
 
 def objective(uvw, N, fov, V, lam, idx, x) -> float:
-    """LASSO objective 1/2 ||V - Phi x||^2 + lambda ||x||_1 (Sect. 3.1)."""
+    """LASSO objective 1/2 ||V - Phi x||^2 + lambda ||x||_1 (Sect. 4.1)."""
     r = residual(uvw, N, fov, V, idx, x)
     return 0.5 * float(np.vdot(r, r).real) + lam * float(np.sum(np.abs(x)))
 
 
 def certificate(uvw, N, fov, V, lam, idx, x, pix=None) -> np.ndarray:
-    """Empirical dual certificate mu = Phi*(V - Phi x) / lambda (Sect. 3.2)."""
+    """Empirical dual certificate mu = Phi*(V - Phi x) / lambda (Sect. 4.2)."""
     r = residual(uvw, N, fov, V, idx, x)
     return adjoint(uvw, N, fov, r, pix) / lam

@@ -1,6 +1,6 @@
 """Polyatomic Frank-Wolfe (Algorithm 2) in FP64 (test infrastructure only).
 
-Steps per iteration k = 0, 1, 2, ... (Algorithm 2 with Sect. 4.1):
+Steps per iteration k = 0, 1, 2, ... (Algorithm 2 with Sect. 5.1):
 
   0. dirty residual    eta_k = Phi*(V - Phi I_k)     (on every pixel)
   1a. exploration      I_{k+1} = select(eta_k)
@@ -13,14 +13,14 @@ Steps per iteration k = 0, 1, 2, ... (Algorithm 2 with Sect. 4.1):
 Readings where the paper gives no value (the GPU path uses the same ones):
 
   * select rule "R2" (default): I = {p : |mu_k[p]| >= 1 - delta}, mu_k = eta_k / lambda,
-    the empirical dual certificate (Sect. 3.2 / 4.1);
+    the empirical dual certificate (Sect. 4.2 / 4.1);
     select rule "R1" (the literal exploration set of Algorithm 2):
     I = {p : |eta_k[p]| >= ||eta_k||_inf - 2 Delta / (k + 2)}, Delta = (1 - delta) lambda_max;
   * eps_k = max(eps_min, eps0 * 2^-k), eps0 = 1e-2, eps_min = 1e-5;
   * objective F_k = 1/2 ||V - Phi I_k||^2 + lambda ||I_k||_1, F_0 = 1/2 ||V||^2;
-  * tol = 1e-4 (Sect. 5.1), at most max_fw iterations.
+  * tol = 1e-4 (Sect. 6.1), at most max_fw iterations.
 
-positive=True is the positivity-constrained variant (remark in Sect. 4.1):
+positive=True is the positivity-constrained variant (remark in Sect. 5.1):
 candidates only at positive values of the certificate (R2: mu >= 1 - delta;
 R1: eta >= max(eta) - 2 Delta/(k + 2) with eta > 0, Delta from
 lambda_max_positive), and the reweighting with x >= 0.

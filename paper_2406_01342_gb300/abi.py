@@ -30,7 +30,8 @@ EXPORTS = [
     "pc_adjoint_sparse", "pc_adjoint_grid", "pc_lambda_max", "pc_certificate", "pc_select",
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
-    "pc_profile_begin_classes",
+    "pc_profile_begin_classes", "pc_server_create", "pc_server_submit", "pc_server_wait",
+    "pc_server_destroy",
 ]
 
 
@@ -44,6 +45,17 @@ class pc_plan_opts(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("max_planes", ctypes.c_int32),
                 ("grid_mode", ctypes.c_int32)]
+
+
+class pc_server_opts(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int32), ("max_jobs", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("batch_apgd", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class pc_job_times(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("finished", ctypes.c_double)]
 
 
 class pc_solve_opts(ctypes.Structure):
@@ -118,6 +130,11 @@ def load(path: str | None = None):
         "pc_adjoint_sparse_noalloc": (_I32, [_P, _I64, _I32, _D, _P, _P, _I32, _P, _P]),
         "pc_profile_begin": (_I32, []),
         "pc_profile_begin_classes": (_I32, [ctypes.c_char_p]),
+        "pc_server_create": (_I32, [_P, ctypes.POINTER(_P)]),
+        "pc_server_submit": (_I32, [_P, _P, _P, _I64, _I32, _D, _D, _D, _P, ctypes.POINTER(_I64)]),
+        "pc_server_wait": (_I32, [_P, _I64, _P, _P, _I32, ctypes.POINTER(pc_solve_stats),
+                                  ctypes.POINTER(pc_job_times)]),
+        "pc_server_destroy": (None, [_P]),
         "pc_profile_end": (_I32, [ctypes.POINTER(pc_kernel_time), _I32, ctypes.POINTER(_I32)]),
         "pc_last_error": (ctypes.c_char_p, []),
         "pc_abi_version": (_I32, []),
@@ -331,7 +348,8 @@ def pc_solve_host(uvw, V, N: int, fov: float, alpha: float, delta: float, cap: i
     _check(status, allow=(PC_OK, PC_ERR_NOT_CONVERGED))
     n = st.n_support
     return dict(idx=idx[:n].copy(), x=x[:n].copy(), status=st.status, iterations=st.iterations,
-                objective=st.objective, lam=st.lambda_, mu_inf=st.mu_inf)
+                objective=st.objective, lam=st.lambda_, mu_inf=st.mu_inf,
+                converged=status == PC_OK)
 
 
 def pc_profile_begin(classes: str | None = None) -> None:
@@ -362,3 +380,52 @@ def pc_adjoint_sparse_noalloc(uvw: torch.Tensor, N: int, fov: float, y: torch.Te
         _dev(y, torch.complex64, "y") if M else None, _dev(idx, torch.int32, "idx"),
         int(idx.numel()), _dev(out, torch.float32, "out"), _stream(stream)))
     return out
+
+
+class Server:
+    """Continuous-batching request loop of the library (pc_server_*): submit
+    imaging requests from the host at any time, collect each result with wait()."""
+
+    def __init__(self, max_jobs: int = 8, memory_budget: int = 0, batch_apgd: int = 1):
+        lib = load()
+        o = pc_server_opts(PC_ABI_VERSION, max_jobs, memory_budget, batch_apgd, 0)
+        h = _P()
+        _check(lib.pc_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, uvw, V, N: int, fov: float, alpha: float, delta: float, **opts) -> int:
+        import numpy as np
+        uvw_np = np.ascontiguousarray(np.asarray(uvw, dtype=np.float64))
+        V_np = np.ascontiguousarray(np.asarray(V, dtype=np.complex64))
+        o = _solve_opts(**opts)
+        jid = _I64()
+        _check(load().pc_server_submit(self.handle, uvw_np.ctypes.data, V_np.ctypes.data,
+                                       int(V_np.shape[0]), int(N), float(fov), float(alpha),
+                                       float(delta), ctypes.byref(o), ctypes.byref(jid)))
+        return jid.value
+
+    def wait(self, job: int, cap: int = 1 << 20) -> dict:
+        import numpy as np
+        idx = np.empty(max(cap, 1), dtype=np.int32)
+        x = np.empty(max(cap, 1), dtype=np.float32)
+        st = pc_solve_stats()
+        tm = pc_job_times()
+        status = load().pc_server_wait(self.handle, int(job), idx.ctypes.data, x.ctypes.data, int(cap),
+                                       ctypes.byref(st), ctypes.byref(tm))
+        _check(status, allow=(PC_OK, PC_ERR_NOT_CONVERGED))
+        n = st.n_support
+        return dict(idx=idx[:n].copy(), x=x[:n].copy(), status=st.status, iterations=st.iterations,
+                    objective=st.objective, lam=st.lambda_, converged=status == PC_OK,
+                    submitted=tm.submitted, admitted=tm.admitted, finished=tm.finished,
+                    latency=tm.finished - tm.submitted)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

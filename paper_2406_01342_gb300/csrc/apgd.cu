@@ -1,5 +1,5 @@
 // Restricted LASSO solve of step 2 of Algorithm 2 by accelerated proximal
-// gradient (FISTA, the APGD the paper names in Sect. 3.4 / 4.1) on the Gram
+// gradient (FISTA, the APGD the paper names in Sect. 4.4 / 4.1) on the Gram
 // form of the support problem:
 //
 //   f(x) = 1/2 x^T G x - b^T x + lambda ||x||_1,   G = Re(Phi_S^H Phi_S), b = Re(Phi_S^H V)
@@ -96,6 +96,14 @@ struct ApgdArgs {
   int n_pad;
   int cache;      // 1: rows of G cached in shared memory
   int vec_ok;     // 1: float4 loads of G rows are aligned
+};
+
+// Several independent restricted problems in one launch: cluster c of the
+// grid solves job c (all jobs of a launch share the cluster size).
+constexpr int APGD_BATCH_MAX = 16;
+struct ApgdBatch {
+  ApgdArgs job[APGD_BATCH_MAX];
+  int n_jobs;
 };
 
 constexpr int APGD_THREADS = 256;
@@ -291,12 +299,13 @@ __device__ float tridiag_top(const float* al, const float* be, int m, float* s_o
   return *s_out;
 }
 
-__global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(ApgdArgs a) {
+__global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(const __grid_constant__ ApgdBatch batch) {
   extern __shared__ __align__(16) float apgd_sm[];
   __shared__ Df scratch[(APGD_THREADS / 32) * NPART];
   __shared__ Df s_tot[NPART];
   __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
   cg::cluster_group cl = cg::this_cluster();
+  const ApgdArgs& a = batch.job[blockIdx.x / cl.num_blocks()];
   const int rank = (int)cl.block_rank();
   const Smem s = carve(apgd_sm, a);
   const int r0 = rank * a.rows_per;
@@ -649,7 +658,7 @@ __device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* v
   return b ? s.rx1 : s.rx0;
 }
 
-__global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
+__global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(const __grid_constant__ ApgdBatch batch) {
   extern __shared__ __align__(16) float apgdf_sm[];
   __shared__ Df scratch[(APGD_THREADS / 32) * NPART];
   __shared__ Df s_part[NPART];
@@ -657,6 +666,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
   __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
   __shared__ __align__(8) uint64_t s_rxbar[2];
   cg::cluster_group cl = cg::this_cluster();
+  const ApgdArgs& a = batch.job[blockIdx.x / cl.num_blocks()];
   const int rank = (int)cl.block_rank();
   const SmemF s = carve_full(apgdf_sm, a);
   const int r0 = rank * a.rows_per;
@@ -830,15 +840,26 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(ApgdArgs a) {
 
 }  // namespace
 
-int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
-             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
-             int* lanczos, int* err, bool positive) {
-  if (S <= 0) return PC_OK;
+namespace {
+
+// Launch shape of one restricted problem: which kernel, cluster size, rows per
+// CTA, whether the CTAs cache their rows of G, dynamic shared memory.
+struct ApgdShape {
+  bool full;
+  int CS;
+  int rows_per;
+  int cache;
+  int n_pad;
+  size_t smem;
+};
+
+// dynamic shared memory ceilings: 227 KB per CTA minus the kernels' static arrays
+constexpr size_t kLimitRows = 200 * 1024;
+constexpr size_t kLimitFull = 226 * 1024;
+
+int apgd_setup(int* cs_max_out) {
   static int cs_max = 0;
   static bool attrs_set = false;
-  // dynamic shared memory ceilings: 227 KB per CTA minus the kernels' static arrays
-  const size_t limit_rows = 200 * 1024;
-  const size_t limit_full = 226 * 1024;
   if (cs_max == 0) {
     cudaError_t e1 = cudaFuncSetAttribute(k_apgd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaError_t e2 = cudaFuncSetAttribute(k_apgd_full, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -846,11 +867,16 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
     cudaGetLastError();
   }
   if (!attrs_set) {
-    PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit_rows));
+    PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLimitRows));
     PC_CUDA(cudaFuncSetAttribute(k_apgd_full, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)limit_full));
+                                 (int)kLimitFull));
     attrs_set = true;
   }
+  *cs_max_out = cs_max;
+  return PC_OK;
+}
+
+int apgd_shape(int S, int cs_max, ApgdShape* out) {
   const int n_pad = (S + 3) & ~3;
   // full-vector kernel: 2 local slices, 2 receive buffers and 6 full vectors
   // (+ cached rows of G); its slices hold a multiple of 4 rows (bulk copies)
@@ -868,71 +894,106 @@ int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, doub
   // cluster size: the smallest power of two whose CTAs each cache at most
   // ~64 KB of G in shared memory (a matrix-vector product then streams it in
   // ~500 cycles), else the smallest that caches G at all, else cs_max
-  bool full = true;
-  int CS = 1;
+  ApgdShape sh;
+  sh.full = true;
+  sh.CS = 1;
   const size_t share_target = 64 * 1024;
-  while (CS < cs_max && (bytes_full(CS, true) > limit_full ||
-                         sizeof(float) * (size_t)rows_full(CS) * n_pad > share_target))
-    CS *= 2;
-  int cache = bytes_full(CS, true) <= limit_full ? 1 : 0;
-  size_t smem = bytes_full(CS, cache != 0);
-  if (smem > limit_full) {
-    full = false;
-    CS = 1;
-    while (CS < cs_max && bytes_rows(CS, true) > limit_rows) CS *= 2;
-    if (bytes_rows(CS, false) > limit_rows)
+  while (sh.CS < cs_max && (bytes_full(sh.CS, true) > kLimitFull ||
+                            sizeof(float) * (size_t)rows_full(sh.CS) * n_pad > share_target))
+    sh.CS *= 2;
+  sh.cache = bytes_full(sh.CS, true) <= kLimitFull ? 1 : 0;
+  sh.smem = bytes_full(sh.CS, sh.cache != 0);
+  if (sh.smem > kLimitFull) {
+    sh.full = false;
+    sh.CS = 1;
+    while (sh.CS < cs_max && bytes_rows(sh.CS, true) > kLimitRows) sh.CS *= 2;
+    if (bytes_rows(sh.CS, false) > kLimitRows)
       return fail(PC_ERR_CAPACITY, "apgd: support of %d atoms exceeds the cluster solver", S);
-    cache = bytes_rows(CS, true) <= limit_rows ? 1 : 0;
-    smem = bytes_rows(CS, cache != 0);
+    sh.cache = bytes_rows(sh.CS, true) <= kLimitRows ? 1 : 0;
+    sh.smem = bytes_rows(sh.CS, sh.cache != 0);
   }
-  const int rows_per = full ? rows_full(CS) : ceil_div(S, CS);
-
-  ApgdArgs a;
-  a.G = G;
-  a.ldg = ldg;
-  a.b = b;
-  a.n = S;
-  a.lam = (float)lambda;
-  a.eps = (float)eps;
-  a.max_iter = max_iter;
-  a.x = x;
-  a.out_iters = iters;
-  a.out_L = L;
-  a.out_F = Fx;
-  a.out_lanczos = lanczos;
-  a.err = err;
-  a.positive = positive ? 1 : 0;
-  a.rows_per = rows_per;
-  a.n_pad = n_pad;
-  a.cache = cache;
-  a.vec_ok = ((ldg & 3) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0) ? 1 : 0;
-
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CS, 1, 1);
-  cfg.blockDim = dim3(APGD_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e;
-  {
-    ProfScope prof_scope_(PROF_APGD, st);
-    prof_scope_.kernels = 1;
-    e = full ? cudaLaunchKernelEx(&cfg, k_apgd_full, a) : cudaLaunchKernelEx(&cfg, k_apgd, a);
-  }
-  if (e != cudaSuccess && CS == 16) {
-    // fall back to a portable cluster size
-    cudaGetLastError();
-    cs_max = 8;
-    return run_apgd(G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, st, lanczos, err, positive);
-  }
-  PC_CUDA(e);
+  sh.rows_per = sh.full ? rows_full(sh.CS) : ceil_div(S, sh.CS);
+  sh.n_pad = n_pad;
+  *out = sh;
   return PC_OK;
+}
+
+ApgdArgs make_args(const ApgdJob& j, const ApgdShape& sh) {
+  ApgdArgs a;
+  a.G = j.G;
+  a.ldg = j.ldg;
+  a.b = j.b;
+  a.n = j.n;
+  a.lam = (float)j.lambda;
+  a.eps = (float)j.eps;
+  a.max_iter = j.max_iter;
+  a.x = j.x;
+  a.out_iters = j.iters;
+  a.out_L = j.L;
+  a.out_F = j.F;
+  a.out_lanczos = j.lanczos;
+  a.err = j.err;
+  a.positive = j.positive ? 1 : 0;
+  a.rows_per = sh.rows_per;
+  a.n_pad = sh.n_pad;
+  a.cache = sh.cache;
+  a.vec_ok = ((j.ldg & 3) == 0 && (reinterpret_cast<uintptr_t>(j.G) & 15) == 0) ? 1 : 0;
+  return a;
+}
+
+}  // namespace
+
+int run_apgd_jobs(const ApgdJob* jobs, int n_jobs, cudaStream_t st) {
+  int cs_max = 0;
+  PC_TRY(apgd_setup(&cs_max));
+  std::vector<ApgdShape> shapes(n_jobs);
+  for (int i = 0; i < n_jobs; ++i)
+    if (jobs[i].n > 0) PC_TRY(apgd_shape(jobs[i].n, cs_max, &shapes[i]));
+  std::vector<char> done(n_jobs, 0);
+  for (int i = 0; i < n_jobs; ++i)
+    if (jobs[i].n <= 0) done[i] = 1;
+  // one launch per (kernel, cluster size) group, at most APGD_BATCH_MAX jobs each
+  for (int i = 0; i < n_jobs; ++i) {
+    if (done[i]) continue;
+    ApgdBatch batch{};
+    size_t smem = 0;
+    const bool full = shapes[i].full;
+    const int CS = shapes[i].CS;
+    for (int j = i; j < n_jobs && batch.n_jobs < APGD_BATCH_MAX; ++j) {
+      if (done[j] || shapes[j].full != full || shapes[j].CS != CS) continue;
+      batch.job[batch.n_jobs++] = make_args(jobs[j], shapes[j]);
+      smem = std::max(smem, shapes[j].smem);
+      done[j] = 1;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS * batch.n_jobs, 1, 1);
+    cfg.blockDim = dim3(APGD_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    {
+      ProfScope prof_scope_(PROF_APGD, st);
+      prof_scope_.kernels = 1;
+      e = full ? cudaLaunchKernelEx(&cfg, k_apgd_full, batch) : cudaLaunchKernelEx(&cfg, k_apgd, batch);
+    }
+    PC_CUDA(e);
+  }
+  return PC_OK;
+}
+
+int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
+             int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
+             int* lanczos, int* err, bool positive) {
+  if (S <= 0) return PC_OK;
+  ApgdJob j{G, ldg, b, S, lambda, eps, max_iter, x, iters, L, Fx, lanczos, err, positive};
+  return run_apgd_jobs(&j, 1, st);
 }
 
 }  // namespace pc

@@ -9,7 +9,7 @@
 // with c_ij = e^{j 2 pi w0 s_ij} / (n_ij psi(i'/G) psi(j'/G) psi(t_ij)),
 // t_ij = dw (s_ij - s_c), s = n - 1 (the w-screen of Sect. 2.1 and the
 // 1/n of the adjoint equation of Sect. 2.2); scale = 1/lambda for the
-// certificate of Sect. 3.2.
+// certificate of Sect. 4.2.
 //
 // Pass 1 (k_fft_rows): for each plane and row b, a length-G inverse FFT
 // along a, keeping the N outputs i' in [-N/2, N/2), stored transposed as

@@ -1,6 +1,6 @@
 // Gridding (type-1 spreading) of a visibility vector onto the w-stacked,
 // oversampled uv grid: the first step of evaluating the adjoint of Sect. 2.2
-// as a non-uniform FFT (Sect. 4.2). For plane q:
+// as a non-uniform FFT (Sect. 5.2). For plane q:
 //
 //   grid_q[b][a] += h_k tau_k phi(a - g_u,k) phi(b - g_v,k) phi(q - x_w,k)
 //

@@ -1,5 +1,5 @@
 // Gridding (type-1 spreading, the first step of the adjoint of Sect. 2.2
-// evaluated as a non-uniform FFT, Sect. 4.2) on the tensor cores.
+// evaluated as a non-uniform FFT, Sect. 5.2) on the tensor cores.
 //
 // For one gridding sub-problem -- a 32 x 32 tile, a group of Q <= 8 w-planes
 // and its K <= 1024 binned visibilities -- the spread is a contraction over

@@ -162,12 +162,31 @@ int launch_compact_old(const int32_t* oldpos, int n, int32_t* rows, int32_t* cou
                        cudaStream_t st);
 
 // apgd.cu
+// One restricted LASSO for the batched APGD (run_apgd_jobs): several jobs in one launch.
+struct ApgdJob {
+  const float* G;
+  int ldg;
+  const float* b;
+  int n;
+  double lambda, eps;
+  int max_iter;
+  float* x;
+  int* iters;
+  double* L;
+  double* F;
+  int* lanczos;
+  int* err;
+  bool positive;
+};
+int run_apgd_jobs(const ApgdJob* jobs, int n_jobs, cudaStream_t st);
 int run_apgd(const float* G, int ldg, const float* b, int S, double lambda, double eps,
              int max_iter, float* x, int* iters, double* L, double* Fx, cudaStream_t st,
              int* lanczos = nullptr, int* err = nullptr, bool positive = false);
 
 // grid.cu / fft.cu
 int launch_grid(pc_plan_s* p, const float2* r, cudaStream_t st);
+// plan.cu: upper estimate of a plan's device bytes (with its solve), for admission by memory
+int64_t plan_bytes_estimate(int64_t M, int N, double fov, double w_min, double w_max, int W = 7);
 // grid_tc.cu: tensor-core gridding (w-stacking plans); err_dev set to 1 if a bounded wait expired
 int launch_grid_tc(pc_plan_s* p, const float2* h, int* err_dev, cudaStream_t st);
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st);

@@ -2,7 +2,7 @@
 // radix sort, sub-problem list, per-pixel kernel-correction table, workspace.
 //
 // The adjoint Phi* of Sect. 2.2 is evaluated as a type-1 non-uniform FFT
-// (Sect. 4.2): each visibility is spread with an exponential-of-semicircle
+// (Sect. 5.2): each visibility is spread with an exponential-of-semicircle
 // kernel of width W onto a 2x (or more) oversampled uv grid of side G, and
 // onto P w-planes (w-stacking, the w-term of Sect. 2.1); every plane is
 // inverse-FFT'd and the image is corrected for the kernel's Fourier transform,
@@ -602,6 +602,36 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   }
   PC_CUDA(cudaStreamSynchronize(st));
   return PC_OK;
+}
+
+// Device bytes a plan and its solve may hold (an upper estimate used to admit
+// jobs by memory): the gridding planes, the pass-1 FFT buffer, the pixel
+// tables, the binned visibilities, the working set of the solver and the
+// tensor-core phase buffer (chunked at 2 GB).
+int64_t plan_bytes_estimate(int64_t M, int N, double fov, double w_min, double w_max, int W) {
+  int64_t G = 32;
+  while (G < 2 * N) G *= 2;
+  const double dl = fov / N;
+  const double half = 0.5 * N * dl;
+  const double r2c = 2.0 * half * half;
+  const double s_min = -r2c / (1.0 + std::sqrt(std::max(1.0 - r2c, 1e-12)));
+  int64_t P = 1;
+  if (M > 0 && w_max > w_min) {
+    const double dw = 1.0 / (2.0 * (0.0 - s_min));
+    P = (int64_t)std::ceil((w_max - w_min) / dw) + W;
+  }
+  const int64_t groups = (P + 7) / 8;
+  const int64_t NN = (int64_t)N * N;
+  int64_t b = 0;
+  b += P * G * G * 8;                       // grid planes
+  b += P * N * G * 8;                       // pass-1 FFT output
+  b += NN * (16 + 4 + 1 + 4);               // pixel table, mu, marks, selection
+  b += M * (16 + 8);                        // fixed-point visibilities, residual
+  b += M * groups * 2 * 24;                 // binned slots (replication into tiles and plane groups)
+  b += 2 * 4096ll * 4096ll * 4;             // Gram working set (grown on demand; 4096 atoms)
+  b += std::min<int64_t>(2ll << 30, 1024 * M * 8);   // phase buffer of the tensor-core Gram
+  b += 64ll << 20;                          // scratch
+  return b;
 }
 
 }  // namespace pc

@@ -8,6 +8,7 @@
 #include <map>
 
 #include "pc_internal.cuh"
+#include "solver.cuh"
 
 namespace pc {
 namespace {
@@ -429,35 +430,20 @@ extern "C" int pc_apgd(const float* G, int32_t ldg, const float* b, int32_t S, d
 
 // ------------------------------------------------------------------ the solver
 
+namespace pc {
 namespace {
 
 inline int round4(int n) { return (n + 3) & ~3; }
 
-struct SolveCfg {
-  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0;
-  double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
-};
-
 }  // namespace
 
-extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double delta,
-                        const pc_solve_opts* opts, int32_t* idx_out, float* x_out, int32_t cap,
-                        float* mu_out, pc_solve_stats* stats, pc_iter_record* hist,
-                        int32_t hist_cap, void* stream) {
-  clear_error();
-  PC_TRY(check_plan(p, "pc_solve"));
-  if (opts && opts->version != PC_ABI_VERSION)
-    return fail(PC_ERR_INVALID_ARG, "pc_solve: opts->version %d != %d", opts->version, PC_ABI_VERSION);
-  if (!(lambda > 0.0) || !std::isfinite(lambda))
-    return fail(PC_ERR_INVALID_ARG, "pc_solve: lambda must be positive and finite");
-  if (!(delta > 0.0 && delta <= 1.0)) return fail(PC_ERR_INVALID_ARG, "pc_solve: delta must be in (0, 1]");
-  if (cap < 0 || hist_cap < 0) return fail(PC_ERR_INVALID_ARG, "pc_solve: negative capacity");
-  PC_TRY(check_dev(V_, p->M > 0, "pc_solve", "V_dev"));
-  PC_TRY(check_dev(idx_out, cap > 0, "pc_solve", "idx_out_dev"));
-  PC_TRY(check_dev(x_out, cap > 0, "pc_solve", "x_out_dev"));
-  if (mu_out) PC_TRY(check_dev(mu_out, true, "pc_solve", "mu_out_dev"));
+// ------------------------------------------------------------------ the solve as a job
+
+int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
   SolveCfg c;
   if (opts) {
+    if (opts->version != PC_ABI_VERSION)
+      return fail(PC_ERR_INVALID_ARG, "%s: opts->version %d != %d", fn, opts->version, PC_ABI_VERSION);
     if (opts->select_rule) c.rule = opts->select_rule;
     if (opts->max_fw) c.max_fw = opts->max_fw;
     if (opts->apgd_max_iter) c.apgd_max = opts->apgd_max_iter;
@@ -468,217 +454,246 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     c.gram_mode = opts->gram_mode;
     c.positive = opts->positivity;
   }
-  if (c.positive != 0 && c.positive != 1) return fail(PC_ERR_INVALID_ARG, "pc_solve: positivity must be 0 or 1");
-  if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: select_rule must be 1 or 2");
-  if (c.gram_mode < 0 || c.gram_mode > 2) return fail(PC_ERR_INVALID_ARG, "pc_solve: gram_mode must be 0, 1 or 2");
-  cudaStream_t st = SS(stream);
-  const float2* V = reinterpret_cast<const float2*>(V_);
-  const int64_t npix = (int64_t)p->N * p->N;
-  const float inv_lam = (float)(1.0 / lambda);
+  if (c.positive != 0 && c.positive != 1) return fail(PC_ERR_INVALID_ARG, "%s: positivity must be 0 or 1", fn);
+  if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "%s: select_rule must be 1 or 2", fn);
+  if (c.gram_mode < 0 || c.gram_mode > 2) return fail(PC_ERR_INVALID_ARG, "%s: gram_mode must be 0, 1 or 2", fn);
+  if (c.max_fw < 1 || c.apgd_max < 1) return fail(PC_ERR_INVALID_ARG, "%s: iteration caps must be positive", fn);
+  *out = c;
+  return PC_OK;
+}
 
-  // capacities of the working set (grown on demand)
-  int wcap = 1024;
-  auto grow = [&](int need) -> int {
-    if (need <= wcap && p->idxB.p) return PC_OK;
-    while (wcap < need) wcap *= 2;
-    const size_t g = (size_t)round4(wcap) * round4(wcap) * sizeof(float);
-    PC_TRY(p->idxA.ensure(sizeof(int32_t) * wcap));
-    PC_TRY(p->idxB.ensure(sizeof(int32_t) * wcap));
-    PC_TRY(p->xA.ensure(sizeof(float) * wcap));
-    PC_TRY(p->xB.ensure(sizeof(float) * wcap));
-    PC_TRY(p->bA.ensure(sizeof(float) * wcap));
-    PC_TRY(p->bB.ensure(sizeof(float) * wcap));
-    PC_TRY(p->oldpos.ensure(sizeof(int32_t) * wcap));
-    PC_TRY(p->newrows.ensure(sizeof(int32_t) * wcap));
-    PC_TRY(p->keep.ensure(sizeof(int32_t) * wcap));
-    PC_TRY(p->atomsA.ensure(sizeof(float4) * wcap));
-    PC_TRY(p->atomsB.ensure(sizeof(float4) * wcap));
-    PC_TRY(p->GA.ensure(g));
-    PC_TRY(p->GB.ensure(g));
-    return PC_OK;
-  };
+SolveJob::~SolveJob() {
+  if (rb) cudaFreeHost(rb);
+  if (ev) cudaEventDestroy(ev);
+}
+
+int SolveJob::grow(int need) {
+  if (need <= wcap && p->idxB.p) return PC_OK;
+  while (wcap < need) wcap *= 2;
+  const size_t g = (size_t)round4(wcap) * round4(wcap) * sizeof(float);
+  PC_TRY(p->idxA.ensure(sizeof(int32_t) * wcap));
+  PC_TRY(p->idxB.ensure(sizeof(int32_t) * wcap));
+  PC_TRY(p->xA.ensure(sizeof(float) * wcap));
+  PC_TRY(p->xB.ensure(sizeof(float) * wcap));
+  PC_TRY(p->bA.ensure(sizeof(float) * wcap));
+  PC_TRY(p->bB.ensure(sizeof(float) * wcap));
+  PC_TRY(p->oldpos.ensure(sizeof(int32_t) * wcap));
+  PC_TRY(p->newrows.ensure(sizeof(int32_t) * wcap));
+  PC_TRY(p->keep.ensure(sizeof(int32_t) * wcap));
+  PC_TRY(p->atomsA.ensure(sizeof(float4) * wcap));
+  PC_TRY(p->atomsB.ensure(sizeof(float4) * wcap));
+  PC_TRY(p->GA.ensure(g));
+  PC_TRY(p->GB.ensure(g));
+  return PC_OK;
+}
+
+int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double delta_,
+                    const SolveCfg& cfg, float* mu_out, pc_iter_record* hist_, int hist_cap_,
+                    cudaStream_t stream) {
+  p = plan;
+  st = stream;
+  V = V_dev;
+  lambda = lambda_;
+  delta = delta_;
+  c = cfg;
+  hist = hist_;
+  hist_cap = hist_cap_;
+  mu_dst = mu_out ? mu_out : p->mu;
+  PC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&rb), sizeof(Readback)));
+  PC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   PC_TRY(grow(1024));
-
   // ||V||^2 and r = V; counters, the pruned-support count and the tensor-core
   // flag cleared (the gridding flag iscal[7] may still report an earlier call)
   PC_CUDA(cudaMemsetAsync(p->iscal, 0, 7 * sizeof(int32_t), st));
   PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
   PC_TRY(launch_residual(p->vis_fx, V, p->M, nullptr, 0, p->resid, p->dscal, st));
-  double sumsqV = 0.0;
-  PC_TRY(sync_read(&sumsqV, p->dscal, sizeof(double), st));
-  {
-    const double d0 = (c.rule == 1 && c.lmax > 0) ? (1.0 - delta) * c.lmax : -1.0;
-    PC_CUDA(cudaMemcpyAsync(p->dscal + 4, &d0, sizeof(double), cudaMemcpyHostToDevice, st));
-  }
-  float* mu_dst = mu_out ? mu_out : p->mu;
-  float* thr_dev = reinterpret_cast<float*>(p->dscal + 5);
+  rb->hd[1] = (c.rule == 1 && c.lmax > 0) ? (1.0 - delta) * c.lmax : -1.0;   // Delta of rule R1
+  PC_CUDA(cudaMemcpyAsync(p->dscal + 4, &rb->hd[1], sizeof(double), cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaMemcpyAsync(&rb->hd[0], p->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  sumsqV = rb->hd[0];
+  F_prev = F = 0.5 * sumsqV;
+  return queue_iteration();
+}
+
+bool SolveJob::ready() const { return cudaEventQuery(ev) == cudaSuccess; }
+
+int SolveJob::explore() {
+  const int64_t npix = (int64_t)p->N * p->N;
   int32_t* n_sup_dev = p->iscal + 3;      // support count after the last pruning
-
-  // One host synchronisation per Frank-Wolfe iteration: the pruning of the
-  // previous reweighting, the residual and objective of the iterate, its
-  // certificate and the exploration set are queued with every count kept on
-  // the device; then the host reads the objective, the certificate maxima,
-  // the new active-set size and the sub-solver statistics together.
-  int nS = 0, ldA = 4, n_prev_act = 0, ldB_prev = 4;
-  double F_prev = 0.5 * sumsqV, F = F_prev;
-  int n_hist = 0, k = 0, status = PC_ERR_NOT_CONVERGED;
-  double mu_inf = 0.0;
-  pc_iter_record cur{};
-  bool have_cur = false;
-
-  for (k = 0;; ++k) {
-    if (k > 0) {
-      // pruning of the previous reweighting: S = {x != 0}, in position order
-      const int32_t* keep = p->keep.as<int32_t>();
-      PC_TRY(gather_vec<int32_t>(p->idxB.as<int32_t>(), keep, n_prev_act, p->idxA.as<int32_t>(), 0, st,
-                                 n_sup_dev));
-      PC_TRY(gather_vec<float>(p->xB.as<float>(), keep, n_prev_act, p->xA.as<float>(), 0.f, st, n_sup_dev));
-      PC_TRY(gather_vec<float>(p->bB.as<float>(), keep, n_prev_act, p->bA.as<float>(), 0.f, st, n_sup_dev));
-      PC_TRY(gather_sym(p->GB.as<float>(), ldB_prev, keep, n_prev_act, p->GA.as<float>(), ldB_prev, st,
-                        n_sup_dev));
-      ldA = ldB_prev;
-      // residual and objective of the current iterate
-      PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
-      if (n_prev_act > 0) {
-        PC_TRY(launch_make_atoms(p->idxA.as<int32_t>(), p->xA.as<float>(), n_prev_act, p->N, p->dl,
-                                 p->atomsA.as<float4>(), st, n_sup_dev));
-        ProfScope prof_scope_(PROF_MISC, st);
-        prof_scope_.kernels = 1;
-        k_l1<<<1, 256, 0, st>>>(p->xA.as<float>(), n_prev_act, p->dscal + 1, n_sup_dev);
-        PC_LAUNCH_CHECK();
-      }
-      PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_prev_act, p->resid, p->dscal,
-                             st, n_sup_dev));
-    }
-    // certificate mu_k = Phi*(r) / lambda (written where the caller wants the final one)
-    PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
-    PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, inv_lam, p->uscal, st));
-    // exploration and union, ascending raster order
-    auto explore = [&]() -> int {
-      const float* thr_d = nullptr;
-      if (c.rule == 1) {
-        ProfScope prof_scope_(PROF_MISC, st);
-        prof_scope_.kernels = 1;
-        k_r1_threshold<<<1, 1, 0, st>>>(p->uscal, c.positive, lambda, delta, k, p->dscal + 4, thr_dev);
-        PC_LAUNCH_CHECK();
-        thr_d = thr_dev;
-      }
-      const int bound = std::max(n_prev_act, 1);
-      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 1, st, n_sup_dev));
-      PC_TRY(launch_select(mu_dst, npix, (float)(1.0 - delta), p->mark, p->idxB.as<int32_t>(), p->iscal,
-                           p->sel_blocks, wcap, st, c.positive != 0, thr_d));
-      PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 0, st, n_sup_dev));
-      return PC_OK;
-    };
-    PC_TRY(explore());
-    // the one synchronisation of the iteration
-    int32_t hi[8];
-    double hd[3];
-    unsigned mb[2];
-    PC_CUDA(cudaMemcpyAsync(hi, p->iscal, sizeof(hi), cudaMemcpyDeviceToHost, st));
-    PC_CUDA(cudaMemcpyAsync(hd, p->dscal, sizeof(hd), cudaMemcpyDeviceToHost, st));
-    PC_CUDA(cudaMemcpyAsync(mb, p->uscal, sizeof(mb), cudaMemcpyDeviceToHost, st));
-    PC_CUDA(cudaStreamSynchronize(st));
-    if (hi[7]) {
-      PC_CUDA(cudaMemsetAsync(p->iscal + 7, 0, sizeof(int32_t), st));
-      return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded tensor-core gridding wait expired");
-    }
-    if (hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded device wait expired");
-    mu_inf = (double)bits_to_float(mb[0]);
-    if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
-    const double mu_top = c.positive ? (double)key_to_float(mb[1]) : mu_inf;
-    if (k > 0) {
-      nS = hi[3];
-      F = 0.5 * hd[0] + lambda * hd[1];
-      const double rel = F_prev > 0 ? (F_prev - F) / F_prev : 0.0;
-      if (have_cur) {
-        cur.n_support = nS;
-        cur.apgd_iterations = hi[2];
-        cur.lanczos_steps = hi[5];
-        cur.lipschitz = hd[2];
-        cur.objective = F;
-        cur.rel_improvement = rel;
-        if (n_hist < hist_cap && hist) hist[n_hist] = cur;
-        ++n_hist;
-        have_cur = false;
-      }
-      F_prev = F;
-      if (!std::isfinite(F)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite objective at iteration %d", k);
-      if (rel < c.tol) { status = PC_OK; break; }
-      if (k >= c.max_fw) { status = PC_ERR_NOT_CONVERGED; break; }
-    }
-    int n_act = hi[0];
-    while (n_act > wcap) {
-      if (n_act > 60000) return fail(PC_ERR_CAPACITY, "pc_solve: active set of %d atoms too large", n_act);
-      // grow, keeping the current support and weights
-      int32_t* old_idx = nullptr;
-      float* old_x = nullptr;
-      float* old_b = nullptr;
-      float* old_G = nullptr;
-      const int old_ld = ldA;
-      const size_t gbytes = (size_t)nS * old_ld * sizeof(float);
-      PC_CUDA(cudaMalloc(&old_idx, sizeof(int32_t) * std::max(nS, 1) * 3 + gbytes + 16));
-      old_x = reinterpret_cast<float*>(old_idx + std::max(nS, 1));
-      old_b = old_x + std::max(nS, 1);
-      old_G = old_b + std::max(nS, 1);
-      PC_CUDA(cudaMemcpyAsync(old_idx, p->idxA.p, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st));
-      PC_CUDA(cudaMemcpyAsync(old_x, p->xA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
-      PC_CUDA(cudaMemcpyAsync(old_b, p->bA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
-      PC_CUDA(cudaMemcpyAsync(old_G, p->GA.p, gbytes, cudaMemcpyDeviceToDevice, st));
-      PC_CUDA(cudaStreamSynchronize(st));
-      int rc = grow(n_act);
-      if (rc == PC_OK) {
-        cudaMemcpyAsync(p->idxA.p, old_idx, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(p->xA.p, old_x, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(p->bA.p, old_b, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(p->GA.p, old_G, gbytes, cudaMemcpyDeviceToDevice, st);
-        cudaStreamSynchronize(st);
-      }
-      cudaFree(old_idx);
-      PC_TRY(rc);
-      PC_LAUNCH_CHECK();
-      PC_TRY(explore());
-      PC_TRY(sync_read(&n_act, p->iscal, sizeof(int), st));
-    }
-    const int n_new = n_act - nS;
-    cur = pc_iter_record{};
-    cur.k = k;
-    cur.n_new = n_new;
-    cur.n_active = n_act;
-    cur.mu_inf = mu_top;
-    have_cur = true;
-
-    const int ldB = round4(std::max(n_act, 1));
-    if (n_act > 0) {
-      int32_t* oldpos = p->oldpos.as<int32_t>();
-      PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
-      PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
-      // old-old block, warm start and b of the old atoms
-      PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
-      PC_TRY(gather_vec<float>(p->xA.as<float>(), oldpos, n_act, p->xB.as<float>(), 0.f, st));
-      PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
-      // Gram rows of the new atoms against every active atom, and b
-      if (n_new > 0) {
-        PC_TRY(launch_make_atoms(p->idxB.as<int32_t>(), nullptr, n_act, p->N, p->dl,
-                                 p->atomsB.as<float4>(), st));
-        PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_new,
-                           oldpos, p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode,
-                           p->iscal + 4, st));
-      }
-      // reweighting: restricted LASSO by APGD
-      const double eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
-      PC_TRY(run_apgd(p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
-                      p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->dscal + 3, st, p->iscal + 5,
-                      p->iscal + 4, c.positive != 0));
-      // the nonzero positions; the gathers run at the start of the next iteration
-      PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), n_sup_dev, st));
-    } else {
-      PC_CUDA(cudaMemsetAsync(n_sup_dev, 0, sizeof(int32_t), st));
-    }
-    n_prev_act = n_act;
-    ldB_prev = ldB;
+  const float* thr_d = nullptr;
+  if (c.rule == 1) {
+    ProfScope prof_scope_(PROF_MISC, st);
+    prof_scope_.kernels = 1;
+    k_r1_threshold<<<1, 1, 0, st>>>(p->uscal, c.positive, lambda, delta, k, p->dscal + 4,
+                                    reinterpret_cast<float*>(p->dscal + 5));
+    PC_LAUNCH_CHECK();
+    thr_d = reinterpret_cast<float*>(p->dscal + 5);
   }
+  const int bound = std::max(n_prev_act, 1);
+  PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 1, st, n_sup_dev));
+  PC_TRY(launch_select(mu_dst, npix, (float)(1.0 - delta), p->mark, p->idxB.as<int32_t>(), p->iscal,
+                       p->sel_blocks, wcap, st, c.positive != 0, thr_d));
+  PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 0, st, n_sup_dev));
+  return PC_OK;
+}
 
+// One iteration up to its readback, with every count kept on the device: the
+// pruning of the previous reweighting, the residual and objective of the
+// iterate, its certificate and the exploration set.
+int SolveJob::queue_iteration() {
+  int32_t* n_sup_dev = p->iscal + 3;
+  if (k > 0) {
+    const int32_t* keep = p->keep.as<int32_t>();
+    PC_TRY(gather_vec<int32_t>(p->idxB.as<int32_t>(), keep, n_prev_act, p->idxA.as<int32_t>(), 0, st,
+                               n_sup_dev));
+    PC_TRY(gather_vec<float>(p->xB.as<float>(), keep, n_prev_act, p->xA.as<float>(), 0.f, st, n_sup_dev));
+    PC_TRY(gather_vec<float>(p->bB.as<float>(), keep, n_prev_act, p->bA.as<float>(), 0.f, st, n_sup_dev));
+    PC_TRY(gather_sym(p->GB.as<float>(), ldB_prev, keep, n_prev_act, p->GA.as<float>(), ldB_prev, st,
+                      n_sup_dev));
+    ldA = ldB_prev;
+    PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
+    if (n_prev_act > 0) {
+      PC_TRY(launch_make_atoms(p->idxA.as<int32_t>(), p->xA.as<float>(), n_prev_act, p->N, p->dl,
+                               p->atomsA.as<float4>(), st, n_sup_dev));
+      ProfScope prof_scope_(PROF_MISC, st);
+      prof_scope_.kernels = 1;
+      k_l1<<<1, 256, 0, st>>>(p->xA.as<float>(), n_prev_act, p->dscal + 1, n_sup_dev);
+      PC_LAUNCH_CHECK();
+    }
+    PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_prev_act, p->resid, p->dscal,
+                           st, n_sup_dev));
+  }
+  PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
+  PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, (float)(1.0 / lambda), p->uscal, st));
+  PC_TRY(explore());
+  PC_CUDA(cudaMemcpyAsync(rb->hi, p->iscal, sizeof(rb->hi), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaMemcpyAsync(rb->hd, p->dscal, sizeof(rb->hd), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaMemcpyAsync(rb->mb, p->uscal, sizeof(rb->mb), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaEventRecord(ev, st));
+  return PC_OK;
+}
+
+int SolveJob::process() {
+  need_apgd = false;
+  const Readback r = *rb;
+  if (r.hi[7]) {
+    PC_CUDA(cudaMemsetAsync(p->iscal + 7, 0, sizeof(int32_t), st));
+    return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded tensor-core gridding wait expired");
+  }
+  if (r.hi[4]) return fail(PC_ERR_TIMEOUT, "pc_solve: a bounded device wait expired");
+  mu_inf = (double)bits_to_float(r.mb[0]);
+  if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
+  const double mu_top = c.positive ? (double)key_to_float(r.mb[1]) : mu_inf;
+  if (k > 0) {
+    nS = r.hi[3];
+    F = 0.5 * r.hd[0] + lambda * r.hd[1];
+    const double rel = F_prev > 0 ? (F_prev - F) / F_prev : 0.0;
+    if (have_cur) {
+      cur.n_support = nS;
+      cur.apgd_iterations = r.hi[2];
+      cur.lanczos_steps = r.hi[5];
+      cur.lipschitz = r.hd[2];
+      cur.objective = F;
+      cur.rel_improvement = rel;
+      if (n_hist < hist_cap && hist) hist[n_hist] = cur;
+      ++n_hist;
+      have_cur = false;
+    }
+    F_prev = F;
+    if (!std::isfinite(F)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite objective at iteration %d", k);
+    if (rel < c.tol) {
+      status = PC_OK;
+      done = true;
+      return PC_OK;
+    }
+    if (k >= c.max_fw) {
+      status = PC_ERR_NOT_CONVERGED;
+      done = true;
+      return PC_OK;
+    }
+  }
+  n_act = r.hi[0];
+  while (n_act > wcap) {
+    if (n_act > 60000) return fail(PC_ERR_CAPACITY, "pc_solve: active set of %d atoms too large", n_act);
+    // grow, keeping the current support and weights
+    int32_t* old_idx = nullptr;
+    const size_t gbytes = (size_t)nS * ldA * sizeof(float);
+    PC_CUDA(cudaMalloc(&old_idx, sizeof(int32_t) * std::max(nS, 1) * 3 + gbytes + 16));
+    float* old_x = reinterpret_cast<float*>(old_idx + std::max(nS, 1));
+    float* old_b = old_x + std::max(nS, 1);
+    float* old_G = old_b + std::max(nS, 1);
+    PC_CUDA(cudaMemcpyAsync(old_idx, p->idxA.p, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(old_x, p->xA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(old_b, p->bA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(old_G, p->GA.p, gbytes, cudaMemcpyDeviceToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    int rc = grow(n_act);
+    if (rc == PC_OK) {
+      cudaMemcpyAsync(p->idxA.p, old_idx, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(p->xA.p, old_x, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(p->bA.p, old_b, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(p->GA.p, old_G, gbytes, cudaMemcpyDeviceToDevice, st);
+      cudaStreamSynchronize(st);
+    }
+    cudaFree(old_idx);
+    PC_TRY(rc);
+    PC_LAUNCH_CHECK();
+    PC_TRY(explore());
+    PC_TRY(sync_read(&n_act, p->iscal, sizeof(int), st));
+  }
+  const int n_new = n_act - nS;
+  cur = pc_iter_record{};
+  cur.k = k;
+  cur.n_new = n_new;
+  cur.n_active = n_act;
+  cur.mu_inf = mu_top;
+  have_cur = true;
+
+  ldB = round4(std::max(n_act, 1));
+  if (n_act > 0) {
+    int32_t* oldpos = p->oldpos.as<int32_t>();
+    PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
+    PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
+    // old-old block, warm start and b of the old atoms
+    PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
+    PC_TRY(gather_vec<float>(p->xA.as<float>(), oldpos, n_act, p->xB.as<float>(), 0.f, st));
+    PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
+    // Gram rows of the new atoms against every active atom, and b
+    if (n_new > 0) {
+      PC_TRY(launch_make_atoms(p->idxB.as<int32_t>(), nullptr, n_act, p->N, p->dl, p->atomsB.as<float4>(),
+                               st));
+      PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_new, oldpos,
+                         p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode, p->iscal + 4, st));
+    }
+    eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
+    need_apgd = true;
+    return PC_OK;
+  }
+  PC_CUDA(cudaMemsetAsync(p->iscal + 3, 0, sizeof(int32_t), st));
+  n_prev_act = 0;
+  ldB_prev = ldB;
+  ++k;
+  return queue_iteration();
+}
+
+ApgdJob SolveJob::apgd_job() const {
+  return ApgdJob{p->GB.as<float>(), ldB, p->bB.as<float>(), n_act, lambda, eps, c.apgd_max,
+                 p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->dscal + 3, p->iscal + 5,
+                 p->iscal + 4, c.positive != 0};
+}
+
+int SolveJob::after_apgd() {
+  need_apgd = false;
+  // the nonzero positions; the gathers run at the start of the next iteration
+  PC_TRY(launch_compact_nonzero(p->xB.as<float>(), n_act, p->keep.as<int32_t>(), p->iscal + 3, st));
+  n_prev_act = n_act;
+  ldB_prev = ldB;
+  ++k;
+  return queue_iteration();
+}
+
+int SolveJob::finish(int32_t* idx_out, float* x_out, int32_t cap, pc_solve_stats* stats) {
   if (stats) {
     stats->status = status;
     stats->iterations = k;
@@ -697,6 +712,41 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
   if (status == PC_ERR_NOT_CONVERGED)
     fail(PC_ERR_NOT_CONVERGED, "pc_solve: no convergence after %d Frank-Wolfe iterations", k);
   return status;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double delta,
+                        const pc_solve_opts* opts, int32_t* idx_out, float* x_out, int32_t cap,
+                        float* mu_out, pc_solve_stats* stats, pc_iter_record* hist,
+                        int32_t hist_cap, void* stream) {
+  clear_error();
+  PC_TRY(check_plan(p, "pc_solve"));
+  if (!(lambda > 0.0) || !std::isfinite(lambda))
+    return fail(PC_ERR_INVALID_ARG, "pc_solve: lambda must be positive and finite");
+  if (!(delta > 0.0 && delta <= 1.0)) return fail(PC_ERR_INVALID_ARG, "pc_solve: delta must be in (0, 1]");
+  if (cap < 0 || hist_cap < 0) return fail(PC_ERR_INVALID_ARG, "pc_solve: negative capacity");
+  PC_TRY(check_dev(V_, p->M > 0, "pc_solve", "V_dev"));
+  PC_TRY(check_dev(idx_out, cap > 0, "pc_solve", "idx_out_dev"));
+  PC_TRY(check_dev(x_out, cap > 0, "pc_solve", "x_out_dev"));
+  if (mu_out) PC_TRY(check_dev(mu_out, true, "pc_solve", "mu_out_dev"));
+  SolveCfg c;
+  PC_TRY(parse_solve_opts(opts, "pc_solve", &c));
+  cudaStream_t st = SS(stream);
+  SolveJob j;
+  PC_TRY(j.start(p, reinterpret_cast<const float2*>(V_), lambda, delta, c, mu_out, hist, hist_cap, st));
+  while (!j.done) {
+    PC_CUDA(cudaEventSynchronize(j.ev));
+    PC_TRY(j.process());
+    if (j.need_apgd) {
+      const ApgdJob aj = j.apgd_job();
+      PC_TRY(run_apgd_jobs(&aj, 1, st));
+      PC_TRY(j.after_apgd());
+    }
+  }
+  return j.finish(idx_out, x_out, cap, stats);
 }
 
 extern "C" int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32_t N,
@@ -733,7 +783,9 @@ extern "C" int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64
     rc = pc_plan_create(d_uvw, M, N, fov_rad, nullptr, stream, &plan);
     if (rc != PC_OK) break;
     double lmax = 0.0;
-    rc = pc_lambda_max(plan, d_V, &lmax, stream);
+    // under positivity lambda_max is max(0, max Phi* V) (the optimality condition at x = 0)
+    rc = (opts && opts->positivity) ? pc_lambda_max_positive(plan, d_V, &lmax, stream)
+                                    : pc_lambda_max(plan, d_V, &lmax, stream);
     if (rc != PC_OK) break;
     if (!(lmax > 0.0)) {   // V == 0: the solution is x = 0
       local.status = PC_OK;

@@ -1,0 +1,80 @@
+// The Frank-Wolfe solve of one plan as a resumable job (Algorithm 2 with the
+// reweighting of Sect. 5.1): each iteration is queued on the job's stream up
+// to one readback of the host-side decisions (objective, certificate maxima,
+// active-set size, flags) into pinned memory, marked by an event; after the
+// host processes it the job either finishes or queues the Gram update and
+// then needs its reweighting (APGD), which the caller launches -- alone
+// (pc_solve) or batched with other jobs in one launch (the serving loop) --
+// before queueing the next iteration.
+#pragma once
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+struct SolveCfg {
+  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0;
+  double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
+};
+
+// Validates and reads pc_solve_opts (NULL = defaults).
+int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out);
+
+struct SolveJob {
+  // ---- inputs
+  pc_plan_s* p = nullptr;
+  cudaStream_t st = nullptr;
+  const float2* V = nullptr;
+  double lambda = 0.0, delta = 0.0;
+  SolveCfg c;
+  float* mu_dst = nullptr;             // certificate of the iterate (the final one at the end)
+  pc_iter_record* hist = nullptr;
+  int hist_cap = 0;
+
+  // ---- state
+  int wcap = 1024;                      // working-set capacity (grown on demand)
+  int k = 0, nS = 0, ldA = 4, n_prev_act = 0, ldB_prev = 4, n_hist = 0;
+  int status = PC_ERR_NOT_CONVERGED;
+  bool done = false;
+  double F_prev = 0.0, F = 0.0, sumsqV = 0.0, mu_inf = 0.0;
+  pc_iter_record cur{};
+  bool have_cur = false;
+
+  // the reweighting this iteration needs (valid when need_apgd)
+  bool need_apgd = false;
+  int n_act = 0, ldB = 4;
+  double eps = 0.0;
+
+  // host readback of an iteration (pinned) and its completion event
+  struct Readback {
+    int32_t hi[8];
+    double hd[3];
+    unsigned mb[2];
+  };
+  Readback* rb = nullptr;
+  cudaEvent_t ev = nullptr;
+
+  ~SolveJob();
+  // Allocates the working set, computes ||V||^2 (synchronises) and queues iteration 0.
+  int start(pc_plan_s* plan, const float2* V_dev, double lambda, double delta, const SolveCfg& cfg,
+            float* mu_out, pc_iter_record* hist, int hist_cap, cudaStream_t stream);
+  // True when the queued iteration's readback has landed (non-blocking).
+  bool ready() const;
+  // Processes the readback: history, stop test (sets done), and, when the
+  // solve goes on, queues the Gram update and sets need_apgd (or queues the
+  // next iteration directly when the active set is empty).
+  int process();
+  // The job's reweighting as a batched-APGD entry.
+  ApgdJob apgd_job() const;
+  // After the reweighting: pruning count, then the next iteration's queue.
+  int after_apgd();
+  // Copies the support and weights (device) and fills the statistics.
+  int finish(int32_t* idx_out, float* x_out, int32_t cap, pc_solve_stats* stats);
+
+ private:
+  int grow(int need);
+  int explore();
+  int queue_iteration();
+};
+
+}  // namespace pc

@@ -1,5 +1,5 @@
 // Sparse-support operators (the forward equation of Sect. 2.2 restricted to
-// the active set of Algorithm 2, a type-3 sum in the paper's HVOX, Sect. 4.2)
+// the active set of Algorithm 2, a type-3 sum in the paper's HVOX, Sect. 5.2)
 // and the support contraction that turns step 2 of Algorithm 2 into a small
 // dense problem:
 //

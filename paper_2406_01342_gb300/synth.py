@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs shaped like the paper's workloads (Sect. 5, Table 1 and Table 3).
+"""Seeded synthetic inputs shaped like the paper's workloads (Sect. 6, Table 1 and Table 3).
 
 This module is the only code shared by the FP64 oracle and the CUDA path. It
 draws random numbers and does array geometry (station layouts, Earth-rotation
@@ -38,7 +38,7 @@ class Workload:
     sky_flux: np.ndarray      # (K,) float64 fluxes
     noise: np.ndarray         # (M,) complex128 unit-power noise realisation
     snr_db: float             # SNR in dB: noise power = mean|V_clean|^2 * 10^(-snr/10)
-    alpha: float              # lambda = alpha * lambda_max (Sect. 4.4)
+    alpha: float              # lambda = alpha * lambda_max (Sect. 5.3)
     delta: float              # exploration quality parameter of the PFW select
     seed: int
 
@@ -248,6 +248,32 @@ def small_wide_field(seed: int = 1010, N: int = 64, fov_deg: float = 12.0, n_sta
     return earth_rotation_workload("small_wide_w", seed, N, fov_deg, n_stations, radius_m,
                                    hours, dump_s, M if M is not None else n_b * n_t, n_src,
                                    snr_db)
+
+
+def serving_stream(seed: int = 1004, n_requests: int = 64, rate_hz: float = 4.0):
+    """The mixed request stream of the serving configuration: Poisson arrivals
+    at rate_hz, grids drawn from {256, 512, 1024, 2048}^2, M log-uniform in
+    [1e4, 1e6], 5-200 log-normal point sources, 20 dB SNR, alpha = 0.1,
+    delta = 0.01. Grids up to 512 use the 40-station / 3 km layout at FOV 2 deg,
+    larger grids the 60-station / 5 km layout at FOV 5 deg. Returns a list of
+    (arrival time in seconds, Workload)."""
+    ss = np.random.SeedSequence(seed)
+    r_arr, r_req = (np.random.default_rng(s) for s in ss.spawn(2))
+    t = np.cumsum(r_arr.exponential(1.0 / rate_hz, n_requests))
+    out = []
+    for i in range(n_requests):
+        N = int(r_req.choice([256, 512, 1024, 2048]))
+        M = int(round(10.0 ** r_req.uniform(4.0, 6.0)))
+        K = int(r_req.integers(5, 201))
+        sub_seed = int(r_req.integers(0, 2 ** 31 - 1))
+        if N <= 512:
+            wl = earth_rotation_workload(f"stream_{i}_{N}", sub_seed, N, 2.0, 40, 3000.0, 4.0, 10.0, M,
+                                         K, 20.0)
+        else:
+            wl = earth_rotation_workload(f"stream_{i}_{N}", sub_seed, N, 5.0, 60, 5000.0, 3.14, 10.0, M,
+                                         K, 20.0)
+        out.append((float(t[i]), wl))
+    return out
 
 
 WORKLOADS = {

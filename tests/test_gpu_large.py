@@ -66,7 +66,7 @@ def _physical_vis(abi, plan, wl):
 def test_full_size_solve_invariants(abi, name):
     """Algorithm 2 at full size: converges at the 1e-4 stop rule, the objective
     never increases and ends below F(0) = ||V||^2 / 2, the certificate of the
-    returned image is ~1 in magnitude on its support (optimality, Sect. 3.2)
+    returned image is ~1 in magnitude on its support (optimality, Sect. 4.2)
     and the brightest true sources are in the support."""
     wl = synth.WORKLOADS[name]()
     plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)

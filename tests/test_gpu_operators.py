@@ -1,5 +1,5 @@
 """GPU parity of the operators (the forward and adjoint equations of Sect. 2.2,
-the certificate of Sect. 3.2, lambda_max of Sect. 4.4) against the FP64 oracle.
+the certificate of Sect. 4.2, lambda_max of Sect. 5.3) against the FP64 oracle.
 
 Tolerance: relative L2 error <= 1e-5 for every operator output (FP32 kernels
 against FP64 direct sums), as the accuracy target of the hot path states.

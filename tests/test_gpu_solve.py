@@ -119,7 +119,7 @@ def test_tensor_core_and_fp32_gram_give_the_same_solve(abi):
     assert a["converged"] and b["converged"]
 
 
-# ---------------------------------------------------------------- positivity (remark of Sect. 4.1)
+# ---------------------------------------------------------------- positivity (remark of Sect. 5.1)
 
 def _signed_workload(name):
     """The workload with its brightest source made negative (so the constraint binds)."""

@@ -4,7 +4,7 @@ Each test checks the oracle against something other than its own formula:
 an identity (adjoint pair), a library routine in a special case (numpy.fft on
 the uv lattice), a closed form (single atom, lambda_max), an independent
 solver (brute force over sign patterns, coordinate descent) or an optimality
-condition of the LASSO (Sect. 3.2: |mu| <= 1, mu = sign(x) on the support).
+condition of the LASSO (Sect. 4.2: |mu| <= 1, mu = sign(x) on the support).
 """
 import math
 
@@ -117,7 +117,7 @@ def test_phase_reduction_keeps_large_arguments_exact():
     assert np.allclose(operators.forward(uvw, N, fov, idx, x), direct, atol=1e-12 * np.abs(direct).max())
 
 
-# ------------------------------------------------------------ LASSO facts (Sect. 3, 4.4)
+# ------------------------------------------------------------ LASSO facts (Sect. 4, 5.3)
 
 def test_single_atom_closed_form():
     """One atom a: argmin 1/2||V - a x||^2 + lam|x| = soft(Re(a^H V), lam) / ||a||^2."""
@@ -182,7 +182,7 @@ def test_pfw_matches_brute_force_on_3x3(seed):
 
 
 def test_lambda_at_lambda_max_gives_zero():
-    """Sect. 4.4: for lambda >= lambda_max = ||Phi* V||_inf the solution is exactly 0."""
+    """Sect. 5.3: for lambda >= lambda_max = ||Phi* V||_inf the solution is exactly 0."""
     wl = synth.tiny_coplanar(M=400, N=32)
     V = _vis(wl)
     lmax = operators.lambda_max(wl.uvw, wl.N, wl.fov, V)
@@ -204,7 +204,7 @@ def tight_tiny():
 
 
 def test_kkt_conditions_at_convergence(tight_tiny):
-    """Sect. 3.2: ||mu||_inf <= 1 and mu = sign(x) on the support; the duality gap vanishes."""
+    """Sect. 4.2: ||mu||_inf <= 1 and mu = sign(x) on the support; the duality gap vanishes."""
     wl, V, lmax, lam, res = tight_tiny
     mu = res.mu.ravel()
     assert np.abs(mu).max() <= 1 + 1e-6
@@ -214,7 +214,7 @@ def test_kkt_conditions_at_convergence(tight_tiny):
 
 
 def test_alpha_identity(tight_tiny):
-    """Sect. 4.4: at convergence ||Phi*(V - Phi x)||_inf / ||Phi* V||_inf = alpha."""
+    """Sect. 5.3: at convergence ||Phi*(V - Phi x)||_inf / ||Phi* V||_inf = alpha."""
     wl, V, lmax, lam, res = tight_tiny
     ratio = np.abs(res.mu).max() * lam / lmax
     assert abs(ratio - wl.alpha) <= 1e-6 * wl.alpha

@@ -1,5 +1,5 @@
 """Pins of the oracle's positivity-constrained variant (the remarks on a
-positivity constraint in Sect. 3.1 and 4.1: candidates only at positive values
+positivity constraint in Sect. 4.1 and 5.1: candidates only at positive values
 of the residual image, reweighting with x >= 0), against what the mathematics
 fixes independently of the oracle: exhaustive enumeration over {0, +1}^n
 patterns, a separately written coordinate descent, the one-sided optimality
