@@ -100,6 +100,24 @@ __device__ __forceinline__ float phase_turns(int4 vis, float4 atom) {
   return t - rintf(t);
 }
 
+// Atom of pixel p (raster index, clamped to the image) with weight x (1 when
+// no weight): packed signed offsets i' = i - N/2, j' = j - N/2 (16 bits each),
+// s = n - 1 as a double-float pair, and x / n -- what the phase kernels read.
+__device__ __forceinline__ float4 make_atom(int p, float x, bool weighted, int N, double dl) {
+  p = min(max(p, 0), N * N - 1);
+  const int i = p / N, j = p - (p / N) * N;
+  const int ip = i - N / 2, jp = j - N / 2;
+  const double l = ip * dl, m = jp * dl;
+  const double r2 = l * l + m * m;
+  const double n = sqrt(1.0 - r2);
+  const double sv = -r2 / (1.0 + n);
+  const float s_hi = (float)sv;
+  const float s_lo = (float)(sv - (double)s_hi);
+  const double w = weighted ? (double)x : 1.0;
+  const int packed = (ip << 16) | (jp & 0xffff);
+  return make_float4(__int_as_float(packed), s_hi, s_lo, (float)(w / n));
+}
+
 // Order-preserving map of a float onto unsigned (atomicMax of signed values):
 // non-negative floats get the sign bit set, negative ones are inverted.
 __host__ __device__ __forceinline__ unsigned float_order_key(float f) {

@@ -484,7 +484,8 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   PC_TRY(dev_alloc_t(p, &p->iscal, 8));
   PC_CUDA(cudaMemsetAsync(p->iscal, 0, 8 * sizeof(int32_t), st));
   p->sel_blocks_n = ceil_div(NN, 4096);
-  PC_TRY(dev_alloc_t(p, &p->sel_blocks, (size_t)p->sel_blocks_n + 1));
+  PC_TRY(dev_alloc_t(p, &p->sel_blocks, (size_t)p->sel_blocks_n + 2));
+  PC_CUDA(cudaMemsetAsync(p->sel_blocks, 0, sizeof(int32_t) * ((size_t)p->sel_blocks_n + 2), st));
   PC_TRY(dev_alloc_t(p, &p->vis_fx, (size_t)std::max<int64_t>(M, 1)));
 
   if (M == 0) {

@@ -19,34 +19,13 @@ __device__ __forceinline__ bool sel_flag(const float* mu, const uint8_t* mark, i
   return (positive ? v : fabsf(v)) >= thr || mark[p] != 0;
 }
 
-__global__ void k_sel_count(const float* __restrict__ mu, const uint8_t* __restrict__ mark,
-                            int64_t npix, float thr, int positive, int32_t* __restrict__ block_counts,
-                            const float* __restrict__ thr_dev) {
-  __shared__ int wsum[SEL_THREADS / 32];
-  if (thr_dev) thr = *thr_dev;
-  int c = 0;
-  const int64_t base = (int64_t)blockIdx.x * SEL_ITEMS;
-  for (int r = 0; r < SEL_ROUNDS; ++r) {
-    const int64_t p = base + r * SEL_THREADS + threadIdx.x;
-    if (p < npix && sel_flag(mu, mark, p, thr, positive)) ++c;
-  }
-  for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < SEL_THREADS / 32; ++w) t += wsum[w];
-    block_counts[blockIdx.x] = t;
-  }
-}
-
 // Exclusive scan of n ints in place by one block; a[n] receives the total.
-__global__ void k_scan_ints(int32_t* __restrict__ a, int n) {
+__device__ void block_exclusive_scan(int32_t* a, int n) {
   __shared__ int warp_tot[32];
   const int chunk = (n + blockDim.x - 1) / blockDim.x;
   const int lo = threadIdx.x * chunk, hi = min(lo + chunk, n);
   int s = 0;
-  for (int i = lo; i < hi; ++i) s += a[i];
+  for (int i = lo; i < hi; ++i) s += ((volatile int32_t*)a)[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int incl = s;
   for (int off = 1; off < 32; off <<= 1) {
@@ -69,9 +48,45 @@ __global__ void k_scan_ints(int32_t* __restrict__ a, int n) {
   __syncthreads();
   int run = warp_tot[wid] + incl - s;
   for (int i = lo; i < hi; ++i) {
-    const int v = a[i];
+    const int v = ((volatile int32_t*)a)[i];
     a[i] = run;
     run += v;
+  }
+}
+
+// Per-block counts; the last block to finish scans them (block_counts[nblk]
+// = total, also written to *count_dev) and resets the arrival counter
+// block_counts[nblk + 1], so the write pass needs no separate scan launch.
+__global__ void k_sel_count(const float* __restrict__ mu, const uint8_t* __restrict__ mark,
+                            int64_t npix, float thr, int positive, int32_t* __restrict__ block_counts,
+                            const float* __restrict__ thr_dev, int nblk, int32_t* __restrict__ count_dev) {
+  __shared__ int wsum[SEL_THREADS / 32];
+  __shared__ bool s_last;
+  if (thr_dev) thr = *thr_dev;
+  int c = 0;
+  const int64_t base = (int64_t)blockIdx.x * SEL_ITEMS;
+  for (int r = 0; r < SEL_ROUNDS; ++r) {
+    const int64_t p = base + r * SEL_THREADS + threadIdx.x;
+    if (p < npix && sel_flag(mu, mark, p, thr, positive)) ++c;
+  }
+  for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < SEL_THREADS / 32; ++w) t += wsum[w];
+    block_counts[blockIdx.x] = t;
+    __threadfence();
+    s_last = atomicAdd(&block_counts[nblk + 1], 1) == nblk - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    block_exclusive_scan(block_counts, nblk);
+    if (threadIdx.x == 0) {
+      *count_dev = block_counts[nblk];
+      block_counts[nblk + 1] = 0;
+    }
   }
 }
 
@@ -167,15 +182,13 @@ int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark,
                   const float* thr_dev) {
   ProfScope prof_scope_(PROF_SELECT, st);
   const int nblk = ceil_div(npix, SEL_ITEMS);
-  prof_scope_.kernels = 4;
-  k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, thr_dev);
-  PC_LAUNCH_CHECK();
-  k_scan_ints<<<1, 1024, 0, st>>>(block_counts, nblk);
+  prof_scope_.kernels = 2;
+  k_sel_count<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, thr_dev,
+                                             nblk, count_dev);
   PC_LAUNCH_CHECK();
   k_sel_write<<<nblk, SEL_THREADS, 0, st>>>(mu, mark, npix, thr, positive ? 1 : 0, block_counts, out, cap,
                                              thr_dev);
   PC_LAUNCH_CHECK();
-  PC_CUDA(cudaMemcpyAsync(count_dev, block_counts + nblk, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   return PC_OK;
 }
 

@@ -79,6 +79,83 @@ int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStre
 
 inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
 
+// Pruning (step 3 of Algorithm 2) in one launch: row i of the new support is
+// entry keep[i] of the active set; copies its Gram row (columns keep[.]) and,
+// in block (0, i), its index, weight, b, atom, support mark and |x| into the
+// objective's l1 sum. The count n is read on the device (bound: its maximum).
+__global__ void k_prune(const int32_t* __restrict__ keep, const int32_t* __restrict__ n_dev, int bound,
+                        const int32_t* __restrict__ idxB, const float* __restrict__ xB,
+                        const float* __restrict__ bB, const float* __restrict__ GB, int ld,
+                        int32_t* __restrict__ idxA, float* __restrict__ xA, float* __restrict__ bA,
+                        float* __restrict__ GA, float4* __restrict__ atomsA, uint8_t* __restrict__ mark,
+                        double* __restrict__ l1, int N, double dl) {
+  const int n = min(bound, *n_dev);
+  const int i = blockIdx.y;
+  if (i >= n) return;
+  const int ki = keep[i];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    GA[(size_t)i * ld + j] = GB[(size_t)ki * ld + keep[j]];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int p = idxB[ki];
+    const float x = xB[ki];
+    idxA[i] = p;
+    xA[i] = x;
+    bA[i] = bB[ki];
+    atomsA[i] = make_atom(p, x, true, N, dl);
+    mark[p] = 1;
+    atomicAdd(l1, fabs((double)x));
+  }
+}
+
+// After the exploration, in one block: for each active atom its position in
+// the old (pruned) support or -1 (binary search), the warm start and b of the
+// old atoms, its atom (unit weight), the ascending list of the new positions
+// and their count; finally the support marks are cleared.
+__global__ void __launch_bounds__(1024)
+k_post_select(const int32_t* __restrict__ idxB, int n_act, const int32_t* __restrict__ idxA, int nS,
+              const float* __restrict__ xA, const float* __restrict__ bA, int32_t* __restrict__ oldpos,
+              int32_t* __restrict__ newrows, int32_t* __restrict__ n_new_dev, float* __restrict__ xB,
+              float* __restrict__ bB, float4* __restrict__ atomsB, uint8_t* __restrict__ mark, int N,
+              double dl) {
+  __shared__ int wcount[32];
+  __shared__ int run_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) run_s = 0;
+  __syncthreads();
+  for (int base = 0; base < n_act; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    bool is_new = false;
+    if (i < n_act) {
+      const int v = idxB[i];
+      int lo = 0, hi = nS;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (idxA[mid] < v) lo = mid + 1; else hi = mid;
+      }
+      const int op = (lo < nS && idxA[lo] == v) ? lo : -1;
+      oldpos[i] = op;
+      xB[i] = op >= 0 ? xA[op] : 0.f;
+      bB[i] = op >= 0 ? bA[op] : 0.f;
+      atomsB[i] = make_atom(v, 1.f, false, N, dl);
+      is_new = op < 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, is_new);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += wcount[w];
+      total += wcount[w];
+    }
+    if (is_new) newrows[run_s + before + __popc(bal & ((1u << lane) - 1u))] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) run_s += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_new_dev = run_s;
+  for (int j = threadIdx.x; j < nS; j += blockDim.x) mark[idxA[j]] = 0;
+}
+
 // Exploration threshold of rule R1 (Algorithm 2) from the certificate maxima
 // on the device: thr = top - 2 Delta / ((k + 2) lambda) with top = max |mu|
 // (max mu under positivity); at k = 0 without a given lambda_max, Delta =
@@ -530,11 +607,10 @@ int SolveJob::explore() {
     PC_LAUNCH_CHECK();
     thr_d = reinterpret_cast<float*>(p->dscal + 5);
   }
-  const int bound = std::max(n_prev_act, 1);
-  PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 1, st, n_sup_dev));
+  // union with the support: its pixels were marked by the pruning kernel
+  // (cleared again after the exploration by k_post_select)
   PC_TRY(launch_select(mu_dst, npix, (float)(1.0 - delta), p->mark, p->idxB.as<int32_t>(), p->iscal,
                        p->sel_blocks, wcap, st, c.positive != 0, thr_d));
-  PC_TRY(launch_mark(p->mark, p->idxA.as<int32_t>(), bound, 0, st, n_sup_dev));
   return PC_OK;
 }
 
@@ -544,21 +620,18 @@ int SolveJob::explore() {
 int SolveJob::queue_iteration() {
   int32_t* n_sup_dev = p->iscal + 3;
   if (k > 0) {
-    const int32_t* keep = p->keep.as<int32_t>();
-    PC_TRY(gather_vec<int32_t>(p->idxB.as<int32_t>(), keep, n_prev_act, p->idxA.as<int32_t>(), 0, st,
-                               n_sup_dev));
-    PC_TRY(gather_vec<float>(p->xB.as<float>(), keep, n_prev_act, p->xA.as<float>(), 0.f, st, n_sup_dev));
-    PC_TRY(gather_vec<float>(p->bB.as<float>(), keep, n_prev_act, p->bA.as<float>(), 0.f, st, n_sup_dev));
-    PC_TRY(gather_sym(p->GB.as<float>(), ldB_prev, keep, n_prev_act, p->GA.as<float>(), ldB_prev, st,
-                      n_sup_dev));
     ldA = ldB_prev;
     PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
     if (n_prev_act > 0) {
-      PC_TRY(launch_make_atoms(p->idxA.as<int32_t>(), p->xA.as<float>(), n_prev_act, p->N, p->dl,
-                               p->atomsA.as<float4>(), st, n_sup_dev));
+      // pruning: gathers, atoms, support marks and ||x||_1 in one launch
       ProfScope prof_scope_(PROF_MISC, st);
       prof_scope_.kernels = 1;
-      k_l1<<<1, 256, 0, st>>>(p->xA.as<float>(), n_prev_act, p->dscal + 1, n_sup_dev);
+      dim3 grid(std::max(1, std::min(ceil_div(n_prev_act, 256), 32)), n_prev_act);
+      k_prune<<<grid, 256, 0, st>>>(p->keep.as<int32_t>(), n_sup_dev, n_prev_act, p->idxB.as<int32_t>(),
+                                    p->xB.as<float>(), p->bB.as<float>(), p->GB.as<float>(), ldB_prev,
+                                    p->idxA.as<int32_t>(), p->xA.as<float>(), p->bA.as<float>(),
+                                    p->GA.as<float>(), p->atomsA.as<float4>(), p->mark, p->dscal + 1,
+                                    p->N, p->dl);
       PC_LAUNCH_CHECK();
     }
     PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_prev_act, p->resid, p->dscal,
@@ -653,16 +726,20 @@ int SolveJob::process() {
   ldB = round4(std::max(n_act, 1));
   if (n_act > 0) {
     int32_t* oldpos = p->oldpos.as<int32_t>();
-    PC_TRY(launch_old_positions(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS, oldpos, st));
-    PC_TRY(launch_compact_new(oldpos, n_act, p->newrows.as<int32_t>(), p->iscal + 1, st));
-    // old-old block, warm start and b of the old atoms
+    {
+      // old positions, new-atom list, warm start, b of the old atoms, atoms; marks cleared
+      ProfScope prof_scope_(PROF_MISC, st);
+      prof_scope_.kernels = 1;
+      k_post_select<<<1, 1024, 0, st>>>(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS,
+                                        p->xA.as<float>(), p->bA.as<float>(), oldpos,
+                                        p->newrows.as<int32_t>(), p->iscal + 1, p->xB.as<float>(),
+                                        p->bB.as<float>(), p->atomsB.as<float4>(), p->mark, p->N, p->dl);
+      PC_LAUNCH_CHECK();
+    }
+    // old-old block of G
     PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
-    PC_TRY(gather_vec<float>(p->xA.as<float>(), oldpos, n_act, p->xB.as<float>(), 0.f, st));
-    PC_TRY(gather_vec<float>(p->bA.as<float>(), oldpos, n_act, p->bB.as<float>(), 0.f, st));
     // Gram rows of the new atoms against every active atom, and b
     if (n_new > 0) {
-      PC_TRY(launch_make_atoms(p->idxB.as<int32_t>(), nullptr, n_act, p->N, p->dl, p->atomsB.as<float4>(),
-                               st));
       PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_new, oldpos,
                          p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode, p->iscal + 4, st));
     }

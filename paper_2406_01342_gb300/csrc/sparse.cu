@@ -21,20 +21,9 @@ __global__ void k_make_atoms(const int32_t* __restrict__ idx, const float* __res
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (S_dev) S = min(S, *S_dev);   // count held on the device (S: its upper bound)
   if (s >= S) return;
-  int p = idx[s];
+  const int p = idx[s];
   if (bad && (p < 0 || p >= N * N || (s > 0 && idx[s - 1] >= p))) atomicOr(bad, 1);
-  p = min(max(p, 0), N * N - 1);
-  int i = p / N, j = p - (p / N) * N;
-  int ip = i - N / 2, jp = j - N / 2;
-  double l = ip * dl, m = jp * dl;
-  double r2 = l * l + m * m;
-  double n = sqrt(1.0 - r2);
-  double sv = -r2 / (1.0 + n);
-  float s_hi = (float)sv;
-  float s_lo = (float)(sv - (double)s_hi);
-  double w = x ? (double)x[s] : 1.0;
-  int packed = (ip << 16) | (jp & 0xffff);
-  atoms[s] = make_float4(__int_as_float(packed), s_hi, s_lo, (float)(w / n));
+  atoms[s] = make_atom(p, x ? x[s] : 1.f, x != nullptr, N, dl);
 }
 
 constexpr int RES_CHUNK = 1024;
