@@ -67,7 +67,20 @@ typedef struct {
   int32_t max_planes;     /* cap on the number of w-planes (default 256)                */
   int32_t grid_mode;      /* gridding: 0 (default) tensor cores when w-stacking, else CUDA
                              cores; 1: FP32 CUDA cores; 2: tensor cores whenever w-stacking */
+  int32_t autotune;       /* 1: time the candidate gridding kernels, gridding sub-problem
+                             sizes and FFT rows per CTA on this plan's visibilities and keep
+                             the fastest (adds a few ms to plan creation); 0 (default): off */
 } pc_plan_opts;
+
+/* What the plan-time autotuner chose (tuned = 0 when it did not run). */
+typedef struct {
+  int32_t tuned;
+  int32_t grid_mode;        /* 1: CUDA cores, 2: tensor cores                        */
+  int32_t grid_piece;       /* gridding sub-problem size in binned slots             */
+  int32_t fft_rows_per_cta; /* rows per CTA of the first FFT pass                    */
+  double  grid_us;          /* measured time of one gridding with that choice        */
+  double  fft_rows_us;      /* measured time of one first FFT pass with that choice  */
+} pc_plan_tuning;
 
 /* Solver options (Algorithm 2 and its sub-solver). Zero fields take defaults. */
 typedef struct {
@@ -129,6 +142,7 @@ void pc_plan_destroy(pc_plan_t plan);
  * of binned (replicated) visibility slots, kernel width. Any pointer may be NULL. */
 int pc_plan_info(pc_plan_t plan, int32_t* grid_side, int32_t* tile, int32_t* n_planes,
                  int64_t* n_slots, int32_t* kernel_width, double* dw);
+int pc_plan_tuning_info(pc_plan_t plan, pc_plan_tuning* out_host);
 
 /* ------------------------------------------------------------------ operators */
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
     "pc_profile_begin_classes", "pc_server_create", "pc_server_submit", "pc_server_wait",
-    "pc_server_destroy",
+    "pc_server_destroy", "pc_plan_tuning_info",
 ]
 
 
@@ -44,7 +44,13 @@ class PcError(RuntimeError):
 class pc_plan_opts(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("max_planes", ctypes.c_int32),
-                ("grid_mode", ctypes.c_int32)]
+                ("grid_mode", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+
+
+class pc_plan_tuning(ctypes.Structure):
+    _fields_ = [("tuned", ctypes.c_int32), ("grid_mode", ctypes.c_int32),
+                ("grid_piece", ctypes.c_int32), ("fft_rows_per_cta", ctypes.c_int32),
+                ("grid_us", ctypes.c_double), ("fft_rows_us", ctypes.c_double)]
 
 
 class pc_server_opts(ctypes.Structure):
@@ -110,6 +116,7 @@ def load(path: str | None = None):
     sig = {
         "pc_plan_create": (_I32, [_P, _I64, _I32, _D, _P, _P, ctypes.POINTER(_P)]),
         "pc_plan_destroy": (None, [_P]),
+        "pc_plan_tuning_info": (_I32, [_P, ctypes.POINTER(pc_plan_tuning)]),
         "pc_plan_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                 ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
         "pc_forward_sparse": (_I32, [_P, _P, _P, _I32, _P, _P]),
@@ -190,9 +197,9 @@ class Plan:
 
 
 def pc_plan_create(uvw: torch.Tensor, N: int, fov: float, kernel_width: int = 0, tile: int = 0,
-                   max_planes: int = 0, stream=None, grid_mode: int = 0) -> Plan:
+                   max_planes: int = 0, stream=None, grid_mode: int = 0, autotune: int = 0) -> Plan:
     lib = load()
-    opts = pc_plan_opts(PC_ABI_VERSION, kernel_width, tile, max_planes, grid_mode)
+    opts = pc_plan_opts(PC_ABI_VERSION, kernel_width, tile, max_planes, grid_mode, autotune)
     h = _P()
     M = int(uvw.shape[0])
     _check(lib.pc_plan_create(_dev(uvw, torch.float64, "uvw") if M else None, M, N, float(fov),
@@ -208,6 +215,13 @@ def pc_plan_info(plan: Plan) -> dict:
                                ctypes.byref(ns), ctypes.byref(w), ctypes.byref(dw)))
     return dict(grid_side=g.value, tile=t.value, n_planes=p.value, n_slots=ns.value,
                 kernel_width=w.value, dw=dw.value)
+
+
+def pc_plan_tuning_info(plan: Plan) -> dict:
+    t = pc_plan_tuning()
+    _check(load().pc_plan_tuning_info(plan.handle, ctypes.byref(t)))
+    return dict(tuned=bool(t.tuned), grid_mode=t.grid_mode, grid_piece=t.grid_piece,
+                fft_rows_per_cta=t.fft_rows_per_cta, grid_us=t.grid_us, fft_rows_us=t.fft_rows_us)
 
 
 def pc_forward_sparse(plan: Plan, idx: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = None,

@@ -94,6 +94,8 @@ cudaEvent_t pool_event() {
 
 }  // namespace
 
+bool prof_active() { return g_prof_on; }
+
 int prof_start(int cls, cudaStream_t st) {
   if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return -1;
   cudaEvent_t a = pool_event(), b = pool_event();

@@ -27,7 +27,7 @@ namespace pc {
 // held in buffer a, using b as scratch. All threads of the block take part.
 // Returns the buffer holding the result.
 __device__ float2* fft_rows_smem(float2* a, float2* b, int rows, int G, int logG, int S,
-                                 const float2* __restrict__ tw) {
+                                 const float2* tw) {
   const int nthr = blockDim.x;
   int ns = 1;
   if (logG & 1) {
@@ -82,6 +82,8 @@ k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int l
   const int S = G + 1;
   float2* A = sm;
   float2* B = sm + R * S;
+  float2* T = B + R * S;                          // twiddles, staged once per CTA
+  for (int k = threadIdx.x; k < G; k += blockDim.x) T[k] = tw[k];
   const int q = blockIdx.y;
   const int b0 = active_rows[blockIdx.x * R];     // R consecutive active rows (R divides 32)
   const float2* src = grid + ((size_t)q * G + b0) * G;
@@ -90,7 +92,7 @@ k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int l
     A[r * S + a] = src[(size_t)r * G + a];
   }
   __syncthreads();
-  const float2* res = fft_rows_smem(A, B, R, G, logG, S, tw);
+  const float2* res = fft_rows_smem(A, B, R, G, logG, S, T);
   float2* dst = X + (size_t)q * N * G + b0;
   const int mask = G - 1, hN = N >> 1;
   for (int f = threadIdx.x; f < N * R; f += blockDim.x) {
@@ -107,6 +109,8 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
   extern __shared__ float2 sm[];
   float2* A = sm;
   float2* B = sm + G;
+  float2* T = sm + 2 * G;                         // twiddles, staged once per CTA
+  for (int k = threadIdx.x; k < G; k += blockDim.x) T[k] = tw[k];
   const int i = blockIdx.x;
   const int mask = G - 1, hN = N >> 1;
   float2 acc[JPT];
@@ -121,7 +125,7 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
     const float2* src = X + ((size_t)q * N + i) * G;
     for (int a = threadIdx.x; a < G; a += blockDim.x) A[a] = src[a];
     __syncthreads();
-    const float2* res = fft_rows_smem(A, B, 1, G, logG, G, tw);
+    const float2* res = fft_rows_smem(A, B, 1, G, logG, G, T);
     const float qf = (float)q;
 #pragma unroll
     for (int jj = 0; jj < JPT; ++jj) {
@@ -174,10 +178,11 @@ int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
   if (p->n_active_rows == 0) return PC_OK;     // all-zero grid: the output stays zero
   // rows per CTA: R * (G + 1) * 8 bytes * 2 buffers <= ~66 KB (3 CTAs per SM);
   // R divides the 32-row tile so a CTA's rows are consecutive active rows
-  int R = 4096 / p->G;
+  int R = p->fft_R > 0 ? p->fft_R : 4096 / p->G;
   if (R < 1) R = 1;
   if (R > 32) R = 32;
-  const size_t smem = (size_t)2 * R * (p->G + 1) * sizeof(float2);
+  const size_t smem = ((size_t)2 * R * (p->G + 1) + p->G) * sizeof(float2);
+  if (smem > 200 * 1024) return fail(PC_ERR_INVALID_ARG, "fft: %d rows per CTA do not fit shared memory", R);
   static bool attr_set = false;
   if (!attr_set) {
     PC_CUDA(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -194,7 +199,7 @@ int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_COLS, st);
-  const size_t smem = (size_t)2 * p->G * sizeof(float2);
+  const size_t smem = (size_t)3 * p->G * sizeof(float2);
   const int jpt = (p->N + 255) / 256;
   prof_scope_.kernels = 1;
   const int ws = p->wstack ? 1 : 0;

@@ -56,6 +56,7 @@ enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RE
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
                  PROF_GRAM_TC, PROF_GRAM_THIN, PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
+bool prof_active();   // kernel-class timing is recording
 void prof_stop(int token, cudaStream_t st, int kernels);
 
 // Records the launches of one launcher function; `kernels` counts the CUDA
@@ -230,6 +231,12 @@ struct pc_plan_s {
   double w0 = 0, dw = 1, s_c = 0, w_min = 0, w_max = 0;
   bool wstack = false;
   int grid_mode = 0;  // 0 auto, 1 CUDA cores, 2 tensor cores (w-stacking only)
+  int grid_piece = 0; // gridding sub-problem size in slots (0: chosen for even waves)
+  int fft_R = 0;      // rows per CTA of the first FFT pass (0: 4096 / G)
+  bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
+  double tune_grid_us = 0.0, tune_fft_us = 0.0;
+  std::vector<int4> sub_ranges;   // (tile, plane group, first slot, end) before splitting
+  int sub_cap = 0;                // capacity of subs (the finest split)
   int64_t n_slots = 0;
   int n_sub = 0;
 

@@ -373,6 +373,105 @@ struct TmpBufs {
   }
 };
 
+// Splits every (tile, plane group) slot range into equal pieces of at most
+// `piece` slots (multiples of 64, the tensor-core stage) and uploads the list.
+static int split_subs(pc_plan_s* p, int piece, cudaStream_t st) {
+  std::vector<int4> subs;
+  for (const int4& r : p->sub_ranges) {
+    const int len = r.w - r.z;
+    const int n_pieces = ceil_div(len, piece);
+    const int sz = ceil_div(ceil_div(len, n_pieces), 64) * 64;
+    for (int s = r.z; s < r.w; s += sz) subs.push_back(make_int4(r.x, r.y, s, std::min(r.w, s + sz)));
+  }
+  if ((int)subs.size() > p->sub_cap) return fail(PC_ERR_CAPACITY, "plan: %zu sub-problems", subs.size());
+  p->n_sub = (int)subs.size();
+  p->grid_piece = piece;
+  if (!subs.empty())
+    PC_CUDA(cudaMemcpyAsync(p->subs, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaStreamSynchronize(st));   // the host vector goes out of scope
+  return PC_OK;
+}
+
+__global__ void k_fill_ones(float2* __restrict__ h, int64_t M) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x)
+    h[k] = make_float2(1.0f, 0.5f);
+}
+
+// Median of `reps` timed calls of f (after one untimed call), in microseconds.
+template <class F>
+static int time_us(cudaStream_t st, int reps, F f, double* out) {
+  cudaEvent_t a, b;
+  PC_CUDA(cudaEventCreate(&a));
+  PC_CUDA(cudaEventCreate(&b));
+  std::vector<double> t;
+  int rc = f();
+  for (int i = 0; i < reps && rc == PC_OK; ++i) {
+    cudaEventRecord(a, st);
+    rc = f();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    t.push_back(1e3 * ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  PC_TRY(rc);
+  std::sort(t.begin(), t.end());
+  *out = t[t.size() / 2];
+  return PC_OK;
+}
+
+// Plan-time autotuner: times, on this plan's binned visibilities, the
+// gridding kernels (tensor cores vs CUDA cores, w-stacked plans) x the
+// sub-problem sizes, then the first FFT pass's rows per CTA, and keeps the
+// fastest of each.
+static int autotune(pc_plan_s* p, cudaStream_t st) {
+  if (p->M <= 0 || p->n_sub == 0) return PC_OK;
+  k_fill_ones<<<(int)std::min<int64_t>(4096, (p->M + 255) / 256), 256, 0, st>>>(p->resid, p->M);
+  PC_LAUNCH_CHECK();
+  const int user_mode = p->grid_mode;
+  std::vector<int> modes = {user_mode};
+  if (user_mode == 0 && p->wstack) modes = {2, 1};
+  double best = 1e300;
+  int best_mode = user_mode, best_piece = p->grid_piece;
+  for (int mode : modes) {
+    for (int piece : {256, 512, 1024}) {
+      p->grid_mode = mode;
+      PC_TRY(split_subs(p, piece, st));
+      double us = 0.0;
+      PC_TRY(time_us(st, 3, [&] { return launch_grid(p, p->resid, st); }, &us));
+      if (us < best) {
+        best = us;
+        best_mode = mode;
+        best_piece = piece;
+      }
+    }
+  }
+  p->grid_mode = best_mode;
+  PC_TRY(split_subs(p, best_piece, st));
+  p->tune_grid_us = best;
+  PC_TRY(launch_grid(p, p->resid, st));         // a gridded plane set for the FFT timing
+  double best_fft = 1e300;
+  int best_R = 0;
+  for (int R : {1, 2, 4, 8, 16, 32}) {
+    if (((size_t)2 * R * (p->G + 1) + p->G) * sizeof(float2) > 200 * 1024) break;
+    p->fft_R = R;
+    double us = 0.0;
+    PC_TRY(time_us(st, 3, [&] { return launch_fft_rows(p, st); }, &us));
+    if (us < best_fft) {
+      best_fft = us;
+      best_R = R;
+    }
+  }
+  p->fft_R = best_R;
+  p->tune_fft_us = best_fft;
+  p->tuned = true;
+  PC_CUDA(cudaMemsetAsync(p->resid, 0, sizeof(float2) * p->M, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
 static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_planes) {
   const int64_t M = p->M;
   const int N = p->N;
@@ -575,22 +674,15 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   const int64_t want = 4ll * n_sm;
   int piece = (int)std::min<int64_t>(kMaxSlotsPerSub, std::max<int64_t>(128, (total_slots + want - 1) / want));
   piece = ceil_div(piece, 64) * 64;
-  std::vector<int4> subs;
-  for (const int4& r : ranges) {
-    const int len = r.w - r.z;
-    const int n_pieces = ceil_div(len, piece);
-    const int sz = ceil_div(ceil_div(len, n_pieces), 64) * 64;
-    for (int s = r.z; s < r.w; s += sz) subs.push_back(make_int4(r.x, r.y, s, std::min(r.w, s + sz)));
-  }
-  p->n_sub = (int)subs.size();
-  PC_TRY(dev_alloc_t(p, &p->subs, std::max<size_t>(subs.size(), 1)));
-  if (!subs.empty())
-    PC_CUDA(cudaMemcpyAsync(p->subs, subs.data(), sizeof(int4) * subs.size(),
-                            cudaMemcpyHostToDevice, st));
+  p->sub_ranges = ranges;
+  // room for the finest split the autotuner may try (pieces of 64 slots)
+  p->sub_cap = (int)(total_slots / 64 + (int64_t)ranges.size() + 1);
+  PC_TRY(dev_alloc_t(p, &p->subs, (size_t)p->sub_cap));
+  PC_TRY(split_subs(p, piece, st));
   // grid rows that any visibility can reach: the rows of tile rows with a sub-problem
   {
     std::vector<char> row_on(p->nT, 0);
-    for (const int4& s : subs) row_on[s.x / p->nT] = 1;
+    for (const int4& s : ranges) row_on[s.x / p->nT] = 1;
     std::vector<int> rows;
     for (int tv = 0; tv < p->nT; ++tv)
       if (row_on[tv])
@@ -664,6 +756,8 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   const int grid_mode = opts ? opts->grid_mode : 0;
   if (grid_mode < 0 || grid_mode > 2)
     return fail(PC_ERR_INVALID_ARG, "pc_plan_create: grid_mode %d not in [0, 2]", grid_mode);
+  const int tune = opts ? opts->autotune : 0;
+  if (tune != 0 && tune != 1) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: autotune must be 0 or 1");
 
   pc_plan_s* p = new pc_plan_s();
   cudaGetDevice(&p->device);
@@ -674,11 +768,25 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   p->T = T;
   p->grid_mode = grid_mode;
   int rc = build_plan(p, uvw_dev, (cudaStream_t)stream, maxP);
+  if (rc == PC_OK && tune) rc = autotune(p, (cudaStream_t)stream);
   if (rc != PC_OK) {
     pc_plan_destroy(p);
     return rc;
   }
   *plan_out = p;
+  return PC_OK;
+}
+
+extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
+  clear_error();
+  if (!p || !out) return fail(PC_ERR_INVALID_ARG, "pc_plan_tuning_info: NULL argument");
+  out->tuned = p->tuned ? 1 : 0;
+  out->grid_mode = (p->wstack && p->grid_mode != 1) ? 2 : 1;
+  out->grid_piece = p->grid_piece;
+  int R = p->fft_R > 0 ? p->fft_R : 4096 / p->G;
+  out->fft_rows_per_cta = std::min(std::max(R, 1), 32);
+  out->grid_us = p->tune_grid_us;
+  out->fft_rows_us = p->tune_fft_us;
   return PC_OK;
 }
 

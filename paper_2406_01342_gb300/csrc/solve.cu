@@ -90,20 +90,20 @@ __global__ void k_prune(const int32_t* __restrict__ keep, const int32_t* __restr
                         float* __restrict__ GA, float4* __restrict__ atomsA, uint8_t* __restrict__ mark,
                         double* __restrict__ l1, int N, double dl) {
   const int n = min(bound, *n_dev);
-  const int i = blockIdx.y;
-  if (i >= n) return;
-  const int ki = keep[i];
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    GA[(size_t)i * ld + j] = GB[(size_t)ki * ld + keep[j]];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int p = idxB[ki];
-    const float x = xB[ki];
-    idxA[i] = p;
-    xA[i] = x;
-    bA[i] = bB[ki];
-    atomsA[i] = make_atom(p, x, true, N, dl);
-    mark[p] = 1;
-    atomicAdd(l1, fabs((double)x));
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const int ki = keep[i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+      GA[(size_t)i * ld + j] = GB[(size_t)ki * ld + keep[j]];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const int p = idxB[ki];
+      const float x = xB[ki];
+      idxA[i] = p;
+      xA[i] = x;
+      bA[i] = bB[ki];
+      atomsA[i] = make_atom(p, x, true, N, dl);
+      mark[p] = 1;
+      atomicAdd(l1, fabs((double)x));
+    }
   }
 }
 
@@ -540,6 +540,8 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
 }
 
 SolveJob::~SolveJob() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (own) cudaStreamDestroy(own);
   if (rb) cudaFreeHost(rb);
   if (ev) cudaEventDestroy(ev);
 }
@@ -568,7 +570,7 @@ int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double
                     const SolveCfg& cfg, float* mu_out, pc_iter_record* hist_, int hist_cap_,
                     cudaStream_t stream) {
   p = plan;
-  st = stream;
+  caller = st = stream;
   V = V_dev;
   lambda = lambda_;
   delta = delta_;
@@ -578,6 +580,12 @@ int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double
   mu_dst = mu_out ? mu_out : p->mu;
   PC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&rb), sizeof(Readback)));
   PC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  if (stream == nullptr || stream == cudaStreamLegacy) {
+    PC_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    PC_CUDA(cudaEventRecord(ev, stream));
+    PC_CUDA(cudaStreamWaitEvent(own, ev, 0));
+    st = own;
+  }
   PC_TRY(grow(1024));
   // ||V||^2 and r = V; counters, the pruned-support count and the tensor-core
   // flag cleared (the gridding flag iscal[7] may still report an earlier call)
@@ -614,35 +622,61 @@ int SolveJob::explore() {
   return PC_OK;
 }
 
-// One iteration up to its readback, with every count kept on the device: the
-// pruning of the previous reweighting, the residual and objective of the
-// iterate, its certificate and the exploration set.
-int SolveJob::queue_iteration() {
+// The chain of one iteration up to its readback, with every count kept on the
+// device (bound: an upper bound of the previous active-set size): the pruning
+// of the previous reweighting, the residual and objective of the iterate, its
+// certificate and the exploration set.
+int SolveJob::enqueue_chain(int bound) {
   int32_t* n_sup_dev = p->iscal + 3;
-  if (k > 0) {
-    ldA = ldB_prev;
-    PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
-    if (n_prev_act > 0) {
-      // pruning: gathers, atoms, support marks and ||x||_1 in one launch
-      ProfScope prof_scope_(PROF_MISC, st);
-      prof_scope_.kernels = 1;
-      dim3 grid(std::max(1, std::min(ceil_div(n_prev_act, 256), 32)), n_prev_act);
-      k_prune<<<grid, 256, 0, st>>>(p->keep.as<int32_t>(), n_sup_dev, n_prev_act, p->idxB.as<int32_t>(),
-                                    p->xB.as<float>(), p->bB.as<float>(), p->GB.as<float>(), ldB_prev,
-                                    p->idxA.as<int32_t>(), p->xA.as<float>(), p->bA.as<float>(),
-                                    p->GA.as<float>(), p->atomsA.as<float4>(), p->mark, p->dscal + 1,
-                                    p->N, p->dl);
-      PC_LAUNCH_CHECK();
-    }
-    PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), n_prev_act, p->resid, p->dscal,
-                           st, n_sup_dev));
+  PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
+  if (bound > 0) {
+    // pruning: gathers, atoms, support marks and ||x||_1 in one launch
+    ProfScope prof_scope_(PROF_MISC, st);
+    prof_scope_.kernels = 1;
+    dim3 grid(std::max(1, std::min(ceil_div(bound, 256), 32)), std::min(bound, 1024));
+    k_prune<<<grid, 256, 0, st>>>(p->keep.as<int32_t>(), n_sup_dev, bound, p->idxB.as<int32_t>(),
+                                  p->xB.as<float>(), p->bB.as<float>(), p->GB.as<float>(), ld(),
+                                  p->idxA.as<int32_t>(), p->xA.as<float>(), p->bA.as<float>(),
+                                  p->GA.as<float>(), p->atomsA.as<float4>(), p->mark, p->dscal + 1,
+                                  p->N, p->dl);
+    PC_LAUNCH_CHECK();
   }
+  PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), bound, p->resid, p->dscal, st,
+                         n_sup_dev));
   PC_CUDA(cudaMemsetAsync(p->uscal, 0, 2 * sizeof(unsigned), st));
   PC_TRY(adjoint_grid_impl(p, p->resid, mu_dst, (float)(1.0 / lambda), p->uscal, st));
   PC_TRY(explore());
   PC_CUDA(cudaMemcpyAsync(rb->hi, p->iscal, sizeof(rb->hi), cudaMemcpyDeviceToHost, st));
   PC_CUDA(cudaMemcpyAsync(rb->hd, p->dscal, sizeof(rb->hd), cudaMemcpyDeviceToHost, st));
   PC_CUDA(cudaMemcpyAsync(rb->mb, p->uscal, sizeof(rb->mb), cudaMemcpyDeviceToHost, st));
+  return PC_OK;
+}
+
+// One iteration. With rule R2 (its threshold does not depend on k) and no
+// kernel-class timing, the chain is captured once as a CUDA graph (bounds =
+// the working-set capacity, every count read on the device) and replayed each
+// iteration: one launch instead of a dozen; re-captured when the capacity grows.
+int SolveJob::queue_iteration() {
+  if (k > 0) ldA = ldB_prev;
+  if (c.rule == 2 && !prof_active()) {
+    if (!gexec || graph_wcap != wcap) {
+      if (gexec) cudaGraphExecDestroy(gexec);
+      gexec = nullptr;
+      cudaGraph_t g = nullptr;
+      PC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const int rc = enqueue_chain(wcap);
+      const cudaError_t e = cudaStreamEndCapture(st, &g);
+      PC_TRY(rc);
+      PC_CUDA(e);
+      const cudaError_t ei = cudaGraphInstantiate(&gexec, g, 0);
+      cudaGraphDestroy(g);
+      PC_CUDA(ei);
+      graph_wcap = wcap;
+    }
+    PC_CUDA(cudaGraphLaunch(gexec, st));
+  } else {
+    PC_TRY(enqueue_chain(k > 0 ? n_prev_act : 0));
+  }
   PC_CUDA(cudaEventRecord(ev, st));
   return PC_OK;
 }
@@ -723,7 +757,7 @@ int SolveJob::process() {
   cur.mu_inf = mu_top;
   have_cur = true;
 
-  ldB = round4(std::max(n_act, 1));
+  ldB = ld();
   if (n_act > 0) {
     int32_t* oldpos = p->oldpos.as<int32_t>();
     {
@@ -786,6 +820,10 @@ int SolveJob::finish(int32_t* idx_out, float* x_out, int32_t cap, pc_solve_stats
     PC_CUDA(cudaMemcpyAsync(idx_out, p->idxA.p, sizeof(int32_t) * nS, cudaMemcpyDeviceToDevice, st));
     PC_CUDA(cudaMemcpyAsync(x_out, p->xA.p, sizeof(float) * nS, cudaMemcpyDeviceToDevice, st));
   }
+  if (own) {
+    PC_CUDA(cudaEventRecord(ev, st));
+    PC_CUDA(cudaStreamWaitEvent(caller, ev, 0));
+  }
   if (status == PC_ERR_NOT_CONVERGED)
     fail(PC_ERR_NOT_CONVERGED, "pc_solve: no convergence after %d Frank-Wolfe iterations", k);
   return status;
@@ -819,7 +857,7 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     PC_TRY(j.process());
     if (j.need_apgd) {
       const ApgdJob aj = j.apgd_job();
-      PC_TRY(run_apgd_jobs(&aj, 1, st));
+      PC_TRY(run_apgd_jobs(&aj, 1, j.st));
       PC_TRY(j.after_apgd());
     }
   }

@@ -53,6 +53,14 @@ struct SolveJob {
   };
   Readback* rb = nullptr;
   cudaEvent_t ev = nullptr;
+  // the iteration chain as a CUDA graph (rule R2 without kernel-class timing)
+  cudaGraphExec_t gexec = nullptr;
+  int graph_wcap = -1;
+  // The legacy default stream cannot be captured: a job given it runs on a
+  // stream of its own, ordered after the caller's earlier work and before its
+  // later work by events.
+  cudaStream_t caller = nullptr;
+  cudaStream_t own = nullptr;
 
   ~SolveJob();
   // Allocates the working set, computes ||V||^2 (synchronises) and queues iteration 0.
@@ -68,12 +76,15 @@ struct SolveJob {
   ApgdJob apgd_job() const;
   // After the reweighting: pruning count, then the next iteration's queue.
   int after_apgd();
-  // Copies the support and weights (device) and fills the statistics.
+  // Copies the support and weights (device), fills the statistics and orders
+  // the caller's stream after the job.
   int finish(int32_t* idx_out, float* x_out, int32_t cap, pc_solve_stats* stats);
 
  private:
+  int ld() const { return (wcap + 3) & ~3; }   // leading dimension of the Gram buffers
   int grow(int need);
   int explore();
+  int enqueue_chain(int bound);
   int queue_iteration();
 };
 

@@ -184,6 +184,27 @@ def test_full_size_medium_sampled(abi, grid_mode):
     assert rel_l2(y[ks], yref) <= TOL
 
 
+def test_autotuned_plan(abi):
+    """A plan with autotune = 1 times the gridding variants (tensor / CUDA
+    cores x sub-problem size) and the FFT row pass on its own layout, keeps a
+    valid choice, and its adjoint still meets the operator tolerance."""
+    wl, V = workload("medium_512_w", M=60_000)
+    plan = _plan(abi, wl, autotune=1)
+    t = abi.pc_plan_tuning_info(plan)
+    assert t["tuned"] and t["grid_mode"] in (1, 2) and t["grid_piece"] in (256, 512, 1024)
+    assert t["fft_rows_per_cta"] in (1, 2, 4, 8, 16, 32)
+    assert 0 < t["grid_us"] < 1e5 and 0 < t["fft_rows_us"] < 1e5
+    assert not abi.pc_plan_tuning_info(_plan(abi, wl))["tuned"]
+    Vs = V.astype(np.complex64)
+    img = abi.pc_adjoint_grid(plan, to_dev(Vs)).cpu().numpy().ravel()
+    pix = np.union1d(np.sort(np.random.default_rng(9).choice(wl.N * wl.N, 1024, replace=False)), wl.sky_idx)
+    ref = operators.adjoint(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128), pix)
+    assert rel_l2(img[pix], ref) <= TOL
+    with pytest.raises(abi.PcError) as e:
+        _plan(abi, wl, autotune=2)
+    assert e.value.status == abi.PC_ERR_INVALID_ARG
+
+
 def test_tensor_core_bounded_wait_reports_timeout(abi):
     """Failure detection without a GPU fault: with its MMAs withheld (mode 3) the
     tensor-core kernel's bounded mbarrier wait expires, the kernel frees its
