@@ -95,8 +95,8 @@ def lambda_max(uvw, N, fov, V) -> float:
 
 def lambda_max_positive(uvw, N, fov, V) -> float:
     """max(0, max_p Phi*(V)_p): the smallest lambda for which x = 0 is optimal
-    when the image is constrained to be non-negative (the positivity variant of
-    Sect. 4.1 / 4.1): the optimality condition at 0 is Phi*(V) <= lambda."""
+    when the image is constrained to be non-negative (the positivity remark of
+    Sect. 4.1): the optimality condition at 0 is Phi*(V) <= lambda."""
     return max(0.0, float(np.max(adjoint(uvw, N, fov, V))))
 
 

@@ -83,11 +83,13 @@ def duality_gap(uvw, N, fov, V, lam, idx, x, positive=False) -> float:
     return F - D
 
 
-def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
-          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None, positive=False) -> SolveResult:
+def frank_wolfe(V, lam, eta_all, columns, lmax, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
+                eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, positive=False):
+    """Algorithm 2 over an abstract set of atoms (pixels, or the atoms of a
+    synthesis dictionary, Sect. 4.3): eta_all(r) is Phi_A*(r) on every atom,
+    columns(S) the columns of the measurement operator of the atoms S (sorted).
+    Returns (S, x, r, F, iterations, converged, history)."""
     V = np.asarray(V, dtype=np.complex128)
-    if lmax is None:
-        lmax = (operators.lambda_max_positive if positive else operators.lambda_max)(uvw, N, fov, V)
     Delta = (1.0 - delta) * lmax
     S = np.zeros(0, dtype=np.int64)
     x = np.zeros(0)
@@ -97,7 +99,7 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
     converged = False
     k = 0
     for k in range(max_fw):
-        eta = operators.adjoint(uvw, N, fov, r)                 # dirty residual, all pixels
+        eta = eta_all(r)                                          # dirty residual, all atoms
         if rule == "R2":
             new = select_r2(eta / lam, delta, positive)
             thr_mu = 1.0 - delta
@@ -107,7 +109,7 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
             thr_mu = (top - 2.0 * Delta / (k + 2)) / lam
         else:
             raise ValueError(rule)
-        # diagnostic (no effect on the iteration): pixels whose candidate value
+        # diagnostic (no effect on the iteration): atoms whose candidate value
         # lies within 1e-5 max|mu| of the threshold, where an FP32 evaluation of
         # the certificate may legitimately take the other side
         cand = eta / lam if positive else np.abs(eta) / lam
@@ -117,8 +119,7 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
         x0 = np.zeros(S_next.size)
         if S.size:
             x0[np.searchsorted(S_next, S)] = x                   # warm start on old atoms
-        l, m, n = operators.pixel_lmn(N, fov, S_next)
-        A = operators.phase_block(uvw, l, m, n)                  # Phi restricted to S_next
+        A = columns(S_next)                                       # operator restricted to S_next
         eps = eps_schedule(k, eps0, eps_min)
         xs, n_it, L = lasso.apgd(A, V, lam, x0, eps, apgd_max_iter, positive=positive)
         keep = xs != 0.0                                          # pruning
@@ -136,5 +137,21 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
         if rel < tol:
             converged = True
             break
+    return S, x, r, F_prev, k + 1, converged, history
+
+
+def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
+          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None, positive=False) -> SolveResult:
+    V = np.asarray(V, dtype=np.complex128)
+    if lmax is None:
+        lmax = (operators.lambda_max_positive if positive else operators.lambda_max)(uvw, N, fov, V)
+
+    def columns(S):
+        l, m, n = operators.pixel_lmn(N, fov, S)
+        return operators.phase_block(uvw, l, m, n)
+
+    S, x, r, F, iters, converged, history = frank_wolfe(
+        V, lam, lambda r: operators.adjoint(uvw, N, fov, r), columns, lmax, delta, rule, tol, max_fw,
+        eps0, eps_min, apgd_max_iter, positive)
     mu = operators.adjoint(uvw, N, fov, r).reshape(N, N) / lam
-    return SolveResult(S, x, mu, F_prev, k + 1, converged, lam, history)
+    return SolveResult(S, x, mu, F, iters, converged, lam, history)
