@@ -5,7 +5,8 @@ defines: the discrete measurement operator and its adjoint (Sect. 2.2, the
 discrete forward equation and its adjoint), the LASSO objective (Sect. 4.1),
 the dual certificate (Sect. 4.2), lambda_max (Sect. 5.3) and the Polyatomic
 Frank-Wolfe loop (Algorithm 2) with an accelerated proximal-gradient
-sub-solver (Sect. 4.4 / Sect. 5.1).
+sub-solver (Sect. 4.4 / Sect. 5.1), over pixels or over the atoms of the
+multi-scale synthesis dictionary (Sect. 4.3, diffuse experiment of Sect. 6).
 
 It is test infrastructure. Only the test-suite, the smoke check of the
 package entry file and the CPU-baseline leg of the benchmark may import it.
@@ -24,4 +25,11 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   pfw.solve                        KKT conditions, monotone objective, alpha identity,
                                    brute force on tiny grids
   pfw.duality_gap                  gap >= 0 and -> 0 at the optimum (KKT test)
+  dictionary.kernel / synthesize   closed form, scipy.signal convolve2d / correlate2d,
+    / analyze                      adjoint identity, single-atom placement and border crop
+  dictionary.columns / forward     composite adjoint identity, sigma = 0 column == Phi column
+    / adjoint / lambda_max
+  dictionary.solve                 one-scale sigma = 0 dictionary == pfw.solve, theta = 0 at
+                                   lambda_max, coordinate descent on the full dictionary
+                                   (also non-negative), optimality conditions
 """
