@@ -239,6 +239,64 @@ int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64_t M, int32
                   int32_t* idx_out_host, float* x_out_host, int32_t cap,
                   pc_solve_stats* stats_host, void* stream);
 
+/* ------------------------------------------------------------------ synthesis dictionary */
+
+/* Multi-scale synthesis dictionary Psi (Sect. 4.3; the diffuse experiment of
+ * Sect. 6 uses sigma = {0, 2, 5, 8}, gamma_i = 1.2^i). The image is
+ * I = Psi theta = sum_i gamma_i g~_i * theta_i with g~_i[n, m] proportional to
+ * exp(-(n^2 + m^2) / sigma_i^2) on the square |n|, |m| <= floor(2 sigma_i),
+ * unit l1 norm; sigma = 0 is the single-pixel (point-source) atom. Each
+ * kernel is centred on its coefficient's pixel and what falls outside the
+ * N x N image is dropped (no renormalisation at the border); Psi* is the
+ * matching correlation over the image. Coefficients are indexed
+ * a = i * N*N + p (scale-major, p the raster pixel), n_scales * N*N of them.
+ * Constraints: 1 <= n_scales <= PC_DICT_MAX_SCALES, 0 <= sigma_i with
+ * floor(2 sigma_i) <= PC_DICT_MAX_RADIUS, gamma_i > 0 and finite. */
+#define PC_DICT_MAX_SCALES 8
+#define PC_DICT_MAX_RADIUS 16
+typedef struct {
+  int32_t version;        /* PC_ABI_VERSION                                      */
+  int32_t n_scales;
+  double  sigma[PC_DICT_MAX_SCALES];
+  double  gamma[PC_DICT_MAX_SCALES];
+} pc_dictionary;
+
+/* eta_out[a] = scale * (Psi* Phi* h)[a] for every coefficient
+ * (n_scales * N*N float32, scale-major). Sect. 4.3 with the adjoint of Sect. 2.2.
+ * Asynchronous on the stream. */
+int pc_dict_adjoint(pc_plan_t plan, const pc_dictionary* dict, const pc_c32* h_dev, double scale,
+                    float* eta_out_dev, void* stream);
+
+/* y_out = Phi Psi theta for S coefficients (idx_dev: strictly ascending in
+ * [0, n_scales N*N); theta_dev float32): each column of Phi Psi is evaluated
+ * as the direct sum of the measurement operator over the atom's footprint
+ * pixels, weighted gamma_i g~_i. Returns PC_ERR_INVALID_ARG for a bad index
+ * list (synchronises the stream to check it). */
+int pc_dict_forward_sparse(pc_plan_t plan, const pc_dictionary* dict, const int32_t* idx_dev,
+                           const float* theta_dev, int32_t S, pc_c32* y_out_dev, void* stream);
+
+/* lambda_max of the synthesis problem: ||Psi* Phi* V||_inf, or with positive
+ * != 0 max(0, max Psi* Phi* V) (the smallest lambda with theta = 0 optimal;
+ * the paper takes lambda_max with Psi). Synchronises the stream. */
+int pc_dict_lambda_max(pc_plan_t plan, const pc_dictionary* dict, const pc_c32* V_dev,
+                       int32_t positive, double* lambda_max_host, void* stream);
+
+/* Synthesis-form solve (Sect. 4.3 with Algorithm 2):
+ * argmin_theta 1/2 ||V - Phi Psi theta||^2 + lambda ||theta||_1 (theta >= 0 with
+ * opts->positivity). Same options, statistics and history as pc_solve, over
+ * the coefficient atoms (rule 2 selects |eta| >= 1 - delta with
+ * eta = Psi* Phi* r / lambda). The diffuse experiment stops at tol = 1e-5.
+ * Writes the support (ascending coefficient indices) and coefficients to
+ * idx_out_dev / theta_out_dev (capacity cap) and, when eta_out_dev is not
+ * NULL, the final certificate (n_scales N*N float32). The columns of Phi Psi
+ * on the active set are kept on the device (M x |S| complex64), so the
+ * working set is limited by device memory (PC_ERR_CAPACITY beyond 60000 atoms). */
+int pc_solve_synthesis(pc_plan_t plan, const pc_dictionary* dict, const pc_c32* V_dev,
+                       double lambda, double delta, const pc_solve_opts* opts,
+                       int32_t* idx_out_dev, float* theta_out_dev, int32_t cap, float* eta_out_dev,
+                       pc_solve_stats* stats_host, pc_iter_record* history_host,
+                       int32_t history_capacity, void* stream);
+
 /* ------------------------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart of this call; it exists for callers that

@@ -117,14 +117,22 @@ def analyze(d: Dictionary, z) -> np.ndarray:
     return out.ravel()
 
 
+_PIXEL_MATRIX_MAX = 1 << 23   # entries of Phi on every pixel worth building once
+
+
 def columns(uvw, fov, d: Dictionary, atoms) -> np.ndarray:
     """Columns of Phi Psi for the atoms (M x len(atoms), complex128): each is
-    Phi applied to the atom's image."""
+    Phi applied to the atom's image, sum_p w_p Phi[:, p] over its footprint.
+    On small problems Phi is built once on every pixel and its columns reused."""
     atoms = np.asarray(atoms, dtype=np.int64)
-    A = np.zeros((uvw.shape[0], atoms.size), dtype=np.complex128)
+    M, N = uvw.shape[0], d.N
+    A = np.zeros((M, atoms.size), dtype=np.complex128)
+    P = None
+    if atoms.size > 1 and M * N * N <= _PIXEL_MATRIX_MAX:
+        P = operators.phase_block(uvw, *operators.pixel_lmn(N, fov, np.arange(N * N)))
     for c, a in enumerate(atoms):
         pix, wts = atom_pixels(d, a)
-        A[:, c] = operators.forward(uvw, d.N, fov, pix, wts)
+        A[:, c] = P[:, pix] @ wts if P is not None else operators.forward(uvw, N, fov, pix, wts)
     return A
 
 

@@ -31,7 +31,8 @@ EXPORTS = [
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
     "pc_profile_begin_classes", "pc_server_create", "pc_server_submit", "pc_server_wait",
-    "pc_server_destroy", "pc_plan_tuning_info",
+    "pc_server_destroy", "pc_plan_tuning_info", "pc_dict_adjoint", "pc_dict_forward_sparse",
+    "pc_dict_lambda_max", "pc_solve_synthesis",
 ]
 
 
@@ -70,6 +71,28 @@ class pc_solve_opts(ctypes.Structure):
                 ("gram_mode", ctypes.c_int32), ("positivity", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("eps_min", ctypes.c_double), ("lambda_max", ctypes.c_double)]
+
+
+PC_DICT_MAX_SCALES = 8
+
+
+class pc_dictionary(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int32), ("n_scales", ctypes.c_int32),
+                ("sigma", ctypes.c_double * PC_DICT_MAX_SCALES),
+                ("gamma", ctypes.c_double * PC_DICT_MAX_SCALES)]
+
+
+def make_dictionary(sigmas=(0.0, 2.0, 5.0, 8.0), gammas=None) -> pc_dictionary:
+    """Multi-scale Gaussian dictionary; gammas default to 1.2^i."""
+    if gammas is None:
+        gammas = [1.2 ** i for i in range(len(sigmas))]
+    d = pc_dictionary()
+    d.version = PC_ABI_VERSION
+    d.n_scales = len(sigmas)
+    for i, (s, g) in enumerate(zip(sigmas, gammas)):
+        d.sigma[i] = float(s)
+        d.gamma[i] = float(g)
+    return d
 
 
 class pc_iter_record(ctypes.Structure):
@@ -134,6 +157,11 @@ def load(path: str | None = None):
                             _P, _I32, _P]),
         "pc_solve_host": (_I32, [_P, _P, _I64, _I32, _D, _D, _D, _P, _P, _P, _I32,
                                  ctypes.POINTER(pc_solve_stats), _P]),
+        "pc_dict_adjoint": (_I32, [_P, ctypes.POINTER(pc_dictionary), _P, _D, _P, _P]),
+        "pc_dict_forward_sparse": (_I32, [_P, ctypes.POINTER(pc_dictionary), _P, _P, _I32, _P, _P]),
+        "pc_dict_lambda_max": (_I32, [_P, ctypes.POINTER(pc_dictionary), _P, _I32, ctypes.POINTER(_D), _P]),
+        "pc_solve_synthesis": (_I32, [_P, ctypes.POINTER(pc_dictionary), _P, _D, _D, _P, _P, _P, _I32, _P,
+                                      ctypes.POINTER(pc_solve_stats), _P, _I32, _P]),
         "pc_adjoint_sparse_noalloc": (_I32, [_P, _I64, _I32, _D, _P, _P, _I32, _P, _P]),
         "pc_profile_begin": (_I32, []),
         "pc_profile_begin_classes": (_I32, [ctypes.c_char_p]),
@@ -341,6 +369,65 @@ def pc_solve(plan: Plan, V: torch.Tensor, lam: float, delta: float, cap: int = 6
                  rel_improvement=h.rel_improvement, lipschitz=h.lipschitz)
             for h in hist[: st.n_history]]
     return dict(idx=idx[:n], x=x[:n], mu=mu, status=st.status, iterations=st.iterations,
+                objective=st.objective, lam=st.lambda_, mu_inf=st.mu_inf, sumsq_V=st.sumsq_V,
+                converged=st.status == PC_OK, history=recs)
+
+
+def pc_dict_adjoint(plan: Plan, dictionary: pc_dictionary, h: torch.Tensor, scale: float = 1.0,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """scale * Psi* Phi* h on every coefficient, shape (n_scales, N, N)."""
+    if out is None:
+        out = torch.empty(dictionary.n_scales, plan.N, plan.N, dtype=torch.float32, device=h.device)
+    _check(load().pc_dict_adjoint(plan.handle, ctypes.byref(dictionary), _dev(h, torch.complex64, "h"),
+                                  float(scale), _dev(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def pc_dict_forward_sparse(plan: Plan, dictionary: pc_dictionary, idx: torch.Tensor, theta: torch.Tensor,
+                           y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Phi Psi theta for coefficients theta on the ascending coefficient indices idx."""
+    if y is None:
+        y = torch.empty(plan.M, dtype=torch.complex64, device=idx.device)
+    _check(load().pc_dict_forward_sparse(plan.handle, ctypes.byref(dictionary), _dev(idx, torch.int32, "idx"),
+                                         _dev(theta, torch.float32, "theta"), int(idx.numel()),
+                                         _dev(y, torch.complex64, "y"), _stream(stream)))
+    return y
+
+
+def pc_dict_lambda_max(plan: Plan, dictionary: pc_dictionary, V: torch.Tensor, positive: bool = False,
+                       stream=None) -> float:
+    out = _D()
+    _check(load().pc_dict_lambda_max(plan.handle, ctypes.byref(dictionary), _dev(V, torch.complex64, "V"),
+                                     int(bool(positive)), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def pc_solve_synthesis(plan: Plan, dictionary: pc_dictionary, V: torch.Tensor, lam: float, delta: float,
+                       cap: int = 65536, want_eta: bool = True, history: int = 256, stream=None,
+                       **opts) -> dict:
+    """Synthesis-form solve over the dictionary; idx are coefficient indices
+    (scale * N^2 + pixel), theta their coefficients."""
+    dev = V.device
+    idx = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    th = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+    eta = (torch.empty(dictionary.n_scales, plan.N, plan.N, dtype=torch.float32, device=dev)
+           if want_eta else None)
+    st = pc_solve_stats()
+    hist = (pc_iter_record * max(history, 1))()
+    o = _solve_opts(**opts)
+    status = load().pc_solve_synthesis(plan.handle, ctypes.byref(dictionary), _dev(V, torch.complex64, "V"),
+                                       float(lam), float(delta), ctypes.byref(o),
+                                       _dev(idx, torch.int32, "idx"), _dev(th, torch.float32, "theta"),
+                                       int(cap), _dev(eta, torch.float32, "eta") if eta is not None else None,
+                                       ctypes.byref(st), hist, int(history), _stream(stream))
+    _check(status, allow=(PC_OK, PC_ERR_NOT_CONVERGED))
+    n = st.n_support
+    recs = [dict(k=h.k, n_new=h.n_new, n_active=h.n_active, n_support=h.n_support,
+                 apgd_iterations=h.apgd_iterations, lanczos_steps=h.lanczos_steps,
+                 mu_inf=h.mu_inf, objective=h.objective,
+                 rel_improvement=h.rel_improvement, lipschitz=h.lipschitz)
+            for h in hist[: st.n_history]]
+    return dict(idx=idx[:n], theta=th[:n], eta=eta, status=st.status, iterations=st.iterations,
                 objective=st.objective, lam=st.lambda_, mu_inf=st.mu_inf, sumsq_V=st.sumsq_V,
                 converged=st.status == PC_OK, history=recs)
 

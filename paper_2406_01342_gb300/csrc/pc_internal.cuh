@@ -54,7 +54,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // when recording is off; prof_stop() records the end event of that token.
 enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
-                 PROF_GRAM_TC, PROF_GRAM_THIN, PROF_NCLASSES };
+                 PROF_GRAM_TC, PROF_GRAM_THIN, PROF_DICT_CORR, PROF_DICT_COLUMNS, PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
 bool prof_active();   // kernel-class timing is recording
 void prof_stop(int token, cudaStream_t st, int kernels);
@@ -67,6 +67,23 @@ struct ProfScope {
   int kernels = 0;
   ProfScope(int cls, cudaStream_t s) : token(prof_start(cls, s)), st(s) {}
   ~ProfScope() { prof_stop(token, st, kernels); }
+};
+
+// Workspace of the synthesis-dictionary calls (dict.cu), created on first use
+// and owned by the plan: the certificate on every coefficient, membership
+// marks, selection block counts, the mu image, and two working sets (support /
+// active set) of indices, weights, b, Gram (ld = capacity rounded to 4) and
+// columns of Phi Psi (capacity x M complex64).
+struct DictWork {
+  DevBuf eta, mark, sel, img, tmpC, oldpos, newrows, keep, acc;
+  DevBuf idx[2], th[2], b[2], G[2], C[2];
+  int64_t n_atoms = 0;
+  int cap = 0;
+  void release() {
+    for (DevBuf* d : {&eta, &mark, &sel, &img, &tmpC, &oldpos, &newrows, &keep, &acc}) d->release();
+    for (int s = 0; s < 2; ++s)
+      for (DevBuf* d : {&idx[s], &th[s], &b[s], &G[s], &C[s]}) d->release();
+  }
 };
 
 // ------------------------------------------------------------------ constants
@@ -266,6 +283,7 @@ struct pc_plan_s {
   // solver workspace (grown on demand)
   pc::DevBuf atomsA, atomsB, idxA, idxB, xA, xB, oldpos, newrows, keep, GA, GB, bA, bB, acc;
   pc::DevBuf perm, atomsP, pbuf;   // tensor-core Gram: atom order (new first), atoms, phase buffer
+  pc::DictWork* dict = nullptr;    // synthesis-dictionary workspace (created on first use)
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
 };

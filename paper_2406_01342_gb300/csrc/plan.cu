@@ -807,6 +807,13 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
   p->bA.release();
   p->bB.release();
   p->acc.release();
+  p->perm.release();
+  p->atomsP.release();
+  p->pbuf.release();
+  if (p->dict) {
+    p->dict->release();
+    delete p->dict;
+  }
   delete p;
 }
 

@@ -77,7 +77,6 @@ int gather_vec(const T* src, const int32_t* map, int n, T* dst, T fill, cudaStre
   return PC_OK;
 }
 
-inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
 
 // Pruning (step 3 of Algorithm 2) in one launch: row i of the new support is
 // entry keep[i] of the active set; copies its Gram row (columns keep[.]) and,
@@ -236,6 +235,8 @@ int gram_update(pc_plan_s* p, const float2* V, const float4* atomsB, int n_act,
   return PC_OK;
 }
 
+}  // namespace
+
 int adjoint_grid_impl(pc_plan_s* p, const float2* h, float* img, float scale, unsigned* maxbits,
                       cudaStream_t st) {
   PC_TRY(launch_grid(p, h, st));
@@ -290,6 +291,8 @@ float key_to_float(unsigned key) {
   if (key == 0) return -INFINITY;
   return bits_to_float((key & 0x80000000u) ? (key & 0x7fffffffu) : ~key);
 }
+
+namespace {
 
 // Small per-device scratch for pc_apgd (no plan): 4 ints + 4 doubles.
 int apgd_scratch(void** out) {

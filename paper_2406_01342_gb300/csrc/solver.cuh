@@ -12,6 +12,20 @@
 
 namespace pc {
 
+inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
+
+// Shared by the solve entry points (solve.cu, dict.cu):
+// mu-image = scale * Phi*(h) on every pixel (gridding, FFT, epilogue), with the
+// max |.| and the signed max as order keys in maxbits[0..1]
+int adjoint_grid_impl(pc_plan_s* p, const float2* h, float* img, float scale, unsigned* maxbits,
+                      cudaStream_t st);
+int check_plan(pc_plan_s* p, const char* fn);
+int check_dev(const void* ptr, bool needed, const char* fn, const char* name);
+// synchronises st and reports an expired bounded wait of the tensor-core gridding
+int grid_flag_sync(pc_plan_s* p, cudaStream_t st, const char* fn);
+float bits_to_float(unsigned b);
+float key_to_float(unsigned key);   // inverse of float_order_key (0 -> -infinity)
+
 struct SolveCfg {
   int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0;
   double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
