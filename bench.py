@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-stream leg (64 requests, Poisson arrivals, p50/p99)")
+    ap.add_argument("--no-diffuse", action="store_true",
+                    help="skip the synthesis-dictionary leg (256^2 diffuse sky, M = 31.6k)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="build the timed plan without the plan-time autotuner")
     return ap.parse_args()
 
 
@@ -144,14 +148,14 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workload
 
-def make_inputs(abi, synth, name, device):
+def make_inputs(abi, synth, name, device, autotune=0):
     """Plan and visibilities on the device. V = Phi(sky) + noise with Phi the
     library's own forward operator; the noise level sets the workload's SNR."""
     import numpy as np
     import torch
     wl = synth.WORKLOADS[name]()
     uvw = torch.from_numpy(wl.uvw).to(device)
-    plan = abi.pc_plan_create(uvw, wl.N, wl.fov)
+    plan = abi.pc_plan_create(uvw, wl.N, wl.fov, autotune=autotune)
     Vc = abi.pc_forward_sparse(plan, torch.from_numpy(wl.sky_idx).to(device),
                                torch.from_numpy(wl.sky_flux.astype(np.float32)).to(device))
     p_sig = float((Vc.abs() ** 2).mean())
@@ -332,6 +336,42 @@ def serving_leg(abi, synth, torch, device, max_jobs: int = 8) -> dict:
                    "alpha 0.1, delta 0.01, 20 dB"}
 
 
+def diffuse_leg(abi, synth, torch, device, steps: int, l2_flush) -> dict:
+    """The synthesis-dictionary solve (Sect. 4.3) on the diffuse 256 x 256,
+    M = 31.6k workload: 4 Gaussian scales, lambda = 0.02 lambda_max, the
+    exploration rule of Algorithm 2 with delta = 0.98, stop at 1e-5; plan and
+    V resident, L2 flushed between solves, CUDA events around each solve."""
+    wl, _, plan, V = make_inputs(abi, synth, "diffuse_256", device)
+    d = abi.make_dictionary()
+    lam = wl.alpha * abi.pc_dict_lambda_max(plan, d, V)
+
+    def solve():
+        return abi.pc_solve_synthesis(plan, d, V, lam, wl.delta, tol=1e-5, select_rule=1, max_fw=1000,
+                                      want_eta=False, history=1)
+
+    for _ in range(2):
+        res = solve()
+    abi.pc_profile_begin()
+    solve()
+    prof = abi.pc_profile_end()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush_l2(l2_flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = solve()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    return {"workload": f"diffuse_256: {wl.N}x{wl.N} image, M={wl.M}, 4 scales sigma 0/2/5/8 "
+                        f"gamma 1.2^i, lambda={wl.alpha} lambda_max, rule R1 delta={wl.delta}, tol 1e-5",
+            "solves_per_s": 1e3 / t, "solve_time_s": t / 1e3, "iterations": res["iterations"],
+            "support": int(res["idx"].numel()), "converged": res["converged"],
+            "kernels_ms": {k: round(v[2], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])}}
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 
 def oracle_sample_seconds(name: str, n_pix: int, seed: int = 0) -> tuple[float, int]:
@@ -402,8 +442,9 @@ def run_ours(args, world, rank, local):
     abi.load()
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    wl, uvw, plan, V = make_inputs(abi, synth, args.workload, device)
+    wl, uvw, plan, V = make_inputs(abi, synth, args.workload, device, autotune=0 if args.no_autotune else 1)
     info = abi.pc_plan_info(plan)
+    tuning = abi.pc_plan_tuning_info(plan)
     lmax = abi.pc_lambda_max(plan, V)
     lam = wl.alpha * lmax
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
@@ -481,6 +522,9 @@ def run_ours(args, world, rank, local):
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_leg(abi, synth, torch, device)
+    diffuse = None
+    if rank == 0 and not args.no_diffuse:
+        diffuse = diffuse_leg(abi, synth, torch, device, args.steps, l2_flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -500,6 +544,7 @@ def run_ours(args, world, rank, local):
                                    f"{info['n_planes']} w-planes, {wl.sky_idx.size} point sources, "
                                    f"lambda={wl.alpha} lambda_max, delta={wl.delta}",
                        "l2": "flushed between timed steps (256 MB write)",
+                       "plan_tuning": tuning,
                        "parallelism": f"replicas x{world}"},
             "solve_time_s": total_ms / args.steps / 1e3,
             "solve": {"iterations": res["iterations"], "support": int(res["idx"].numel()),
@@ -511,7 +556,7 @@ def run_ours(args, world, rank, local):
             "roofline_kernel": {k: rl[k] for k in ("kernel", "avg_launch_ms", "launches")},
             "peaks_source": "MEASURED_PEAKS.json (measured)" if "_fallback" not in peaks else "fallback",
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
-            "cpu_baseline": cpu, "serving": serving, "wall_s": t_wall,
+            "cpu_baseline": cpu, "serving": serving, "diffuse": diffuse, "wall_s": t_wall,
         }
         print(json.dumps(line), flush=True)
 
