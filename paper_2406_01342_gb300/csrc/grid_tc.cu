@@ -52,6 +52,7 @@ constexpr int GT_SMEM = 2 * GT_A_BYTES + 2 * GT_B_BYTES;   // 80 KB
 constexpr int GT_THREADS = 256;
 constexpr uint32_t GT_TMEM_COLS = 128;         // two 128 x 64 accumulators
 constexpr long long GT_WAIT_CYCLES = 4000000000ll;
+constexpr int GT_FOLD = 4;                     // stages accumulated in TMEM per fold
 
 __device__ __forceinline__ void red_add_v2(float2* addr, float x, float y) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(x), "f"(y) : "memory");
@@ -121,7 +122,10 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
 
   const uint32_t idesc = tc::instr_desc_f16(128, GT_N);
   bool ok = true;
+  bool pending = false;        // thread 0: MMAs committed and not yet waited for
+  int committed = 0;           // thread 0: stage of the last commit
   int stage = 0;
+  if (tid == 0) s_go = 1;
   for (int c0 = sub.z; c0 < sub.w; c0 += GT_KS, ++stage) {
     const int cnt = min(GT_KS, sub.w - c0);
     // ---- 1a. per-visibility weights, one role per warp pair (no divergence):
@@ -186,7 +190,17 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
       const __half hl = __float2half_rn(v - __half2float(hh));
       *dst = (uint32_t)__half_as_ushort(hh) | ((uint32_t)__half_as_ushort(hl) << 16);
     }
+    // the previous stage's MMAs still read A and B: wait for them (bounded)
+    // before overwriting; their latency hid behind steps 1a and 1b
+    if (tid == 0 && pending) {
+      s_go = tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)((stage - 1) & 1), nullptr, GT_WAIT_CYCLES) ? 1 : 0;
+      pending = !s_go;
+    }
     __syncthreads();
+    if (!s_go) {
+      ok = false;
+      break;
+    }
     // ---- 2a. A: thread = row (plane q, column a); 8 visibilities per 16-byte store
     if (tid < n_tiles * 128) {
       const int R = tid, q = R >> 5, a = R & 31;
@@ -240,7 +254,8 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
-    // ---- 3. MMAs (one thread) and commit
+    // ---- 3. MMAs (one thread) and commit; the accumulators restart after each fold
+    const bool fold_now = (stage % GT_FOLD) == GT_FOLD - 1 || c0 + GT_KS >= sub.w;
     if (tid == 0) {
       tc::fence_after_sync();
       const uint32_t ah = tc::smem_u32(A_hi), al = tc::smem_u32(A_lo);
@@ -252,7 +267,8 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
         for (int ks = 0; ks < GT_KS / 16; ++ks) {
           const uint32_t koff = (uint32_t)ks * 2 * GT_LBO;
           tc::mma_f16(d, tc::smem_desc(ah + toff + koff, GT_LBO, GT_SBO),
-                      tc::smem_desc(bh + koff, GT_LBO, GT_SBO), idesc, ks > 0 ? 1u : 0u);
+                      tc::smem_desc(bh + koff, GT_LBO, GT_SBO), idesc,
+                      (ks > 0 || stage % GT_FOLD != 0) ? 1u : 0u);
           tc::mma_f16(d, tc::smem_desc(ah + toff + koff, GT_LBO, GT_SBO),
                       tc::smem_desc(bl + koff, GT_LBO, GT_SBO), idesc, 1u);
           tc::mma_f16(d, tc::smem_desc(al + toff + koff, GT_LBO, GT_SBO),
@@ -260,14 +276,20 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
         }
       }
       tc::mma_commit(tc::smem_u32(&s_mbar));
-      s_go = tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)(stage & 1), nullptr, GT_WAIT_CYCLES) ? 1 : 0;
+      pending = true;
+      committed = stage;
+      if (fold_now) {
+        s_go = tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)(stage & 1), nullptr, GT_WAIT_CYCLES) ? 1 : 0;
+        pending = !s_go;
+      }
     }
+    if (!fold_now) continue;
     __syncthreads();
     if (!s_go) {
       ok = false;
       break;
     }
-    // ---- 4. fold the stage's partial tile into the register accumulators
+    // ---- 4. fold the partial tile of the last GT_FOLD stages into the registers
     tc::fence_after_sync();
     if (my_tile < n_tiles) {
       __syncwarp();
@@ -285,10 +307,11 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
   }
 
   if (!ok) {
-    // the MMAs of the stage may still be running: wait for them (bounded) before
-    // freeing tensor memory; report the expiry
+    // MMAs may still be running: wait for them (bounded) before freeing tensor
+    // memory; report the expiry
     if (tid == 0) {
-      tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)(stage & 1), nullptr, GT_WAIT_CYCLES);
+      if (pending)
+        tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)(committed & 1), nullptr, GT_WAIT_CYCLES);
       atomicExch(err, 1);
     }
   } else {
