@@ -86,6 +86,30 @@ struct DictWork {
   }
 };
 
+// Per-plan resources of the solver loop, created by the first solve on the
+// plan and kept until it is destroyed: the pinned readback buffer, the
+// completion event, a private stream for callers on the legacy default
+// stream, and the instantiated graph of the iteration chain together with the
+// arguments it was captured for (a later solve with the same arguments
+// launches it without capturing again).
+struct SolveCache {
+  void* rb = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaStream_t own = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint64_t> key;
+  void release() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (own) cudaStreamDestroy(own);
+    if (ev) cudaEventDestroy(ev);
+    if (rb) cudaFreeHost(rb);
+    gexec = nullptr;
+    own = nullptr;
+    ev = nullptr;
+    rb = nullptr;
+  }
+};
+
 // ------------------------------------------------------------------ constants
 
 constexpr int kMaxW = 8;              // largest supported ES kernel width
@@ -284,6 +308,7 @@ struct pc_plan_s {
   pc::DevBuf atomsA, atomsB, idxA, idxB, xA, xB, oldpos, newrows, keep, GA, GB, bA, bB, acc;
   pc::DevBuf perm, atomsP, pbuf;   // tensor-core Gram: atom order (new first), atoms, phase buffer
   pc::DictWork* dict = nullptr;    // synthesis-dictionary workspace (created on first use)
+  pc::SolveCache* scache = nullptr; // solver-loop resources (created by the first solve)
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
 };

@@ -317,13 +317,12 @@ __global__ void k_pix_tab(PixGeom g, const double* __restrict__ psi_uv,
   double s = -r2 / (1.0 + n);        // n - 1 without cancellation
   double t = 0.0, psiw = 1.0;
   if (g.wstack) {
+    // psi_w(t) = W sum_q w_q phi(z_q) cos(pi W z_q t): glx holds W z_q and glw
+    // w_q phi(z_q) (node-only factors, from the host); |W z_q t| <= W/4, where an
+    // FP32 cosine is accurate to ~1e-7
     t = g.dw * (s - g.s_c);
     double acc = 0.0;
-    for (int q = 0; q < nq; ++q) {
-      double z = glx[q];
-      double phi = exp(g.beta * (sqrt(fmax(0.0, 1.0 - z * z)) - 1.0));
-      acc += glw[q] * phi * cospi(g.W * z * t);
-    }
+    for (int q = 0; q < nq; ++q) acc += glw[q] * (double)cospif((float)(glx[q] * t));
     psiw = g.W * acc;
   }
   double ct = g.w0 * s;
@@ -550,8 +549,14 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   d_gx = d_psi + N;
   d_gw = d_gx + kGlNodes;
   PC_CUDA(cudaMemcpyAsync(d_psi, psi.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
-  PC_CUDA(cudaMemcpyAsync(d_gx, gx.data(), sizeof(double) * kGlNodes, cudaMemcpyHostToDevice, st));
-  PC_CUDA(cudaMemcpyAsync(d_gw, gw.data(), sizeof(double) * kGlNodes, cudaMemcpyHostToDevice, st));
+  // node factors of the w-kernel correction: W z_q and w_q phi(z_q)
+  std::vector<double> wz(kGlNodes), wphi(kGlNodes);
+  for (int q = 0; q < kGlNodes; ++q) {
+    wz[q] = p->W * gx[q];
+    wphi[q] = gw[q] * std::exp(p->beta * (std::sqrt(std::max(0.0, 1.0 - gx[q] * gx[q])) - 1.0));
+  }
+  PC_CUDA(cudaMemcpyAsync(d_gx, wz.data(), sizeof(double) * kGlNodes, cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaMemcpyAsync(d_gw, wphi.data(), sizeof(double) * kGlNodes, cudaMemcpyHostToDevice, st));
   const int64_t NN = (int64_t)N * N;
   PC_TRY(dev_alloc_t(p, &p->pix_tab, NN));
   {
@@ -813,6 +818,10 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
   if (p->dict) {
     p->dict->release();
     delete p->dict;
+  }
+  if (p->scache) {
+    p->scache->release();
+    delete p->scache;
   }
   delete p;
 }

@@ -542,12 +542,7 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
   return PC_OK;
 }
 
-SolveJob::~SolveJob() {
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (own) cudaStreamDestroy(own);
-  if (rb) cudaFreeHost(rb);
-  if (ev) cudaEventDestroy(ev);
-}
+SolveJob::~SolveJob() {}   // rb, ev, own and the graph stay with the plan
 
 int SolveJob::grow(int need) {
   if (need <= wcap && p->idxB.p) return PC_OK;
@@ -581,10 +576,15 @@ int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double
   hist = hist_;
   hist_cap = hist_cap_;
   mu_dst = mu_out ? mu_out : p->mu;
-  PC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&rb), sizeof(Readback)));
-  PC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  if (!p->scache) p->scache = new SolveCache();
+  SolveCache& sc = *p->scache;
+  if (!sc.rb) PC_CUDA(cudaMallocHost(&sc.rb, sizeof(Readback)));
+  if (!sc.ev) PC_CUDA(cudaEventCreateWithFlags(&sc.ev, cudaEventDisableTiming));
+  rb = static_cast<Readback*>(sc.rb);
+  ev = sc.ev;
   if (stream == nullptr || stream == cudaStreamLegacy) {
-    PC_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    if (!sc.own) PC_CUDA(cudaStreamCreateWithFlags(&sc.own, cudaStreamNonBlocking));
+    own = sc.own;
     PC_CUDA(cudaEventRecord(ev, stream));
     PC_CUDA(cudaStreamWaitEvent(own, ev, 0));
     st = own;
@@ -655,28 +655,52 @@ int SolveJob::enqueue_chain(int bound) {
   return PC_OK;
 }
 
+std::vector<uint64_t> SolveJob::graph_key() const {
+  auto u = [](const void* q) { return (uint64_t)(uintptr_t)q; };
+  const float inv_l = (float)(1.0 / lambda), thr = (float)(1.0 - delta);
+  uint32_t bl, bt;
+  std::memcpy(&bl, &inv_l, 4);
+  std::memcpy(&bt, &thr, 4);
+  return {u(V), u(mu_dst), u(rb), bl, bt, (uint64_t)c.positive, (uint64_t)wcap, u(p->keep.p),
+          u(p->idxA.p), u(p->idxB.p), u(p->xA.p), u(p->xB.p), u(p->bA.p), u(p->bB.p), u(p->GA.p),
+          u(p->GB.p), u(p->atomsA.p)};
+}
+
 // One iteration. With rule R2 (its threshold does not depend on k) and no
-// kernel-class timing, the chain is captured once as a CUDA graph (bounds =
-// the working-set capacity, every count read on the device) and replayed each
-// iteration: one launch instead of a dozen; re-captured when the capacity grows.
+// kernel-class timing, the chain is captured as a CUDA graph (bounds = the
+// working-set capacity, every count read on the device) and replayed each
+// iteration: one launch instead of a dozen. The plan keeps the instantiated
+// graph with the arguments it was captured for; it is captured again (and
+// the executable updated in place where the topology allows) only when one
+// of them changes, e.g. when the working set grows or another V is solved.
 int SolveJob::queue_iteration() {
   if (k > 0) ldA = ldB_prev;
   if (c.rule == 2 && !prof_active()) {
-    if (!gexec || graph_wcap != wcap) {
-      if (gexec) cudaGraphExecDestroy(gexec);
-      gexec = nullptr;
+    SolveCache& sc = *p->scache;
+    std::vector<uint64_t> key = graph_key();
+    if (!sc.gexec || sc.key != key) {
       cudaGraph_t g = nullptr;
       PC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       const int rc = enqueue_chain(wcap);
       const cudaError_t e = cudaStreamEndCapture(st, &g);
       PC_TRY(rc);
       PC_CUDA(e);
-      const cudaError_t ei = cudaGraphInstantiate(&gexec, g, 0);
+      if (sc.gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(sc.gexec, g, &info) != cudaSuccess) {
+          cudaGetLastError();
+          cudaGraphExecDestroy(sc.gexec);
+          sc.gexec = nullptr;
+        }
+      }
+      cudaError_t ei = cudaSuccess;
+      if (!sc.gexec) ei = cudaGraphInstantiate(&sc.gexec, g, 0);
       cudaGraphDestroy(g);
+      if (ei != cudaSuccess) sc.gexec = nullptr;
       PC_CUDA(ei);
-      graph_wcap = wcap;
+      sc.key = std::move(key);
     }
-    PC_CUDA(cudaGraphLaunch(gexec, st));
+    PC_CUDA(cudaGraphLaunch(sc.gexec, st));
   } else {
     PC_TRY(enqueue_chain(k > 0 ? n_prev_act : 0));
   }

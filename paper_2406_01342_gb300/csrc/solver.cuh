@@ -65,14 +65,12 @@ struct SolveJob {
     double hd[3];
     unsigned mb[2];
   };
+  // readback buffer, event and private stream belong to the plan's SolveCache
   Readback* rb = nullptr;
   cudaEvent_t ev = nullptr;
-  // the iteration chain as a CUDA graph (rule R2 without kernel-class timing)
-  cudaGraphExec_t gexec = nullptr;
-  int graph_wcap = -1;
-  // The legacy default stream cannot be captured: a job given it runs on a
-  // stream of its own, ordered after the caller's earlier work and before its
-  // later work by events.
+  // The legacy default stream cannot be captured: a job given it runs on the
+  // plan's private stream, ordered after the caller's earlier work and before
+  // its later work by events.
   cudaStream_t caller = nullptr;
   cudaStream_t own = nullptr;
 
@@ -96,6 +94,7 @@ struct SolveJob {
 
  private:
   int ld() const { return (wcap + 3) & ~3; }   // leading dimension of the Gram buffers
+  std::vector<uint64_t> graph_key() const;     // every argument the captured chain depends on
   int grow(int need);
   int explore();
   int enqueue_chain(int bound);
