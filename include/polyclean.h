@@ -395,6 +395,15 @@ int pc_profile_end(pc_kernel_time* out_host, int32_t cap, int32_t* n_out_host);
 const char* pc_last_error(void);
 int pc_abi_version(void);
 
+/* Device memory the library allocates (plans, solver working sets, the
+ * server's per-request buffers) comes from a stream-ordered pool per device
+ * that keeps freed memory for reuse, so repeated plans and solves do not pay
+ * for cudaMalloc / cudaFree; pinned host blocks and streams are recycled the
+ * same way. pc_trim_memory waits for the device, then returns every cached
+ * block that no plan or server holds to the system. PC_ERR_CUDA reports an
+ * earlier asynchronous error. */
+int pc_trim_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

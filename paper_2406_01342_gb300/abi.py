@@ -32,7 +32,7 @@ EXPORTS = [
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
     "pc_profile_begin_classes", "pc_server_create", "pc_server_submit", "pc_server_wait",
     "pc_server_destroy", "pc_plan_tuning_info", "pc_dict_adjoint", "pc_dict_forward_sparse",
-    "pc_dict_lambda_max", "pc_solve_synthesis",
+    "pc_dict_lambda_max", "pc_solve_synthesis", "pc_trim_memory",
 ]
 
 
@@ -173,6 +173,7 @@ def load(path: str | None = None):
         "pc_profile_end": (_I32, [ctypes.POINTER(pc_kernel_time), _I32, ctypes.POINTER(_I32)]),
         "pc_last_error": (ctypes.c_char_p, []),
         "pc_abi_version": (_I32, []),
+        "pc_trim_memory": (_I32, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -530,3 +531,8 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def pc_trim_memory() -> None:
+    """Return the library's cached device and pinned memory to the system."""
+    _check(load().pc_trim_memory())

@@ -1,6 +1,9 @@
-// Error reporting, device-pointer checks and grow-only device buffers.
+// Error reporting, device-pointer checks, the library's memory pools and
+// grow-only device buffers.
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "pc_internal.cuh"
 
@@ -29,25 +32,146 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// ---------------------------------------------------------------- memory pools
+
+namespace {
+std::mutex g_mem_mutex;
+std::map<int, cudaMemPool_t> g_pools;
+std::vector<std::pair<size_t, void*>> g_pinned;       // free pinned host blocks
+std::map<void*, size_t> g_pinned_size;                // size of every pinned block handed out
+std::map<int, std::vector<cudaStream_t>> g_streams;   // free non-blocking streams per device
+
+cudaMemPool_t pool_of_current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = ~0ull;   // keep freed memory for reuse (pc_trim_memory returns it)
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  g_pools[dev] = pool;
+  return pool;
+}
+}  // namespace
+
+int dmalloc(void** ptr, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 256;
+  cudaMemPool_t pool = pool_of_current_device();
+  if (!pool) return fail(PC_ERR_CUDA, "device memory pool could not be created");
+  const cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA,
+                "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return PC_OK;
+}
+
+void dfree(void* ptr, cudaStream_t st) {
+  if (ptr) cudaFreeAsync(ptr, st);
+}
+
+void dfree_idle(void* ptr) {
+  if (!ptr) return;
+  cudaDeviceSynchronize();
+  cudaFreeAsync(ptr, 0);
+}
+
+void* pinned_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mutex);
+    long best = -1;   // the smallest free block that fits
+    for (size_t i = 0; i < g_pinned.size(); ++i)
+      if (g_pinned[i].first >= bytes && (best < 0 || g_pinned[i].first < g_pinned[(size_t)best].first))
+        best = (long)i;
+    if (best >= 0) {
+      void* q = g_pinned[(size_t)best].second;
+      g_pinned.erase(g_pinned.begin() + best);
+      return q;
+    }
+  }
+  void* q = nullptr;
+  const size_t want = bytes < 4096 ? 4096 : bytes;
+  if (cudaMallocHost(&q, want) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  g_pinned_size[q] = want;
+  return q;
+}
+
+void pinned_put(void* q) {
+  if (!q) return;
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  g_pinned.emplace_back(g_pinned_size[q], q);
+}
+
+cudaStream_t stream_get() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mutex);
+    auto& v = g_streams[dev];
+    if (!v.empty()) {
+      cudaStream_t s = v.back();
+      v.pop_back();
+      return s;
+    }
+  }
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return s;
+}
+
+void stream_put(cudaStream_t s) {
+  if (!s) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  g_streams[dev].push_back(s);
+}
+
+int trim_memory() {
+  if (cudaDeviceSynchronize() != cudaSuccess)
+    return fail(PC_ERR_CUDA, "pc_trim_memory: %s", cudaGetErrorString(cudaGetLastError()));
+  std::lock_guard<std::mutex> lk(g_mem_mutex);
+  for (auto& kv : g_pools) cudaMemPoolTrimTo(kv.second, 0);
+  for (auto& b : g_pinned) {
+    g_pinned_size.erase(b.second);
+    cudaFreeHost(b.second);
+  }
+  g_pinned.clear();
+  return PC_OK;
+}
+
 int DevBuf::ensure(size_t nbytes) {
   if (nbytes <= bytes && p != nullptr) return PC_OK;
-  if (p) cudaFree(p);
+  dfree_idle(p);
   p = nullptr;
   bytes = 0;
   size_t want = nbytes < 256 ? 256 : nbytes;
-  cudaError_t e = cudaMalloc(&p, want);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
-    return fail(PC_ERR_OOM, "device allocation of %zu bytes failed: %s", want,
-                cudaGetErrorString(e));
-  }
+  PC_TRY(dmalloc(&p, want, 0));
+  PC_CUDA(cudaStreamSynchronize(0));   // usable from every stream
   bytes = want;
   return PC_OK;
 }
 
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  dfree_idle(p);
   p = nullptr;
   bytes = 0;
 }
@@ -57,6 +181,11 @@ void DevBuf::release() {
 extern "C" const char* pc_last_error(void) { return pc::g_last_error; }
 
 extern "C" int pc_abi_version(void) { return PC_ABI_VERSION; }
+
+extern "C" int pc_trim_memory(void) {
+  pc::clear_error();
+  return pc::trim_memory();
+}
 
 // ------------------------------------------------------------------ kernel timing
 

@@ -335,15 +335,13 @@ __global__ void k_pix_tab(PixGeom g, const double* __restrict__ psi_uv,
   out[p] = make_float4((float)(cs * d), (float)(sn * d), t_hi, t_lo);
 }
 
+// The stream plan construction runs on: plan buffers come from the library's
+// pool ordered on it (construction ends with a synchronisation of this stream,
+// after which every stream may use them).
+static thread_local cudaStream_t g_build_stream = nullptr;
+
 static int dev_alloc(pc_plan_s* p, void** ptr, size_t bytes) {
-  if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(ptr, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *ptr = nullptr;
-    return fail(PC_ERR_OOM, "plan: device allocation of %zu bytes failed: %s", bytes,
-                cudaGetErrorString(e));
-  }
+  PC_TRY(dmalloc(ptr, bytes == 0 ? 16 : bytes, g_build_stream));
   p->owned.push_back(*ptr);
   return PC_OK;
 }
@@ -356,17 +354,12 @@ static int dev_alloc_t(pc_plan_s* p, T** ptr, size_t count) {
 // Temporary device buffers of plan construction, freed on every exit path.
 struct TmpBufs {
   std::vector<void*> v;
+  cudaStream_t st = nullptr;
   ~TmpBufs() {
-    for (void* q : v) cudaFree(q);
+    for (void* q : v) dfree(q, st);   // ordered after their last use on st
   }
   int alloc(void** ptr, size_t bytes) {
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(ptr, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      *ptr = nullptr;
-      return fail(PC_ERR_OOM, "plan: temporary allocation of %zu bytes failed", bytes);
-    }
+    PC_TRY(dmalloc(ptr, bytes == 0 ? 16 : bytes, st));
     v.push_back(*ptr);
     return PC_OK;
   }
@@ -474,7 +467,9 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
 static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_planes) {
   const int64_t M = p->M;
   const int N = p->N;
+  g_build_stream = st;
   TmpBufs tmp;
+  tmp.st = st;
 
   // ---- w range and finiteness
   if (M > 0) {
@@ -797,7 +792,10 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
 
 extern "C" void pc_plan_destroy(pc_plan_t p) {
   if (!p) return;
-  for (void* q : p->owned) cudaFree(q);
+  // the buffers may still be in use on any stream: wait for the device once
+  // (as cudaFree would), then return them to the pool
+  cudaDeviceSynchronize();
+  for (void* q : p->owned) dfree(q, 0);
   p->atomsA.release();
   p->atomsB.release();
   p->idxA.release();

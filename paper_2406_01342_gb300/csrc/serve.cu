@@ -114,13 +114,16 @@ void release(Active* a) {
   a->job.reset();                                   // pinned readback, event
   if (a->plan) pc_plan_destroy(a->plan);
   a->plan = nullptr;
-  if (a->d_uvw) cudaFree(a->d_uvw);
+  if (a->d_uvw) dfree(a->d_uvw, a->st);
   a->d_uvw = nullptr;
-  if (a->st) cudaStreamDestroy(a->st);
+  if (a->st) {
+    cudaStreamSynchronize(a->st);
+    stream_put(a->st);
+  }
   a->st = nullptr;
   if (a->req) {
-    cudaFreeHost(a->req->uvw);
-    cudaFreeHost(a->req->V);
+    pinned_put(a->req->uvw);
+    pinned_put(a->req->V);
     a->req->uvw = nullptr;
     a->req->V = nullptr;
   }
@@ -129,13 +132,13 @@ void release(Active* a) {
 // Inputs to the device, plan, lambda = alpha lambda_max, first iteration queued.
 int admit(pc_server_s* s, Active* a) {
   Request& r = *a->req;
-  PC_CUDA(cudaStreamCreateWithFlags(&a->st, cudaStreamNonBlocking));
+  if (!(a->st = stream_get())) return fail(PC_ERR_CUDA, "pc_server: stream creation failed");
   a->cap = (int)std::min<int64_t>((int64_t)r.N * r.N, 1 << 20);
   const size_t b_uvw = sizeof(double) * 3 * (size_t)std::max<int64_t>(r.M, 1);
   const size_t b_V = sizeof(float2) * (size_t)std::max<int64_t>(r.M, 1);
   const size_t b_out = (sizeof(int32_t) + sizeof(float)) * (size_t)a->cap;
   char* base = nullptr;
-  PC_CUDA(cudaMalloc(&base, b_uvw + b_V + b_out + 64));
+  PC_TRY(dmalloc(reinterpret_cast<void**>(&base), b_uvw + b_V + b_out + 64, a->st));
   a->d_uvw = reinterpret_cast<double*>(base);
   a->d_V = reinterpret_cast<float2*>(base + b_uvw);
   a->d_idx = reinterpret_cast<int32_t*>(base + b_uvw + b_V);
@@ -372,10 +375,11 @@ extern "C" int pc_server_submit(pc_server_t s, const double* uvw, const pc_c32* 
   r->fov = fov;
   r->alpha = alpha;
   r->delta = delta;
-  PC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&r->uvw), sizeof(double) * 3 * std::max<int64_t>(M, 1)));
-  if (cudaMallocHost(reinterpret_cast<void**>(&r->V), sizeof(pc_c32) * std::max<int64_t>(M, 1)) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFreeHost(r->uvw);
+  r->uvw = static_cast<double*>(pinned_get(sizeof(double) * 3 * std::max<int64_t>(M, 1)));
+  r->V = static_cast<pc_c32*>(pinned_get(sizeof(pc_c32) * std::max<int64_t>(M, 1)));
+  if (!r->uvw || !r->V) {
+    pinned_put(r->uvw);
+    pinned_put(r->V);
     return fail(PC_ERR_OOM, "pc_server_submit: pinned host allocation failed");
   }
   double wmin = 0.0, wmax = 0.0;
@@ -392,8 +396,8 @@ extern "C" int pc_server_submit(pc_server_t s, const double* uvw, const pc_c32* 
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
-      cudaFreeHost(r->uvw);
-      cudaFreeHost(r->V);
+      pinned_put(r->uvw);
+      pinned_put(r->V);
       return fail(PC_ERR_INVALID_ARG, "pc_server_submit: server is shutting down");
     }
     r->id = s->next_id++;

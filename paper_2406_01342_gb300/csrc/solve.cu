@@ -578,12 +578,13 @@ int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double
   mu_dst = mu_out ? mu_out : p->mu;
   if (!p->scache) p->scache = new SolveCache();
   SolveCache& sc = *p->scache;
-  if (!sc.rb) PC_CUDA(cudaMallocHost(&sc.rb, sizeof(Readback)));
+  if (!sc.rb && !(sc.rb = pinned_get(sizeof(Readback))))
+    return fail(PC_ERR_OOM, "pc_solve: pinned host allocation failed");
   if (!sc.ev) PC_CUDA(cudaEventCreateWithFlags(&sc.ev, cudaEventDisableTiming));
   rb = static_cast<Readback*>(sc.rb);
   ev = sc.ev;
   if (stream == nullptr || stream == cudaStreamLegacy) {
-    if (!sc.own) PC_CUDA(cudaStreamCreateWithFlags(&sc.own, cudaStreamNonBlocking));
+    if (!sc.own && !(sc.own = stream_get())) return fail(PC_ERR_CUDA, "pc_solve: stream creation failed");
     own = sc.own;
     PC_CUDA(cudaEventRecord(ev, stream));
     PC_CUDA(cudaStreamWaitEvent(own, ev, 0));
@@ -753,7 +754,7 @@ int SolveJob::process() {
     // grow, keeping the current support and weights
     int32_t* old_idx = nullptr;
     const size_t gbytes = (size_t)nS * ldA * sizeof(float);
-    PC_CUDA(cudaMalloc(&old_idx, sizeof(int32_t) * std::max(nS, 1) * 3 + gbytes + 16));
+    PC_TRY(dmalloc(reinterpret_cast<void**>(&old_idx), sizeof(int32_t) * std::max(nS, 1) * 3 + gbytes + 16, st));
     float* old_x = reinterpret_cast<float*>(old_idx + std::max(nS, 1));
     float* old_b = old_x + std::max(nS, 1);
     float* old_G = old_b + std::max(nS, 1);
@@ -770,7 +771,7 @@ int SolveJob::process() {
       cudaMemcpyAsync(p->GA.p, old_G, gbytes, cudaMemcpyDeviceToDevice, st);
       cudaStreamSynchronize(st);
     }
-    cudaFree(old_idx);
+    dfree(old_idx, st);
     PC_TRY(rc);
     PC_LAUNCH_CHECK();
     PC_TRY(explore());
@@ -905,7 +906,7 @@ extern "C" int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64
   const size_t b_V = sizeof(pc_c32) * (size_t)std::max<int64_t>(M, 1);
   const size_t b_idx = sizeof(int32_t) * (size_t)std::max(cap, 1);
   const size_t b_x = sizeof(float) * (size_t)std::max(cap, 1);
-  PC_CUDA(cudaMalloc(&buf, b_uvw + b_V + b_idx + b_x + 64));
+  PC_TRY(dmalloc(&buf, b_uvw + b_V + b_idx + b_x + 64, st));
   char* base = static_cast<char*>(buf);
   double* d_uvw = reinterpret_cast<double*>(base);
   pc_c32* d_V = reinterpret_cast<pc_c32*>(base + b_uvw);
@@ -944,7 +945,7 @@ extern "C" int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PC_ERR_CUDA, "pc_solve_host: device-to-host copy failed");
   } while (0);
   if (plan) pc_plan_destroy(plan);
-  cudaFree(buf);
+  dfree(buf, st);
   if (stats_host) *stats_host = local;
   return rc;
 }

@@ -173,3 +173,28 @@ def test_apgd_positive_matches_oracle_subsolver(abi):
     assert abs(L - L_ref) <= 1e-4 * L_ref
     assert rel_l2(xg, x_ref) <= 1e-3
     assert set(np.nonzero(xg)[0]) == set(np.nonzero(x_ref)[0])
+
+
+def test_pooled_memory_reuse_and_trim(abi):
+    """Plans and solves draw device memory from the library's pool: building,
+    solving and destroying plans repeatedly gives the same result (support
+    identical; weights and objective up to the order of atomic additions), and
+    pc_trim_memory returns the cached memory without disturbing a later solve."""
+    wl, V = workload("small_wide_w")
+    Vd = to_dev(V.astype(np.complex64))
+    first = None
+    for rep in range(3):
+        plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+        lam = 0.05 * abi.pc_lambda_max(plan, Vd)
+        res = abi.pc_solve(plan, Vd, lam, wl.delta)
+        got = (res["idx"].cpu().numpy().tolist(), res["x"].cpu().numpy(), res["objective"])
+        if first is None:
+            first = got
+        assert got[0] == first[0]
+        assert np.allclose(got[1], first[1], rtol=1e-5, atol=0)
+        assert abs(got[2] - first[2]) <= 1e-7 * first[2]
+        del plan
+        if rep == 1:
+            abi.pc_trim_memory()
+    r = abi.pc_solve_host(wl.uvw, V.astype(np.complex64), wl.N, wl.fov, 0.05, wl.delta)
+    assert r["idx"].tolist() == first[0]
