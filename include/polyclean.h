@@ -80,6 +80,9 @@ typedef struct {
   int32_t fft_rows_per_cta; /* rows per CTA of the first FFT pass                    */
   double  grid_us;          /* measured time of one gridding with that choice        */
   double  fft_rows_us;      /* measured time of one first FFT pass with that choice  */
+  int32_t fft_cols_planes;  /* w-planes transformed together by the second FFT pass   */
+  int32_t reserved;
+  double  fft_cols_us;      /* measured time of one second FFT pass with that choice */
 } pc_plan_tuning;
 
 /* Solver options (Algorithm 2 and its sub-solver). Zero fields take defaults. */

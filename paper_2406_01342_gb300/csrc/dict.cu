@@ -417,7 +417,7 @@ int ensure_atom_buffers(pc_plan_s* p, int64_t n_atoms, cudaStream_t st) {
   DictWork& W = work(p);
   PC_TRY(W.img.ensure(sizeof(float) * (size_t)p->N * p->N));
   if (W.n_atoms >= n_atoms) return PC_OK;
-  const int nblk = ceil_div(n_atoms, 4096);
+  const int nblk = ceil_div(n_atoms, kSelItems);
   PC_TRY(W.eta.ensure(sizeof(float) * (size_t)n_atoms));
   PC_TRY(W.mark.ensure((size_t)n_atoms));
   PC_TRY(W.sel.ensure(sizeof(int32_t) * ((size_t)nblk + 2)));

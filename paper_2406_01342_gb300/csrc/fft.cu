@@ -104,12 +104,12 @@ k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int l
 template <int JPT>
 __global__ void __launch_bounds__(256)
 k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* __restrict__ mu,
-           int G, int logG, int N, int P, int wstack, const float2* __restrict__ tw, float scale,
+           int G, int logG, int N, int P, int PG, int wstack, const float2* __restrict__ tw, float scale,
            unsigned* __restrict__ maxbits) {
   extern __shared__ float2 sm[];
-  float2* A = sm;
-  float2* B = sm + G;
-  float2* T = sm + 2 * G;                         // twiddles, staged once per CTA
+  float2* A = sm;                                 // PG planes' rows at a time
+  float2* B = sm + (size_t)PG * G;
+  float2* T = sm + 2 * (size_t)PG * G;            // twiddles, staged once per CTA
   for (int k = threadIdx.x; k < G; k += blockDim.x) T[k] = tw[k];
   const int i = blockIdx.x;
   const int mask = G - 1, hN = N >> 1;
@@ -121,17 +121,23 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
     const int j = threadIdx.x + jj * blockDim.x;
     pt[jj] = j < N ? pix[(size_t)i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  for (int q = 0; q < P; ++q) {
-    const float2* src = X + ((size_t)q * N + i) * G;
-    for (int a = threadIdx.x; a < G; a += blockDim.x) A[a] = src[a];
+  for (int q0 = 0; q0 < P; q0 += PG) {
+    // rows of PG planes loaded and transformed together: fewer barriers per
+    // plane and PG independent loads in flight
+    const int Qn = min(PG, P - q0);
+    for (int e = threadIdx.x; e < Qn * G; e += blockDim.x) {
+      const int r = e / G, a = e - r * G;
+      A[e] = X[((size_t)(q0 + r) * N + i) * G + a];
+    }
     __syncthreads();
-    const float2* res = fft_rows_smem(A, B, 1, G, logG, G, T);
-    const float qf = (float)q;
+    const float2* res = fft_rows_smem(A, B, Qn, G, logG, G, T);
+    for (int r = 0; r < Qn; ++r) {
+    const float qf = (float)(q0 + r);
 #pragma unroll
     for (int jj = 0; jj < JPT; ++jj) {
       const int j = threadIdx.x + jj * blockDim.x;
       if (j < N) {
-        const float2 v = res[(j - hN + G) & mask];
+        const float2 v = res[(size_t)r * G + ((j - hN + G) & mask)];
         if (wstack) {
           // q t in turns, with t = t_hi + t_lo, reduced exactly before sincospi
           const float p = qf * pt[jj].z;
@@ -146,6 +152,7 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
           acc[jj].y += v.y;
         }
       }
+    }
     }
     __syncthreads();
   }
@@ -196,10 +203,20 @@ int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
   return PC_OK;
 }
 
+// Planes per pass of the second FFT pass: the plan's choice (autotuner), else
+// 2 (five CTAs per SM at G = 1024), never more than shared memory holds.
+int cols_planes_per_pass(const pc_plan_s* p) {
+  int pg = p->fft_cols_pg > 0 ? p->fft_cols_pg : 2;
+  pg = std::min(pg, p->P);
+  while (pg > 1 && ((size_t)2 * pg * p->G + p->G) * sizeof(float2) > 200 * 1024) --pg;
+  return std::max(pg, 1);
+}
+
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_COLS, st);
-  const size_t smem = (size_t)3 * p->G * sizeof(float2);
+  const int PG = cols_planes_per_pass(p);
+  const size_t smem = ((size_t)2 * PG * p->G + p->G) * sizeof(float2);
   const int jpt = (p->N + 255) / 256;
   prof_scope_.kernels = 1;
   const int ws = p->wstack ? 1 : 0;
@@ -212,7 +229,7 @@ int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* max
       attr_set = true;                                                                          \
     }                                                                                           \
     k_fft_cols<J><<<p->N, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->G, p->logG, p->N, p->P,  \
-                                           ws, p->twiddle, scale, maxbits);                     \
+                                           PG, ws, p->twiddle, scale, maxbits);                 \
     break;                                                                                      \
   }
   switch (jpt) {

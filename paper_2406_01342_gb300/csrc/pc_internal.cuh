@@ -220,6 +220,8 @@ int make_atoms_checked(const int32_t* idx, const float* x, int S, int N, double 
 
 // select.cu
 // thr_dev (optional): the threshold is read on the device
+// candidates examined per selection block; block_counts needs ceil(npix / kSelItems) + 2 entries
+constexpr int kSelItems = 1024;
 int launch_select(const float* mu, int64_t npix, float thr, const uint8_t* mark, int32_t* out,
                   int32_t* count_dev, int32_t* block_counts, int cap, cudaStream_t st,
                   bool positive = false, const float* thr_dev = nullptr);
@@ -266,6 +268,7 @@ int launch_grid_tc(pc_plan_s* p, const float2* h, int* err_dev, cudaStream_t st)
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st);
+int cols_planes_per_pass(const pc_plan_s* p);
 
 }  // namespace pc
 
@@ -288,8 +291,9 @@ struct pc_plan_s {
   int grid_mode = 0;  // 0 auto, 1 CUDA cores, 2 tensor cores (w-stacking only)
   int grid_piece = 0; // gridding sub-problem size in slots (0: chosen for even waves)
   int fft_R = 0;      // rows per CTA of the first FFT pass (0: 4096 / G)
+  int fft_cols_pg = 0; // planes per pass of the second FFT pass (0: default)
   bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
-  double tune_grid_us = 0.0, tune_fft_us = 0.0;
+  double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0;
   std::vector<int4> sub_ranges;   // (tile, plane group, first slot, end) before splitting
   int sub_cap = 0;                // capacity of subs (the finest split)
   int64_t n_slots = 0;

@@ -458,6 +458,22 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   }
   p->fft_R = best_R;
   p->tune_fft_us = best_fft;
+  // second pass: planes transformed together per pass (shared memory vs CTAs per SM)
+  PC_TRY(launch_fft_rows(p, st));
+  double best_cols = 1e300;
+  int best_pg = 1;
+  for (int pg : {1, 2, 4, 8}) {
+    p->fft_cols_pg = pg;
+    if (cols_planes_per_pass(p) != pg) break;   // beyond the planes or shared memory
+    double us = 0.0;
+    PC_TRY(time_us(st, 3, [&] { return launch_fft_cols_epilogue(p, p->mu, 1.0f, nullptr, st); }, &us));
+    if (us < best_cols) {
+      best_cols = us;
+      best_pg = pg;
+    }
+  }
+  p->fft_cols_pg = best_pg;
+  p->tune_fft_cols_us = best_cols;
   p->tuned = true;
   PC_CUDA(cudaMemsetAsync(p->resid, 0, sizeof(float2) * p->M, st));
   PC_CUDA(cudaStreamSynchronize(st));
@@ -582,7 +598,7 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   PC_TRY(dev_alloc_t(p, &p->uscal, 8));
   PC_TRY(dev_alloc_t(p, &p->iscal, 8));
   PC_CUDA(cudaMemsetAsync(p->iscal, 0, 8 * sizeof(int32_t), st));
-  p->sel_blocks_n = ceil_div(NN, 4096);
+  p->sel_blocks_n = ceil_div(NN, kSelItems);
   PC_TRY(dev_alloc_t(p, &p->sel_blocks, (size_t)p->sel_blocks_n + 2));
   PC_CUDA(cudaMemsetAsync(p->sel_blocks, 0, sizeof(int32_t) * ((size_t)p->sel_blocks_n + 2), st));
   PC_TRY(dev_alloc_t(p, &p->vis_fx, (size_t)std::max<int64_t>(M, 1)));
@@ -787,6 +803,9 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
   out->fft_rows_per_cta = std::min(std::max(R, 1), 32);
   out->grid_us = p->tune_grid_us;
   out->fft_rows_us = p->tune_fft_us;
+  out->fft_cols_planes = cols_planes_per_pass(p);
+  out->fft_cols_us = p->tune_fft_cols_us;
+  out->reserved = 0;
   return PC_OK;
 }
 

@@ -10,8 +10,8 @@ namespace pc {
 namespace {
 
 constexpr int SEL_THREADS = 256;
-constexpr int SEL_ROUNDS = 16;
-constexpr int SEL_ITEMS = SEL_THREADS * SEL_ROUNDS;
+constexpr int SEL_ITEMS = kSelItems;   // 1024 per block: 256 blocks for 512 x 512, several per SM
+constexpr int SEL_ROUNDS = SEL_ITEMS / SEL_THREADS;
 
 __device__ __forceinline__ bool sel_flag(const float* mu, const uint8_t* mark, int64_t p, float thr,
                                          int positive) {

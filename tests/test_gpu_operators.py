@@ -194,6 +194,7 @@ def test_autotuned_plan(abi):
     assert t["tuned"] and t["grid_mode"] in (1, 2) and t["grid_piece"] in (256, 512, 1024)
     assert t["fft_rows_per_cta"] in (1, 2, 4, 8, 16, 32)
     assert 0 < t["grid_us"] < 1e5 and 0 < t["fft_rows_us"] < 1e5
+    assert t["fft_cols_planes"] in (1, 2, 4, 8) and 0 < t["fft_cols_us"] < 1e5
     assert not abi.pc_plan_tuning_info(_plan(abi, wl))["tuned"]
     Vs = V.astype(np.complex64)
     img = abi.pc_adjoint_grid(plan, to_dev(Vs)).cpu().numpy().ravel()
