@@ -69,8 +69,6 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
   __shared__ float s_fw[GT_KS][GT_Q];
   __shared__ float2 s_h[GT_KS];
   __shared__ int s_a0[GT_KS], s_b0[GT_KS];
-  __shared__ uint32_t s_pa[GT_KS * 64];   // {hi, lo} FP16 pairs of phi_w(q) phi_u(i)
-  __shared__ uint32_t s_pb[GT_KS * 16];   // {hi, lo} FP16 pairs of (Re|Im h) phi_v(i)
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
   __shared__ float s_red[GT_THREADS / 32];
@@ -171,29 +169,10 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
       }
     }
     __syncthreads();
-    // ---- 1b. product tables, each entry an FP16 pair {hi, lo} in one word:
-    //      s_pa[k][q][i] = phi_w(q) phi_u(i),  s_pb[k][c][i] = (Re|Im h) phi_v(i)
-    for (int e = tid; e < GT_KS * 80; e += GT_THREADS) {
-      float v;
-      uint32_t* dst;
-      if (e < GT_KS * 64) {
-        const int k = e >> 6, q = (e >> 3) & 7, i = e & 7;
-        v = s_fw[k][q] * s_fu[k][i];
-        dst = &s_pa[e];
-      } else {
-        const int e2 = e - GT_KS * 64;
-        const int k = e2 >> 4, c = (e2 >> 3) & 1, i = e2 & 7;
-        v = (c ? s_h[k].y : s_h[k].x) * s_fv[k][i];
-        dst = &s_pb[e2];
-      }
-      const __half hh = __float2half_rn(v);
-      const __half hl = __float2half_rn(v - __half2float(hh));
-      *dst = (uint32_t)__half_as_ushort(hh) | ((uint32_t)__half_as_ushort(hl) << 16);
-    }
     // the previous stage's MMAs still read A and B: wait for them (bounded)
-    // before overwriting; their latency hid behind steps 1a and 1b
+    // before overwriting; their latency hid behind step 1
     if (tid == 0 && pending) {
-      s_go = tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)((stage - 1) & 1), nullptr, GT_WAIT_CYCLES) ? 1 : 0;
+      s_go = tc::mbar_wait(tc::smem_u32(&s_mbar), (uint32_t)(committed & 1), nullptr, GT_WAIT_CYCLES) ? 1 : 0;
       pending = !s_go;
     }
     __syncthreads();
@@ -201,55 +180,59 @@ k_grid_tc(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
       ok = false;
       break;
     }
-    // ---- 2a. A: thread = row (plane q, column a); 8 visibilities per 16-byte store
-    if (tid < n_tiles * 128) {
-      const int R = tid, q = R >> 5, a = R & 31;
-      const uint32_t rowoff = (uint32_t)(R >> 3) * GT_SBO + (uint32_t)(R & 7) * 16;
-      const uint32_t* pa_q = s_pa + q * 8;
-#pragma unroll 2
-      for (int kg = 0; kg < GT_KS / 8; ++kg) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          uint32_t pr[2];
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const int k = kg * 8 + 2 * i + s;
-            const unsigned da = (unsigned)(a - s_a0[k]);
-            pr[s] = da < (unsigned)W ? pa_q[k * 64 + da] : 0u;
-          }
-          hi[i] = __byte_perm(pr[0], pr[1], 0x5410);
-          lo[i] = __byte_perm(pr[0], pr[1], 0x7632);
-        }
-        const uint32_t off = rowoff + (uint32_t)kg * 128;
-        *reinterpret_cast<uint4*>(A_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(A_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
-    }
-    // ---- 2b. B: row n = (b, Re|Im); 4 threads per row, 2 K-groups each
+    // ---- 2a. clear the operand rows in use (16-byte stores)
     {
-      const int n = tid & 63, b = n >> 1, im = n & 1;
-      const uint32_t rowoff = (uint32_t)(n >> 3) * GT_SBO + (uint32_t)(n & 7) * 16;
-      const uint32_t* pb_c = s_pb + im * 8;
+      const int a_words = n_tiles * 128 * GT_KS * 2 / 16;   // per half
+      uint4* ah = reinterpret_cast<uint4*>(A_hi);
+      uint4* al = reinterpret_cast<uint4*>(A_lo);
+      uint4* bh = reinterpret_cast<uint4*>(B_hi);
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      for (int e = tid; e < a_words; e += GT_THREADS) {
+        ah[e] = z;
+        al[e] = z;
+      }
+      for (int e = tid; e < 2 * GT_B_BYTES / 16; e += GT_THREADS) bh[e] = z;   // B_hi and B_lo
+    }
+    __syncthreads();
+    // ---- 2b. scatter the nonzero entries, each an FP16 {hi, lo} split of its
+    //      FP32 value, into the K-major core-matrix layout: A[(q, a0 + i), k] =
+    //      phi_w(q) phi_u(i) and B[(b0 + i, Re|Im), k] = (Re|Im h) phi_v(i); only
+    //      the W x Q and 2 W entries a visibility touches are written
+    {
+      const int k = tid & (GT_KS - 1), part = tid >> 6;   // 4 threads per visibility
+      const int a0 = s_a0[k], b0 = s_b0[k];
+      const uint32_t koff = (uint32_t)(k >> 3) * 128 + (uint32_t)(k & 7) * 2;
 #pragma unroll
-      for (int g2 = 0; g2 < 2; ++g2) {
-        const int kg = 2 * (tid >> 6) + g2;
-        uint32_t hi[4], lo[4];
+      for (int qq = 0; qq < 2; ++qq) {
+        const int q = part + 4 * qq;
+        if (q >= Q) continue;
+        const float fw = s_fw[k][q];
+        if (fw == 0.f) continue;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          uint32_t pr[2];
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const int k = kg * 8 + 2 * i + s;
-            const unsigned db = (unsigned)(b - s_b0[k]);
-            pr[s] = db < (unsigned)W ? pb_c[k * 16 + db] : 0u;
-          }
-          hi[i] = __byte_perm(pr[0], pr[1], 0x5410);
-          lo[i] = __byte_perm(pr[0], pr[1], 0x7632);
+        for (int i = 0; i < W; ++i) {
+          const int a = a0 + i;
+          if (a < 0 || a >= GT_T) continue;
+          const float v = fw * s_fu[k][i];
+          const __half hh = __float2half_rn(v);
+          const __half hl = __float2half_rn(v - __half2float(hh));
+          const int R = q * GT_T + a;
+          const uint32_t off = (uint32_t)(R >> 3) * GT_SBO + (uint32_t)(R & 7) * 16 + koff;
+          *reinterpret_cast<__half*>(A_hi + off) = hh;
+          *reinterpret_cast<__half*>(A_lo + off) = hl;
         }
-        const uint32_t off = rowoff + (uint32_t)kg * 128;
-        *reinterpret_cast<uint4*>(B_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(B_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      const float2 hv = s_h[k];
+      for (int j = part; j < 2 * W; j += 4) {
+        const int i = j >> 1, c = j & 1;
+        const int b = b0 + i;
+        if (b < 0 || b >= GT_T) continue;
+        const float v = (c ? hv.y : hv.x) * s_fv[k][i];
+        const __half hh = __float2half_rn(v);
+        const __half hl = __float2half_rn(v - __half2float(hh));
+        const int n = 2 * b + c;
+        const uint32_t off = (uint32_t)(n >> 3) * GT_SBO + (uint32_t)(n & 7) * 16 + koff;
+        *reinterpret_cast<__half*>(B_hi + off) = hh;
+        *reinterpret_cast<__half*>(B_lo + off) = hl;
       }
     }
     tc::fence_proxy_async_smem();
