@@ -592,7 +592,10 @@ __device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* v
                                Exchange& ex, bool& ok) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int b = ex.buf;
-  float* pub = b ? s.pub1 : s.pub0;
+  // a one-CTA cluster writes the product straight into its receive buffer: no
+  // bulk copy to itself, no mbarrier round trip
+  const bool solo = ex.CS == 1;
+  float* pub = solo ? (b ? s.rx1 : s.rx0) : (b ? s.pub1 : s.pub0);
   const bool vecld = a.cache || a.vec_ok;
   const int n4 = a.n >> 2;
   const float4* v4 = reinterpret_cast<const float4*>(vec);
@@ -639,6 +642,11 @@ __device__ float* cluster_gemv(const ApgdArgs& a, const SmemF& s, const float* v
   // the slice (padded to 4 floats) goes to every CTA in one bulk copy each
   const int nr4 = (nr + 3) & ~3;
   for (int r = nr + threadIdx.x; r < nr4; r += blockDim.x) pub[r] = 0.f;
+  if (solo) {
+    __syncthreads();
+    ex.buf ^= 1;
+    return pub;
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if ((int)threadIdx.x < ex.CS && nr4 > 0) {
