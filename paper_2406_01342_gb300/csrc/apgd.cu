@@ -849,6 +849,144 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(const __grid_cons
   cl.sync();   // no CTA leaves while others may still address its shared memory
 }
 
+// ---------------------------------------------------------------------------
+// One-warp variant for small supports (n <= 64, the later Frank-Wolfe
+// iterations): the same Lanczos step size, monotone FISTA, stop rule and
+// reported objective as k_apgd_full, with G in shared memory, lane l owning
+// rows l and l + 32 of every vector, warp-shuffle reductions and no block or
+// cluster barrier in the loop: an iteration is a few hundred instructions.
+constexpr int WARP_NMAX = 64;
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ Df warp_df_sum(Df v) {
+  for (int off = 16; off; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+  return v;
+}
+
+__global__ void __launch_bounds__(32) k_apgd_warp(const __grid_constant__ ApgdBatch batch) {
+  __shared__ float Gs[WARP_NMAX][WARP_NMAX + 1];
+  __shared__ float vs[WARP_NMAX];
+  __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
+  const ApgdArgs& a = batch.job[blockIdx.x];
+  const int n = a.n, lane = threadIdx.x;
+  for (int e = lane; e < n * n; e += 32) {
+    const int r = e / n, c = e - r * n;
+    Gs[r][c] = a.G[(size_t)r * a.ldg + c];
+  }
+  const int i0 = lane, i1 = lane + 32;
+  const bool v0ok = i0 < n, v1ok = i1 < n;
+  float bb0 = v0ok ? a.b[i0] : 0.f, bb1 = v1ok ? a.b[i1] : 0.f;
+  float x0 = v0ok ? a.x[i0] : 0.f, x1 = v1ok ? a.x[i1] : 0.f;
+  __syncwarp();
+  // G v for the lane's two rows (v broadcast through shared memory)
+  auto gemv = [&](float v0, float v1, float& g0, float& g1) {
+    vs[i0] = v0;
+    vs[i1] = v1;
+    __syncwarp();
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int j = 0; j < n; ++j) {
+      const float vj = vs[j];
+      acc0 = fmaf(Gs[v0ok ? i0 : 0][j], vj, acc0);
+      acc1 = fmaf(Gs[v1ok ? i1 : 0][j], vj, acc1);
+    }
+    __syncwarp();
+    g0 = v0ok ? acc0 : 0.f;
+    g1 = v1ok ? acc1 : 0.f;
+  };
+
+  // ---- Lipschitz constant: Lanczos from the all-ones vector
+  const float vinit = rsqrtf((float)n);
+  float y0 = v0ok ? vinit : 0.f, y1 = v1ok ? vinit : 0.f;   // v_j
+  float z0 = 0.f, z1 = 0.f;                                 // v_{j-1}
+  float theta = 0.f, theta_prev = 0.f, beta_prev = 0.f;
+  int m = 0;
+  for (int j = 0; j < LZ_MAX; ++j) {
+    float g0, g1;
+    gemv(y0, y1, g0, g1);
+    const float alpha = warp_sum(fmaf(y0, g0, y1 * g1));
+    const float w0 = g0 - alpha * y0 - beta_prev * z0;
+    const float w1 = g1 - alpha * y1 - beta_prev * z1;
+    const float beta = sqrtf(fmaxf(warp_sum(fmaf(w0, w0, w1 * w1)), 0.f));
+    if (lane == 0) {
+      s_al[j] = alpha;
+      s_be[j] = beta;
+    }
+    m = j + 1;
+    __syncwarp();
+    const bool last = (m == n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
+    if (last || (m % 4) == 0) {
+      theta = tridiag_top(s_al, s_be, m, &s_theta);
+      if (last || fabsf(theta - theta_prev) <= LZ_TOL * fabsf(theta)) break;
+      theta_prev = theta;
+    }
+    const float inv = 1.f / beta;
+    z0 = y0;
+    z1 = y1;
+    y0 = w0 * inv;
+    y1 = w1 * inv;
+    beta_prev = beta;
+  }
+  const float L = 1.01f * (theta > 0.f ? theta : 1.f);
+  const float invL = 1.f / L;
+  const float thr = a.lam * invL;
+
+  // ---- monotone FISTA
+  float Gx0, Gx1;
+  gemv(x0, x1, Gx0, Gx1);
+  y0 = x0;
+  y1 = x1;
+  float Gy0 = Gx0, Gy1 = Gx1;
+  float t = 1.f;
+  int it = 0;
+  for (it = 1; it <= a.max_iter; ++it) {
+    const float u0 = y0 - (Gy0 - bb0) * invL, u1 = y1 - (Gy1 - bb1) * invL;
+    float zz0 = a.positive ? fmaxf(u0 - thr, 0.f) : copysignf(fmaxf(fabsf(u0) - thr, 0.f), u0);
+    float zz1 = a.positive ? fmaxf(u1 - thr, 0.f) : copysignf(fmaxf(fabsf(u1) - thr, 0.f), u1);
+    if (!v0ok) zz0 = 0.f;
+    if (!v1ok) zz1 = 0.f;
+    float Gz0, Gz1;
+    gemv(zz0, zz1, Gz0, Gz1);
+    // F(z) - F(x) from the difference itself (see k_apgd_full)
+    const float dF = warp_sum(fmaf(zz0 - x0, 0.5f * (Gz0 + Gx0) - bb0, a.lam * (fabsf(zz0) - fabsf(x0))) +
+                              fmaf(zz1 - x1, 0.5f * (Gz1 + Gx1) - bb1, a.lam * (fabsf(zz1) - fabsf(x1))));
+    const float d0 = zz0 - y0, d1 = zz1 - y1;
+    const float step = sqrtf(warp_sum(fmaf(d0, d0, d1 * d1)));
+    const float nz = sqrtf(warp_sum(fmaf(zz0, zz0, zz1 * zz1)));
+    const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+    const bool accept = dF <= 0.f;
+    const float c1 = t / t1, c2 = (t - 1.f) / t1;
+    const float xn0 = accept ? zz0 : x0, xn1 = accept ? zz1 : x1;
+    const float Gxn0 = accept ? Gz0 : Gx0, Gxn1 = accept ? Gz1 : Gx1;
+    y0 = xn0 + c1 * (zz0 - xn0) + c2 * (xn0 - x0);
+    y1 = xn1 + c1 * (zz1 - xn1) + c2 * (xn1 - x1);
+    Gy0 = Gxn0 + c1 * (Gz0 - Gxn0) + c2 * (Gxn0 - Gx0);
+    Gy1 = Gxn1 + c1 * (Gz1 - Gxn1) + c2 * (Gxn1 - Gx1);
+    x0 = xn0;
+    x1 = xn1;
+    Gx0 = Gxn0;
+    Gx1 = Gxn1;
+    t = t1;
+    if (step <= a.eps * nz) break;
+  }
+  if (it > a.max_iter) it = a.max_iter;
+  // objective of the returned x, in double-float (reported only)
+  const Df xg = warp_df_sum(df_add(df_prod(x0, Gx0), df_prod(x1, Gx1)));
+  const Df bx = warp_df_sum(df_add(df_prod(bb0, x0), df_prod(bb1, x1)));
+  const Df l1 = warp_df_sum(df_add(Df{fabsf(x0), 0.f}, Df{fabsf(x1), 0.f}));
+  const Df Fx = df_add(df_add(df_scale(xg, 0.5f), df_neg(bx)), df_scale(l1, a.lam));
+  if (v0ok) a.x[i0] = x0;
+  if (v1ok) a.x[i1] = x1;
+  if (lane == 0) {
+    if (a.out_iters) *a.out_iters = it;
+    if (a.out_L) *a.out_L = (double)L;
+    if (a.out_F) *a.out_F = (double)Fx.hi + (double)Fx.lo;
+    if (a.out_lanczos) *a.out_lanczos = m;
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -856,6 +994,7 @@ namespace {
 // Launch shape of one restricted problem: which kernel, cluster size, rows per
 // CTA, whether the CTAs cache their rows of G, dynamic shared memory.
 struct ApgdShape {
+  bool warp = false;   // one-warp kernel (n <= WARP_NMAX)
   bool full;
   int CS;
   int rows_per;
@@ -906,6 +1045,17 @@ int apgd_shape(int S, int cs_max, ApgdShape* out) {
   // ~64 KB of G in shared memory (a matrix-vector product then streams it in
   // ~500 cycles), else the smallest that caches G at all, else cs_max
   ApgdShape sh;
+  if (S <= WARP_NMAX) {
+    sh.warp = true;
+    sh.full = true;
+    sh.CS = 1;
+    sh.cache = 1;
+    sh.smem = 0;
+    sh.rows_per = S;
+    sh.n_pad = n_pad;
+    *out = sh;
+    return PC_OK;
+  }
   sh.full = true;
   sh.CS = 1;
   const size_t share_target = 64 * 1024;
@@ -969,12 +1119,20 @@ int run_apgd_jobs(const ApgdJob* jobs, int n_jobs, cudaStream_t st) {
     ApgdBatch batch{};
     size_t smem = 0;
     const bool full = shapes[i].full;
+    const bool warp = shapes[i].warp;
     const int CS = shapes[i].CS;
     for (int j = i; j < n_jobs && batch.n_jobs < APGD_BATCH_MAX; ++j) {
-      if (done[j] || shapes[j].full != full || shapes[j].CS != CS) continue;
+      if (done[j] || shapes[j].full != full || shapes[j].CS != CS || shapes[j].warp != warp) continue;
       batch.job[batch.n_jobs++] = make_args(jobs[j], shapes[j]);
       smem = std::max(smem, shapes[j].smem);
       done[j] = 1;
+    }
+    if (warp) {
+      ProfScope prof_scope_(PROF_APGD, st);
+      prof_scope_.kernels = 1;
+      k_apgd_warp<<<batch.n_jobs, 32, 0, st>>>(batch);
+      PC_LAUNCH_CHECK();
+      continue;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CS * batch.n_jobs, 1, 1);
