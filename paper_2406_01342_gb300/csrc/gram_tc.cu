@@ -184,6 +184,7 @@ struct GbArgs {
   int ldacc;
   int* err;
   int withhold;              // self-test: issue no MMA / commit, so the first buffer wait expires
+  int slice_stages;          // stages per K-slice (blockIdx.z)
 };
 
 __global__ void __launch_bounds__(GB_THREADS, 1) k_gram_bulk(GbArgs g) {
@@ -206,8 +207,8 @@ __global__ void __launch_bounds__(GB_THREADS, 1) k_gram_bulk(GbArgs g) {
   const uint32_t tx_bytes = (uint32_t)buf_bytes;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int a0 = blockIdx.y * GB_M, b0 = blockIdx.x * NT;
-  const int s_lo = blockIdx.z * (GB_SLICE / GB_KV);
-  const int s_hi = min(g.n_stages, s_lo + GB_SLICE / GB_KV);
+  const int s_lo = blockIdx.z * g.slice_stages;
+  const int s_hi = min(g.n_stages, s_lo + g.slice_stages);
   const int nst = max(0, s_hi - s_lo);
   const uint32_t ncols = (uint32_t)(2 * NT);          // fast + slow accumulators
   const size_t stage_stride = (size_t)g.rows_pad * GB_ROW_BYTES;
@@ -421,10 +422,35 @@ int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4*
     k_phase_gen<<<dim3(bx, by), 256, 0, st>>>(vis_fx, V, k0, k0 + kc, atoms, n_atoms, V ? n_atoms : -1,
                                               rows_pad, n_stages, vscale_dev, hi, lo);
     PC_LAUNCH_CHECK();
+    // K-slices: the count that makes the CTAs left after the diagonal skip fill
+    // whole waves (a partial last wave idles most of the GPU for a slice's
+    // time), fewest slices among the best (fewer float64 flushes)
+    const int gx = ceil_div(rows, NT), gy = ceil_div(nA, GB_M);
+    int tiles = 0;
+    for (int y = 0; y < gy; ++y)
+      for (int x = 0; x < gx; ++x) tiles += ((x + 1) * NT <= y * GB_M) ? 0 : 1;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 152;
+    }
+    const int z_max = std::max(1, n_stages / 16);          // slices of at least 256 visibilities
+    int best_z = 1;
+    int64_t best_cost = INT64_MAX;
+    for (int z = 1; z <= z_max; ++z) {
+      const int64_t waves = ceil_div((int64_t)tiles * z, n_sm);
+      const int64_t cost = waves * ceil_div(n_stages, z);
+      if (cost < best_cost) {
+        best_cost = cost;
+        best_z = z;
+      }
+    }
+    const int slice_stages = ceil_div(n_stages, best_z);
     GbArgs a{reinterpret_cast<const unsigned char*>(hi), reinterpret_cast<const unsigned char*>(lo),
              rows_pad, n_stages, nA, rows, V ? n_atoms : -1, V ? vscale_dev : nullptr, NT, acc, ldacc,
-             err_dev, withhold ? 1 : 0};
-    dim3 grid(ceil_div(rows, NT), ceil_div(nA, GB_M), ceil_div(n_stages, GB_SLICE / GB_KV));
+             err_dev, withhold ? 1 : 0, slice_stages};
+    dim3 grid(gx, gy, ceil_div(n_stages, slice_stages));
     k_gram_bulk<<<grid, GB_THREADS, smem, st>>>(a);
     PC_LAUNCH_CHECK();
     nk += 2;
