@@ -47,8 +47,9 @@ def parse():
                     help="skip the serving-stream leg (64 requests, Poisson arrivals, p50/p99)")
     ap.add_argument("--no-diffuse", action="store_true",
                     help="skip the synthesis-dictionary leg (256^2 diffuse sky, M = 31.6k)")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="build the timed plan without the plan-time autotuner")
+    ap.add_argument("--autotune", action="store_true",
+                    help="build the timed plan with the plan-time autotuner (its timings are meaningless "
+                         "under a profiler, which serialises launches)")
     return ap.parse_args()
 
 
@@ -442,7 +443,7 @@ def run_ours(args, world, rank, local):
     abi.load()
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    wl, uvw, plan, V = make_inputs(abi, synth, args.workload, device, autotune=0 if args.no_autotune else 1)
+    wl, uvw, plan, V = make_inputs(abi, synth, args.workload, device, autotune=1 if args.autotune else 0)
     info = abi.pc_plan_info(plan)
     tuning = abi.pc_plan_tuning_info(plan)
     lmax = abi.pc_lambda_max(plan, V)
