@@ -165,6 +165,16 @@ int pc_adjoint_sparse(pc_plan_t plan, const pc_c32* y_dev, const int32_t* idx_de
  * correction. With y = V this is the dirty image. img_dev: N*N floats. */
 int pc_adjoint_grid(pc_plan_t plan, const pc_c32* y_dev, float* img_dev, void* stream);
 
+/* y = Phi(img) for a dense N x N image (the forward equation of Sect. 2.2), by
+ * degridding (Sect. 5.2: the type-2 half of the non-uniform FFT): the exact
+ * adjoint of pc_adjoint_grid's steps in reverse -- per-pixel correction and
+ * w-screen, two forward FFT passes per w-plane, interpolation of the binned
+ * visibilities with the same kernel. Cost independent of how many pixels are
+ * nonzero (use it instead of pc_forward_sparse for dense or extended images).
+ * img_dev: N*N floats; y_dev: M complex (overwritten, original order of uvw).
+ * Uses the plan's grid workspace: not concurrent with other calls on the plan. */
+int pc_forward_grid(pc_plan_t plan, const float* img_dev, pc_c32* y_dev, void* stream);
+
 /* lambda_max = ||Phi* V||_inf (Sect. 5.3), returned in host memory. */
 int pc_lambda_max(pc_plan_t plan, const pc_c32* V_dev, double* lambda_max_host, void* stream);
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
     "pc_profile_begin_classes", "pc_server_create", "pc_server_submit", "pc_server_wait",
     "pc_server_destroy", "pc_plan_tuning_info", "pc_dict_adjoint", "pc_dict_forward_sparse",
-    "pc_dict_lambda_max", "pc_solve_synthesis", "pc_trim_memory",
+    "pc_dict_lambda_max", "pc_solve_synthesis", "pc_forward_grid", "pc_trim_memory",
 ]
 
 
@@ -147,6 +147,7 @@ def load(path: str | None = None):
         "pc_forward_sparse": (_I32, [_P, _P, _P, _I32, _P, _P]),
         "pc_adjoint_sparse": (_I32, [_P, _P, _P, _I32, _P, _P]),
         "pc_adjoint_grid": (_I32, [_P, _P, _P, _P]),
+        "pc_forward_grid": (_I32, [_P, _P, _P, _P]),
         "pc_lambda_max": (_I32, [_P, _P, ctypes.POINTER(_D), _P]),
         "pc_lambda_max_positive": (_I32, [_P, _P, ctypes.POINTER(_D), _P]),
         "pc_certificate": (_I32, [_P, _P, _P, _P, _I32, _D, _P, ctypes.POINTER(_D),
@@ -284,6 +285,15 @@ def pc_adjoint_grid(plan: Plan, y: torch.Tensor, img: torch.Tensor | None = None
     _check(load().pc_adjoint_grid(plan.handle, _dev(y, torch.complex64, "y"),
                                   _dev(img, torch.float32, "img"), _stream(stream)))
     return img
+
+
+def pc_forward_grid(plan: Plan, img: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Phi(img) for a dense N x N float32 image (degridding)."""
+    if y is None:
+        y = torch.empty(plan.M, dtype=torch.complex64, device=img.device)
+    _check(load().pc_forward_grid(plan.handle, _dev(img, torch.float32, "img"), _dev(y, torch.complex64, "y"),
+                                  _stream(stream)))
+    return y
 
 
 def pc_lambda_max(plan: Plan, V: torch.Tensor, stream=None) -> float:

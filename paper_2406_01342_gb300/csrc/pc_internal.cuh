@@ -269,6 +269,8 @@ int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st);
 int cols_planes_per_pass(const pc_plan_s* p);
+// degrid.cu: y = Phi(img) for a dense N x N image (type-2 NUFFT), y cleared first
+int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st);
 
 }  // namespace pc
 
@@ -327,6 +329,7 @@ struct pc_plan_s {
   pc::DevBuf perm, atomsP, pbuf;   // tensor-core Gram: atom order (new first), atoms, phase buffer
   pc::DictWork* dict = nullptr;    // synthesis-dictionary workspace (created on first use)
   pc::SolveCache* scache = nullptr; // solver-loop resources (created by the first solve)
+  pc::DevBuf degrid_buf;            // forward on a dense image: P x active rows x N (first pass)
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
 };

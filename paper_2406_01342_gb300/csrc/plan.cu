@@ -832,6 +832,7 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
   p->perm.release();
   p->atomsP.release();
   p->pbuf.release();
+  p->degrid_buf.release();
   if (p->dict) {
     p->dict->release();
     delete p->dict;

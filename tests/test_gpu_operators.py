@@ -74,6 +74,37 @@ def test_adjoint_grid(abi, name, kw, grid_mode):
     assert rel_l2(img[pix], ref) <= TOL
 
 
+@pytest.mark.parametrize("name,kw", CASES)
+def test_forward_grid(abi, name, kw):
+    """Degridding (the type-2 non-uniform FFT of Sect. 5.2) of a dense random
+    image against the direct sum of the forward equation (Sect. 2.2), on all
+    visibilities or a seeded sample of them."""
+    wl, V = workload(name, **kw)
+    plan = _plan(abi, wl)
+    rng = np.random.default_rng(31)
+    img = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
+    y = abi.pc_forward_grid(plan, to_dev(img)).cpu().numpy()
+    ks = np.arange(wl.M) if wl.N * wl.N * wl.M <= 5e7 else np.sort(rng.choice(wl.M, 2000, replace=False))
+    ref = operators.forward(wl.uvw[ks], wl.N, wl.fov, np.arange(wl.N * wl.N), img.ravel().astype(np.float64))
+    assert rel_l2(y[ks], ref) <= TOL
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+def test_forward_grid_is_the_adjoint_of_adjoint_grid(abi, name, kw):
+    """Re<Phi x, h> = <x, Phi* h> between the two NUFFT directions of one plan
+    (they are built as exact adjoints: equal up to FP32 rounding)."""
+    wl, _ = workload(name, **kw)
+    plan = _plan(abi, wl)
+    rng = np.random.default_rng(32)
+    x = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
+    h = (rng.normal(size=wl.M) + 1j * rng.normal(size=wl.M)).astype(np.complex64)
+    y = abi.pc_forward_grid(plan, to_dev(x)).cpu().numpy().astype(np.complex128)
+    g = abi.pc_adjoint_grid(plan, to_dev(h)).cpu().numpy().astype(np.float64)
+    lhs = float(np.real(np.vdot(y, h.astype(np.complex128))))
+    rhs = float(np.sum(x.astype(np.float64) * g))
+    assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(y) ** 2) * np.sum(np.abs(h) ** 2))
+
+
 @pytest.mark.parametrize("name,kw", CASES[:2])
 def test_adjoint_sparse(abi, name, kw):
     wl, V = workload(name, **kw)
