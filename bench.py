@@ -217,6 +217,33 @@ def gridding_roofline(prof, info, wl, peaks):
             "frac": ach / hbm, "bytes_per_launch": b, "vis_per_s": wl.M / (avg_ms * 1e-3)}
 
 
+def degridding_leg(abi, torch, plan, wl, info, peaks, steps, l2_flush) -> dict:
+    """The forward operator on a dense image by degridding (pc_forward_grid):
+    per call, CUDA events on the launching stream, L2 flushed between calls;
+    bytes = the N^2 image read + 8 B per visibility written + the grid planes
+    (written by the second FFT pass and read by the interpolation)."""
+    img = torch.randn(wl.N, wl.N, dtype=torch.float32, device=l2_flush.device)
+    y = torch.empty(wl.M, dtype=torch.complex64, device=l2_flush.device)
+    for _ in range(3):
+        abi.pc_forward_grid(plan, img, y)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(max(steps, 3)):
+        flush_l2(l2_flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        abi.pc_forward_grid(plan, img, y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    G, P = info["grid_side"], info["n_planes"]
+    byt = 4.0 * wl.N * wl.N + 8.0 * wl.M + 2 * 8.0 * P * G * G
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    return {"ms": t, "vis_per_s": wl.M / (t * 1e-3), "achieved_gbs": byt / (t * 1e-3) / 1e9,
+            "peak_gbs": hbm, "frac": byt / (t * 1e-3) / 1e9 / hbm}
+
+
 def roofline(prof, info, wl, history, steps, peaks, dom):
     """Achieved vs peak for the dominant kernel class `dom`, from its CUDA-event
     launch durations in `prof` (recorded over the timed region)."""
@@ -520,6 +547,8 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(wl.M * (24 + 8)),
                "d2h_bytes_per_step": int(n_sup * 8 + 64)}
 
+    degrid = degridding_leg(abi, torch, plan, wl, info, peaks, args.steps, l2_flush) if rank == 0 else None
+
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_leg(abi, synth, torch, device)
@@ -552,6 +581,7 @@ def run_ours(args, world, rank, local):
                       "objective": res["objective"], "converged": res["converged"]},
             "gridding_vis_per_s": vis_per_s,
             "gridding_roofline": gridding_roofline(prof_timed, info, wl, peaks),
+            "degridding": degrid,
             "kernels_ms": {k: round(v[2] / args.steps, 4) for k, v in prof.items()},
             "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
             "roofline_kernel": {k: rl[k] for k in ("kernel", "avg_launch_ms", "launches")},

@@ -132,9 +132,9 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_ROWS, st);
   if (p->n_active_rows == 0) return PC_OK;     // all-zero grid: the output stays zero
-  // rows per CTA: R * (G + 1) * 8 bytes * 2 buffers <= ~66 KB (3 CTAs per SM);
+  // rows per CTA (default): R * (G + 1) * 8 bytes * 2 buffers ~ 33 KB;
   // R divides the 32-row tile so a CTA's rows are consecutive active rows
-  int R = p->fft_R > 0 ? p->fft_R : 4096 / p->G;
+  int R = p->fft_R > 0 ? p->fft_R : 2048 / p->G;
   if (R < 1) R = 1;
   if (R > 32) R = 32;
   const size_t smem = ((size_t)2 * R * (p->G + 1) + p->G) * sizeof(float2);

@@ -292,7 +292,7 @@ struct pc_plan_s {
   bool wstack = false;
   int grid_mode = 0;  // 0 auto, 1 CUDA cores, 2 tensor cores (w-stacking only)
   int grid_piece = 0; // gridding sub-problem size in slots (0: chosen for even waves)
-  int fft_R = 0;      // rows per CTA of the first FFT pass (0: 4096 / G)
+  int fft_R = 0;      // rows per CTA of the first FFT pass (0: 2048 / G)
   int fft_cols_pg = 0; // planes per pass of the second FFT pass (0: default)
   bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
   double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0;

@@ -665,7 +665,7 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   // the tensor-core stage) sized so that the pieces fill the GPU in about two
   // even waves of two CTAs per SM -- a few long sub-problems left over for a
   // second wave would otherwise double the gridding time.
-  const int kMaxSlotsPerSub = 1024;
+  const int kMaxSlotsPerSub = 512;   // the autotuner's usual pick (smaller pieces: more CTAs in flight)
   std::vector<int4> ranges;
   int64_t total_slots = 0;
   const int ngroups = ceil_div(p->P, p->Qg);
@@ -799,7 +799,7 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
   out->tuned = p->tuned ? 1 : 0;
   out->grid_mode = (p->wstack && p->grid_mode != 1) ? 2 : 1;
   out->grid_piece = p->grid_piece;
-  int R = p->fft_R > 0 ? p->fft_R : 4096 / p->G;
+  int R = p->fft_R > 0 ? p->fft_R : 2048 / p->G;
   out->fft_rows_per_cta = std::min(std::max(R, 1), 32);
   out->grid_us = p->tune_grid_us;
   out->fft_rows_us = p->tune_fft_us;
