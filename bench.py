@@ -532,7 +532,7 @@ def run_ours(args, world, rank, local):
         uvw_h = torch.from_numpy(wl.uvw).pin_memory()
         V_h = V.cpu().pin_memory()
         n_sup = 0
-        for _ in range(2):
+        for _ in range(max(3, args.warmup)):
             r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta)
         t = []
         for i in range(args.steps):

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PC_ABI_VERSION 2
+#define PC_ABI_VERSION 3
 
 typedef enum {
   PC_OK = 0,
@@ -68,8 +68,11 @@ typedef struct {
   int32_t grid_mode;      /* gridding: 0 (default) tensor cores when w-stacking, else CUDA
                              cores; 1: FP32 CUDA cores; 2: tensor cores whenever w-stacking */
   int32_t autotune;       /* 1: time the candidate gridding kernels, gridding sub-problem
-                             sizes and FFT rows per CTA on this plan's visibilities and keep
+                             sizes and FFT kernels on this plan's visibilities and keep
                              the fastest (adds a few ms to plan creation); 0 (default): off */
+  int32_t fft_kernel;     /* FFT passes: 0 (default) one warp per row, in registers, where G
+                             is 512 or 1024, else shared-memory Stockham stages; 1: Stockham
+                             everywhere. The autotuner, when on, chooses per pass instead. */
 } pc_plan_opts;
 
 /* What the plan-time autotuner chose (tuned = 0 when it did not run). */
@@ -81,7 +84,10 @@ typedef struct {
   double  grid_us;          /* measured time of one gridding with that choice        */
   double  fft_rows_us;      /* measured time of one first FFT pass with that choice  */
   int32_t fft_cols_planes;  /* w-planes transformed together by the second FFT pass   */
-  int32_t reserved;
+  int32_t fft_warp;         /* bit 0 / bit 1: the first / second FFT pass gives each row
+                               to one warp, which transforms it in registers (G = 512 or
+                               1024; 8 rows per CTA in the first pass, one plane per warp
+                               in the second)                                           */
   double  fft_cols_us;      /* measured time of one second FFT pass with that choice */
 } pc_plan_tuning;
 

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-PC_ABI_VERSION = 2
+PC_ABI_VERSION = 3
 PC_OK = 0
 PC_ERR_INVALID_ARG = -1
 PC_ERR_OOM = -2
@@ -45,14 +45,15 @@ class PcError(RuntimeError):
 class pc_plan_opts(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("max_planes", ctypes.c_int32),
-                ("grid_mode", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("grid_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("fft_kernel", ctypes.c_int32)]
 
 
 class pc_plan_tuning(ctypes.Structure):
     _fields_ = [("tuned", ctypes.c_int32), ("grid_mode", ctypes.c_int32),
                 ("grid_piece", ctypes.c_int32), ("fft_rows_per_cta", ctypes.c_int32),
                 ("grid_us", ctypes.c_double), ("fft_rows_us", ctypes.c_double),
-                ("fft_cols_planes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("fft_cols_planes", ctypes.c_int32), ("fft_warp", ctypes.c_int32),
                 ("fft_cols_us", ctypes.c_double)]
 
 
@@ -229,9 +230,10 @@ class Plan:
 
 
 def pc_plan_create(uvw: torch.Tensor, N: int, fov: float, kernel_width: int = 0, tile: int = 0,
-                   max_planes: int = 0, stream=None, grid_mode: int = 0, autotune: int = 0) -> Plan:
+                   max_planes: int = 0, stream=None, grid_mode: int = 0, autotune: int = 0,
+                   fft_kernel: int = 0) -> Plan:
     lib = load()
-    opts = pc_plan_opts(PC_ABI_VERSION, kernel_width, tile, max_planes, grid_mode, autotune)
+    opts = pc_plan_opts(PC_ABI_VERSION, kernel_width, tile, max_planes, grid_mode, autotune, fft_kernel)
     h = _P()
     M = int(uvw.shape[0])
     _check(lib.pc_plan_create(_dev(uvw, torch.float64, "uvw") if M else None, M, N, float(fov),
@@ -254,7 +256,8 @@ def pc_plan_tuning_info(plan: Plan) -> dict:
     _check(load().pc_plan_tuning_info(plan.handle, ctypes.byref(t)))
     return dict(tuned=bool(t.tuned), grid_mode=t.grid_mode, grid_piece=t.grid_piece,
                 fft_rows_per_cta=t.fft_rows_per_cta, grid_us=t.grid_us, fft_rows_us=t.fft_rows_us,
-                fft_cols_planes=t.fft_cols_planes, fft_cols_us=t.fft_cols_us)
+                fft_cols_planes=t.fft_cols_planes, fft_cols_us=t.fft_cols_us,
+                fft_warp=t.fft_warp)
 
 
 def pc_forward_sparse(plan: Plan, idx: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = None,

@@ -17,10 +17,14 @@
 // Pass 2 (k_fft_cols): one CTA per image row i; for every plane a length-G
 // inverse FFT along b, keep N outputs, apply the plane phase and accumulate
 // in registers; then the per-pixel correction, write mu and its max |mu|.
-// Both passes run radix-4 (plus one radix-2) Stockham stages in shared memory
-// with a twiddle table e^{+2 pi i k / G}.
+// Where G is 512 or 1024 both passes give each row to one warp, which holds
+// it in registers (fft_warp.cuh): no block-wide barrier inside a transform.
+// Otherwise, and where the autotuner measured it faster, they run radix-4
+// (plus one radix-2) Stockham stages in shared memory with a twiddle table
+// e^{+2 pi i k / G}.
 #include "pc_internal.cuh"
 #include "fft.cuh"
+#include "fft_warp.cuh"
 
 namespace pc {
 
@@ -47,6 +51,134 @@ k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int l
   for (int f = threadIdx.x; f < N * R; f += blockDim.x) {
     const int i = f / R, r = f - i * R;
     dst[(size_t)i * G + r] = res[r * S + ((i - hN + G) & mask)];
+  }
+}
+
+// Pass 1 on one-warp FFTs: a CTA takes 8 consecutive active rows of one
+// plane, one per warp, and writes the N kept outputs of each, staged in the
+// warps' buffers, as 64-byte runs X_q[i][b0 .. b0 + 8).
+template <int L>
+__global__ void __launch_bounds__(256, 2)
+k_fft_rows_w(const float2* __restrict__ grid, float2* __restrict__ X, int N,
+             const float2* __restrict__ tw, const int* __restrict__ active_rows) {
+  constexpr int G = 32 * L, WB = wfft::Shape<L>::buf;
+  extern __shared__ float2 sm[];
+  float2* T2 = sm;
+  float2* bufs = sm + 32 * L;
+  wfft::build_t2<L>(T2, tw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.y;
+  const int b0 = active_rows[blockIdx.x * 8];     // 8 consecutive active rows (8 divides 32)
+  const float2* src = grid + ((size_t)q * G + b0 + warp) * G + lane;
+  float2 v[L];
+#pragma unroll
+  for (int m = 0; m < L; ++m) v[m] = src[32 * m];
+  __syncthreads();                                // T2 complete
+  float2* buf = bufs + warp * WB;
+  wfft::fft<L>(v, buf, T2, lane);
+  const int hN = N >> 1;
+#pragma unroll
+  for (int c = 0; c < wfft::Shape<L>::kept; ++c) {
+    const int i = (wfft::kept_freq<L>(c, lane) + hN) & (G - 1);
+    if (i < N) buf[i] = wfft::kept_value<L>(v, c, lane);
+  }
+  __syncthreads();
+  float2* dst = X + (size_t)q * N * G + b0;
+  for (int e = threadIdx.x; e < N * 8; e += 256) {
+    const int i = e >> 3, r = e & 7;
+    dst[(size_t)i * G + r] = bufs[r * WB + i];
+  }
+}
+
+// Pass 2 on one-warp FFTs: a CTA takes 8 / WPR image rows, WPR warps per
+// row; warp w of a row transforms planes w, w + WPR, ... and accumulates the
+// plane-phased kept outputs in registers. The warps' partial sums meet in
+// shared memory, are added in warp order and get the per-pixel correction.
+template <int L>
+__global__ void __launch_bounds__(256, 2)
+k_fft_cols_w(const float2* __restrict__ X, const float4* __restrict__ pix, float* __restrict__ mu, int N,
+             int P, int WPR, int wstack, const float2* __restrict__ tw, float scale,
+             unsigned* __restrict__ maxbits) {
+  constexpr int G = 32 * L, WB = wfft::Shape<L>::buf, KEPT = wfft::Shape<L>::kept;
+  extern __shared__ float2 sm[];
+  float2* T2 = sm;
+  float2* bufs = sm + 32 * L;
+  wfft::build_t2<L>(T2, tw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RPC = 8 / WPR;
+  const int i = blockIdx.x * RPC + warp / WPR;
+  const int hN = N >> 1;
+  float2* buf = bufs + warp * WB;
+  float2 acc[KEPT];
+#pragma unroll
+  for (int c = 0; c < KEPT; ++c) acc[c] = make_float2(0.f, 0.f);
+  __syncthreads();                                // T2 complete
+  if (i < N) {
+    // (t_hi, t_lo) of pixel (i, j) at tzw[2 j]
+    const float2* tzw = reinterpret_cast<const float2*>(pix + (size_t)i * N) + 1;
+    for (int q = warp % WPR; q < P; q += WPR) {
+      const float2* src = X + ((size_t)q * N + i) * G + lane;
+      float2 v[L];
+#pragma unroll
+      for (int m = 0; m < L; ++m) v[m] = src[32 * m];
+      wfft::fft<L>(v, buf, T2, lane);
+      const float qf = (float)q;
+#pragma unroll
+      for (int c = 0; c < KEPT; ++c) {
+        const int j = (wfft::kept_freq<L>(c, lane) + hN) & (G - 1);
+        if (j < N) {
+          const float2 val = wfft::kept_value<L>(v, c, lane);
+          if (wstack) {
+            // q t in turns, with t = t_hi + t_lo, reduced exactly before sincospi
+            const float2 t = tzw[2 * j];
+            const float p = qf * t.x;
+            const float e = fmaf(qf, t.x, -p) + qf * t.y;
+            const float th = (p - rintf(p)) + e;
+            float sn, cs;
+            sincospif(2.0f * th, &sn, &cs);
+            acc[c].x += val.x * cs - val.y * sn;
+            acc[c].y += val.x * sn + val.y * cs;
+          } else {
+            acc[c].x += val.x;
+            acc[c].y += val.y;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KEPT; ++c) {
+    const int j = (wfft::kept_freq<L>(c, lane) + hN) & (G - 1);
+    if (j < N) buf[j] = acc[c];
+  }
+  __syncthreads();
+  float amax = 0.0f;
+  unsigned skey = 0;   // order-preserving key of the signed maximum (0 below every number)
+  for (int e = threadIdx.x; e < RPC * N; e += 256) {
+    const int r = e / N, j = e - r * N;
+    const int ii = blockIdx.x * RPC + r;
+    if (ii >= N) continue;
+    const float2* pb = bufs + (size_t)r * WPR * WB + j;
+    float2 s = pb[0];
+    for (int w = 1; w < WPR; ++w) {
+      s.x += pb[w * WB].x;
+      s.y += pb[w * WB].y;
+    }
+    const float4 pt = pix[(size_t)ii * N + j];
+    const float m = (pt.x * s.x - pt.y * s.y) * scale;
+    mu[(size_t)ii * N + j] = m;
+    amax = fmaxf(amax, fabsf(m));
+    if (m != m) amax = __int_as_float(0x7fc00000);
+    skey = max(skey, float_order_key(m));
+  }
+  unsigned bits = __float_as_uint(amax);
+  for (int off = 16; off; off >>= 1) {
+    bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    skey = max(skey, __shfl_xor_sync(0xffffffffu, skey, off));
+  }
+  if (lane == 0 && maxbits) {
+    atomicMax(maxbits, bits);
+    atomicMax(maxbits + 1, skey);
   }
 }
 
@@ -129,9 +261,54 @@ k_fft_cols(const float2* __restrict__ X, const float4* __restrict__ pix, float* 
   }
 }
 
+namespace {
+
+bool warp_fft_size(int G) { return G == 512 || G == 1024; }
+
+size_t warp_fft_smem(int G) {
+  const int L = G / 32;
+  const int WB = L == 32 ? wfft::Shape<32>::buf : wfft::Shape<16>::buf;
+  return ((size_t)32 * L + 8 * (size_t)WB) * sizeof(float2);
+}
+
+template <typename K>
+int allow_smem(K* kernel, size_t bytes, bool& done) {
+  if (!done) {
+    PC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done = true;
+  }
+  return PC_OK;
+}
+
+}  // namespace
+
+bool fft_rows_warp(const pc_plan_s* p) {
+  return warp_fft_size(p->G) && (p->fft_warp < 0 || (p->fft_warp & 1));
+}
+
+bool fft_cols_warp(const pc_plan_s* p) {
+  return warp_fft_size(p->G) && (p->fft_warp < 0 || (p->fft_warp & 2));
+}
+
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_ROWS, st);
   if (p->n_active_rows == 0) return PC_OK;     // all-zero grid: the output stays zero
+  if (fft_rows_warp(p)) {
+    const size_t smem = warp_fft_smem(p->G);
+    dim3 grid(p->n_active_rows / 8, p->P);
+    prof_scope_.kernels = 1;
+    if (p->G == 1024) {
+      static bool done = false;
+      PC_TRY(allow_smem(k_fft_rows_w<32>, smem, done));
+      k_fft_rows_w<32><<<grid, 256, smem, st>>>(p->grid, p->fft1, p->N, p->twiddle, p->active_rows);
+    } else {
+      static bool done = false;
+      PC_TRY(allow_smem(k_fft_rows_w<16>, smem, done));
+      k_fft_rows_w<16><<<grid, 256, smem, st>>>(p->grid, p->fft1, p->N, p->twiddle, p->active_rows);
+    }
+    PC_LAUNCH_CHECK();
+    return PC_OK;
+  }
   // rows per CTA (default): R * (G + 1) * 8 bytes * 2 buffers ~ 33 KB;
   // R divides the 32-row tile so a CTA's rows are consecutive active rows
   int R = p->fft_R > 0 ? p->fft_R : 2048 / p->G;
@@ -164,6 +341,28 @@ int cols_planes_per_pass(const pc_plan_s* p) {
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_COLS, st);
+  if (fft_cols_warp(p)) {
+    const size_t smem = warp_fft_smem(p->G);
+    int wpr = 8;                                   // warps per image row: a power of 2 <= P
+    while (wpr > p->P) wpr >>= 1;
+    const int rpc = 8 / wpr;
+    const int ws = p->wstack ? 1 : 0;
+    prof_scope_.kernels = 1;
+    const unsigned nb = (unsigned)ceil_div(p->N, rpc);
+    if (p->G == 1024) {
+      static bool done = false;
+      PC_TRY(allow_smem(k_fft_cols_w<32>, smem, done));
+      k_fft_cols_w<32><<<nb, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->N, p->P, wpr, ws, p->twiddle,
+                                               scale, maxbits);
+    } else {
+      static bool done = false;
+      PC_TRY(allow_smem(k_fft_cols_w<16>, smem, done));
+      k_fft_cols_w<16><<<nb, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->N, p->P, wpr, ws, p->twiddle,
+                                               scale, maxbits);
+    }
+    PC_LAUNCH_CHECK();
+    return PC_OK;
+  }
   const int PG = cols_planes_per_pass(p);
   const size_t smem = ((size_t)2 * PG * p->G + p->G) * sizeof(float2);
   const int jpt = (p->N + 255) / 256;

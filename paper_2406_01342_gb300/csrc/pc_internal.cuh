@@ -269,6 +269,8 @@ int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st);
 int cols_planes_per_pass(const pc_plan_s* p);
+bool fft_rows_warp(const pc_plan_s* p);   // the first pass runs the one-warp register FFT
+bool fft_cols_warp(const pc_plan_s* p);   // the second pass does
 // degrid.cu: y = Phi(img) for a dense N x N image (type-2 NUFFT), y cleared first
 int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st);
 
@@ -294,6 +296,8 @@ struct pc_plan_s {
   int grid_piece = 0; // gridding sub-problem size in slots (0: chosen for even waves)
   int fft_R = 0;      // rows per CTA of the first FFT pass (0: 2048 / G)
   int fft_cols_pg = 0; // planes per pass of the second FFT pass (0: default)
+  int fft_warp = -1;  // bit 0 / bit 1: first / second FFT pass as one-warp register FFTs
+                      // (-1: both wherever G is 512 or 1024, the sizes those kernels take)
   bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
   double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0;
   std::vector<int4> sub_ranges;   // (tile, plane group, first slot, end) before splitting

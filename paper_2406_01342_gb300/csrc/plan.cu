@@ -444,8 +444,16 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   PC_TRY(split_subs(p, best_piece, st));
   p->tune_grid_us = best;
   PC_TRY(launch_grid(p, p->resid, st));         // a gridded plane set for the FFT timing
+  // first pass: the one-warp register FFT (where G allows it) against the
+  // shared-memory Stockham kernel at each rows-per-CTA
   double best_fft = 1e300;
-  int best_R = 0;
+  int best_R = 0, best_rw = 0;
+  p->fft_warp = 1;
+  if (fft_rows_warp(p)) {
+    PC_TRY(time_us(st, 3, [&] { return launch_fft_rows(p, st); }, &best_fft));
+    best_rw = 1;
+  }
+  p->fft_warp = 0;
   for (int R : {1, 2, 4, 8, 16, 32}) {
     if (((size_t)2 * R * (p->G + 1) + p->G) * sizeof(float2) > 200 * 1024) break;
     p->fft_R = R;
@@ -454,14 +462,24 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
     if (us < best_fft) {
       best_fft = us;
       best_R = R;
+      best_rw = 0;
     }
   }
   p->fft_R = best_R;
   p->tune_fft_us = best_fft;
-  // second pass: planes transformed together per pass (shared memory vs CTAs per SM)
+  p->fft_warp = best_rw;
+  // second pass: one-warp register FFTs against the Stockham kernel at each
+  // number of planes transformed together (shared memory vs CTAs per SM)
   PC_TRY(launch_fft_rows(p, st));
   double best_cols = 1e300;
-  int best_pg = 1;
+  int best_pg = 1, best_cw = 0;
+  p->fft_warp = best_rw | 2;
+  if (fft_cols_warp(p)) {
+    PC_TRY(time_us(st, 3, [&] { return launch_fft_cols_epilogue(p, p->mu, 1.0f, nullptr, st); },
+                   &best_cols));
+    best_cw = 2;
+  }
+  p->fft_warp = best_rw;
   for (int pg : {1, 2, 4, 8}) {
     p->fft_cols_pg = pg;
     if (cols_planes_per_pass(p) != pg) break;   // beyond the planes or shared memory
@@ -470,10 +488,12 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
     if (us < best_cols) {
       best_cols = us;
       best_pg = pg;
+      best_cw = 0;
     }
   }
   p->fft_cols_pg = best_pg;
   p->tune_fft_cols_us = best_cols;
+  p->fft_warp = best_rw | best_cw;
   p->tuned = true;
   PC_CUDA(cudaMemsetAsync(p->resid, 0, sizeof(float2) * p->M, st));
   PC_CUDA(cudaStreamSynchronize(st));
@@ -774,6 +794,9 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
     return fail(PC_ERR_INVALID_ARG, "pc_plan_create: grid_mode %d not in [0, 2]", grid_mode);
   const int tune = opts ? opts->autotune : 0;
   if (tune != 0 && tune != 1) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: autotune must be 0 or 1");
+  const int fft_kernel = opts ? opts->fft_kernel : 0;
+  if (fft_kernel != 0 && fft_kernel != 1)
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: fft_kernel must be 0 or 1");
 
   pc_plan_s* p = new pc_plan_s();
   cudaGetDevice(&p->device);
@@ -783,6 +806,7 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   p->W = W;
   p->T = T;
   p->grid_mode = grid_mode;
+  p->fft_warp = fft_kernel == 1 ? 0 : -1;
   int rc = build_plan(p, uvw_dev, (cudaStream_t)stream, maxP);
   if (rc == PC_OK && tune) rc = autotune(p, (cudaStream_t)stream);
   if (rc != PC_OK) {
@@ -800,12 +824,13 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
   out->grid_mode = (p->wstack && p->grid_mode != 1) ? 2 : 1;
   out->grid_piece = p->grid_piece;
   int R = p->fft_R > 0 ? p->fft_R : 2048 / p->G;
-  out->fft_rows_per_cta = std::min(std::max(R, 1), 32);
+  const bool rw = fft_rows_warp(p), cw = fft_cols_warp(p);
+  out->fft_rows_per_cta = rw ? 8 : std::min(std::max(R, 1), 32);
   out->grid_us = p->tune_grid_us;
   out->fft_rows_us = p->tune_fft_us;
-  out->fft_cols_planes = cols_planes_per_pass(p);
+  out->fft_cols_planes = cw ? 1 : cols_planes_per_pass(p);
   out->fft_cols_us = p->tune_fft_cols_us;
-  out->reserved = 0;
+  out->fft_warp = (rw ? 1 : 0) | (cw ? 2 : 0);
   return PC_OK;
 }
 

@@ -74,6 +74,33 @@ def test_adjoint_grid(abi, name, kw, grid_mode):
     assert rel_l2(img[pix], ref) <= TOL
 
 
+@pytest.mark.parametrize("name,kw", [("small_wide_w", {"N": 200}), ("small_wide_w", {"N": 256}),
+                                     ("small_wide_w", {"N": 300}), ("diffuse_256", {}),
+                                     ("medium_512_w", {"M": 20_000})])
+def test_fft_kernels(abi, name, kw):
+    """The FFT passes of the adjoint on one warp per row in registers (the
+    default at G = 512 and 1024) and on shared-memory Stockham stages
+    (fft_kernel = 1): each meets the tolerance against the direct sum on the
+    image's border rows and columns and on random pixels, and the two agree
+    on the whole image. N = 200 and 300 leave part of the kept band empty."""
+    wl, V = workload(name, **kw)
+    Vd = to_dev(V.astype(np.complex64))
+    pw, ps = _plan(abi, wl), _plan(abi, wl, fft_kernel=1)
+    assert abi.pc_plan_info(pw)["grid_side"] in (512, 1024)
+    assert abi.pc_plan_tuning_info(pw)["fft_warp"] == 3
+    assert abi.pc_plan_tuning_info(ps)["fft_warp"] == 0
+    aw = abi.pc_adjoint_grid(pw, Vd).cpu().numpy().ravel()
+    as_ = abi.pc_adjoint_grid(ps, Vd).cpu().numpy().ravel()
+    N = wl.N
+    border = np.concatenate([np.arange(N), (N - 1) * N + np.arange(N), np.arange(N) * N,
+                             np.arange(N) * N + N - 1])
+    pix = np.union1d(border, np.random.default_rng(5).choice(N * N, 1024, replace=False))
+    ref = operators.adjoint(wl.uvw, N, wl.fov, V.astype(np.complex64).astype(np.complex128), pix)
+    assert rel_l2(aw[pix], ref) <= TOL
+    assert rel_l2(as_[pix], ref) <= TOL
+    assert rel_l2(aw, as_) <= TOL
+
+
 @pytest.mark.parametrize("name,kw", CASES)
 def test_forward_grid(abi, name, kw):
     """Degridding (the type-2 non-uniform FFT of Sect. 5.2) of a dense random
@@ -226,6 +253,11 @@ def test_autotuned_plan(abi):
     assert t["fft_rows_per_cta"] in (1, 2, 4, 8, 16, 32)
     assert 0 < t["grid_us"] < 1e5 and 0 < t["fft_rows_us"] < 1e5
     assert t["fft_cols_planes"] in (1, 2, 4, 8) and 0 < t["fft_cols_us"] < 1e5
+    assert t["fft_warp"] in (0, 1, 2, 3)
+    if t["fft_warp"] & 1:
+        assert t["fft_rows_per_cta"] == 8
+    if t["fft_warp"] & 2:
+        assert t["fft_cols_planes"] == 1
     assert not abi.pc_plan_tuning_info(_plan(abi, wl))["tuned"]
     Vs = V.astype(np.complex64)
     img = abi.pc_adjoint_grid(plan, to_dev(Vs)).cpu().numpy().ravel()
