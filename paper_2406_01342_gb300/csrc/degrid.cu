@@ -22,9 +22,12 @@
 //                      (the conjugate of the gridding pre-twiddle), added to
 //                      y_k (a visibility's footprint may span several tiles).
 //
-// A forward FFT is evaluated as conj(IFFT(conj(.))) with the inverse Stockham
-// passes of fft.cu, so both directions share one FFT code path.
+// A forward FFT is evaluated as conj(IFFT(conj(.))) with the inverse FFTs of
+// the certificate path, so both directions share one FFT code path: one warp
+// per row in registers where G is 512 or 1024 (fft_warp.cuh), else the
+// shared-memory Stockham stages (fft.cuh).
 #include "fft.cuh"
+#include "fft_warp.cuh"
 
 namespace pc {
 namespace {
@@ -102,6 +105,91 @@ k_degrid_rows(const float2* __restrict__ Xt, int N, int G, int logG, int R, cons
   for (int e = threadIdx.x; e < rows * G; e += blockDim.x) {
     const int r = e / G, a = e - r * G;
     grid[((size_t)q * G + active_rows[ar0 + r]) * G + a] = conj2(res[r * S + a]);
+  }
+}
+
+// Pass 1 on one-warp FFTs: a CTA takes 8 image rows of one plane, one per
+// warp; each row's transform is staged in its warp's buffer and the CTA
+// writes the reachable rows b as 64-byte runs Xt_q[b][i0 .. i0 + 8).
+template <int L>
+__global__ void __launch_bounds__(256, 2)
+k_degrid_cols_w(const float* __restrict__ x, const float4* __restrict__ pix, int N, int wstack,
+                const float2* __restrict__ T2, const int* __restrict__ active_rows, int n_active,
+                float2* __restrict__ Xt) {
+  constexpr int G = 32 * L, WB = wfft::Shape<L>::buf;
+  extern __shared__ float2 bufs[];                  // 8 warps x WB
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.y, i0 = blockIdx.x * 8, i = i0 + warp;
+  const int hN = N >> 1;
+  const float qf = (float)q;
+  float2 v[L];
+#pragma unroll
+  for (int m = 0; m < L; ++m) {
+    const int j = (lane + 32 * m + hN) & (G - 1);     // pixel at row position lane + 32 m
+    v[m] = make_float2(0.f, 0.f);
+    if (i < N && j < N) {
+      const size_t p = (size_t)i * N + j;
+      const float4 pt = pix[p];
+      float2 c = make_float2(pt.x, pt.y);
+      if (wstack) {
+        // q t in turns, t = t_hi + t_lo, reduced exactly to [-1/2, 1/2] (as the
+        // one-warp epilogue; the fast sine and cosine are accurate to ~4e-7 there)
+        const float pp = qf * pt.z;
+        const float ee = fmaf(qf, pt.z, -pp) + qf * pt.w;
+        const float th = (pp - rintf(pp)) + ee;
+        float sn, cs;
+        __sincosf(6.283185307179586f * th, &sn, &cs);
+        c = cmul(c, make_float2(cs, sn));
+      }
+      const float xv = x[p];
+      // conj of the forward-FFT input conj(c) e^{-j 2 pi q t} x: inverse FFT below
+      v[m] = make_float2(c.x * xv, c.y * xv);
+    }
+  }
+  float2* buf = bufs + warp * WB;
+  wfft::fft<L>(v, buf, T2, lane);
+  // every output frequency: L = 32 lane + 32 k2; L = 16 (lane >> 1) + 16 k' + 256 (lane & 1)
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const int f = (L == 32) ? lane + 32 * k : (lane >> 1) + 16 * k + 256 * (lane & 1);
+    buf[f] = v[wfft::brev(k, wfft::log2c(L))];
+  }
+  __syncthreads();
+  const int rows = min(8, N - i0);
+  for (int e = threadIdx.x; e < n_active * 8; e += 256) {
+    const int ar = e >> 3, r = e & 7;
+    if (r < rows) Xt[((size_t)q * n_active + ar) * N + i0 + r] = conj2(bufs[r * WB + active_rows[ar]]);
+  }
+}
+
+// Pass 2 on one-warp FFTs: one warp per (plane, reachable row); the N inputs
+// sit on the centre of the length-G row, and the transformed row is stored
+// with coalesced 256-byte (L = 32) or 128-byte (L = 16) runs in the 32-column
+// groups that hold visibilities (col_mask: the interpolation reads no other).
+template <int L>
+__global__ void __launch_bounds__(256, 2)
+k_degrid_rows_w(const float2* __restrict__ Xt, int N, const float2* __restrict__ T2,
+                const int* __restrict__ active_rows, int n_active, uint32_t col_mask,
+                float2* __restrict__ grid) {
+  constexpr int G = 32 * L, WB = wfft::Shape<L>::buf;
+  extern __shared__ float2 bufs[];                  // 8 warps x WB
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.y, ar = blockIdx.x * 8 + warp;
+  const int hN = N >> 1;
+  float2 v[L];
+  const float2* src = Xt + ((size_t)q * n_active + ar) * N;
+#pragma unroll
+  for (int m = 0; m < L; ++m) {
+    const int i = (lane + 32 * m + hN) & (G - 1);
+    v[m] = (ar < n_active && i < N) ? conj2(src[i]) : make_float2(0.f, 0.f);
+  }
+  if (ar >= n_active) return;                       // no block barrier in this kernel
+  wfft::fft<L>(v, bufs + warp * WB, T2, lane);
+  float2* dst = grid + ((size_t)q * G + active_rows[ar]) * G;
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const int f = (L == 32) ? lane + 32 * k : (lane >> 1) + 16 * k + 256 * (lane & 1);
+    if ((col_mask >> (f >> 5)) & 1u) dst[f] = conj2(v[wfft::brev(k, wfft::log2c(L))]);
   }
 }
 
@@ -187,6 +275,37 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
   PC_TRY(p->degrid_buf.ensure(sizeof(float2) * (size_t)p->P * n_act * N));
   float2* Xt = p->degrid_buf.as<float2>();
   const int ws = p->wstack ? 1 : 0;
+  if (fft_cols_warp(p)) {
+    // one-warp FFTs for both passes (the plan's choice for its second FFT pass)
+    const int L = G / 32;
+    const size_t smem = 8 * (size_t)(L == 32 ? wfft::Shape<32>::buf : wfft::Shape<16>::buf) * sizeof(float2);
+    dim3 g1(ceil_div(N, 8), p->P), g2(ceil_div(n_act, 8), p->P);
+    if (L == 32) {
+      static bool attr = false;
+      if (!attr) {
+        PC_CUDA(cudaFuncSetAttribute(k_degrid_cols_w<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PC_CUDA(cudaFuncSetAttribute(k_degrid_rows_w<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+      }
+      k_degrid_cols_w<32><<<g1, 256, smem, st>>>(img, p->pix_tab, N, ws, p->tw2, p->active_rows, n_act, Xt);
+      PC_LAUNCH_CHECK();
+      k_degrid_rows_w<32><<<g2, 256, smem, st>>>(Xt, N, p->tw2, p->active_rows, n_act, p->col_mask,
+                                                    p->grid);
+      PC_LAUNCH_CHECK();
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        PC_CUDA(cudaFuncSetAttribute(k_degrid_cols_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PC_CUDA(cudaFuncSetAttribute(k_degrid_rows_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+      }
+      k_degrid_cols_w<16><<<g1, 256, smem, st>>>(img, p->pix_tab, N, ws, p->tw2, p->active_rows, n_act, Xt);
+      PC_LAUNCH_CHECK();
+      k_degrid_rows_w<16><<<g2, 256, smem, st>>>(Xt, N, p->tw2, p->active_rows, n_act, p->col_mask,
+                                                    p->grid);
+      PC_LAUNCH_CHECK();
+    }
+  } else {
   {
     const size_t smem = ((size_t)2 * DG_R1 * G + G) * sizeof(float2);
     if (smem > 200 * 1024) return fail(PC_ERR_INVALID_ARG, "forward: grid side %d too large for degridding", G);
@@ -211,6 +330,7 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
     dim3 grid(ceil_div(n_act, R), p->P);
     k_degrid_rows<<<grid, 256, smem, st>>>(Xt, N, G, p->logG, R, p->twiddle, p->active_rows, n_act, p->grid);
     PC_LAUNCH_CHECK();
+  }
   }
   {
     if (p->T != DG_T || p->Qg > 8) return fail(PC_ERR_INVALID_ARG, "forward: needs 32-cell tiles, <= 8 planes");

@@ -56,24 +56,21 @@ k_fft_rows(const float2* __restrict__ grid, float2* __restrict__ X, int G, int l
 
 // Pass 1 on one-warp FFTs: a CTA takes 8 consecutive active rows of one
 // plane, one per warp, and writes the N kept outputs of each, staged in the
-// warps' buffers, as 64-byte runs X_q[i][b0 .. b0 + 8).
+// warps' buffers, as 64-byte runs X_q[i][b0 .. b0 + 8). Only the 32-column
+// groups that can hold data (col_mask) are read; the rest of a row is zero.
 template <int L>
 __global__ void __launch_bounds__(256, 2)
 k_fft_rows_w(const float2* __restrict__ grid, float2* __restrict__ X, int N,
-             const float2* __restrict__ tw, const int* __restrict__ active_rows) {
+             const float2* __restrict__ T2, const int* __restrict__ active_rows, uint32_t col_mask) {
   constexpr int G = 32 * L, WB = wfft::Shape<L>::buf;
-  extern __shared__ float2 sm[];
-  float2* T2 = sm;
-  float2* bufs = sm + 32 * L;
-  wfft::build_t2<L>(T2, tw);
+  extern __shared__ float2 bufs[];                 // 8 warps x WB
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = blockIdx.y;
   const int b0 = active_rows[blockIdx.x * 8];     // 8 consecutive active rows (8 divides 32)
   const float2* src = grid + ((size_t)q * G + b0 + warp) * G + lane;
   float2 v[L];
 #pragma unroll
-  for (int m = 0; m < L; ++m) v[m] = src[32 * m];
-  __syncthreads();                                // T2 complete
+  for (int m = 0; m < L; ++m) v[m] = ((col_mask >> m) & 1u) ? src[32 * m] : make_float2(0.f, 0.f);
   float2* buf = bufs + warp * WB;
   wfft::fft<L>(v, buf, T2, lane);
   const int hN = N >> 1;
@@ -91,78 +88,114 @@ k_fft_rows_w(const float2* __restrict__ grid, float2* __restrict__ X, int N,
 }
 
 // Pass 2 on one-warp FFTs: a CTA takes 8 / WPR image rows, WPR warps per
-// row; warp w of a row transforms planes w, w + WPR, ... and accumulates the
-// plane-phased kept outputs in registers. The warps' partial sums meet in
+// row; warp w of a row transforms planes w, w + WPR, ... (reading only the
+// 32-entry groups of reachable grid rows, row_mask) and sums the
+// plane-phased kept outputs (ONE: exactly one plane per warp, written
+// straight to its buffer; else running sums in shared memory). The rows' w-screen turns are staged in shared
+// memory while the first loads are in flight. The warps' partial sums meet in
 // shared memory, are added in warp order and get the per-pixel correction.
 template <int L>
+__device__ __forceinline__ float2 plane_phased(float2 val, float2 t, float qf, bool wstack) {
+  if (!wstack) return val;
+  // q t in turns, with t = t_hi + t_lo, reduced exactly to [-1/2, 1/2]
+  // (the fast sine and cosine are accurate to ~4e-7 absolute there)
+  const float p = qf * t.x;
+  const float e = fmaf(qf, t.x, -p) + qf * t.y;
+  const float th = (p - rintf(p)) + e;
+  float sn, cs;
+  __sincosf(6.283185307179586f * th, &sn, &cs);
+  return make_float2(val.x * cs - val.y * sn, val.x * sn + val.y * cs);
+}
+
+template <int L, bool ONE>
 __global__ void __launch_bounds__(256, 2)
 k_fft_cols_w(const float2* __restrict__ X, const float4* __restrict__ pix, float* __restrict__ mu, int N,
-             int P, int WPR, int wstack, const float2* __restrict__ tw, float scale,
+             int P, int WPR, int wstack, const float2* __restrict__ T2, uint32_t row_mask, float scale,
              unsigned* __restrict__ maxbits) {
   constexpr int G = 32 * L, WB = wfft::Shape<L>::buf, KEPT = wfft::Shape<L>::kept;
   extern __shared__ float2 sm[];
-  float2* T2 = sm;
-  float2* bufs = sm + 32 * L;
-  wfft::build_t2<L>(T2, tw);
+  float2* bufs = sm;                              // 8 warps x WB
+  float2* tz = sm + 8 * WB;                       // (t_hi, t_lo) of the CTA's rows, RPC x N
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int RPC = 8 / WPR;
   const int i = blockIdx.x * RPC + warp / WPR;
   const int hN = N >> 1;
   float2* buf = bufs + warp * WB;
-  float2 acc[KEPT];
+  int q = warp % WPR;
+  float2 v[L];
+  const bool live = i < N && q < P;
+  if (live) {
+    const float2* src = X + ((size_t)q * N + i) * G + lane;
 #pragma unroll
-  for (int c = 0; c < KEPT; ++c) acc[c] = make_float2(0.f, 0.f);
-  __syncthreads();                                // T2 complete
-  if (i < N) {
-    // (t_hi, t_lo) of pixel (i, j) at tzw[2 j]
-    const float2* tzw = reinterpret_cast<const float2*>(pix + (size_t)i * N) + 1;
-    for (int q = warp % WPR; q < P; q += WPR) {
-      const float2* src = X + ((size_t)q * N + i) * G + lane;
-      float2 v[L];
-#pragma unroll
-      for (int m = 0; m < L; ++m) v[m] = src[32 * m];
+    for (int m = 0; m < L; ++m) v[m] = ((row_mask >> m) & 1u) ? src[32 * m] : make_float2(0.f, 0.f);
+  }
+  if (wstack) {
+    const int i0 = blockIdx.x * RPC;
+    for (int e = threadIdx.x; e < RPC * N; e += 256) {
+      if (i0 + e / N < N) {
+        const float4 pt = pix[(size_t)i0 * N + e];
+        tz[e] = make_float2(pt.z, pt.w);
+      }
+    }
+  }
+  __syncthreads();                                // turns staged
+  const float2* tzr = tz + (size_t)(warp / WPR) * N;
+  if (ONE) {
+    if (live) {
       wfft::fft<L>(v, buf, T2, lane);
       const float qf = (float)q;
 #pragma unroll
       for (int c = 0; c < KEPT; ++c) {
         const int j = (wfft::kept_freq<L>(c, lane) + hN) & (G - 1);
-        if (j < N) {
-          const float2 val = wfft::kept_value<L>(v, c, lane);
-          if (wstack) {
-            // q t in turns, with t = t_hi + t_lo, reduced exactly before sincospi
-            const float2 t = tzw[2 * j];
-            const float p = qf * t.x;
-            const float e = fmaf(qf, t.x, -p) + qf * t.y;
-            const float th = (p - rintf(p)) + e;
-            float sn, cs;
-            sincospif(2.0f * th, &sn, &cs);
-            acc[c].x += val.x * cs - val.y * sn;
-            acc[c].y += val.x * sn + val.y * cs;
-          } else {
-            acc[c].x += val.x;
-            acc[c].y += val.y;
+        if (j < N) buf[j] = plane_phased<L>(wfft::kept_value<L>(v, c, lane), wstack ? tzr[j] : make_float2(0.f, 0.f),
+                                            qf, wstack);
+      }
+    } else {
+      for (int j = lane; j < N; j += 32) buf[j] = make_float2(0.f, 0.f);
+    }
+  } else {
+    // several planes per warp: the running sums live in the warp's own N
+    // entries after the turns (each lane owns its pixels: no races)
+    float2* acc = tz + (size_t)RPC * N + (size_t)warp * N;
+    for (int j = lane; j < N; j += 32) acc[j] = make_float2(0.f, 0.f);
+    __syncwarp();
+    if (live) {
+      for (;;) {
+        wfft::fft<L>(v, buf, T2, lane);
+        const float qf = (float)q;
+#pragma unroll
+        for (int c = 0; c < KEPT; ++c) {
+          const int j = (wfft::kept_freq<L>(c, lane) + hN) & (G - 1);
+          if (j < N) {
+            const float2 pv = plane_phased<L>(wfft::kept_value<L>(v, c, lane),
+                                              wstack ? tzr[j] : make_float2(0.f, 0.f), qf, wstack);
+            acc[j].x += pv.x;
+            acc[j].y += pv.y;
           }
         }
+        q += WPR;
+        if (q >= P) break;
+        const float2* src = X + ((size_t)q * N + i) * G + lane;
+#pragma unroll
+        for (int m = 0; m < L; ++m) v[m] = ((row_mask >> m) & 1u) ? src[32 * m] : make_float2(0.f, 0.f);
       }
     }
   }
-#pragma unroll
-  for (int c = 0; c < KEPT; ++c) {
-    const int j = (wfft::kept_freq<L>(c, lane) + hN) & (G - 1);
-    if (j < N) buf[j] = acc[c];
-  }
   __syncthreads();
+  // partial sums of warp w at part + w * pstride
+  const float2* part = ONE ? bufs : tz + (size_t)RPC * N;
+  const int pstride = ONE ? WB : N;
   float amax = 0.0f;
   unsigned skey = 0;   // order-preserving key of the signed maximum (0 below every number)
   for (int e = threadIdx.x; e < RPC * N; e += 256) {
     const int r = e / N, j = e - r * N;
     const int ii = blockIdx.x * RPC + r;
     if (ii >= N) continue;
-    const float2* pb = bufs + (size_t)r * WPR * WB + j;
+    const float2* pb = part + (size_t)r * WPR * pstride + j;
     float2 s = pb[0];
     for (int w = 1; w < WPR; ++w) {
-      s.x += pb[w * WB].x;
-      s.y += pb[w * WB].y;
+      s.x += pb[w * pstride].x;
+      s.y += pb[w * pstride].y;
     }
     const float4 pt = pix[(size_t)ii * N + j];
     const float m = (pt.x * s.x - pt.y * s.y) * scale;
@@ -265,16 +298,17 @@ namespace {
 
 bool warp_fft_size(int G) { return G == 512 || G == 1024; }
 
-size_t warp_fft_smem(int G) {
-  const int L = G / 32;
-  const int WB = L == 32 ? wfft::Shape<32>::buf : wfft::Shape<16>::buf;
-  return ((size_t)32 * L + 8 * (size_t)WB) * sizeof(float2);
+// the 8 warps' buffers, plus (second pass) the w-screen turns of the CTA's rows
+size_t warp_fft_smem(int G, int turns = 0) {
+  const int WB = G == 1024 ? wfft::Shape<32>::buf : wfft::Shape<16>::buf;
+  return (8 * (size_t)WB + (size_t)turns) * sizeof(float2);
 }
 
+// opt in once to the shared memory any plan's launch may ask for
 template <typename K>
-int allow_smem(K* kernel, size_t bytes, bool& done) {
+int allow_smem(K* kernel, bool& done) {
   if (!done) {
-    PC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    PC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     done = true;
   }
   return PC_OK;
@@ -299,12 +333,12 @@ int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
     prof_scope_.kernels = 1;
     if (p->G == 1024) {
       static bool done = false;
-      PC_TRY(allow_smem(k_fft_rows_w<32>, smem, done));
-      k_fft_rows_w<32><<<grid, 256, smem, st>>>(p->grid, p->fft1, p->N, p->twiddle, p->active_rows);
+      PC_TRY(allow_smem(k_fft_rows_w<32>, done));
+      k_fft_rows_w<32><<<grid, 256, smem, st>>>(p->grid, p->fft1, p->N, p->tw2, p->active_rows, p->col_mask);
     } else {
       static bool done = false;
-      PC_TRY(allow_smem(k_fft_rows_w<16>, smem, done));
-      k_fft_rows_w<16><<<grid, 256, smem, st>>>(p->grid, p->fft1, p->N, p->twiddle, p->active_rows);
+      PC_TRY(allow_smem(k_fft_rows_w<16>, done));
+      k_fft_rows_w<16><<<grid, 256, smem, st>>>(p->grid, p->fft1, p->N, p->tw2, p->active_rows, p->col_mask);
     }
     PC_LAUNCH_CHECK();
     return PC_OK;
@@ -342,24 +376,28 @@ int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* max
                              cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_COLS, st);
   if (fft_cols_warp(p)) {
-    const size_t smem = warp_fft_smem(p->G);
     int wpr = 8;                                   // warps per image row: a power of 2 <= P
     while (wpr > p->P) wpr >>= 1;
     const int rpc = 8 / wpr;
     const int ws = p->wstack ? 1 : 0;
+    const bool one = wpr == p->P;                  // every warp exactly one plane
+    // turns of the CTA's rows; with several planes per warp also 8 running sums of N
+    const size_t smem = warp_fft_smem(p->G, one ? (ws ? rpc * p->N : 0) : rpc * p->N + 8 * p->N);
     prof_scope_.kernels = 1;
     const unsigned nb = (unsigned)ceil_div(p->N, rpc);
+#define PC_COLS_W(LL, ONE)                                                                        \
+  {                                                                                               \
+    static bool done = false;                                                                     \
+    PC_TRY(allow_smem(k_fft_cols_w<LL, ONE>, done));                                              \
+    k_fft_cols_w<LL, ONE><<<nb, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->N, p->P, wpr, ws,   \
+                                                 p->tw2, p->row_mask, scale, maxbits);            \
+  }
     if (p->G == 1024) {
-      static bool done = false;
-      PC_TRY(allow_smem(k_fft_cols_w<32>, smem, done));
-      k_fft_cols_w<32><<<nb, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->N, p->P, wpr, ws, p->twiddle,
-                                               scale, maxbits);
+      if (one) PC_COLS_W(32, true) else PC_COLS_W(32, false)
     } else {
-      static bool done = false;
-      PC_TRY(allow_smem(k_fft_cols_w<16>, smem, done));
-      k_fft_cols_w<16><<<nb, 256, smem, st>>>(p->fft1, p->pix_tab, mu, p->N, p->P, wpr, ws, p->twiddle,
-                                               scale, maxbits);
+      if (one) PC_COLS_W(16, true) else PC_COLS_W(16, false)
     }
+#undef PC_COLS_W
     PC_LAUNCH_CHECK();
     return PC_OK;
   }

@@ -98,31 +98,22 @@ template <int L> struct Shape {
   static constexpr int kept = L / 2;       // outputs per lane inside the N <= G / 2 image
 };
 
-// Twiddle table of step 2, T2[k1 * 32 + l] = e^{+2 pi i l k1 / G}, built by
-// the whole block from the plan's table tw[k] = e^{+2 pi i k / G}.
-template <int L>
-__device__ __forceinline__ void build_t2(float2* T2, const float2* __restrict__ tw) {
-  constexpr int G = 32 * L;
-  for (int e = threadIdx.x; e < 32 * L; e += blockDim.x) {
-    const int k1 = e >> 5, l = e & 31;
-    T2[e] = tw[(k1 * l) & (G - 1)];
-  }
-}
-
 // The inverse G-point FFT of the row held in v (see the top of the file).
 // Afterwards output frequency f of lane `lane` is at
 //   L = 32: f = lane + 32 k2                          in v[brev(k2, 5)], k2 < 32
 //   L = 16: f = (lane >> 1) + 16 k' + 256 (lane & 1)  in v[brev(k', 4)], k' < 16
-// `buf` is this warp's buffer (Shape<L>::buf elements); it is free again on return.
+// `buf` is this warp's buffer (Shape<L>::buf elements); it is free again on
+// return. T2 is the plan's global table T2[k1 * 32 + l] = e^{+2 pi i l k1 / G}
+// (8 KB at G = 1024, read through the L1 cache: every warp reads all of it).
 template <int L>
-__device__ __forceinline__ void fft(float2 (&v)[L], float2* buf, const float2* T2, int lane) {
+__device__ __forceinline__ void fft(float2 (&v)[L], float2* buf, const float2* __restrict__ T2, int lane) {
   constexpr int LB = log2c(L);
   constexpr int RW = Shape<L>::row;
   dft_dif<L>(v);                                       // v[brev(k1)] = step-1 output k1
 #pragma unroll
   for (int k1 = 0; k1 < L; ++k1) {
     float2 y = v[brev(k1, LB)];
-    if (k1 > 0) y = cmul(y, T2[k1 * 32 + lane]);
+    if (k1 > 0) y = cmul(y, __ldg(T2 + k1 * 32 + lane));
     buf[k1 * RW + lane] = y;
   }
   __syncwarp();

@@ -316,6 +316,9 @@ struct pc_plan_s {
   // image-domain tables
   float4* pix_tab = nullptr;     // per pixel {Re c d, Im c d, t_hi, t_lo}
   float2* twiddle = nullptr;     // e^{+2 pi i k / G}
+  float2* tw2 = nullptr;         // one-warp FFT twiddles e^{+2 pi i l k1 / G}, [k1 < G/32][l < 32]
+  uint32_t row_mask = 0;         // G <= 1024: bit t set if grid rows 32 t .. 32 t + 31 can hold data
+  uint32_t col_mask = 0;         // G <= 1024: the same for grid columns
   // workspaces
   float2* grid = nullptr;        // P x G x G  (b-major rows, a contiguous)
   float2* fft1 = nullptr;        // P x N x G  (after the pass along a)

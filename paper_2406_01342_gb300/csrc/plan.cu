@@ -602,6 +602,14 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   }
   PC_TRY(dev_alloc_t(p, &p->twiddle, p->G));
   PC_CUDA(cudaMemcpyAsync(p->twiddle, tw.data(), sizeof(float2) * p->G, cudaMemcpyHostToDevice, st));
+  if (p->G == 512 || p->G == 1024) {
+    const int L = p->G / 32;
+    std::vector<float2> t2((size_t)32 * L);
+    for (int k1 = 0; k1 < L; ++k1)
+      for (int l = 0; l < 32; ++l) t2[(size_t)k1 * 32 + l] = tw[(size_t)(k1 * l) % p->G];
+    PC_TRY(dev_alloc_t(p, &p->tw2, t2.size()));
+    PC_CUDA(cudaMemcpyAsync(p->tw2, t2.data(), sizeof(float2) * t2.size(), cudaMemcpyHostToDevice, st));
+  }
 
   // ---- workspaces
   PC_TRY(dev_alloc_t(p, &p->grid, (size_t)p->P * p->G * p->G));
@@ -711,6 +719,13 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   int piece = (int)std::min<int64_t>(kMaxSlotsPerSub, std::max<int64_t>(128, (total_slots + want - 1) / want));
   piece = ceil_div(piece, 64) * 64;
   p->sub_ranges = ranges;
+  // tile rows / columns that hold visibilities (the one-warp FFTs skip the rest, which stay zero)
+  p->row_mask = p->col_mask = 0;
+  if (p->nT <= 32)
+    for (const int4& s : ranges) {
+      p->row_mask |= 1u << (s.x / p->nT);
+      p->col_mask |= 1u << (s.x % p->nT);
+    }
   // room for the finest split the autotuner may try (pieces of 64 slots)
   p->sub_cap = (int)(total_slots / 64 + (int64_t)ranges.size() + 1);
   PC_TRY(dev_alloc_t(p, &p->subs, (size_t)p->sub_cap));

@@ -116,6 +116,30 @@ def test_forward_grid(abi, name, kw):
     assert rel_l2(y[ks], ref) <= TOL
 
 
+@pytest.mark.parametrize("fft_kernel", [0, 1])
+@pytest.mark.parametrize("name,kw", [("small_wide_w", {"N": 200}), ("small_wide_w", {"N": 300}),
+                                     ("diffuse_256", {})])
+def test_forward_grid_fft_kernels(abi, name, kw, fft_kernel):
+    """Degridding with one-warp register FFTs (default at G = 512 and 1024)
+    and with the Stockham passes (fft_kernel = 1), N = 200 and 300 leaving
+    part of the length-G rows empty: against the direct sum on every
+    visibility, and the adjoint identity with the same plan's gridding."""
+    wl, _ = workload(name, **kw)
+    plan = _plan(abi, wl, fft_kernel=fft_kernel)
+    assert abi.pc_plan_tuning_info(plan)["fft_warp"] == (0 if fft_kernel else 3)
+    rng = np.random.default_rng(33)
+    img = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
+    y = abi.pc_forward_grid(plan, to_dev(img)).cpu().numpy()
+    ks = np.sort(rng.choice(wl.M, min(wl.M, 3000), replace=False))
+    ref = operators.forward(wl.uvw[ks], wl.N, wl.fov, np.arange(wl.N * wl.N), img.ravel().astype(np.float64))
+    assert rel_l2(y[ks], ref) <= TOL
+    h = (rng.normal(size=wl.M) + 1j * rng.normal(size=wl.M)).astype(np.complex64)
+    g = abi.pc_adjoint_grid(plan, to_dev(h)).cpu().numpy().astype(np.float64)
+    lhs = float(np.real(np.vdot(y.astype(np.complex128), h.astype(np.complex128))))
+    rhs = float(np.sum(img.astype(np.float64) * g))
+    assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(y) ** 2) * np.sum(np.abs(h) ** 2))
+
+
 @pytest.mark.parametrize("name,kw", CASES)
 def test_forward_grid_is_the_adjoint_of_adjoint_grid(abi, name, kw):
     """Re<Phi x, h> = <x, Phi* h> between the two NUFFT directions of one plan
