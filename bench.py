@@ -244,6 +244,19 @@ def degridding_leg(abi, torch, plan, wl, info, peaks, steps, l2_flush) -> dict:
             "peak_gbs": hbm, "frac": byt / (t * 1e-3) / 1e9 / hbm}
 
 
+def tc_iterations(history):
+    """Frank-Wolfe iterations whose Gram ran on the tensor cores (the library's
+    switch: at least 16 new atoms and 4096 new x active entries)."""
+    return [h for h in history if h["n_new"] >= 16 and h["n_new"] * h["n_active"] >= 4096]
+
+
+def phase_gen_bytes(M, history):
+    """Bytes the phase generation writes for one solve: per tensor-core Gram,
+    FP16 hi + lo of cos and sin (8 B) per visibility for every row of the
+    padded atom list (active atoms + V, rounded up to 256)."""
+    return sum(8.0 * M * (-(-(h["n_active"] + 1) // 256) * 256) for h in tc_iterations(history))
+
+
 def roofline(prof, info, wl, history, steps, peaks, dom):
     """Achieved vs peak for the dominant kernel class `dom`, from its CUDA-event
     launch durations in `prof` (recorded over the timed region)."""
@@ -273,10 +286,13 @@ def roofline(prof, info, wl, history, steps, peaks, dom):
         # split-FP16 tensor work: 3 products x 4 flops (Re*Re + Im*Im) per visibility and
         # distinct Gram entry (new x (active + V), pairs of new atoms counted once), for
         # the Frank-Wolfe iterations that used the tensor cores
-        tc = [h for h in history if h["n_new"] >= 16 and h["n_new"] * h["n_active"] >= 4096]
+        tc = tc_iterations(history)
         f = sum(12.0 * M * gram_entries(h["n_new"], h["n_active"]) for h in tc) * steps / max(launches, 1)
         out.update(bound="tensor", achieved=f / (avg_ms * 1e-3) / 1e12,
                    peak=peaks.get("bf16_tflops", 1900.0), unit="TFLOP/s")
+    elif dom == "phase_gen":
+        b = phase_gen_bytes(M, history) * steps / max(launches, 1)
+        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
     elif dom in ("gram_fp32", "gram_thin"):
         f = sum(4.0 * M * h["n_new"] * h["n_active"] for h in history) * steps / max(launches, 1)
         fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -502,7 +518,7 @@ def run_ours(args, world, rank, local):
     with ClockSampler(local) as clk:
         # the timed pass: events only around the dominant kernel class and the
         # gridding (for the roofline objects), a handful per solve
-        abi.pc_profile_begin(",".join(sorted({dom, "grid"})))
+        abi.pc_profile_begin(",".join(sorted({dom, "grid", "phase_gen"})))
         for i in range(args.steps):
             flush_l2(l2_flush)
             starts[i].record(stream)
@@ -581,6 +597,9 @@ def run_ours(args, world, rank, local):
                       "objective": res["objective"], "converged": res["converged"]},
             "gridding_vis_per_s": vis_per_s,
             "gridding_roofline": gridding_roofline(prof_timed, info, wl, peaks),
+            "phase_gen_roofline": ({k: v for k, v in roofline(prof_timed, info, wl, res["history"], args.steps,
+                                                                peaks, "phase_gen").items() if k != "traffic"}
+                                   if "phase_gen" in prof_timed else None),
             "degridding": degrid,
             "kernels_ms": {k: round(v[2] / args.steps, 4) for k, v in prof.items()},
             "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},

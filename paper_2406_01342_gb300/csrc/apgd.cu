@@ -100,6 +100,39 @@ struct ApgdArgs {
   int vec_ok;     // 1: float4 loads of G rows are aligned
 };
 
+// Rows [r0, r0 + nr) of G (leading dimension ldg, n columns) into dst (row
+// stride ld floats, ld a multiple of 4, dst 16-byte aligned), columns [n, ld)
+// zero, by asynchronous copies: a warp per row, no register round trip per
+// element, so every load of the block is in flight at once. The calling
+// thread's copies are complete on return; the caller's barrier publishes them.
+__device__ void load_rows_async(float* dst, int ld, const float* __restrict__ G, int ldg, int r0, int nr,
+                                int n, bool vec) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < nr; r += nw) {
+    const float* src = G + (size_t)(r0 + r) * ldg;
+    float* d = dst + (size_t)r * ld;
+    if (vec) {
+      for (int c = 4 * lane; c < ld; c += 128) {
+        const int bytes = max(0, min(16, (n - c) * 4));
+        const uint32_t da = (uint32_t)__cvta_generic_to_shared(d + c);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(da), "l"(bytes > 0 ? src + c : src),
+                     "r"(bytes)
+                     : "memory");
+      }
+    } else {
+      for (int c = lane; c < ld; c += 32) {
+        if (c < n) {
+          const uint32_t da = (uint32_t)__cvta_generic_to_shared(d + c);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(da), "l"(src + c) : "memory");
+        } else {
+          d[c] = 0.f;
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Several independent restricted problems in one launch: cluster c of the
 // grid solves job c (all jobs of a launch share the cluster size).
 constexpr int APGD_BATCH_MAX = 16;
@@ -315,12 +348,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd(const __grid_constant_
   const int nr = max(0, min(a.n, r0 + a.rows_per) - r0);
   Df* part2 = s.part + 8;
 
-  if (a.cache) {
-    for (int e = threadIdx.x; e < nr * a.n_pad; e += blockDim.x) {
-      const int r = e / a.n_pad, c = e - r * a.n_pad;
-      s.Gc[e] = c < a.n ? a.G[(size_t)(r0 + r) * a.ldg + c] : 0.f;
-    }
-  }
+  if (a.cache) load_rows_async(s.Gc, a.n_pad, a.G, a.ldg, r0, nr, a.n, a.vec_ok != 0);
   const float v0 = rsqrtf((float)a.n);        // Lanczos start: all ones / sqrt(n)
   for (int r = threadIdx.x; r < a.rows_per; r += blockDim.x) {
     const bool own = r < nr;
@@ -701,12 +729,7 @@ __global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_full(const __grid_cons
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  if (a.cache) {
-    for (int e = tid; e < nr * a.n_pad; e += nt) {
-      const int r = e / a.n_pad, c = e - r * a.n_pad;
-      s.Gc[e] = c < n ? a.G[(size_t)(r0 + r) * a.ldg + c] : 0.f;
-    }
-  }
+  if (a.cache) load_rows_async(s.Gc, a.n_pad, a.G, a.ldg, r0, nr, n, a.vec_ok != 0);
   const float v0 = rsqrtf((float)n);        // Lanczos start: all ones / sqrt(n)
   for (int i = tid; i < a.n_pad; i += nt) {
     const bool in = i < n;
@@ -867,34 +890,45 @@ __device__ __forceinline__ Df warp_df_sum(Df v) {
 }
 
 __global__ void __launch_bounds__(32) k_apgd_warp(const __grid_constant__ ApgdBatch batch) {
-  __shared__ float Gs[WARP_NMAX][WARP_NMAX + 1];
-  __shared__ float vs[WARP_NMAX];
+  __shared__ __align__(16) float vs[WARP_NMAX];
   __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
   const ApgdArgs& a = batch.job[blockIdx.x];
   const int n = a.n, lane = threadIdx.x;
-  for (int e = lane; e < n * n; e += 32) {
-    const int r = e / n, c = e - r * n;
-    Gs[r][c] = a.G[(size_t)r * a.ldg + c];
-  }
   const int i0 = lane, i1 = lane + 32;
   const bool v0ok = i0 < n, v1ok = i1 < n;
+  // the lane's two rows of G live in registers (zero beyond n): every load in
+  // flight at once, and a product reads only the broadcast input vector
+  float g0[WARP_NMAX], g1[WARP_NMAX];
+#pragma unroll
+  for (int j = 0; j < WARP_NMAX; ++j) {
+    g0[j] = (v0ok && j < n) ? a.G[(size_t)i0 * a.ldg + j] : 0.f;
+    g1[j] = (v1ok && j < n) ? a.G[(size_t)i1 * a.ldg + j] : 0.f;
+  }
   float bb0 = v0ok ? a.b[i0] : 0.f, bb1 = v1ok ? a.b[i1] : 0.f;
   float x0 = v0ok ? a.x[i0] : 0.f, x1 = v1ok ? a.x[i1] : 0.f;
-  __syncwarp();
-  // G v for the lane's two rows (v broadcast through shared memory)
-  auto gemv = [&](float v0, float v1, float& g0, float& g1) {
+  // G v for the lane's two rows (v broadcast through shared memory, 16-byte
+  // reads; four partial sums per row for independent FMA chains)
+  auto gemv = [&](float v0, float v1, float& g0o, float& g1o) {
     vs[i0] = v0;
     vs[i1] = v1;
     __syncwarp();
-    float acc0 = 0.f, acc1 = 0.f;
-    for (int j = 0; j < n; ++j) {
-      const float vj = vs[j];
-      acc0 = fmaf(Gs[v0ok ? i0 : 0][j], vj, acc0);
-      acc1 = fmaf(Gs[v1ok ? i1 : 0][j], vj, acc1);
+    float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
+    const float4* v4 = reinterpret_cast<const float4*>(vs);
+#pragma unroll
+    for (int j4 = 0; j4 < WARP_NMAX / 4; ++j4) {
+      const float4 z = v4[j4];
+      p0[0] = fmaf(g0[4 * j4], z.x, p0[0]);
+      p0[1] = fmaf(g0[4 * j4 + 1], z.y, p0[1]);
+      p0[2] = fmaf(g0[4 * j4 + 2], z.z, p0[2]);
+      p0[3] = fmaf(g0[4 * j4 + 3], z.w, p0[3]);
+      p1[0] = fmaf(g1[4 * j4], z.x, p1[0]);
+      p1[1] = fmaf(g1[4 * j4 + 1], z.y, p1[1]);
+      p1[2] = fmaf(g1[4 * j4 + 2], z.z, p1[2]);
+      p1[3] = fmaf(g1[4 * j4 + 3], z.w, p1[3]);
     }
     __syncwarp();
-    g0 = v0ok ? acc0 : 0.f;
-    g1 = v1ok ? acc1 : 0.f;
+    g0o = v0ok ? (p0[0] + p0[1]) + (p0[2] + p0[3]) : 0.f;
+    g1o = v1ok ? (p1[0] + p1[1]) + (p1[2] + p1[3]) : 0.f;
   };
 
   // ---- Lipschitz constant: Lanczos from the all-ones vector
@@ -987,6 +1021,172 @@ __global__ void __launch_bounds__(32) k_apgd_warp(const __grid_constant__ ApgdBa
   }
 }
 
+// ---------------------------------------------------------------------------
+// One-CTA variant for mid-size supports (WARP_NMAX < n <= CTA_NMAX): the same
+// Lanczos step size, monotone FISTA, stop rule and reported objective, with G
+// cached in shared memory and thread i owning row i of every vector, so the
+// matrix-vector product (thread i: its row of G against the broadcast input)
+// and all elementwise steps need no exchange. A FISTA iteration crosses two
+// block barriers (input vector complete; partial sums complete) instead of a
+// cluster exchange and five barriers.
+constexpr int CTA_NMAX = 224;
+constexpr int CTA_LDG = 228;   // G row stride in floats: 16-byte aligned, 57 x 16 B (odd) so
+                               // eight rows read by a 128-bit phase hit distinct banks
+
+__device__ __forceinline__ float row_dot(const float* __restrict__ Grow, const float* __restrict__ v, int n4) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  const float4* g4 = reinterpret_cast<const float4*>(Grow);
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+#pragma unroll 4
+  for (int c = 0; c < n4; ++c) {
+    const float4 g = g4[c], z = v4[c];
+    a0 = fmaf(g.x, z.x, a0);
+    a1 = fmaf(g.y, z.y, a1);
+    a2 = fmaf(g.z, z.z, a2);
+    a3 = fmaf(g.w, z.w, a3);
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Sum of K per-thread values over the block, the same in every thread (each
+// adds the warps' partials in warp order). buf alternates between two
+// halves, so back-to-back reductions need no extra barrier.
+template <int K>
+__device__ __forceinline__ void cta_sum(float (&v)[K], float* red, int& parity) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int off = 16; off; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+  float* buf = red + parity * (APGD_THREADS / 32) * 4;
+  parity ^= 1;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < K; ++q) buf[warp * 4 + q] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w) t += buf[w * 4 + q];
+    v[q] = t;
+  }
+}
+
+__global__ void __launch_bounds__(APGD_THREADS, 1) k_apgd_cta(const __grid_constant__ ApgdBatch batch) {
+  extern __shared__ __align__(16) float apgdc_sm[];
+  __shared__ __align__(16) float vs[CTA_LDG];      // the broadcast input of a product
+  __shared__ float s_red[2 * (APGD_THREADS / 32) * 4];
+  __shared__ Df s_dred[(APGD_THREADS / 32) * 3];
+  __shared__ float s_al[LZ_MAX], s_be[LZ_MAX], s_theta;
+  const ApgdArgs& a = batch.job[blockIdx.x];
+  float* Gc = apgdc_sm;                             // n rows of CTA_LDG floats
+  const int n = a.n, tid = threadIdx.x;
+  const int n4 = (n + 3) >> 2;
+  load_rows_async(Gc, CTA_LDG, a.G, a.ldg, 0, n, n, a.vec_ok != 0);
+  const bool own = tid < n;
+  const float* Grow = Gc + (size_t)(own ? tid : 0) * CTA_LDG;
+  const float bb = own ? a.b[tid] : 0.f;
+  float x = own ? a.x[tid] : 0.f;
+  int parity = 0;
+
+  // ---- Lipschitz constant: Lanczos from the all-ones vector
+  float v = own ? rsqrtf((float)n) : 0.f, vprev = 0.f;
+  if (tid < CTA_LDG) vs[tid] = v;
+  __syncthreads();
+  float theta = 0.f, theta_prev = 0.f, beta_prev = 0.f;
+  int m = 0;
+  for (int j = 0; j < LZ_MAX; ++j) {
+    const float g = own ? row_dot(Grow, vs, n4) : 0.f;
+    float ra[1] = {v * g};
+    cta_sum<1>(ra, s_red, parity);
+    const float alpha = ra[0];
+    const float w = own ? g - alpha * v - beta_prev * vprev : 0.f;
+    float rb[1] = {w * w};
+    cta_sum<1>(rb, s_red, parity);
+    const float beta = sqrtf(fmaxf(rb[0], 0.f));
+    if (tid == 0) {
+      s_al[j] = alpha;
+      s_be[j] = beta;
+    }
+    m = j + 1;
+    const bool last = (m == n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
+    if (last || (m % 4) == 0) {
+      __syncthreads();                              // s_al, s_be written
+      theta = tridiag_top(s_al, s_be, m, &s_theta);
+      if (last || fabsf(theta - theta_prev) <= LZ_TOL * fabsf(theta)) break;
+      theta_prev = theta;
+    }
+    vprev = v;
+    v = w / beta;
+    if (own) vs[tid] = v;                           // every read of vs ended before the sums
+    beta_prev = beta;
+    __syncthreads();
+  }
+  const float L = 1.01f * (theta > 0.f ? theta : 1.f);
+  const float invL = 1.f / L;
+  const float thr = a.lam * invL;
+
+  // ---- initial G x
+  __syncthreads();                                  // every read of vs ended
+  if (own) vs[tid] = x;
+  __syncthreads();
+  float Gx = own ? row_dot(Grow, vs, n4) : 0.f;
+  float y = x, Gy = Gx;
+  __syncthreads();                                  // every read of vs ended
+
+  // ---- monotone FISTA
+  float t = 1.f;
+  int it = 0;
+  for (it = 1; it <= a.max_iter; ++it) {
+    const float u = y - (Gy - bb) * invL;
+    float z = a.positive ? fmaxf(u - thr, 0.f) : copysignf(fmaxf(fabsf(u) - thr, 0.f), u);
+    if (!own) z = 0.f;
+    if (own) vs[tid] = z;                           // the last product's reads ended before its sums
+    __syncthreads();
+    const float Gz = own ? row_dot(Grow, vs, n4) : 0.f;
+    // F(z) - F(x) from the difference itself (see k_apgd_full)
+    const float d = z - y;
+    float r3[3] = {own ? fmaf(z - x, 0.5f * (Gz + Gx) - bb, a.lam * (fabsf(z) - fabsf(x))) : 0.f, d * d, z * z};
+    cta_sum<3>(r3, s_red, parity);
+    const float step = sqrtf(r3[1]);
+    const float nz = sqrtf(r3[2]);
+    const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+    const bool accept = r3[0] <= 0.f;
+    const float c1 = t / t1, c2 = (t - 1.f) / t1;
+    const float xn = accept ? z : x, Gxn = accept ? Gz : Gx;
+    y = xn + c1 * (z - xn) + c2 * (xn - x);
+    Gy = Gxn + c1 * (Gz - Gxn) + c2 * (Gxn - Gx);
+    x = xn;
+    Gx = Gxn;
+    t = t1;
+    if (step <= a.eps * nz) break;
+  }
+  if (it > a.max_iter) it = a.max_iter;
+  // objective of the returned x, in double-float (reported only)
+  {
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    Df p[3] = {df_prod(x, Gx), df_prod(bb, x), Df{fabsf(x), 0.f}};
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) p[q] = df_add(p[q], df_shfl_xor(p[q], off));
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s_dred[warp * 3 + q] = p[q];
+    __syncthreads();
+    if (tid == 0) {
+      Df tot[3] = {};
+      for (int w = 0; w < nw; ++w)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) tot[q] = df_add(tot[q], s_dred[w * 3 + q]);
+      const Df Fx = df_add(df_add(df_scale(tot[0], 0.5f), df_neg(tot[1])), df_scale(tot[2], a.lam));
+      if (a.out_iters) *a.out_iters = it;
+      if (a.out_L) *a.out_L = (double)L;
+      if (a.out_F) *a.out_F = (double)Fx.hi + (double)Fx.lo;
+      if (a.out_lanczos) *a.out_lanczos = m;
+    }
+  }
+  if (own) a.x[tid] = x;
+}
+
 }  // namespace
 
 namespace {
@@ -995,6 +1195,7 @@ namespace {
 // CTA, whether the CTAs cache their rows of G, dynamic shared memory.
 struct ApgdShape {
   bool warp = false;   // one-warp kernel (n <= WARP_NMAX)
+  bool cta = false;    // one-CTA kernel (WARP_NMAX < n <= CTA_NMAX)
   bool full;
   int CS;
   int rows_per;
@@ -1020,6 +1221,8 @@ int apgd_setup(int* cs_max_out) {
     PC_CUDA(cudaFuncSetAttribute(k_apgd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLimitRows));
     PC_CUDA(cudaFuncSetAttribute(k_apgd_full, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kLimitFull));
+    PC_CUDA(cudaFuncSetAttribute(k_apgd_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * CTA_NMAX * CTA_LDG)));
     attrs_set = true;
   }
   *cs_max_out = cs_max;
@@ -1051,6 +1254,17 @@ int apgd_shape(int S, int cs_max, ApgdShape* out) {
     sh.CS = 1;
     sh.cache = 1;
     sh.smem = 0;
+    sh.rows_per = S;
+    sh.n_pad = n_pad;
+    *out = sh;
+    return PC_OK;
+  }
+  if (S <= CTA_NMAX) {
+    sh.cta = true;
+    sh.full = true;
+    sh.CS = 1;
+    sh.cache = 1;
+    sh.smem = sizeof(float) * (size_t)S * CTA_LDG;
     sh.rows_per = S;
     sh.n_pad = n_pad;
     *out = sh;
@@ -1119,10 +1333,12 @@ int run_apgd_jobs(const ApgdJob* jobs, int n_jobs, cudaStream_t st) {
     ApgdBatch batch{};
     size_t smem = 0;
     const bool full = shapes[i].full;
-    const bool warp = shapes[i].warp;
+    const bool warp = shapes[i].warp, cta = shapes[i].cta;
     const int CS = shapes[i].CS;
     for (int j = i; j < n_jobs && batch.n_jobs < APGD_BATCH_MAX; ++j) {
-      if (done[j] || shapes[j].full != full || shapes[j].CS != CS || shapes[j].warp != warp) continue;
+      if (done[j] || shapes[j].full != full || shapes[j].CS != CS || shapes[j].warp != warp ||
+          shapes[j].cta != cta)
+        continue;
       batch.job[batch.n_jobs++] = make_args(jobs[j], shapes[j]);
       smem = std::max(smem, shapes[j].smem);
       done[j] = 1;
@@ -1131,6 +1347,13 @@ int run_apgd_jobs(const ApgdJob* jobs, int n_jobs, cudaStream_t st) {
       ProfScope prof_scope_(PROF_APGD, st);
       prof_scope_.kernels = 1;
       k_apgd_warp<<<batch.n_jobs, 32, 0, st>>>(batch);
+      PC_LAUNCH_CHECK();
+      continue;
+    }
+    if (cta) {
+      ProfScope prof_scope_(PROF_APGD, st);
+      prof_scope_.kernels = 1;
+      k_apgd_cta<<<batch.n_jobs, APGD_THREADS, smem, st>>>(batch);
       PC_LAUNCH_CHECK();
       continue;
     }

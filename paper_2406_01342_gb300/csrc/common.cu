@@ -195,7 +195,7 @@ namespace {
 const char* const kProfNames[PROF_NCLASSES] = {"plan",     "grid",     "fft_rows", "fft_cols",
                                                "residual", "gram_fp32", "gram_finalize",
                                                "apgd",     "select",   "misc",     "gram_tc",
-                                               "gram_thin", "dict_corr", "dict_columns"};
+                                               "gram_thin", "dict_corr", "dict_columns", "phase_gen"};
 
 struct ProfRec {
   int cls;

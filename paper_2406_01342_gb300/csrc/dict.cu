@@ -135,7 +135,7 @@ k_dict_corr(const float* __restrict__ img, int N, const __grid_constant__ DictPa
 
 __global__ void __launch_bounds__(256)
 k_dict_columns(const int4* __restrict__ vis, int64_t M, const int32_t* __restrict__ idx,
-               const int32_t* __restrict__ rows, int n_rows, int N, double dl,
+               const int32_t* __restrict__ rows, int n_rows, int N, const float4* __restrict__ atom_tab,
                const __grid_constant__ DictParams D, float2* __restrict__ C, int64_t ldc) {
   __shared__ float4 fp[DTAPS * DTAPS];
   const int r = blockIdx.y;
@@ -152,7 +152,9 @@ k_dict_columns(const int4* __restrict__ vis, int64_t M, const int32_t* __restric
     const int x = x0 + n, y = y0 + m;
     const bool in = x >= 0 && x < N && y >= 0 && y < N;
     const float w = in ? gam * D.g1[i][n + K] * D.g1[i][m + K] : 0.f;
-    fp[f] = make_atom(in ? x * N + y : p, w, true, N, dl);   // weight w / n_pixel
+    float4 at = atom_tab[in ? x * N + y : p];                // weight w / n_pixel
+    at.w *= w;
+    fp[f] = at;
   }
   __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,7 +166,9 @@ k_dict_columns(const int4* __restrict__ vis, int64_t M, const int32_t* __restric
     for (int m = 0; m < side; ++m) {
       const float4 at = fp[n * side + m];
       float sn, cs;
-      sincospif(2.0f * phase_turns(vk, at), &sn, &cs);
+      // phase reduced exactly to [-1/2, 1/2] turns: fast sine and cosine
+      // accurate to ~4e-7 absolute there (as the other phase kernels)
+      __sincosf(6.283185307179586f * phase_turns(vk, at), &sn, &cs);
       rr = fmaf(at.w, cs, rr);
       ri = fmaf(-at.w, sn, ri);
     }
@@ -387,7 +391,7 @@ int launch_columns(pc_plan_s* p, const int32_t* idx, const int32_t* rows, int n_
   if (n_rows <= 0 || p->M <= 0) return PC_OK;
   prof_scope_.kernels = 1;
   dim3 grid(ceil_div(p->M, 256), n_rows);
-  k_dict_columns<<<grid, 256, 0, st>>>(p->vis_fx, p->M, idx, rows, n_rows, p->N, p->dl, D, C, ldc);
+  k_dict_columns<<<grid, 256, 0, st>>>(p->vis_fx, p->M, idx, rows, n_rows, p->N, p->atom_tab, D, C, ldc);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }

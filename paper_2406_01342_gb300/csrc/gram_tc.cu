@@ -384,7 +384,6 @@ __global__ void __launch_bounds__(GB_THREADS, 1) k_gram_bulk(GbArgs g) {
 int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4* atoms, int n_atoms,
                    int nA, double* acc, int ldacc, int* err_dev, cudaStream_t st, bool withhold,
                    DevBuf& pbuf, float* vscale_dev, unsigned* vbits_dev) {
-  ProfScope prof_scope_(PROF_GRAM_TC, st);
   if (M <= 0 || nA <= 0 || n_atoms <= 0) return PC_OK;
   const int rows = n_atoms + (V ? 1 : 0);
   const int rows_pad = ceil_div(rows, 256) * 256;
@@ -405,23 +404,28 @@ int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4*
     PC_CUDA(cudaFuncSetAttribute(k_gram_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
-  int nk = 0;
-  if (V) {
-    PC_CUDA(cudaMemsetAsync(vbits_dev, 0, sizeof(unsigned), st));
-    k_vmax<<<(int)std::min<int64_t>(1024, ceil_div(M, 256)), 256, 0, st>>>(V, M, vbits_dev);
-    k_vscale<<<1, 1, 0, st>>>(vbits_dev, vscale_dev);
-    PC_LAUNCH_CHECK();
-    nk += 3;
-  }
+  // timed as two classes: the phase generation (HBM-bound; the V scale with
+  // the first chunk) and the contraction
   for (int64_t k0 = 0; k0 < M; k0 += KC) {
     const int64_t kc = std::min(KC, M - k0);
     const int n_stages = (int)((kc + GB_KV - 1) / GB_KV);
-    // ~16 resident 256-thread blocks per SM; each thread walks stages with stride gridDim.y
-    const int bx = rows_pad / 256;
-    const int by = (int)std::min<int64_t>(n_stages, std::max<int64_t>(1, (int64_t)152 * 16 / bx));
-    k_phase_gen<<<dim3(bx, by), 256, 0, st>>>(vis_fx, V, k0, k0 + kc, atoms, n_atoms, V ? n_atoms : -1,
-                                              rows_pad, n_stages, vscale_dev, hi, lo);
-    PC_LAUNCH_CHECK();
+    {
+      ProfScope ps(PROF_PHASE_GEN, st);
+      ps.kernels = 1;
+      if (V && k0 == 0) {
+        PC_CUDA(cudaMemsetAsync(vbits_dev, 0, sizeof(unsigned), st));
+        k_vmax<<<(int)std::min<int64_t>(1024, ceil_div(M, 256)), 256, 0, st>>>(V, M, vbits_dev);
+        k_vscale<<<1, 1, 0, st>>>(vbits_dev, vscale_dev);
+        PC_LAUNCH_CHECK();
+        ps.kernels += 2;
+      }
+      // ~16 resident 256-thread blocks per SM; each thread walks stages with stride gridDim.y
+      const int bx = rows_pad / 256;
+      const int by = (int)std::min<int64_t>(n_stages, std::max<int64_t>(1, (int64_t)152 * 16 / bx));
+      k_phase_gen<<<dim3(bx, by), 256, 0, st>>>(vis_fx, V, k0, k0 + kc, atoms, n_atoms, V ? n_atoms : -1,
+                                                rows_pad, n_stages, vscale_dev, hi, lo);
+      PC_LAUNCH_CHECK();
+    }
     // K-slices: the count that makes the CTAs left after the diagonal skip fill
     // whole waves (a partial last wave idles most of the GPU for a slice's
     // time), fewest slices among the best (fewer float64 flushes)
@@ -451,11 +455,11 @@ int launch_gram_tc(const int4* vis_fx, const float2* V, int64_t M, const float4*
              rows_pad, n_stages, nA, rows, V ? n_atoms : -1, V ? vscale_dev : nullptr, NT, acc, ldacc,
              err_dev, withhold ? 1 : 0, slice_stages};
     dim3 grid(gx, gy, ceil_div(n_stages, slice_stages));
+    ProfScope pg(PROF_GRAM_TC, st);
+    pg.kernels = 1;
     k_gram_bulk<<<grid, GB_THREADS, smem, st>>>(a);
     PC_LAUNCH_CHECK();
-    nk += 2;
   }
-  prof_scope_.kernels = nk;
   return PC_OK;
 }
 

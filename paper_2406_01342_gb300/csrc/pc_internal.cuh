@@ -68,7 +68,8 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // when recording is off; prof_stop() records the end event of that token.
 enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
-                 PROF_GRAM_TC, PROF_GRAM_THIN, PROF_DICT_CORR, PROF_DICT_COLUMNS, PROF_NCLASSES };
+                 PROF_GRAM_TC, PROF_GRAM_THIN, PROF_DICT_CORR, PROF_DICT_COLUMNS, PROF_PHASE_GEN,
+                 PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
 bool prof_active();   // kernel-class timing is recording
 void prof_stop(int token, cudaStream_t st, int kernels);
@@ -315,6 +316,8 @@ struct pc_plan_s {
   int n_active_rows = 0;
   // image-domain tables
   float4* pix_tab = nullptr;     // per pixel {Re c d, Im c d, t_hi, t_lo}
+  float4* atom_tab = nullptr;    // per pixel its unit-weight atom (make_atom); a weighted
+                                 // atom is the entry with .w times the weight
   float2* twiddle = nullptr;     // e^{+2 pi i k / G}
   float2* tw2 = nullptr;         // one-warp FFT twiddles e^{+2 pi i l k1 / G}, [k1 < G/32][l < 32]
   uint32_t row_mask = 0;         // G <= 1024: bit t set if grid rows 32 t .. 32 t + 31 can hold data

@@ -335,6 +335,15 @@ __global__ void k_pix_tab(PixGeom g, const double* __restrict__ psi_uv,
   out[p] = make_float4((float)(cs * d), (float)(sn * d), t_hi, t_lo);
 }
 
+// Per-pixel unit-weight atoms, evaluated once per plan: their s = n - 1 and
+// 1 / n take FP64 square roots and divisions, a slow pipe on this GPU, which
+// the solver's per-iteration bookkeeping then only gathers.
+__global__ void k_atom_tab(int N, double dl, float4* __restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= (int64_t)N * N) return;
+  out[p] = make_atom((int)p, 1.f, false, N, dl);
+}
+
 // The stream plan construction runs on: plan buffers come from the library's
 // pool ordered on it (construction ends with a synchronisation of this stream,
 // after which every stream may use them).
@@ -595,6 +604,9 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
     k_pix_tab<<<ceil_div(NN, 256), 256, 0, st>>>(pg, d_psi, d_gx, d_gw, kGlNodes, p->pix_tab);
     PC_LAUNCH_CHECK();
   }
+  PC_TRY(dev_alloc_t(p, &p->atom_tab, NN));
+  k_atom_tab<<<ceil_div(NN, 256), 256, 0, st>>>(N, p->dl, p->atom_tab);
+  PC_LAUNCH_CHECK();
   std::vector<float2> tw(p->G);
   for (int k = 0; k < p->G; ++k) {
     double a = 2.0 * M_PI * k / p->G;
@@ -769,7 +781,7 @@ int64_t plan_bytes_estimate(int64_t M, int N, double fov, double w_min, double w
   int64_t b = 0;
   b += P * G * G * 8;                       // grid planes
   b += P * N * G * 8;                       // pass-1 FFT output
-  b += NN * (16 + 4 + 1 + 4);               // pixel table, mu, marks, selection
+  b += NN * (16 + 16 + 4 + 1 + 4);          // pixel and atom tables, mu, marks, selection
   b += M * (16 + 8);                        // fixed-point visibilities, residual
   b += M * groups * 2 * 24;                 // binned slots (replication into tiles and plane groups)
   b += 2 * 4096ll * 4096ll * 4;             // Gram working set (grown on demand; 4096 atoms)

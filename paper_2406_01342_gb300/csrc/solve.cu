@@ -87,7 +87,7 @@ __global__ void k_prune(const int32_t* __restrict__ keep, const int32_t* __restr
                         const float* __restrict__ bB, const float* __restrict__ GB, int ld,
                         int32_t* __restrict__ idxA, float* __restrict__ xA, float* __restrict__ bA,
                         float* __restrict__ GA, float4* __restrict__ atomsA, uint8_t* __restrict__ mark,
-                        double* __restrict__ l1, int N, double dl) {
+                        double* __restrict__ l1, const float4* __restrict__ atom_tab) {
   const int n = min(bound, *n_dev);
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
     const int ki = keep[i];
@@ -99,7 +99,9 @@ __global__ void k_prune(const int32_t* __restrict__ keep, const int32_t* __restr
       idxA[i] = p;
       xA[i] = x;
       bA[i] = bB[ki];
-      atomsA[i] = make_atom(p, x, true, N, dl);
+      float4 at = atom_tab[p];
+      at.w *= x;
+      atomsA[i] = at;
       mark[p] = 1;
       atomicAdd(l1, fabs((double)x));
     }
@@ -114,8 +116,8 @@ __global__ void __launch_bounds__(1024)
 k_post_select(const int32_t* __restrict__ idxB, int n_act, const int32_t* __restrict__ idxA, int nS,
               const float* __restrict__ xA, const float* __restrict__ bA, int32_t* __restrict__ oldpos,
               int32_t* __restrict__ newrows, int32_t* __restrict__ n_new_dev, float* __restrict__ xB,
-              float* __restrict__ bB, float4* __restrict__ atomsB, uint8_t* __restrict__ mark, int N,
-              double dl) {
+              float* __restrict__ bB, float4* __restrict__ atomsB, uint8_t* __restrict__ mark,
+              const float4* __restrict__ atom_tab) {
   __shared__ int wcount[32];
   __shared__ int run_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -135,7 +137,7 @@ k_post_select(const int32_t* __restrict__ idxB, int n_act, const int32_t* __rest
       oldpos[i] = op;
       xB[i] = op >= 0 ? xA[op] : 0.f;
       bB[i] = op >= 0 ? bA[op] : 0.f;
-      atomsB[i] = make_atom(v, 1.f, false, N, dl);
+      atomsB[i] = atom_tab[v];
       is_new = op < 0;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, is_new);
@@ -642,7 +644,7 @@ int SolveJob::enqueue_chain(int bound) {
                                   p->xB.as<float>(), p->bB.as<float>(), p->GB.as<float>(), ld(),
                                   p->idxA.as<int32_t>(), p->xA.as<float>(), p->bA.as<float>(),
                                   p->GA.as<float>(), p->atomsA.as<float4>(), p->mark, p->dscal + 1,
-                                  p->N, p->dl);
+                                  p->atom_tab);
     PC_LAUNCH_CHECK();
   }
   PC_TRY(launch_residual(p->vis_fx, V, p->M, p->atomsA.as<float4>(), bound, p->resid, p->dscal, st,
@@ -795,7 +797,7 @@ int SolveJob::process() {
       k_post_select<<<1, 1024, 0, st>>>(p->idxB.as<int32_t>(), n_act, p->idxA.as<int32_t>(), nS,
                                         p->xA.as<float>(), p->bA.as<float>(), oldpos,
                                         p->newrows.as<int32_t>(), p->iscal + 1, p->xB.as<float>(),
-                                        p->bB.as<float>(), p->atomsB.as<float4>(), p->mark, p->N, p->dl);
+                                        p->bB.as<float>(), p->atomsB.as<float4>(), p->mark, p->atom_tab);
       PC_LAUNCH_CHECK();
     }
     // old-old block of G

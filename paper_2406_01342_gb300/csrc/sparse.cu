@@ -47,9 +47,10 @@ k_residual(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M
     if (active) {
       for (int t = 0; t < cnt; ++t) {
         const float4 at = sa[t];
-        const float th = phase_turns(vk, at);
+        // the phase is reduced exactly to [-1/2, 1/2] turns, where the fast
+        // sine and cosine are accurate to ~4e-7 absolute (as in the Gram kernels)
         float sn, cs;
-        sincospif(2.0f * th, &sn, &cs);
+        __sincosf(6.283185307179586f * phase_turns(vk, at), &sn, &cs);
         ar = fmaf(at.w, cs, ar);
         ai = fmaf(-at.w, sn, ai);
       }

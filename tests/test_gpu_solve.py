@@ -73,12 +73,14 @@ def test_lambda_above_lambda_max_gives_zero(abi):
     assert abs(res["objective"] - 0.5 * res["sumsq_V"]) <= 1e-12 * res["sumsq_V"]
 
 
-def test_apgd_matches_oracle_subsolver(abi):
-    """Restricted LASSO by the cluster APGD kernel vs the oracle's FISTA on the same support."""
+@pytest.mark.parametrize("n_rand", [30, 60, 150, 290])
+def test_apgd_matches_oracle_subsolver(abi, n_rand):
+    """Restricted LASSO by the APGD kernels vs the oracle's FISTA on the same
+    support: about 36 atoms (one warp), 66 and 156 (one CTA), 296 (cluster)."""
     wl, V = workload("small_wide_w")
     Vs = V.astype(np.complex64).astype(np.complex128)
     lam = 0.05 * operators.lambda_max(wl.uvw, wl.N, wl.fov, Vs)
-    idx = np.sort(np.random.default_rng(9).choice(wl.N * wl.N, 60, replace=False))
+    idx = np.sort(np.random.default_rng(9).choice(wl.N * wl.N, n_rand, replace=False))
     idx = np.union1d(idx, wl.sky_idx)
     l, m, n = operators.pixel_lmn(wl.N, wl.fov, idx)
     A = operators.phase_block(wl.uvw, l, m, n)
