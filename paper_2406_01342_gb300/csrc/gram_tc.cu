@@ -117,20 +117,41 @@ __global__ void k_vscale(const unsigned* __restrict__ bits, float* __restrict__ 
 // (or the V row), as four 16-byte items of FP16 re/im pairs in hi and in lo.
 // Item order equals memory order: [stage][row group][K-group][row in group],
 // so a warp (32 consecutive rows) writes 4 x 128 contiguous bytes per K-group.
-// The atom stays in registers across the stages a thread visits; the stage's
-// visibilities are the same for the whole block (broadcast loads).
-__global__ void __launch_bounds__(256)
+// The atom stays in registers across the stages a thread visits; every thread
+// of a block visits the same stages, whose visibilities 16 threads copy into
+// shared memory one stage ahead (asynchronous copies), so the phase work
+// never waits on a global load.
+// Threads 0..15 copy the visibilities of a stage into dst (asynchronously);
+// every thread commits its (possibly empty) group of copies.
+__device__ __forceinline__ void phase_prefetch(const int4* __restrict__ vis, int4* dst, int64_t k0, int64_t k_end,
+                                               int stage, int n_stages) {
+  if (threadIdx.x < GB_KV && stage < n_stages) {
+    const int64_t k = k0 + (int64_t)stage * GB_KV + threadIdx.x;
+    if (k < k_end) {
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + threadIdx.x);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(vis + k) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256, 6)
 k_phase_gen(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t k0, int64_t k_end,
             const float4* __restrict__ atoms, int n_atoms, int v_row, int rows_pad, int n_stages,
             const float* __restrict__ vscale, uint4* __restrict__ hi, uint4* __restrict__ lo) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= rows_pad) return;
+  __shared__ __align__(16) int4 s_vis[2][GB_KV];
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;   // < rows_pad (a multiple of 256)
   const float sc = V ? vscale[0] : 0.f;
   const bool is_atom = row < n_atoms, is_v = row == v_row;
   const float4 at = is_atom ? atoms[row] : make_float4(0.f, 0.f, 0.f, 0.f);
   const size_t row_item = (size_t)(row >> 3) * (GB_KG * 8) + (row & 7);
   const size_t stage_items = (size_t)rows_pad * GB_KG;
-  for (int stage = blockIdx.y; stage < n_stages; stage += gridDim.y) {
+  int b = 0;
+  phase_prefetch(vis, s_vis[0], k0, k_end, blockIdx.y, n_stages);
+  for (int stage = blockIdx.y; stage < n_stages; stage += gridDim.y, b ^= 1) {
+    phase_prefetch(vis, s_vis[b ^ 1], k0, k_end, stage + gridDim.y, n_stages);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this stage's copies landed
+    __syncthreads();
     const int64_t kbase = k0 + (int64_t)stage * GB_KV;
     const size_t base = (size_t)stage * stage_items + row_item;
 #pragma unroll
@@ -141,13 +162,14 @@ k_phase_gen(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
         float re[2], im[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const int64_t k = kbase + kg * 4 + v + s;
+          const int j = kg * 4 + v + s;
+          const int64_t k = kbase + j;
           re[s] = 0.f;
           im[s] = 0.f;
           if (k < k_end) {
             if (is_atom) {
               float sn, cs;
-              __sincosf(6.283185307179586f * phase_turns(vis[k], at), &sn, &cs);
+              __sincosf(6.283185307179586f * phase_turns(s_vis[b][j], at), &sn, &cs);
               re[s] = cs * at.w;
               im[s] = sn * at.w;
             } else if (is_v) {
@@ -165,7 +187,9 @@ k_phase_gen(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
       hi[item] = make_uint4(h[0], h[1], h[2], h[3]);
       lo[item] = make_uint4(l[0], l[1], l[2], l[3]);
     }
+    __syncthreads();   // every read of s_vis[b] ended before the next prefetch overwrites it
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ bulk-copy GEMM

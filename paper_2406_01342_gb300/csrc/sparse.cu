@@ -254,7 +254,8 @@ k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
     float inner[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) inner[r] = 0.f;
-    for (int t = half; t < cnt; t += 2) {
+    // columns past nB (the last CTA's unused threads) skip the phase work
+    for (int t = half; t < (c_glob < nB ? cnt : 0); t += 2) {
       float sn, cs;
       __sincosf(6.283185307179586f * phase_turns(sVis[t], bt), &sn, &cs);
       const float br = cs * bt.w, bi = sn * bt.w;
