@@ -326,9 +326,10 @@ __global__ void k_pix_tab(PixGeom g, const double* __restrict__ psi_uv,
     psiw = g.W * acc;
   }
   double ct = g.w0 * s;
-  ct -= rint(ct);
-  double sn, cs;
-  sincospi(2.0 * ct, &sn, &cs);
+  ct -= rint(ct);                    // exact reduction to [-1/2, 1/2] turns in FP64
+  float snf, csf;                    // then an FP32 sine / cosine (~1e-7): FP64 ones are slow here
+  sincospif(2.0f * (float)ct, &snf, &csf);
+  const double sn = snf, cs = csf;
   double d = 1.0 / (n * psi_uv[i] * psi_uv[j] * psiw);
   float t_hi = (float)t;
   float t_lo = (float)(t - (double)t_hi);
