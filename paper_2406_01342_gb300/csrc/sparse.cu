@@ -196,7 +196,7 @@ k_gram(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
 constexpr int THIN_RMAX = 16;     // rows (atoms + the V row) of the thin contraction
 constexpr int THIN_COLS = 128;    // columns (atoms) per CTA
 constexpr int THIN_CHUNK = 256;   // visibilities staged per chunk
-constexpr int THIN_SLICE = 1024;  // visibilities per CTA
+constexpr int THIN_SLICE_MAX = 4096;  // visibilities per CTA at most (the launcher picks the slice)
 
 // Thin contraction for a few rows: for row r < nA (an atom of atomsA) and
 // column c (an atom of atomsB)
@@ -211,7 +211,7 @@ template <int R>
 __global__ void __launch_bounds__(256)
 k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t M,
             const float4* __restrict__ atomsA, int nA, const float4* __restrict__ atomsB, int nB,
-            double* __restrict__ acc, int ldacc, double* __restrict__ b64) {
+            double* __restrict__ acc, int ldacc, double* __restrict__ b64, int slice) {
   __shared__ float sRe[R][THIN_CHUNK];
   __shared__ float sIm[R][THIN_CHUNK];
   __shared__ int4 sVis[THIN_CHUNK];
@@ -222,8 +222,8 @@ k_gram_thin(const int4* __restrict__ vis, const float2* __restrict__ V, int64_t 
   const int c_glob = blockIdx.x * THIN_COLS + col;
   const float4 bt = c_glob < nB ? atomsB[c_glob] : make_float4(0.f, 0.f, 0.f, 0.f);
   if (tid < R) sA[tid] = tid < nA ? atomsA[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const int64_t k_lo = (int64_t)blockIdx.y * THIN_SLICE;
-  const int64_t k_hi = min(M, k_lo + THIN_SLICE);
+  const int64_t k_lo = (int64_t)blockIdx.y * slice;
+  const int64_t k_hi = min(M, k_lo + slice);
   float outer[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) outer[r] = 0.f;
@@ -395,19 +395,32 @@ int launch_gram_thin(const int4* vis_fx, const float2* V, int64_t M, const float
   if (M <= 0 || nB <= 0 || (nA <= 0 && !V)) return PC_OK;
   if (nA + (V ? 1 : 0) > THIN_RMAX) return fail(PC_ERR_INVALID_ARG, "thin Gram: too many rows");
   prof_scope_.kernels = 1;
-  dim3 grid(ceil_div(nB, THIN_COLS), ceil_div(M, THIN_SLICE));
+  // visibilities per CTA: a multiple of the chunk, sized for about six CTAs
+  // per SM (the phase chains are latency-bound; each CTA adds its partial
+  // sums to the float64 accumulators once)
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 152;
+  }
+  const int gx = ceil_div(nB, THIN_COLS);
+  int64_t slice = ((int64_t)M * gx + (int64_t)n_sm * 6 - 1) / ((int64_t)n_sm * 6);
+  slice = std::min<int64_t>(THIN_SLICE_MAX, std::max<int64_t>(THIN_CHUNK, ceil_div(slice, THIN_CHUNK) * (int64_t)THIN_CHUNK));
+  dim3 grid(gx, ceil_div(M, slice));
+  const int sl = (int)slice;
   // rows padded to a power of two: the per-row loops are unrolled at that size
   const int rows = nA + (V ? 1 : 0);
   if (rows <= 1)
-    k_gram_thin<1><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+    k_gram_thin<1><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64, sl);
   else if (rows <= 2)
-    k_gram_thin<2><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+    k_gram_thin<2><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64, sl);
   else if (rows <= 4)
-    k_gram_thin<4><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+    k_gram_thin<4><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64, sl);
   else if (rows <= 8)
-    k_gram_thin<8><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+    k_gram_thin<8><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64, sl);
   else
-    k_gram_thin<16><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64);
+    k_gram_thin<16><<<grid, 256, 0, st>>>(vis_fx, V, M, atomsA, nA, atomsB, nB, acc, ldacc, b64, sl);
   PC_LAUNCH_CHECK();
   return PC_OK;
 }
