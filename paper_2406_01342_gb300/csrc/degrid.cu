@@ -194,13 +194,14 @@ k_degrid_rows_w(const float2* __restrict__ Xt, int N, const float2* __restrict__
 }
 
 constexpr int DG_T = 32;   // tile side (the plan's)
+constexpr int DG_TP = 33;  // padded tile row in shared memory: rows start on different banks
 
 template <int W>
 __global__ void __launch_bounds__(256)
 k_degrid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis, const float4* __restrict__ slot_geom,
          const float2* __restrict__ grid, int G, int nT, int P, int Qg, float beta, int wstack,
          float2* __restrict__ y) {
-  extern __shared__ float2 tile[];   // [Q][32][32]
+  extern __shared__ float2 tile[];   // [Q][32][33] (row padded)
   const int4 sub = subs[blockIdx.x];
   const int tu = sub.x % nT, tv = sub.x / nT;
   const int q0 = sub.y * Qg;
@@ -208,7 +209,7 @@ k_degrid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis, const
   for (int e = threadIdx.x; e < Q * DG_T * DG_T; e += blockDim.x) {
     const int q = e / (DG_T * DG_T), rem = e - q * DG_T * DG_T;
     const int bb = rem / DG_T, aa = rem - bb * DG_T;
-    tile[e] = grid[((size_t)(q0 + q) * G + tv * DG_T + bb) * G + tu * DG_T + aa];
+    tile[(q * DG_T + bb) * DG_TP + aa] = grid[((size_t)(q0 + q) * G + tv * DG_T + bb) * G + tu * DG_T + aa];
   }
   __syncthreads();
   const float two_over_w = 2.0f / W;
@@ -230,7 +231,7 @@ k_degrid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis, const
         if (cw < 0 || cw >= W) continue;
         fw = es_kernel((cw - gm.z) * two_over_w, beta);
       }
-      const float2* tq = tile + q * DG_T * DG_T;
+      const float2* tq = tile + q * DG_T * DG_TP;
       float pr = 0.f, pi = 0.f;
 #pragma unroll
       for (int jb = 0; jb < W; ++jb) {
@@ -241,7 +242,7 @@ k_degrid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis, const
         for (int ia = 0; ia < W; ++ia) {
           const int a = a0 + ia;
           if (a < 0 || a >= DG_T) continue;
-          const float2 g = tq[b * DG_T + a];
+          const float2 g = tq[b * DG_TP + a];
           rr = fmaf(fu[ia], g.x, rr);
           ri = fmaf(fu[ia], g.y, ri);
         }
@@ -334,13 +335,14 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
   }
   {
     if (p->T != DG_T || p->Qg > 8) return fail(PC_ERR_INVALID_ARG, "forward: needs 32-cell tiles, <= 8 planes");
-    const size_t smem = sizeof(float2) * (size_t)p->Qg * DG_T * DG_T;
+    const size_t smem = sizeof(float2) * (size_t)p->Qg * DG_T * DG_TP;
     const float beta = (float)p->beta;
 #define PC_DEGRID_CASE(WW)                                                                              \
   case WW: {                                                                                            \
     static bool attr = false;                                                                           \
     if (!attr) {                                                                                        \
-      PC_CUDA(cudaFuncSetAttribute(k_degrid<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024)); \
+      PC_CUDA(cudaFuncSetAttribute(k_degrid<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                   (int)(sizeof(float2) * 8 * DG_T * DG_TP)));                         \
       attr = true;                                                                                      \
     }                                                                                                   \
     k_degrid<WW><<<p->n_sub, 256, smem, st>>>(p->subs, p->slot_vis, p->slot_geom, p->grid, G, p->nT, p->P, \
