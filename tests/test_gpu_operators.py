@@ -76,13 +76,16 @@ def test_adjoint_grid(abi, name, kw, grid_mode):
 
 @pytest.mark.parametrize("name,kw", [("small_wide_w", {"N": 200}), ("small_wide_w", {"N": 256}),
                                      ("small_wide_w", {"N": 300}), ("diffuse_256", {}),
-                                     ("medium_512_w", {"M": 20_000})])
+                                     ("medium_512_w", {"M": 20_000}),
+                                     ("tiny_64_coplanar", {"N": 256}), ("tiny_64_coplanar", {"N": 512})])
 def test_fft_kernels(abi, name, kw):
     """The FFT passes of the adjoint on one warp per row in registers (the
     default at G = 512 and 1024) and on shared-memory Stockham stages
     (fft_kernel = 1): each meets the tolerance against the direct sum on the
     image's border rows and columns and on random pixels, and the two agree
-    on the whole image. N = 200 and 300 leave part of the kept band empty."""
+    on the whole image. N = 200 and 300 leave part of the kept band empty;
+    the coplanar cases (one plane, no w-screen) put eight image rows in each
+    CTA of the second pass."""
     wl, V = workload(name, **kw)
     Vd = to_dev(V.astype(np.complex64))
     pw, ps = _plan(abi, wl), _plan(abi, wl, fft_kernel=1)
@@ -118,7 +121,7 @@ def test_forward_grid(abi, name, kw):
 
 @pytest.mark.parametrize("fft_kernel", [0, 1])
 @pytest.mark.parametrize("name,kw", [("small_wide_w", {"N": 200}), ("small_wide_w", {"N": 300}),
-                                     ("diffuse_256", {})])
+                                     ("diffuse_256", {}), ("tiny_64_coplanar", {"N": 256})])
 def test_forward_grid_fft_kernels(abi, name, kw, fft_kernel):
     """Degridding with one-warp register FFTs (default at G = 512 and 1024)
     and with the Stockham passes (fft_kernel = 1), N = 200 and 300 leaving
