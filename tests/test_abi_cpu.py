@@ -32,3 +32,32 @@ def test_header_cites_the_paper_for_each_entry_point():
     src = open(os.path.join(ROOT, "include", "polyclean.h")).read()
     for needle in ("Sect. 2.2", "Sect. 4.2", "Sect. 5.3", "Algorithm 2"):
         assert needle in src
+
+
+def test_plan_create_rejects_bad_arguments_without_a_gpu():
+    """pc_plan_create checks every argument before its first CUDA call: each
+    bad value returns PC_ERR_INVALID_ARG with a message naming it (M = 0, so
+    no device pointer is needed; no GPU is touched)."""
+    import ctypes
+    import math
+
+    from paper_2406_01342_gb300 import abi
+    lib = abi.load()
+
+    def create(N=64, fov=math.radians(2.0), version=abi.PC_ABI_VERSION, **opt):
+        o = abi.pc_plan_opts(version, opt.get("kernel_width", 0), opt.get("tile", 0),
+                             opt.get("max_planes", 0), opt.get("grid_mode", 0), opt.get("autotune", 0),
+                             opt.get("fft_kernel", 0))
+        h = ctypes.c_void_p()
+        rc = lib.pc_plan_create(None, ctypes.c_int64(0), N, ctypes.c_double(fov), ctypes.byref(o), None,
+                                ctypes.byref(h))
+        return rc, lib.pc_last_error().decode()
+
+    cases = [(dict(version=abi.PC_ABI_VERSION - 1), "version"), (dict(N=63), "N ="), (dict(N=8), "N ="),
+             (dict(fov=0.0), "fov_rad"), (dict(fov=2.0), "fov_rad"), (dict(kernel_width=3), "kernel_width"),
+             (dict(kernel_width=9), "kernel_width"), (dict(tile=16), "tile"), (dict(max_planes=5000), "max_planes"),
+             (dict(grid_mode=3), "grid_mode"), (dict(autotune=2), "autotune"), (dict(fft_kernel=2), "fft_kernel")]
+    for kw, needle in cases:
+        rc, msg = create(**kw)
+        assert rc == abi.PC_ERR_INVALID_ARG, (kw, rc, msg)
+        assert needle in msg, (kw, msg)
