@@ -2,15 +2,20 @@
 """Benchmark of the PolyCLEAN hot path on one GB300 (or N independent replicas).
 
 One step = one full PolyCLEAN solve (Algorithm 2 to a 1e-4 relative objective
-improvement) of the 512 x 512, M = 200k w-stacked synthetic workload
-(40-station Earth-rotation layout, 50 log-normal point sources, 20 dB SNR,
-lambda = 0.1 lambda_max, delta = 0.01), with the plan built and V resident in
-HBM before the timed region. Prints one JSON line (rank 0).
+improvement) of the largest single-GPU workload: the fine-resolution
+4096 x 4096 grid with M = 10M w-stacked visibilities (100-station
+Earth-rotation layout, 500 log-normal point sources, 20 dB SNR, lambda = 0.1
+lambda_max, delta = 0.01), with the plan built and V resident in HBM before
+the timed region. Secondary objects time the 2048 x 2048 / M = 2M workload
+with its diffuse part and the 512 x 512 / M = 200k workload, the plain-FP32
+support contraction beside the split-FP16 tensor-core one, the coplanar
+gridding, the degridding operator, the serving stream and the synthesis
+dictionary. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
-project) on a bounded sample of the same workload.
+project) on a bounded sample of the same workload, over the host's cores.
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -29,10 +35,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PolyCLEAN solve time at 1e-4 rel. objective; gridding vis/s vs HBM roofline; p99"
 UNIT = "solves/s"
-WORKLOAD = "medium_512_w"
-# Frank-Wolfe iterations the GPU solve of this workload runs (measured); the
-# reference arm scales its per-certificate oracle time by this count.
-FW_CERTIFICATES = {"medium_512_w": None}
+WORKLOAD = "fine_4096_w"
+SECONDARY = ("large_2048_blobs", "medium_512_w")
+# Full-image certificates one GPU solve of each workload evaluates (its
+# Frank-Wolfe iterations, measured on the GPU): the oracle arms scale their
+# per-certificate time by this count, and the GPU arm reports whether its own
+# solve still matches it.
+FW_CERTIFICATES = {"fine_4096_w": None, "large_2048_blobs": None, "medium_512_w": 6}
 
 
 def parse():
@@ -44,6 +53,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the other configurations (2048^2 / 2M with blobs, 512^2 / 200k) and the "
+                         "coplanar gridding leg")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the serving-stream leg (64 requests, Poisson arrivals, p50/p99)")
     ap.add_argument("--no-diffuse", action="store_true",
@@ -158,7 +170,7 @@ def make_inputs(abi, synth, name, device, autotune=0):
     wl = synth.WORKLOADS[name]()
     uvw = torch.from_numpy(wl.uvw).to(device)
     plan = abi.pc_plan_create(uvw, wl.N, wl.fov, autotune=autotune)
-    Vc = abi.pc_forward_sparse(plan, torch.from_numpy(wl.sky_idx).to(device),
+    Vc = abi.pc_forward_sparse(plan, torch.from_numpy(wl.sky_idx.astype(np.int32)).to(device),
                                torch.from_numpy(wl.sky_flux.astype(np.float32)).to(device))
     p_sig = float((Vc.abs() ** 2).mean())
     noise = torch.from_numpy(wl.noise.astype(np.complex64)).to(device)
@@ -426,38 +438,100 @@ def diffuse_leg(abi, synth, torch, device, steps: int, l2_flush) -> dict:
 
 # ------------------------------------------------------------------ CPU oracle sample
 
-def oracle_sample_seconds(name: str, n_pix: int, seed: int = 0) -> tuple[float, int]:
-    """Time the FP64 oracle's direct-sum adjoint on n_pix seeded pixels of the
-    workload's certificate (one thread). Returns (seconds, n_pix)."""
-    code = (
-        "import sys, time, numpy as np; sys.path.insert(0, %r)\n"
-        "from oracle import operators\n"
-        "from paper_2406_01342_gb300 import synth\n"
-        "wl = synth.WORKLOADS[%r]()\n"
-        "V = operators.forward(wl.uvw, wl.N, wl.fov, wl.sky_idx, wl.sky_flux) + wl.noise\n"
-        "pix = np.sort(np.random.default_rng(%d).choice(wl.N * wl.N, %d, replace=False))\n"
-        "t = time.perf_counter(); operators.adjoint(wl.uvw, wl.N, wl.fov, V, pix); "
-        "print(time.perf_counter() - t)\n" % (ROOT, name, seed, n_pix))
+def host_cpu() -> dict:
+    """Cores this process may use and the CPU model string (lscpu, else /proc/cpuinfo)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cores": cores, "model": model or platform.machine()}
+
+
+_SAMPLE: dict = {}
+
+
+def _oracle_init(name: str) -> None:
+    from paper_2406_01342_gb300 import synth
+    wl = synth.WORKLOADS[name]()
+    _SAMPLE.update(uvw=wl.uvw, N=wl.N, fov=wl.fov, h=wl.noise)
+
+
+def _oracle_chunk(pix):
+    from oracle import operators
+    return operators.adjoint(_SAMPLE["uvw"], _SAMPLE["N"], _SAMPLE["fov"], _SAMPLE["h"], pix)
+
+
+def oracle_pool_sample(name: str, workers: int, target_s: float, seed: int) -> dict:
+    """The FP64 oracle's direct-sum adjoint (a certificate's dense part) on
+    seeded pixels of the workload, spread over `workers` spawned processes of
+    one thread each. The pixel count is sized from a first untimed round (one
+    pixel per worker) so the timed round takes about target_s. The input is
+    the workload's unit noise: a direct sum costs the same for any values."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from paper_2406_01342_gb300 import synth
+    wl = synth.WORKLOADS[name]()
+    rng = np.random.default_rng(seed)
+    with mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(name,)) as pool:
+        warm = np.sort(rng.choice(wl.N * wl.N, workers, replace=False))
+        t = time.perf_counter()
+        pool.map(_oracle_chunk, [warm[i:i + 1] for i in range(workers)])
+        per_pix = time.perf_counter() - t          # one pixel on every worker at once
+        per_worker = max(1, int(target_s / max(per_pix, 1e-3)))
+        n_pix = min(workers * per_worker, wl.N * wl.N)
+        pix = np.sort(rng.choice(wl.N * wl.N, n_pix, replace=False))
+        t = time.perf_counter()
+        pool.map(_oracle_chunk, np.array_split(pix, workers))
+        sec = time.perf_counter() - t
+    return {"seconds": sec, "n_pix": int(n_pix), "workers": workers, "N": wl.N, "M": wl.M}
+
+
+def oracle_solves_per_s(name: str, certificates: int, target_s: float = 15.0, seed: int = 0):
+    """Oracle solves/s on the host cores, extrapolated from the timed sample:
+    the sample's time per pixel x N^2 pixels x the certificates one solve
+    evaluates (the forward and sub-solver costs are left out, so this is an
+    upper bound on the oracle's rate). Runs in a child process with no GPU
+    visible. Returns (value, cpu_baseline dict)."""
+    cpu = host_cpu()
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_pool_sample(%r, %d, %r, %d)))"
+            % (ROOT, name, cpu["cores"], target_s, seed))
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=600)
+                         timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    return float(out.stdout.strip().splitlines()[-1]), n_pix
-
-
-def oracle_solves_per_s(name: str, n_pix: int, certificates: int, seed: int = 0):
-    from paper_2406_01342_gb300 import synth
-    wl = synth.WORKLOADS[name]()
-    sec, n = oracle_sample_seconds(name, n_pix, seed)
-    per_cert = sec * (wl.N * wl.N) / n
-    solve_s = per_cert * certificates
-    sample = (f"FP64 oracle direct-sum adjoint on {n} seeded pixels x all {wl.M} visibilities "
-              f"({sec:.2f} s, 1 thread), extrapolated to {wl.N}x{wl.N} pixels x {certificates} "
-              f"certificates per solve (forward and sub-solver costs not counted: an upper bound "
-              f"on oracle solves/s)")
-    return 1.0 / solve_s, sample
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    per_cert = r["seconds"] * r["N"] * r["N"] / r["n_pix"]
+    value = 1.0 / (per_cert * certificates)
+    sample = (f"FP64 oracle direct-sum adjoint on {r['n_pix']} seeded pixels x all {r['M']} visibilities "
+              f"in {r['seconds']:.1f} s over {r['workers']} one-thread processes ({cpu['model']}); "
+              f"EXTRAPOLATED to {r['N']}x{r['N']} pixels x {certificates} certificates per solve "
+              f"(the GPU solve's Frank-Wolfe iterations; forward and sub-solver costs not counted: "
+              f"an upper bound on oracle solves/s)")
+    return value, {"value": value, "unit": UNIT, "cores": r["workers"], "kind": "oracle",
+                   "cpu_model": cpu["model"], "nproc": cpu["cores"], "extrapolated": True,
+                   "certificates": certificates, "sample": sample}
 
 
 # ------------------------------------------------------------------ arms
@@ -465,22 +539,112 @@ def oracle_solves_per_s(name: str, n_pix: int, certificates: int, seed: int = 0)
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    certs = FW_CERTIFICATES.get(args.workload) or 12
+    certs = FW_CERTIFICATES.get(args.workload) or 8
     vals = []
-    sample = ""
+    base = None
     for i in range(args.warmup + args.steps):
-        v, sample = oracle_solves_per_s(args.workload, 256, certs, seed=i)
+        v, base = oracle_solves_per_s(args.workload, certs, target_s=10.0, seed=i)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
+    base = dict(base, value=value)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
-                             "unit": UNIT},
+            "data": "synthetic", "config": {"workload": args.workload, "certificates_per_solve": certs},
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def timed_solves(abi, torch, plan, V, lam, delta, n, l2_flush, **opts):
+    """n solves, each bracketed by CUDA events on the launching stream, L2
+    flushed before each; returns (per-solve ms, last result)."""
+    stream = torch.cuda.current_stream()
+    ms, res = [], None
+    for _ in range(n):
+        flush_l2(l2_flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = abi.pc_solve(plan, V, lam, delta, want_mu=True, history=256, **opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms, res
+
+
+def precision_pair(abi, torch, plan, V, lam, delta, n, l2_flush, mixed_ms, mixed_res) -> dict:
+    """The same solve with the support contraction on FP32 CUDA cores
+    (gram_mode 1, the plain path) beside the default split-FP16 tensor-core
+    form: solve times and whether both reach the same support and objective."""
+    abi.pc_solve(plan, V, lam, delta, want_mu=False, gram_mode=1)
+    ms, res = timed_solves(abi, torch, plan, V, lam, delta, n, l2_flush, gram_mode=1)
+    same = res["idx"].cpu().tolist() == mixed_res["idx"].cpu().tolist()
+    dF = abs(res["objective"] - mixed_res["objective"]) / mixed_res["objective"]
+    return {"mixed_split_fp16_tensor": {"solve_time_s": statistics.median(mixed_ms) / 1e3,
+                                        "objective": mixed_res["objective"],
+                                        "support": int(mixed_res["idx"].numel()),
+                                        "iterations": mixed_res["iterations"]},
+            "plain_fp32": {"solve_time_s": statistics.median(ms) / 1e3, "objective": res["objective"],
+                           "support": int(res["idx"].numel()), "iterations": res["iterations"]},
+            "same_support": same, "objective_rel_diff": dF,
+            "mixed_speedup": statistics.median(ms) / statistics.median(mixed_ms)}
+
+
+def secondary_leg(abi, synth, torch, device, name, steps, l2_flush, peaks) -> dict:
+    """Another configuration: plan and V resident, warm-up solves, a per-class
+    breakdown pass, then timed solves (median), the dominant kernel's
+    roofline and the plain-FP32 contraction beside the default."""
+    wl, _, plan, V = make_inputs(abi, synth, name, device)
+    info = abi.pc_plan_info(plan)
+    lam = wl.alpha * abi.pc_lambda_max(plan, V)
+    for _ in range(2):
+        abi.pc_solve(plan, V, lam, wl.delta, want_mu=False)
+    abi.pc_profile_begin()
+    res = abi.pc_solve(plan, V, lam, wl.delta, want_mu=True, history=256)
+    prof = abi.pc_profile_end()
+    ms, res = timed_solves(abi, torch, plan, V, lam, wl.delta, steps, l2_flush)
+    dom = max(prof, key=lambda c: prof[c][2])
+    rl = roofline(prof, info, wl, res["history"], 1, peaks, dom)
+    out = {"workload": f"{name}: {wl.N}x{wl.N} image, M={wl.M} visibilities, {info['n_planes']} w-planes, "
+                       f"{wl.sky_idx.size} sky pixels, lambda={wl.alpha} lambda_max, delta={wl.delta}",
+           "solve_time_s": statistics.median(ms) / 1e3, "solves_per_s": 1e3 / statistics.median(ms),
+           "steps": steps, "iterations": res["iterations"], "support": int(res["idx"].numel()),
+           "objective": res["objective"], "converged": res["converged"],
+           "kernels_ms": {k: round(v[2], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
+           "roofline": {k: rl[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac")},
+           "gridding_roofline": gridding_roofline(prof, info, wl, peaks)}
+    out["precision"] = precision_pair(abi, torch, plan, V, lam, wl.delta, max(3, steps // 2), l2_flush, ms, res)
+    return out
+
+
+def coplanar_gridding_leg(abi, synth, torch, device, names, l2_flush, peaks, reps: int = 10) -> dict:
+    """Gridding on the w = 0 path, where the gridding roofline target is
+    judged: the uv tracks of the named workloads with w set to zero (one grid
+    plane, CUDA-core gridding), timed as the gridding class (grid clear +
+    spread) of repeated adjoint calls, L2 flushed before each."""
+    import numpy as np
+    out = {}
+    for name in names:
+        wl = synth.WORKLOADS[name]()
+        uvw = wl.uvw.copy()
+        uvw[:, 2] = 0.0
+        plan = abi.pc_plan_create(torch.from_numpy(uvw).to(device), wl.N, wl.fov)
+        info = abi.pc_plan_info(plan)
+        h = torch.from_numpy(wl.noise.astype(np.complex64)).to(device)
+        for _ in range(3):
+            abi.pc_adjoint_grid(plan, h)
+        torch.cuda.synchronize()
+        abi.pc_profile_begin("grid")
+        for _ in range(reps):
+            flush_l2(l2_flush)
+            abi.pc_adjoint_grid(plan, h)
+        prof = abi.pc_profile_end()
+        torch.cuda.synchronize()
+        out[name + "_coplanar"] = dict(gridding_roofline(prof, info, wl, peaks), n_planes=info["n_planes"],
+                                       grid_side=info["grid_side"], M=wl.M)
+        del plan
+    return out
 
 
 def run_ours(args, world, rank, local):
@@ -550,6 +714,16 @@ def run_ours(args, world, rank, local):
     vis_per_s = wl.M / (grid_ms * 1e-3) if grid_ms == grid_ms else None
     gpu_launches = sum(v[1] for v in prof.values())
 
+    # the secondary legs report an error in their object instead of ending the run
+    def leg(fn, *a):
+        try:
+            return fn(*a)
+        except Exception as e:   # noqa: BLE001 -- recorded in the JSON line
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    precision = leg(precision_pair, abi, torch, plan, V, lam, wl.delta, max(3, args.steps), l2_flush,
+                    step_ms, res) if rank == 0 else None
+
     # end to end through the C ABI on host buffers (plan + lambda_max + solve + copies)
     e2e = None
     if not args.no_e2e:
@@ -571,15 +745,19 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(wl.M * (24 + 8)),
                "d2h_bytes_per_step": int(n_sup * 8 + 64)}
 
-    # the secondary legs report an error in their object instead of ending the run
-    def leg(fn, *a):
-        try:
-            return fn(*a)
-        except Exception as e:   # noqa: BLE001 -- recorded in the JSON line
-            return {"error": f"{type(e).__name__}: {e}"}
-
     degrid = leg(degridding_leg, abi, torch, plan, wl, info, peaks, args.steps, l2_flush) if rank == 0 else None
+    del plan, V, uvw
+    abi.pc_trim_memory()
 
+    configs = None
+    coplanar = None
+    if rank == 0 and not args.no_secondary:
+        configs = {n: leg(secondary_leg, abi, synth, torch, device, n, args.steps, l2_flush, peaks)
+                   for n in SECONDARY if n != args.workload}
+        abi.pc_trim_memory()
+        coplanar = leg(coplanar_gridding_leg, abi, synth, torch, device, ("medium_512_w", args.workload),
+                       l2_flush, peaks)
+        abi.pc_trim_memory()
     serving = None
     if rank == 0 and not args.no_serving:
         serving = leg(serving_leg, abi, synth, torch, device)
@@ -587,13 +765,13 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_diffuse:
         diffuse = leg(diffuse_leg, abi, synth, torch, device, args.steps, l2_flush)
 
+    certs = res["iterations"]
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            v, sample = oracle_solves_per_s(args.workload, 1024, res["iterations"] + 2)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            _, cpu = oracle_solves_per_s(args.workload, certs, target_s=15.0)
         except Exception as e:  # the oracle leg never hides the GPU result
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": None, "unit": UNIT, "cores": host_cpu()["cores"], "kind": "oracle",
                    "sample": f"failed: {e}"[:300]}
 
     if rank == 0:
@@ -604,14 +782,18 @@ def run_ours(args, world, rank, local):
             "config": {"workload": f"{args.workload}: {wl.N}x{wl.N} image, M={wl.M} visibilities, "
                                    f"{info['n_planes']} w-planes, {wl.sky_idx.size} point sources, "
                                    f"lambda={wl.alpha} lambda_max, delta={wl.delta}",
-                       "l2": "flushed between timed steps (256 MB write)",
+                       "l2": "flushed between timed steps (256 MB write); the inputs are larger than L2",
                        "plan_tuning": tuning,
+                       "certificates_per_solve": certs,
+                       "same_certificates_as_reference_arm": FW_CERTIFICATES.get(args.workload) == certs,
                        "parallelism": f"replicas x{world}"},
             "solve_time_s": total_ms / args.steps / 1e3,
             "solve": {"iterations": res["iterations"], "support": int(res["idx"].numel()),
                       "objective": res["objective"], "converged": res["converged"]},
+            "precision": precision,
             "gridding_vis_per_s": vis_per_s,
             "gridding_roofline": gridding_roofline(prof_timed, info, wl, peaks),
+            "gridding_coplanar": coplanar,
             "phase_gen_roofline": ({k: v for k, v in roofline(prof_timed, info, wl, res["history"], args.steps,
                                                                 peaks, "phase_gen").items() if k != "traffic"}
                                    if "phase_gen" in prof_timed else None),
@@ -621,7 +803,8 @@ def run_ours(args, world, rank, local):
             "roofline_kernel": {k: rl[k] for k in ("kernel", "avg_launch_ms", "launches")},
             "peaks_source": "MEASURED_PEAKS.json (measured)" if "_fallback" not in peaks else "fallback",
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
-            "cpu_baseline": cpu, "serving": serving, "diffuse": diffuse, "wall_s": t_wall,
+            "cpu_baseline": cpu, "configs": configs, "serving": serving, "diffuse": diffuse,
+            "wall_s": t_wall,
         }
         print(json.dumps(line), flush=True)
 

@@ -328,14 +328,19 @@ int pc_solve_synthesis(pc_plan_t plan, const pc_dictionary* dict, const pc_c32* 
  * path). The caller passes every input and output; the only scratch is a
  * file-scope __device__ array of PC_NOALLOC_MAX_PIXELS float64 accumulators
  * (64 KB per device that loads the library, held until the process exits).
- * The call never allocates or frees device memory. S > PC_NOALLOC_MAX_PIXELS
- * is rejected with PC_ERR_INVALID_ARG. An index outside [0, N*N) gives NaN
- * in its output slot (no ordering is required). All calls share the scratch
- * array and each clears the part it uses: calls whose kernels overlap on
- * the GPU race on it and must be serialised. The first call on a device
- * looks up the array's address (cudaGetSymbolAddress, that device current);
- * make that first call before any stream capture. */
+ * The call never allocates or frees device memory once the library's module
+ * is resident on the device. S > PC_NOALLOC_MAX_PIXELS or M >
+ * PC_NOALLOC_MAX_VIS is rejected with PC_ERR_INVALID_ARG. An index outside
+ * [0, N*N) gives NaN in its output slot (no ordering is required). All
+ * calls share the scratch array and each clears the part it uses: calls
+ * whose kernels overlap on the GPU race on it and must be serialised. The
+ * first call on a device looks up the array's address (cudaGetSymbolAddress,
+ * that device current); under lazy module loading, the CUDA default, that
+ * first call also loads the kernels and the 64 KB array, which takes device
+ * memory then. Make the first call at start-up, before an arena or budget
+ * takes the device's memory and before any stream capture. */
 #define PC_NOALLOC_MAX_PIXELS 8192
+#define PC_NOALLOC_MAX_VIS (65535LL * 8192LL)
 int pc_adjoint_sparse_noalloc(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
                               const pc_c32* y_dev, const int32_t* idx_dev, int32_t S,
                               float* out_dev, void* stream);

@@ -113,7 +113,8 @@ def frank_wolfe(V, lam, eta_all, columns, lmax, delta=0.01, rule="R2", tol=1e-4,
         # lies within 1e-5 max|mu| of the threshold, where an FP32 evaluation of
         # the certificate may legitimately take the other side
         cand = eta / lam if positive else np.abs(eta) / lam
-        n_border = int(np.count_nonzero(np.abs(cand - thr_mu) <= 1e-5 * np.abs(eta).max() / lam))
+        border = np.nonzero(np.abs(cand - thr_mu) <= 1e-5 * np.abs(eta).max() / lam)[0]
+        n_border = int(border.size)
         n_new = int(np.setdiff1d(new, S).size)
         S_next = np.union1d(S, new).astype(np.int64)            # sorted, unique
         x0 = np.zeros(S_next.size)
@@ -132,7 +133,8 @@ def frank_wolfe(V, lam, eta_all, columns, lmax, delta=0.01, rule="R2", tol=1e-4,
                             mu_inf=float(np.max(eta if positive else np.abs(eta)) / lam),
                             objective=F,
                             rel_improvement=rel, apgd_iterations=int(n_it), L=float(L),
-                            eps=eps, n_borderline=n_border))
+                            eps=eps, n_borderline=n_border,
+                            active=S_next.copy(), support=S.copy(), borderline=border))
         F_prev = F
         if rel < tol:
             converged = True

@@ -15,8 +15,12 @@
 // array, so calls whose kernels overlap on the GPU (different streams, or
 // different host threads) race on it and give wrong results: serialise them.
 // The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current); make that first call
-// before any stream capture begins.
+// cudaGetSymbolAddress (with that device current); under lazy module loading
+// (the CUDA default) that first call also loads this file's kernels and the
+// array itself, which takes device memory at that moment. So make the first
+// call at start-up, before an arena or a memory budget takes the device's
+// memory, and before any stream capture begins; later calls allocate nothing.
+// At most 65535 x 8192 visibilities (the launch's y dimension) per call.
 #include <mutex>
 
 #include "pc_internal.cuh"
@@ -32,6 +36,8 @@ static __device__ __align__(256) double g_noalloc_acc[kNoAllocMaxPixels];
 constexpr int NA_PIX = 128;        // pixels per CTA
 constexpr int NA_CHUNK = 256;      // visibilities staged per shared-memory chunk
 constexpr int NA_SLICE = 8192;     // visibilities per CTA (one float64 flush per slice)
+// The slices are the launch's y dimension (at most 65535 blocks).
+constexpr int64_t kNoAllocMaxVis = 65535ll * NA_SLICE;
 
 // acc[s] += sum_k Re(y_k e^{+j 2 pi theta_ks}) / n_s over one slice of visibilities,
 // phases formed exactly as in the plan-based path (32-bit fixed-point lattice
@@ -54,8 +60,8 @@ k_adjoint_sparse_noalloc(const double* __restrict__ uvw, int64_t M, int N, doubl
       const double l = ip * dl, m = jp * dl, r2 = l * l + m * m;
       const double n = sqrt(1.0 - r2), sv = -r2 / (1.0 + n);
       const float s_hi = (float)sv;
-      at = make_float4(__int_as_float((ip << 16) | (jp & 0xffff)), s_hi, (float)(sv - (double)s_hi),
-                       (float)(1.0 / n));
+      const int packed = (int)(((unsigned)ip << 16) | ((unsigned)jp & 0xffffu));
+      at = make_float4(__int_as_float(packed), s_hi, (float)(sv - (double)s_hi), (float)(1.0 / n));
     }
     s_atom[t] = at;
   }
@@ -143,6 +149,10 @@ extern "C" int pc_adjoint_sparse_noalloc(const double* uvw_dev, int64_t M, int32
                 S, kNoAllocMaxPixels);
   if (M < 0 || N < 2 || N > 4096 || (N & 1) || !(fov_rad > 0.0) || !(fov_rad < 1.4))
     return fail(PC_ERR_INVALID_ARG, "pc_adjoint_sparse_noalloc: bad geometry (M, N, fov)");
+  if (M > kNoAllocMaxVis)
+    return fail(PC_ERR_INVALID_ARG,
+                "pc_adjoint_sparse_noalloc: M = %lld visibilities, the allocation-free path takes at most %lld",
+                (long long)M, (long long)kNoAllocMaxVis);
   if (S == 0) return PC_OK;
   if (!is_device_ptr(idx_dev) || !is_device_ptr(out_dev) ||
       (M > 0 && (!is_device_ptr(uvw_dev) || !is_device_ptr(y_dev))))

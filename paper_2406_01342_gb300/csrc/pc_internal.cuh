@@ -171,7 +171,7 @@ __device__ __forceinline__ float4 make_atom(int p, float x, bool weighted, int N
   const float s_hi = (float)sv;
   const float s_lo = (float)(sv - (double)s_hi);
   const double w = weighted ? (double)x : 1.0;
-  const int packed = (ip << 16) | (jp & 0xffff);
+  const int packed = (int)(((unsigned)ip << 16) | ((unsigned)jp & 0xffffu));
   return make_float4(__int_as_float(packed), s_hi, s_lo, (float)(w / n));
 }
 

@@ -292,7 +292,7 @@ __global__ void k_slot_gather(const double* __restrict__ uvw, const unsigned* __
     double tt = (w - g.w0) * g.s_c;     // pre-twiddle e^{j 2 pi (w - w0) s_c}, in turns
     tau = (float)(tt - rint(tt));
   }
-  slot_vis[j] = make_int2((int)k, (a0l + 64) | ((b0l + 64) << 8) | (ps << 16));
+  slot_vis[j] = make_int2((int)k, (int)((unsigned)(a0l + 64) | ((unsigned)(b0l + 64) << 8) | ((unsigned)ps << 16)));
   slot_geom[j] = make_float4((float)(gu - a0), (float)(gv - b0), xw, tau);
 }
 

@@ -321,6 +321,7 @@ WORKLOADS = {
     "tiny_64_coplanar": tiny_coplanar,
     "medium_512_w": medium_512,
     "large_2048_w": large_2048,
+    "large_2048_blobs": lambda: large_2048(blobs=True),
     "fine_4096_w": fine_4096,
     "small_wide_w": small_wide_field,
     "diffuse_256": diffuse_256,

@@ -75,3 +75,15 @@ def test_traffic_record_needs_the_profiled_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("gram_tc") is None
     os.remove(src)
     assert bench.recorded_traffic("gram_tc") is None
+
+
+def test_cpu_baseline_runs_the_oracle_over_the_host_cores():
+    """The CPU baseline leg: spawned one-thread oracle processes on every core
+    this process may use, the CPU model named, the extrapolation labelled."""
+    value, base = bench.oracle_solves_per_s("tiny_64_coplanar", 4, target_s=0.3)
+    info = bench.host_cpu()
+    assert value > 0 and base["value"] == value
+    assert base["cores"] == info["cores"] >= 1 and base["nproc"] == info["cores"]
+    assert isinstance(base["cpu_model"], str) and base["cpu_model"]
+    assert base["extrapolated"] is True and "EXTRAPOLATED" in base["sample"]
+    assert base["certificates"] == 4 and base["kind"] == "oracle"

@@ -85,3 +85,59 @@ def test_full_size_solve_invariants(abi, name):
     assert np.all(np.sign(mu[idx]) == np.sign(x))
     bright = wl.sky_idx[np.argsort(wl.sky_flux)[-10:]]
     assert np.isin(bright, idx).all()
+
+
+def clustered_atoms(N: int, S: int, rng, n_clusters: int = 8) -> np.ndarray:
+    """S distinct pixels in n_clusters square blocks around random centres (the
+    shape of a Frank-Wolfe active set, which gathers around bright sources, so
+    neighbouring atoms give Gram entries close to the diagonal), sorted."""
+    side = int(np.ceil(np.sqrt(S / n_clusters))) + 1
+    out = set()
+    while len(out) < S:
+        ci, cj = rng.integers(side, N - side, 2)
+        for di in range(side):
+            for dj in range(side):
+                if len(out) < S:
+                    out.add(int((ci + di) * N + cj + dj))
+    return np.array(sorted(out), dtype=np.int32)
+
+
+def gram_errors(wl, G, b, V, idx, sub):
+    """Errors of the Gram entries G[sub][sub] and of b[sub] against the FP64
+    oracle's columns (operators.phase_block), each normalised by its
+    Cauchy-Schwarz bound: |dG_ij| / sqrt(G_ii G_jj) and |db_i| / (sqrt(G_ii) ||V||)."""
+    l, m, n = operators.pixel_lmn(wl.N, wl.fov, idx[sub])
+    A = np.empty((wl.M, sub.size), dtype=np.complex128)
+    for c in range(sub.size):          # one column at a time keeps the temporaries small
+        A[:, c] = operators.phase_block(wl.uvw, l[c:c + 1], m[c:c + 1], n[c:c + 1])[:, 0]
+    Gref = np.real(A.conj().T @ A)
+    bref = np.real(A.conj().T @ V.astype(np.complex128))
+    d = np.sqrt(np.diag(Gref))
+    eG = np.abs(G[np.ix_(sub, sub)] - Gref) / np.outer(d, d)
+    eb = np.abs(b[sub] - bref) / (d * np.linalg.norm(V))
+    return float(eG.max()), float(eb.max())
+
+
+@pytest.mark.parametrize("name,S", [("medium_512_w", 873), ("large_2048_w", 512), ("fine_4096_w", 512)])
+def test_tensor_core_gram_sampled_at_full_size(abi, name, S):
+    """The split-FP16 tensor-core contraction (pc_gram mode 2) at the
+    visibility counts the solves use (M = 200k with 873 atoms, the first Gram of
+    the benchmark's solve; M = 2M and 10M with 512): 16 seeded atoms (two
+    clusters' worth of neighbours among them), all their 136 distinct G entries
+    and their b entries against the FP64 oracle, within 1e-5 of each entry's
+    Cauchy-Schwarz bound. The accumulation drift of the tensor core grows with
+    the number of MMA adds, which these sizes exercise (8192-visibility slices
+    of 256-visibility sub-slices, phase-buffer chunks at 10M)."""
+    wl = synth.WORKLOADS[name]()
+    rng = np.random.default_rng(47)
+    idx = clustered_atoms(wl.N, S, rng)
+    V = synth.unit_complex_noise(wl.M, rng).astype(np.complex64)
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    G, b = abi.pc_gram(plan, to_dev(V), to_dev(idx), mode=2)
+    G = G.cpu().numpy().astype(np.float64)
+    b = b.cpu().numpy().astype(np.float64)
+    assert np.array_equal(G, G.T)
+    sub = np.sort(np.concatenate([np.arange(8), rng.choice(np.arange(8, S), 8, replace=False)]))
+    eG, eb = gram_errors(wl, G, b, V, idx, sub)
+    assert eG <= 1e-5, eG
+    assert eb <= 1e-5, eb
