@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PC_ABI_VERSION 3
+#define PC_ABI_VERSION 4
 
 typedef enum {
   PC_OK = 0,
@@ -105,6 +105,13 @@ typedef struct {
   double  eps_min;        /* (default 1e-5)                                                           */
   double  lambda_max;     /* for rule 1: lambda_max if known (<= 0: computed; under positivity the
                              positive lambda_max of pc_lambda_max_positive)                          */
+  int32_t reweight;       /* form of the reweighting (step 2 of Algorithm 2): 0 (default) per
+                             Frank-Wolfe iteration the cheaper of the Gram form (G_S, b_S contracted,
+                             then APGD on them) and the operator form (APGD whose gradient
+                             Re Phi_S^H (Phi_S x - V) is evaluated by degridding and gridding every
+                             iteration, Sect. 5.1); 1: always the Gram form; 2: always the operator
+                             form (same iterations, step size and stop rule)                          */
+  int32_t reserved;
 } pc_solve_opts;
 
 /* Per-iteration record of pc_solve (host memory). */
@@ -145,6 +152,11 @@ typedef struct {
  * M may be 0 (all operators then return zeros). */
 int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
                    const pc_plan_opts* opts, void* stream, pc_plan_t* plan_out);
+/* The same call under the short name of the problem statement (plan of the
+ * measurement operator for uvw, M, N_pix, fov): identical arguments and
+ * behaviour. */
+int pc_plan(const double* uvw_dev, int64_t M, int32_t N, double fov_rad, const pc_plan_opts* opts,
+            void* stream, pc_plan_t* plan_out);
 void pc_plan_destroy(pc_plan_t plan);
 
 /* Plan geometry: oversampled grid side, tile side, number of w-planes, number
@@ -210,10 +222,12 @@ int pc_select(pc_plan_t plan, const float* mu_dev, float thr, const int32_t* pre
 
 /* Support contraction (step 2 of Algorithm 2, in Gram form): for the S atoms
  * idx, G = Re(Phi_S^H Phi_S) (S x S, row-major, leading dimension ldg) and
- * b = Re(Phi_S^H V) (S; skipped when V_dev is NULL). The phase matrix is
- * generated tile by tile and never stored. mode 1: FP32 CUDA-core products;
- * mode 2: tcgen05 tensor cores on split-FP16 (hi + lo) operands with FP32
- * accumulation (hi*hi + hi*lo + lo*hi); mode 0: tensor cores when S*S >= 4096.
+ * b = Re(Phi_S^H V) (S; skipped when V_dev is NULL). mode 1: FP32 CUDA-core
+ * products, phases generated per tile in shared memory; mode 2: tcgen05
+ * tensor cores on split-FP16 (hi + lo) operands with FP32 accumulation
+ * (hi*hi + hi*lo + lo*hi), the phases of each chunk of visibilities (at most
+ * ~2 GB of FP16 pairs) written once to a plan-owned buffer in HBM and streamed
+ * into the MMA pipeline from L2; mode 0: tensor cores when S*S >= 4096.
  * Both accumulate K-slices in float64. PC_ERR_TIMEOUT if a bounded
  * tensor-core wait expired. mode 3 is a self-test of that path: the tensor-core
  * kernel withholds its MMAs, its first buffer wait expires after about 2 s and

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-PC_ABI_VERSION = 3
+PC_ABI_VERSION = 4
 PC_OK = 0
 PC_ERR_INVALID_ARG = -1
 PC_ERR_OOM = -2
@@ -26,7 +26,7 @@ PC_ERR_CAPACITY = -7
 
 # Every function the header declares (checked by the CPU test-suite).
 EXPORTS = [
-    "pc_plan_create", "pc_plan_destroy", "pc_plan_info", "pc_forward_sparse",
+    "pc_plan_create", "pc_plan", "pc_plan_destroy", "pc_plan_info", "pc_forward_sparse",
     "pc_adjoint_sparse", "pc_adjoint_grid", "pc_lambda_max", "pc_certificate", "pc_select",
     "pc_gram", "pc_apgd", "pc_solve", "pc_solve_host", "pc_profile_begin", "pc_profile_end",
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
@@ -73,7 +73,8 @@ class pc_solve_opts(ctypes.Structure):
                 ("max_fw", ctypes.c_int32), ("apgd_max_iter", ctypes.c_int32),
                 ("gram_mode", ctypes.c_int32), ("positivity", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eps0", ctypes.c_double),
-                ("eps_min", ctypes.c_double), ("lambda_max", ctypes.c_double)]
+                ("eps_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("reweight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 PC_DICT_MAX_SCALES = 8
@@ -141,6 +142,7 @@ def load(path: str | None = None):
     lib = ctypes.CDLL(path)
     sig = {
         "pc_plan_create": (_I32, [_P, _I64, _I32, _D, _P, _P, ctypes.POINTER(_P)]),
+        "pc_plan": (_I32, [_P, _I64, _I32, _D, _P, _P, ctypes.POINTER(_P)]),
         "pc_plan_destroy": (None, [_P]),
         "pc_plan_tuning_info": (_I32, [_P, ctypes.POINTER(pc_plan_tuning)]),
         "pc_plan_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
@@ -359,9 +361,9 @@ def pc_apgd(G: torch.Tensor, b: torch.Tensor, lam: float, eps: float, max_iter: 
 
 
 def _solve_opts(select_rule=0, max_fw=0, apgd_max_iter=0, tol=0.0, eps0=0.0, eps_min=0.0,
-                lambda_max=0.0, gram_mode=0, positivity=0):
+                lambda_max=0.0, gram_mode=0, positivity=0, reweight=0):
     return pc_solve_opts(PC_ABI_VERSION, select_rule, max_fw, apgd_max_iter, gram_mode,
-                         int(positivity), tol, eps0, eps_min, lambda_max)
+                         int(positivity), tol, eps0, eps_min, lambda_max, int(reweight), 0)
 
 
 def pc_solve(plan: Plan, V: torch.Tensor, lam: float, delta: float, cap: int = 65536,

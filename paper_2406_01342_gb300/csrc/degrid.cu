@@ -273,9 +273,13 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
   prof_scope_.kernels = 1;
   if (p->n_sub == 0 || p->n_active_rows == 0) return PC_OK;
   const int N = p->N, G = p->G, n_act = p->n_active_rows;
+  const int ws = p->wstack ? 1 : 0;
+  if (fft_big_size(G) && p->fft_warp != 0) {
+    // one-CTA transforms (fft_big.cu) for G = 2048 .. 8192
+    PC_TRY(launch_degrid_ffts_big(p, img, st));
+  } else {
   PC_TRY(p->degrid_buf.ensure(sizeof(float2) * (size_t)p->P * n_act * N));
   float2* Xt = p->degrid_buf.as<float2>();
-  const int ws = p->wstack ? 1 : 0;
   if (fft_cols_warp(p)) {
     // one-warp FFTs for both passes (the plan's choice for its second FFT pass)
     const int L = G / 32;
@@ -331,6 +335,7 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
     dim3 grid(ceil_div(n_act, R), p->P);
     k_degrid_rows<<<grid, 256, smem, st>>>(Xt, N, G, p->logG, R, p->twiddle, p->active_rows, n_act, p->grid);
     PC_LAUNCH_CHECK();
+  }
   }
   }
   {

@@ -327,6 +327,10 @@ bool fft_cols_warp(const pc_plan_s* p) {
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_ROWS, st);
   if (p->n_active_rows == 0) return PC_OK;     // all-zero grid: the output stays zero
+  if (fft_rows_big(p)) {
+    prof_scope_.kernels = 1;
+    return launch_fft_rows_big(p, st);
+  }
   if (fft_rows_warp(p)) {
     const size_t smem = warp_fft_smem(p->G);
     dim3 grid(p->n_active_rows / 8, p->P);
@@ -375,6 +379,14 @@ int cols_planes_per_pass(const pc_plan_s* p) {
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st) {
   ProfScope prof_scope_(PROF_FFT_COLS, st);
+  if (fft_cols_big(p)) {
+    if (p->n_active_rows == 0) {                // nothing reaches the grid: mu = 0
+      PC_CUDA(cudaMemsetAsync(mu, 0, sizeof(float) * (size_t)p->N * p->N, st));
+      return PC_OK;
+    }
+    prof_scope_.kernels = 1;
+    return launch_fft_cols_big(p, mu, scale, maxbits, st);
+  }
   if (fft_cols_warp(p)) {
     int wpr = 8;                                   // warps per image row: a power of 2 <= P
     while (wpr > p->P) wpr >>= 1;

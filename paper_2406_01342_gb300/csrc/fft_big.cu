@@ -1,0 +1,329 @@
+// FFT passes of the certificate (adjoint) and of the degridding forward
+// operator for grids of side G = 2048, 4096 and 8192, one CTA per row
+// (fft_cta.cuh), with the pass-1 output kept only at the grid rows b that a
+// visibility can reach.
+//
+// Compact pass-1 storage. The c-th reachable row (c < n_rows, ascending b)
+// of plane q holds N image-domain values i, stored in blocks of four rows:
+//
+//   Xc[((q * nb + c / 4) * N + i) * 4 + c % 4],   nb = ceil(n_rows / 4).
+//
+// A CTA that owns one row c writes every fourth 8-byte word (the three
+// sibling rows, owned by the CTAs launched next to it, fill the rest of
+// each 32-byte sector in L2); a CTA that owns one image row i reads its
+// n_rows values as whole 32-byte sectors. At 4096^2 with 23 w-planes this is
+// ~1.4k of 8192 rows: the pass-2 input shrinks six-fold against full rows.
+//
+// Certificate (the adjoint of Sect. 2.2 via the NUFFT of Sect. 5.2):
+//   k_fft_rows_big   per (reachable row b, plane q): inverse FFT along a of
+//                    grid_q[b][.] (only the 32-column groups that can hold
+//                    data are read), the N kept outputs -> Xc;
+//   k_fft_cols_big   per image row i: for every plane an inverse FFT along b
+//                    of the compact row, the plane phase e^{+2 pi i q t_ij},
+//                    summed in registers; then the per-pixel correction, mu
+//                    and its maxima (as k_fft_cols).
+// Degridding (the exact adjoint of the above, in reverse order, with the
+// forward FFTs as conj(IFFT(conj(.))), as degrid.cu):
+//   k_degrid_cols_big  per image row i: for every plane c_ij e^{+2 pi i q t_ij}
+//                      x_ij centred on a length-G row, inverse FFT along j,
+//                      conjugated outputs at the reachable rows b -> Xc;
+//   k_degrid_rows_big  per (reachable row, plane): the N values of Xc centred
+//                      on a length-G row, inverse FFT along i, conjugated ->
+//                      grid_q[b][.] in the column groups that hold data.
+#include "fft_cta.cuh"
+
+namespace pc {
+namespace {
+
+__device__ __forceinline__ bool group_on(const uint32_t* __restrict__ colw, int n) {
+  const int g = n >> 5;
+  return (__ldg(colw + (g >> 5)) >> (g & 31)) & 1u;
+}
+
+__device__ __forceinline__ float2 conj2(float2 v) { return make_float2(v.x, -v.y); }
+
+// e^{+2 pi i q t} for t = t_hi + t_lo, q t reduced exactly to [-1/2, 1/2]
+// before the fast sine and cosine (accurate to ~4e-7 absolute there).
+__device__ __forceinline__ float2 plane_phase(float qf, float2 t) {
+  const float p = qf * t.x;
+  const float e = fmaf(qf, t.x, -p) + qf * t.y;
+  const float th = (p - rintf(p)) + e;
+  float sn, cs;
+  __sincosf(6.283185307179586f * th, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * R, 2)
+k_fft_rows_big(const float2* __restrict__ grid, float2* __restrict__ Xc, int N, int nb,
+               const int* __restrict__ active_rows, const uint32_t* __restrict__ colw,
+               const float2* __restrict__ tw, const float2* __restrict__ T2) {
+  constexpr int G = cfft::Cfg<R>::G;
+  extern __shared__ float2 Z[];
+  const int c = blockIdx.x, q = blockIdx.y;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const float2* src = grid + ((size_t)q * G + active_rows[c]) * G;
+  float2 u[cfft::L];
+#pragma unroll
+  for (int e = 0; e < cfft::L; ++e) {
+    const int n = cfft::pos<R>(t, e);
+    u[e] = group_on(colw, n) ? src[n] : make_float2(0.f, 0.f);
+  }
+  cfft::fft<R>(u, Z, tw, T2);
+  __syncthreads();                                  // every warp is done with its row of Z
+  const int hN = N >> 1;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int i = (cfft::kept_freq<R>(warp, lane, k) + hN) & (G - 1);
+    if (i < N) Z[i] = wfft::kept_value<cfft::L>(u, k, lane);
+  }
+  __syncthreads();
+  float2* dst = Xc + (size_t)(q * nb + (c >> 2)) * N * 4 + (c & 3);
+  for (int i = t; i < N; i += 32 * R) dst[(size_t)i * 4] = Z[i];
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * R, R == 16 ? 1 : 2)
+k_fft_cols_big(const float2* __restrict__ Xc, const float4* __restrict__ pix, float* __restrict__ mu, int N,
+               int P, int nb, int wstack, const int* __restrict__ row_pos, const float2* __restrict__ tw,
+               const float2* __restrict__ T2, float scale, unsigned* __restrict__ maxbits) {
+  constexpr int G = cfft::Cfg<R>::G;
+  extern __shared__ float2 Z[];
+  const int i = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int hN = N >> 1;
+  // compact row of each input register (-1: a row no visibility reaches)
+  int cpos[cfft::L];
+#pragma unroll
+  for (int e = 0; e < cfft::L; ++e) cpos[e] = __ldg(row_pos + cfft::pos<R>(t, e));
+  // w-screen turns of the kept outputs' pixels
+  float2 tz[8];
+  float2 acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = (cfft::kept_freq<R>(warp, lane, k) + hN) & (G - 1);
+    tz[k] = make_float2(0.f, 0.f);
+    if (wstack && j < N) {
+      const float4 pt = pix[(size_t)i * N + j];
+      tz[k] = make_float2(pt.z, pt.w);
+    }
+    acc[k] = make_float2(0.f, 0.f);
+  }
+  for (int q = 0; q < P; ++q) {
+    const float2* src = Xc + (size_t)q * nb * N * 4 + (size_t)i * 4;
+    float2 u[cfft::L];
+#pragma unroll
+    for (int e = 0; e < cfft::L; ++e) {
+      const int cc = cpos[e];
+      u[e] = cc >= 0 ? src[(size_t)(cc >> 2) * N * 4 + (cc & 3)] : make_float2(0.f, 0.f);
+    }
+    cfft::fft<R>(u, Z, tw, T2);
+    const float qf = (float)q;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float2 v = wfft::kept_value<cfft::L>(u, k, lane);
+      if (wstack) v = cmul(v, plane_phase(qf, tz[k]));
+      acc[k].x += v.x;
+      acc[k].y += v.y;
+    }
+    __syncthreads();                                // Z is free for the next plane
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = (cfft::kept_freq<R>(warp, lane, k) + hN) & (G - 1);
+    if (j < N) Z[j] = acc[k];
+  }
+  __syncthreads();
+  float amax = 0.0f;
+  unsigned skey = 0;   // order-preserving key of the signed maximum (0 below every number)
+  for (int j = t; j < N; j += 32 * R) {
+    const float4 pt = pix[(size_t)i * N + j];
+    const float2 s = Z[j];
+    const float m = (pt.x * s.x - pt.y * s.y) * scale;
+    mu[(size_t)i * N + j] = m;
+    amax = fmaxf(amax, fabsf(m));
+    if (m != m) amax = __int_as_float(0x7fc00000);
+    skey = max(skey, float_order_key(m));
+  }
+  unsigned bits = __float_as_uint(amax);
+  for (int off = 16; off; off >>= 1) {
+    bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, off));
+    skey = max(skey, __shfl_xor_sync(0xffffffffu, skey, off));
+  }
+  if (lane == 0 && maxbits) {
+    atomicMax(maxbits, bits);
+    atomicMax(maxbits + 1, skey);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * R, R == 16 ? 1 : 2)
+k_degrid_cols_big(const float* __restrict__ x, const float4* __restrict__ pix, int N, int P, int nb, int n_rows,
+                  int wstack, const int* __restrict__ row_pos, const float2* __restrict__ tw,
+                  const float2* __restrict__ T2, float2* __restrict__ Xc) {
+  constexpr int G = cfft::Cfg<R>::G;
+  extern __shared__ float2 Z[];
+  const int i = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int hN = N >> 1;
+  // input register e sits at row position n, pixel j = (n + N/2) mod G (< N
+  // only for n < N/2 or n >= G - N/2): its c_ij x_ij and w-screen turns
+  float2 base[cfft::L], tz[cfft::L];
+#pragma unroll
+  for (int e = 0; e < cfft::L; ++e) {
+    const int j = (cfft::pos<R>(t, e) + hN) & (G - 1);
+    base[e] = make_float2(0.f, 0.f);
+    tz[e] = make_float2(0.f, 0.f);
+    if (cfft::centred_reg<R>(e) && j < N) {
+      const size_t p = (size_t)i * N + j;
+      const float4 pt = pix[p];
+      const float xv = x[p];
+      base[e] = make_float2(pt.x * xv, pt.y * xv);
+      tz[e] = make_float2(pt.z, pt.w);
+    }
+  }
+  // compact row of each output register (-1: not a reachable row)
+  int cpos[cfft::L];
+#pragma unroll
+  for (int kp = 0; kp < cfft::L; ++kp) cpos[kp] = __ldg(row_pos + cfft::freq<R>(warp, lane, kp));
+  for (int q = 0; q < P; ++q) {
+    const float qf = (float)q;
+    float2 u[cfft::L];
+#pragma unroll
+    for (int e = 0; e < cfft::L; ++e)
+      u[e] = !cfft::centred_reg<R>(e) ? make_float2(0.f, 0.f)
+             : wstack                 ? cmul(base[e], plane_phase(qf, tz[e]))
+                                      : base[e];
+    cfft::fft<R>(u, Z, tw, T2);
+    __syncthreads();                                // Z free: stage the reachable rows' values
+#pragma unroll
+    for (int kp = 0; kp < cfft::L; ++kp)
+      if (cpos[kp] >= 0) Z[cpos[kp]] = conj2(u[wfft::brev(kp, 4)]);
+    __syncthreads();
+    float2* dst = Xc + (size_t)q * nb * N * 4 + (size_t)i * 4;
+    for (int c = t; c < n_rows; c += 32 * R) dst[(size_t)(c >> 2) * N * 4 + (c & 3)] = Z[c];
+    __syncthreads();
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * R, 2)
+k_degrid_rows_big(const float2* __restrict__ Xc, int N, int nb, const int* __restrict__ active_rows,
+                  const uint32_t* __restrict__ colw, const float2* __restrict__ tw, const float2* __restrict__ T2,
+                  float2* __restrict__ grid) {
+  constexpr int G = cfft::Cfg<R>::G;
+  extern __shared__ float2 Z[];
+  const int c = blockIdx.x, q = blockIdx.y;
+  const int t = threadIdx.x;
+  const int hN = N >> 1;
+  const float2* src = Xc + (size_t)(q * nb + (c >> 2)) * N * 4 + (c & 3);
+  float2 u[cfft::L];
+#pragma unroll
+  for (int e = 0; e < cfft::L; ++e) {
+    const int i = (cfft::pos<R>(t, e) + hN) & (G - 1);
+    u[e] = (cfft::centred_reg<R>(e) && i < N) ? conj2(src[(size_t)i * 4]) : make_float2(0.f, 0.f);
+  }
+  cfft::fft<R>(u, Z, tw, T2);
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+#pragma unroll
+  for (int kp = 0; kp < cfft::L; ++kp) Z[cfft::freq<R>(warp, lane, kp)] = conj2(u[wfft::brev(kp, 4)]);
+  __syncthreads();
+  float4* dst = reinterpret_cast<float4*>(grid + ((size_t)q * G + active_rows[c]) * G);
+  const float4* s4 = reinterpret_cast<const float4*>(Z);
+  for (int h = t; h < G / 2; h += 32 * R)
+    if (group_on(colw, 2 * h)) dst[h] = s4[h];
+}
+
+template <typename K>
+int allow(K* kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess
+             ? PC_OK
+             : fail(PC_ERR_CUDA, "fft: shared-memory opt-in failed");
+}
+
+}  // namespace
+
+bool fft_big_size(int G) { return G == 2048 || G == 4096 || G == 8192; }
+
+bool fft_rows_big(const pc_plan_s* p) { return fft_big_size(p->G) && (p->fft_warp < 0 || (p->fft_warp & 1)); }
+
+bool fft_cols_big(const pc_plan_s* p) { return fft_big_size(p->G) && (p->fft_warp < 0 || (p->fft_warp & 2)); }
+
+int compact_blocks(const pc_plan_s* p) { return ceil_div(std::max(p->n_active_rows, 1), 4); }
+
+#define PC_BIG_DISPATCH(G, CALL)   \
+  switch (G) {                     \
+    case 2048: { CALL(4) } break;  \
+    case 4096: { CALL(8) } break;  \
+    default: { CALL(16) } break;   \
+  }
+
+int launch_fft_rows_big(pc_plan_s* p, cudaStream_t st) {
+  const int nb = compact_blocks(p);
+  PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * p->N * 4));
+  float2* Xc = p->xc.as<float2>();
+#define PC_ROWS(RR)                                                                                        \
+  const size_t smem = sizeof(float2) * cfft::Cfg<RR>::Z_ELEMS;                                             \
+  static bool done = false;                                                                                \
+  if (!done) {                                                                                             \
+    PC_TRY(allow(k_fft_rows_big<RR>, smem));                                                               \
+    done = true;                                                                                           \
+  }                                                                                                        \
+  k_fft_rows_big<RR><<<dim3(p->n_active_rows, p->P), 32 * RR, smem, st>>>(p->grid, Xc, p->N, nb,           \
+                                                                           p->active_rows, p->col_bits,    \
+                                                                           p->twiddle, p->tw_in);
+  PC_BIG_DISPATCH(p->G, PC_ROWS)
+#undef PC_ROWS
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits, cudaStream_t st) {
+  const int nb = compact_blocks(p);
+  PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * p->N * 4));
+  const float2* Xc = p->xc.as<float2>();
+  const int ws = p->wstack ? 1 : 0;
+#define PC_COLS(RR)                                                                                        \
+  const size_t smem = sizeof(float2) * cfft::Cfg<RR>::Z_ELEMS;                                             \
+  static bool done = false;                                                                                \
+  if (!done) {                                                                                             \
+    PC_TRY(allow(k_fft_cols_big<RR>, smem));                                                               \
+    done = true;                                                                                           \
+  }                                                                                                        \
+  k_fft_cols_big<RR><<<p->N, 32 * RR, smem, st>>>(Xc, p->pix_tab, mu, p->N, p->P, nb, ws, p->row_pos,      \
+                                                  p->twiddle, p->tw_in, scale, maxbits);
+  PC_BIG_DISPATCH(p->G, PC_COLS)
+#undef PC_COLS
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+// The degridding's two FFT passes: img (N x N) -> grid_q[b][.] at the reachable rows.
+int launch_degrid_ffts_big(pc_plan_s* p, const float* img, cudaStream_t st) {
+  const int nb = compact_blocks(p);
+  PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * p->N * 4));
+  float2* Xc = p->xc.as<float2>();
+  const int ws = p->wstack ? 1 : 0;
+#define PC_DG(RR)                                                                                          \
+  const size_t smem = sizeof(float2) * cfft::Cfg<RR>::Z_ELEMS;                                             \
+  static bool done = false;                                                                                \
+  if (!done) {                                                                                             \
+    PC_TRY(allow(k_degrid_cols_big<RR>, smem));                                                            \
+    PC_TRY(allow(k_degrid_rows_big<RR>, smem));                                                            \
+    done = true;                                                                                           \
+  }                                                                                                        \
+  k_degrid_cols_big<RR><<<p->N, 32 * RR, smem, st>>>(img, p->pix_tab, p->N, p->P, nb, p->n_active_rows,   \
+                                                     ws, p->row_pos, p->twiddle, p->tw_in, Xc);            \
+  PC_LAUNCH_CHECK();                                                                                       \
+  k_degrid_rows_big<RR><<<dim3(p->n_active_rows, p->P), 32 * RR, smem, st>>>(                              \
+      Xc, p->N, nb, p->active_rows, p->col_bits, p->twiddle, p->tw_in, p->grid);
+  PC_BIG_DISPATCH(p->G, PC_DG)
+#undef PC_DG
+  PC_LAUNCH_CHECK();
+  return PC_OK;
+}
+
+#undef PC_BIG_DISPATCH
+
+}  // namespace pc

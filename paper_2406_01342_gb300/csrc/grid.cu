@@ -136,12 +136,14 @@ k_grid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis,
 // (all when the first FFT pass reads whole rows; else only the groups that
 // hold visibilities, the only ones the one-warp pass reads).
 __global__ void k_zero_rows(float2* __restrict__ grid, const int* __restrict__ rows, int n_rows,
-                            int G, int P, uint32_t cols) {
+                            int G, int P, const uint32_t* __restrict__ colw) {
   const int rr = blockIdx.x, q = blockIdx.y;
   if (rr >= n_rows) return;
   float4* dst = reinterpret_cast<float4*>(grid + ((size_t)q * G + rows[rr]) * G);
-  for (int c = threadIdx.x; c < G / 2; c += blockDim.x)
-    if ((cols >> ((c >> 4) & 31)) & 1u) dst[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = threadIdx.x; c < G / 2; c += blockDim.x) {
+    const int g = c >> 4;                          // 32-column group of the pair of cells
+    if (!colw || ((__ldg(colw + (g >> 5)) >> (g & 31)) & 1u)) dst[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 }
 
 int launch_grid(pc_plan_s* p, const float2* h, cudaStream_t st) {
@@ -149,7 +151,9 @@ int launch_grid(pc_plan_s* p, const float2* h, cudaStream_t st) {
   if (p->n_sub == 0) return PC_OK;        // nothing is ever written: the grid stays zero
   {
     dim3 zg(p->n_active_rows, p->P);
-    const uint32_t cols = fft_rows_warp(p) ? p->col_mask : 0xffffffffu;
+    // the one-warp and one-CTA first passes read only the column groups that
+    // can hold data; the Stockham pass reads whole rows
+    const uint32_t* cols = (fft_rows_warp(p) || fft_rows_big(p)) ? p->col_bits : nullptr;
     k_zero_rows<<<zg, 256, 0, st>>>(p->grid, p->active_rows, p->n_active_rows, p->G, p->P, cols);
     PC_LAUNCH_CHECK();
   }

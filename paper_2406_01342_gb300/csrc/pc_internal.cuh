@@ -69,13 +69,21 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
                  PROF_GRAM_TC, PROF_GRAM_THIN, PROF_DICT_CORR, PROF_DICT_COLUMNS, PROF_PHASE_GEN,
-                 PROF_NCLASSES };
+                 PROF_APGD_OP, PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
 bool prof_active();   // kernel-class timing is recording
 void prof_stop(int token, cudaStream_t st, int kernels);
 
 // Records the launches of one launcher function; `kernels` counts the CUDA
 // kernels and memsets it issued (set before the scope ends).
+// While one is alive on this thread, kernel-class scopes record nothing (a
+// scope that encloses a whole composite step, e.g. the operator-form
+// reweighting, keeps its launchers' own classes out of the breakdown).
+struct ProfMute {
+  ProfMute();
+  ~ProfMute();
+};
+
 struct ProfScope {
   int token;
   cudaStream_t st;
@@ -272,6 +280,13 @@ int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* max
 int cols_planes_per_pass(const pc_plan_s* p);
 bool fft_rows_warp(const pc_plan_s* p);   // the first pass runs the one-warp register FFT
 bool fft_cols_warp(const pc_plan_s* p);   // the second pass does
+// fft_big.cu: one-CTA FFT passes for G = 2048, 4096, 8192 (compact pass-1 rows)
+bool fft_big_size(int G);
+bool fft_rows_big(const pc_plan_s* p);
+bool fft_cols_big(const pc_plan_s* p);
+int launch_fft_rows_big(pc_plan_s* p, cudaStream_t st);
+int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits, cudaStream_t st);
+int launch_degrid_ffts_big(pc_plan_s* p, const float* img, cudaStream_t st);
 // degrid.cu: y = Phi(img) for a dense N x N image (type-2 NUFFT), y cleared first
 int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st);
 
@@ -300,6 +315,7 @@ struct pc_plan_s {
   int fft_warp = -1;  // bit 0 / bit 1: first / second FFT pass as one-warp register FFTs
                       // (-1: both wherever G is 512 or 1024, the sizes those kernels take)
   bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
+  bool want_tune = false; // the autotuner will run (it may pick the Stockham passes)
   double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0;
   std::vector<int4> sub_ranges;   // (tile, plane group, first slot, end) before splitting
   int sub_cap = 0;                // capacity of subs (the finest split)
@@ -322,6 +338,9 @@ struct pc_plan_s {
   float2* tw2 = nullptr;         // one-warp FFT twiddles e^{+2 pi i l k1 / G}, [k1 < G/32][l < 32]
   uint32_t row_mask = 0;         // G <= 1024: bit t set if grid rows 32 t .. 32 t + 31 can hold data
   uint32_t col_mask = 0;         // G <= 1024: the same for grid columns
+  uint32_t* col_bits = nullptr;  // G / 1024 words: bit g set if grid columns 32 g .. 32 g + 31 can hold data
+  int* row_pos = nullptr;        // G entries: compact index of a reachable grid row, else -1
+  float2* tw_in = nullptr;       // G >= 2048: the 512-point one-warp FFT's twiddles [k1 < 16][l < 32]
   // workspaces
   float2* grid = nullptr;        // P x G x G  (b-major rows, a contiguous)
   float2* fft1 = nullptr;        // P x N x G  (after the pass along a)
@@ -340,6 +359,9 @@ struct pc_plan_s {
   pc::DictWork* dict = nullptr;    // synthesis-dictionary workspace (created on first use)
   pc::SolveCache* scache = nullptr; // solver-loop resources (created by the first solve)
   pc::DevBuf degrid_buf;            // forward on a dense image: P x active rows x N (first pass)
+  pc::DevBuf xc;                    // G >= 2048: compact pass-1 rows, P x ceil(rows / 4) x N x 4
+  pc::DevBuf opw;                   // operator-form reweighting: images, visibilities, vectors
+  double op_pair_s = 0.0;           // measured time of one degridding + gridding pair (0: not yet)
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
 };

@@ -459,7 +459,7 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   double best_fft = 1e300;
   int best_R = 0, best_rw = 0;
   p->fft_warp = 1;
-  if (fft_rows_warp(p)) {
+  if (fft_rows_warp(p) || fft_rows_big(p)) {
     PC_TRY(time_us(st, 3, [&] { return launch_fft_rows(p, st); }, &best_fft));
     best_rw = 1;
   }
@@ -484,7 +484,7 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   double best_cols = 1e300;
   int best_pg = 1, best_cw = 0;
   p->fft_warp = best_rw | 2;
-  if (fft_cols_warp(p)) {
+  if (fft_cols_warp(p) || fft_cols_big(p)) {
     PC_TRY(time_us(st, 3, [&] { return launch_fft_cols_epilogue(p, p->mu, 1.0f, nullptr, st); },
                    &best_cols));
     best_cw = 2;
@@ -624,13 +624,28 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
     PC_CUDA(cudaMemcpyAsync(p->tw2, t2.data(), sizeof(float2) * t2.size(), cudaMemcpyHostToDevice, st));
   }
 
+  if (fft_big_size(p->G)) {
+    // the 512-point one-warp FFT inside the one-CTA transform: e^{+2 pi i l k1 / 512}
+    std::vector<float2> t2(16 * 32);
+    const int step = p->G / 512;
+    for (int k1 = 0; k1 < 16; ++k1)
+      for (int l = 0; l < 32; ++l) t2[(size_t)k1 * 32 + l] = tw[(size_t)(k1 * l * step) % p->G];
+    PC_TRY(dev_alloc_t(p, &p->tw_in, t2.size()));
+    PC_CUDA(cudaMemcpyAsync(p->tw_in, t2.data(), sizeof(float2) * t2.size(), cudaMemcpyHostToDevice, st));
+  }
+
   // ---- workspaces
   PC_TRY(dev_alloc_t(p, &p->grid, (size_t)p->P * p->G * p->G));
   PC_CUDA(cudaMemsetAsync(p->grid, 0, sizeof(float2) * (size_t)p->P * p->G * p->G, st));
-  PC_TRY(dev_alloc_t(p, &p->fft1, (size_t)p->P * N * p->G));
-  // columns b of the transposed pass-1 output whose grid rows never hold a
-  // visibility stay zero for every certificate: clear them once here
-  PC_CUDA(cudaMemsetAsync(p->fft1, 0, sizeof(float2) * (size_t)p->P * N * p->G, st));
+  // the Stockham passes' transposed pass-1 output (every G up to 1024; for
+  // larger grids only when those passes can be chosen: forced, or timed by
+  // the autotuner; the one-CTA passes use the compact buffer xc instead)
+  if (!fft_big_size(p->G) || p->fft_warp == 0 || p->want_tune) {
+    PC_TRY(dev_alloc_t(p, &p->fft1, (size_t)p->P * N * p->G));
+    // columns b of the transposed pass-1 output whose grid rows never hold a
+    // visibility stay zero for every certificate: clear them once here
+    PC_CUDA(cudaMemsetAsync(p->fft1, 0, sizeof(float2) * (size_t)p->P * N * p->G, st));
+  }
   PC_TRY(dev_alloc_t(p, &p->resid, (size_t)std::max<int64_t>(M, 1)));
   PC_TRY(dev_alloc_t(p, &p->mu, (size_t)NN));
   PC_TRY(dev_alloc_t(p, &p->mark, (size_t)NN));
@@ -756,6 +771,24 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
     if (!rows.empty())
       PC_CUDA(cudaMemcpyAsync(p->active_rows, rows.data(), sizeof(int) * rows.size(),
                               cudaMemcpyHostToDevice, st));
+    // compact position of every grid row, and the column groups that can hold data
+    std::vector<int> pos(p->G, -1);
+    for (size_t c = 0; c < rows.size(); ++c) pos[rows[c]] = (int)c;
+    PC_TRY(dev_alloc_t(p, &p->row_pos, (size_t)p->G));
+    PC_CUDA(cudaMemcpyAsync(p->row_pos, pos.data(), sizeof(int) * p->G, cudaMemcpyHostToDevice, st));
+    std::vector<uint32_t> colw((size_t)std::max(1, p->G / 1024), 0u);
+    for (const int4& s : ranges) {
+      const int g = s.x % p->nT;                  // a tile column is one 32-column group
+      colw[(size_t)g >> 5] |= 1u << (g & 31);
+    }
+    PC_TRY(dev_alloc_t(p, &p->col_bits, colw.size()));
+    PC_CUDA(cudaMemcpyAsync(p->col_bits, colw.data(), sizeof(uint32_t) * colw.size(), cudaMemcpyHostToDevice,
+                            st));
+    if (fft_big_size(p->G)) {
+      // the one-CTA passes' compact rows, allocated here (never inside a captured solve)
+      const size_t nb = (size_t)ceil_div(std::max(p->n_active_rows, 1), 4);
+      PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * N * 4));
+    }
   }
   PC_CUDA(cudaStreamSynchronize(st));
   return PC_OK;
@@ -835,6 +868,7 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   p->T = T;
   p->grid_mode = grid_mode;
   p->fft_warp = fft_kernel == 1 ? 0 : -1;
+  p->want_tune = tune == 1;
   int rc = build_plan(p, uvw_dev, (cudaStream_t)stream, maxP);
   if (rc == PC_OK && tune) rc = autotune(p, (cudaStream_t)stream);
   if (rc != PC_OK) {
@@ -852,8 +886,8 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
   out->grid_mode = (p->wstack && p->grid_mode != 1) ? 2 : 1;
   out->grid_piece = p->grid_piece;
   int R = p->fft_R > 0 ? p->fft_R : 2048 / p->G;
-  const bool rw = fft_rows_warp(p), cw = fft_cols_warp(p);
-  out->fft_rows_per_cta = rw ? 8 : std::min(std::max(R, 1), 32);
+  const bool rw = fft_rows_warp(p) || fft_rows_big(p), cw = fft_cols_warp(p) || fft_cols_big(p);
+  out->fft_rows_per_cta = fft_rows_big(p) ? 1 : rw ? 8 : std::min(std::max(R, 1), 32);
   out->grid_us = p->tune_grid_us;
   out->fft_rows_us = p->tune_fft_us;
   out->fft_cols_planes = cw ? 1 : cols_planes_per_pass(p);
@@ -886,6 +920,8 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
   p->atomsP.release();
   p->pbuf.release();
   p->degrid_buf.release();
+  p->xc.release();
+  p->opw.release();
   if (p->dict) {
     p->dict->release();
     delete p->dict;
@@ -895,6 +931,11 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
     delete p->scache;
   }
   delete p;
+}
+
+extern "C" int pc_plan(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,
+                       const pc_plan_opts* opts, void* stream, pc_plan_t* plan_out) {
+  return pc_plan_create(uvw_dev, M, N, fov_rad, opts, stream, plan_out);
 }
 
 extern "C" int pc_plan_info(pc_plan_t p, int32_t* grid_side, int32_t* tile, int32_t* n_planes,

@@ -262,6 +262,20 @@ void scheduler(pc_server_s* s) {
         want_apgd.push_back(a);
       }
     }
+    // ---- reweightings in operator form (large active sets): one operator
+    // pair per step on the job's own stream, not batchable with the others
+    for (size_t i = 0; i < want_apgd.size();) {
+      Active* a = want_apgd[i];
+      if (!a->job->op_form) {
+        ++i;
+        continue;
+      }
+      int rc = a->job->run_apgd_op();
+      if (rc == PC_OK) rc = a->job->after_apgd();
+      if (rc != PC_OK) fail_job(a, rc);
+      want_apgd.erase(want_apgd.begin() + (long)i);
+      progressed = true;
+    }
     // ---- the reweightings, batched
     if (!want_apgd.empty()) {
       if (s->opts.batch_apgd == 2) {

@@ -535,7 +535,9 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
     if (opts->lambda_max > 0) c.lmax = opts->lambda_max;
     c.gram_mode = opts->gram_mode;
     c.positive = opts->positivity;
+    c.reweight = opts->reweight;
   }
+  if (c.reweight < 0 || c.reweight > 2) return fail(PC_ERR_INVALID_ARG, "%s: reweight must be 0, 1 or 2", fn);
   if (c.positive != 0 && c.positive != 1) return fail(PC_ERR_INVALID_ARG, "%s: positivity must be 0 or 1", fn);
   if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "%s: select_rule must be 1 or 2", fn);
   if (c.gram_mode < 0 || c.gram_mode > 2) return fail(PC_ERR_INVALID_ARG, "%s: gram_mode must be 0, 1 or 2", fn);
@@ -729,6 +731,7 @@ int SolveJob::process() {
     if (have_cur) {
       cur.n_support = nS;
       cur.apgd_iterations = r.hi[2];
+      last_apgd_iters = r.hi[2];
       cur.lanczos_steps = r.hi[5];
       cur.lipschitz = r.hd[2];
       cur.objective = F;
@@ -790,6 +793,7 @@ int SolveJob::process() {
   ldB = ld();
   if (n_act > 0) {
     int32_t* oldpos = p->oldpos.as<int32_t>();
+    PC_TRY(choose_form(n_new, n_act, &op_form));
     {
       // old positions, new-atom list, warm start, b of the old atoms, atoms; marks cleared
       ProfScope prof_scope_(PROF_MISC, st);
@@ -800,15 +804,29 @@ int SolveJob::process() {
                                         p->bB.as<float>(), p->atomsB.as<float4>(), p->mark, p->atom_tab);
       PC_LAUNCH_CHECK();
     }
-    // old-old block of G
-    PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
-    // Gram rows of the new atoms against every active atom, and b
-    if (n_new > 0) {
-      PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_new, oldpos,
-                         p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode, p->iscal + 4, st));
-    }
     eps = std::max(c.eps_min, c.eps0 * std::pow(2.0, -k));
     need_apgd = true;
+    if (op_form) {
+      // operator form: no Gram; the next Gram-form iteration rebuilds all of G_S
+      gram_valid = false;
+      return PC_OK;
+    }
+    if (gram_valid) {
+      // old-old block of G
+      PC_TRY(gather_sym(p->GA.as<float>(), ldA, oldpos, n_act, p->GB.as<float>(), ldB, st));
+      // Gram rows of the new atoms against every active atom, and b
+      if (n_new > 0) {
+        PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_new, oldpos,
+                           p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode, p->iscal + 4, st));
+      }
+    } else {
+      // after an operator-form iteration: every row of G_S and all of b
+      k_iota<<<ceil_div(n_act, 256), 256, 0, st>>>(p->newrows.as<int32_t>(), n_act);
+      PC_LAUNCH_CHECK();
+      PC_TRY(gram_update(p, V, p->atomsB.as<float4>(), n_act, p->newrows.as<int32_t>(), n_act, nullptr,
+                         p->GB.as<float>(), ldB, p->bB.as<float>(), c.gram_mode, p->iscal + 4, st));
+      gram_valid = true;
+    }
     return PC_OK;
   }
   PC_CUDA(cudaMemsetAsync(p->iscal + 3, 0, sizeof(int32_t), st));
@@ -816,6 +834,44 @@ int SolveJob::process() {
   ldB_prev = ldB;
   ++k;
   return queue_iteration();
+}
+
+// The form of this iteration's reweighting: the Gram form costs the
+// contraction of the Gram rows it needs (all of them after an operator-form
+// iteration) plus a negligible APGD on G; the operator form costs one
+// degridding + gridding pair per Lanczos step (about 16) and per FISTA
+// iteration (estimated by the previous reweighting's count, at least 20).
+// Contraction rates are the ones measured on this GPU for the kernel the
+// Gram form would use (tensor cores ~0.5 PFLOP/s on split FP16 including the
+// phase generation; FP32 CUDA cores ~24 TFLOP/s on full tiles).
+int SolveJob::choose_form(int n_new, int n_act, bool* op) {
+  *op = false;
+  if (c.reweight == 1 || p->M <= 0) return PC_OK;
+  if (c.reweight == 2) {
+    *op = true;
+    return PC_OK;
+  }
+  const double M = (double)p->M;
+  const int rows = gram_valid ? n_new : n_act;            // Gram rows to contract
+  if (rows <= 0) return PC_OK;
+  const bool thin = rows + 1 <= 16 && c.gram_mode < 2;
+  const bool tc = !thin && (c.gram_mode >= 2 || (c.gram_mode == 0 && (int64_t)rows * n_act >= 64 * 64));
+  const double entries = (double)rows * (n_act + 1) - (double)rows * (rows - 1) / 2.0;
+  double t_gram;
+  if (tc) t_gram = 12.0 * M * entries / 5.0e14;
+  else if (thin) t_gram = 2.0 * M * (double)(rows + 1) * n_act / 2.0e12;   // latency-bound phase chains
+  else t_gram = 4.0 * M * (double)rows * (n_act + 1) / 2.4e13;
+  if (t_gram < 0.02) return PC_OK;                         // not worth timing the operators
+  double pair = 0.0;
+  PC_TRY(op_pair_seconds(p, st, &pair));
+  const double iters = std::max(20, last_apgd_iters) + 16;
+  *op = iters * pair < t_gram;
+  return PC_OK;
+}
+
+int SolveJob::run_apgd_op() {
+  return run_operator_apgd(p, V, p->idxB.as<int32_t>(), n_act, lambda, eps, c.apgd_max, c.positive != 0,
+                           p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->iscal + 5, st);
 }
 
 ApgdJob SolveJob::apgd_job() const {
@@ -886,8 +942,12 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
     PC_CUDA(cudaEventSynchronize(j.ev));
     PC_TRY(j.process());
     if (j.need_apgd) {
-      const ApgdJob aj = j.apgd_job();
-      PC_TRY(run_apgd_jobs(&aj, 1, j.st));
+      if (j.op_form) {
+        PC_TRY(j.run_apgd_op());
+      } else {
+        const ApgdJob aj = j.apgd_job();
+        PC_TRY(run_apgd_jobs(&aj, 1, j.st));
+      }
       PC_TRY(j.after_apgd());
     }
   }

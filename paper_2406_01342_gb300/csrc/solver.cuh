@@ -27,12 +27,22 @@ float bits_to_float(unsigned b);
 float key_to_float(unsigned key);   // inverse of float_order_key (0 -> -infinity)
 
 struct SolveCfg {
-  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0;
+  int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0, reweight = 0;
   double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
 };
 
 // Validates and reads pc_solve_opts (NULL = defaults).
 int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out);
+
+// reweight_op.cu: the reweighting in operator form (monotone FISTA on
+// g(v) = Re Phi_S^H (Phi_S v - V), one degridding + gridding pair per step)
+// on the n atoms idx (raster order), warm start and result in x; iterations,
+// step size and Lanczos steps written to the device scalars given.
+int run_operator_apgd(pc_plan_s* p, const float2* V, const int32_t* idx, int n, double lambda, double eps,
+                      int max_iter, bool positive, float* x, int* iters_dev, double* L_dev, int* lz_dev,
+                      cudaStream_t st);
+// Measured seconds of one degridding + gridding pair on this plan (cached).
+int op_pair_seconds(pc_plan_s* p, cudaStream_t st, double* out);
 
 struct SolveJob {
   // ---- inputs
@@ -54,8 +64,12 @@ struct SolveJob {
   pc_iter_record cur{};
   bool have_cur = false;
 
-  // the reweighting this iteration needs (valid when need_apgd)
+  // the reweighting this iteration needs (valid when need_apgd); op_form:
+  // it runs in operator form (run_apgd_op), else on the Gram form (apgd_job)
   bool need_apgd = false;
+  bool op_form = false;
+  bool gram_valid = true;               // GA holds G of the support (false after an operator-form step)
+  int last_apgd_iters = 0;
   int n_act = 0, ldB = 4;
   double eps = 0.0;
 
@@ -84,8 +98,10 @@ struct SolveJob {
   // solve goes on, queues the Gram update and sets need_apgd (or queues the
   // next iteration directly when the active set is empty).
   int process();
-  // The job's reweighting as a batched-APGD entry.
+  // The job's reweighting as a batched-APGD entry (Gram form).
   ApgdJob apgd_job() const;
+  // The job's reweighting in operator form (op_form), on the job's stream.
+  int run_apgd_op();
   // After the reweighting: pruning count, then the next iteration's queue.
   int after_apgd();
   // Copies the support and weights (device), fills the statistics and orders
@@ -99,6 +115,7 @@ struct SolveJob {
   int explore();
   int enqueue_chain(int bound);
   int queue_iteration();
+  int choose_form(int n_new, int n_act, bool* op);
 };
 
 }  // namespace pc

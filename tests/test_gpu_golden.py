@@ -80,14 +80,17 @@ def test_golden_is_a_converged_oracle_solve(golden):
     assert golden["mu_inf"] <= 1.0 + 1e-2
 
 
-def test_solve_matches_oracle_at_benchmark_size(abi, golden, problem):
+@pytest.mark.parametrize("reweight", [0, 2])
+def test_solve_matches_oracle_at_benchmark_size(abi, golden, problem, reweight):
+    """The default solve (the cost model picks the Gram form here) and the
+    solve with every reweighting in operator form."""
     wl, V = problem
     lam = golden["lambda"]
     plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
     Vd = to_dev(V.astype(np.complex64))
     # lambda_max by the GPU certificate agrees with the oracle's
     assert abs(abi.pc_lambda_max(plan, Vd) - golden["lambda_max"]) <= 1e-5 * golden["lambda_max"]
-    res = abi.pc_solve(plan, Vd, lam, golden["delta"])
+    res = abi.pc_solve(plan, Vd, lam, golden["delta"], reweight=reweight)
     idx = res["idx"].cpu().numpy()
     x = res["x"].cpu().numpy().astype(np.float64)
     assert res["converged"]

@@ -50,6 +50,11 @@ def test_operators_full_size_sampled(abi, name, n_pix):
     ks = np.sort(rng.choice(wl.M, 4000, replace=False))
     yref = operators.forward(wl.uvw[ks], N, wl.fov, idx, x.astype(np.float64))
     assert rel_l2(y[ks], yref) <= TOL
+    # the same image through degridding (one-CTA FFT passes at these grid sizes)
+    img = torch.zeros(N * N, dtype=torch.float32, device="cuda")
+    img[torch.from_numpy(idx.astype(np.int64)).cuda()] = torch.from_numpy(x).cuda()
+    y2 = abi.pc_forward_grid(plan, img.view(N, N)).cpu().numpy()
+    assert rel_l2(y2[ks], yref) <= TOL
 
 
 def _physical_vis(abi, plan, wl):

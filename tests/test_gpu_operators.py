@@ -143,6 +143,60 @@ def test_forward_grid_fft_kernels(abi, name, kw, fft_kernel):
     assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(y) ** 2) * np.sum(np.abs(h) ** 2))
 
 
+BIG = [("small_wide_w", {"N": 600}), ("tiny_64_coplanar", {"N": 1024}), ("small_wide_w", {"N": 1100}),
+       ("small_wide_w", {"N": 2100})]
+
+
+@pytest.mark.parametrize("name,kw", BIG)
+def test_fft_big_kernels(abi, name, kw):
+    """The one-CTA FFT passes (the default at G = 2048, 4096 and 8192, with
+    the pass-1 rows stored compactly) against the direct sum on the image's
+    border rows and columns and random pixels, and against the shared-memory
+    Stockham passes (fft_kernel = 1) on the whole image. N = 600, 1100 and
+    2100 leave part of the kept band empty; the coplanar case has one plane."""
+    wl, V = workload(name, **kw)
+    Vd = to_dev(V.astype(np.complex64))
+    pb, ps = _plan(abi, wl), _plan(abi, wl, fft_kernel=1)
+    assert abi.pc_plan_info(pb)["grid_side"] in (2048, 4096, 8192)
+    assert abi.pc_plan_tuning_info(pb)["fft_warp"] == 3
+    assert abi.pc_plan_tuning_info(ps)["fft_warp"] == 0
+    ab = abi.pc_adjoint_grid(pb, Vd).cpu().numpy().ravel()
+    as_ = abi.pc_adjoint_grid(ps, Vd).cpu().numpy().ravel()
+    N = wl.N
+    border = np.concatenate([np.arange(N), (N - 1) * N + np.arange(N), np.arange(N) * N,
+                             np.arange(N) * N + N - 1])
+    pix = np.union1d(border, np.random.default_rng(5).choice(N * N, 1024, replace=False))
+    ref = operators.adjoint(wl.uvw, N, wl.fov, V.astype(np.complex64).astype(np.complex128), pix)
+    assert rel_l2(ab[pix], ref) <= TOL
+    assert rel_l2(as_[pix], ref) <= TOL
+    assert rel_l2(ab, as_) <= TOL
+
+
+@pytest.mark.parametrize("name,kw", BIG)
+def test_forward_grid_big(abi, name, kw):
+    """Degridding through the one-CTA FFT passes: against the direct sum of
+    the forward equation on sampled visibilities (a random image on a random
+    fifth of the pixels), and the adjoint identity with the same plan's
+    gridding."""
+    wl, _ = workload(name, **kw)
+    plan = _plan(abi, wl)
+    rng = np.random.default_rng(34)
+    NN = wl.N * wl.N
+    on = np.sort(rng.choice(NN, NN // 5, replace=False))
+    img = np.zeros(NN, dtype=np.float32)
+    img[on] = rng.normal(size=on.size).astype(np.float32)
+    img = img.reshape(wl.N, wl.N)
+    y = abi.pc_forward_grid(plan, to_dev(img)).cpu().numpy()
+    ks = np.sort(rng.choice(wl.M, 400 if wl.N <= 1100 else 120, replace=False))
+    ref = operators.forward(wl.uvw[ks], wl.N, wl.fov, on, img.ravel()[on].astype(np.float64))
+    assert rel_l2(y[ks], ref) <= TOL
+    h = (rng.normal(size=wl.M) + 1j * rng.normal(size=wl.M)).astype(np.complex64)
+    g = abi.pc_adjoint_grid(plan, to_dev(h)).cpu().numpy().astype(np.float64)
+    lhs = float(np.real(np.vdot(y.astype(np.complex128), h.astype(np.complex128))))
+    rhs = float(np.sum(img.astype(np.float64) * g))
+    assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(y) ** 2) * np.sum(np.abs(h) ** 2))
+
+
 @pytest.mark.parametrize("name,kw", CASES)
 def test_forward_grid_is_the_adjoint_of_adjoint_grid(abi, name, kw):
     """Re<Phi x, h> = <x, Phi* h> between the two NUFFT directions of one plan
