@@ -41,7 +41,7 @@ SECONDARY = ("large_2048_blobs", "medium_512_w")
 # Frank-Wolfe iterations, measured on the GPU): the oracle arms scale their
 # per-certificate time by this count, and the GPU arm reports whether its own
 # solve still matches it.
-FW_CERTIFICATES = {"fine_4096_w": None, "large_2048_blobs": None, "medium_512_w": 6}
+FW_CERTIFICATES = {"fine_4096_w": 9, "large_2048_blobs": 8, "medium_512_w": 6}
 
 
 def parse():
@@ -214,20 +214,32 @@ def gram_entries(n_new: int, n_act: int) -> float:
     return n_new * (n_act + 1) - n_new * (n_new - 1) / 2.0
 
 
-def gridding_roofline(prof, info, wl, peaks):
-    """Gridding (all launches in the timed region) against the HBM roofline:
-    20 B per visibility (complex64 residual + three float32 coordinates) plus
-    the grid planes written once, per certificate."""
+def reach_cells(info, reach):
+    """Grid cells per w-plane that visibilities can reach (the gridding, the
+    first FFT pass and the degridding touch no others)."""
+    if not reach:
+        return float(info["grid_side"]) ** 2
+    return float(reach["rows"]) * 32.0 * reach["col_groups"]
+
+
+def gridding_roofline(prof, info, wl, peaks, reach=None):
+    """Gridding (all launches in the timed region: grid clear + spread) against
+    the HBM roofline. Algorithmic bytes per launch: 20 B per visibility
+    (complex64 residual + three float32 coordinates) plus the reachable part
+    of every w-plane written once; the full-plane count of the formula
+    P (sigma N)^2 8 B is reported beside it (frac_full_planes)."""
     if "grid" not in prof:
         return None
     launches, _, total_ms = prof["grid"]
     avg_ms = total_ms / max(launches, 1)
     G, P = info["grid_side"], info["n_planes"]
-    b = 20.0 * wl.M + 8.0 * P * G * G
+    b = 20.0 * wl.M + 8.0 * P * reach_cells(info, reach)
+    b_full = 20.0 * wl.M + 8.0 * P * G * G
     hbm = peaks.get("hbm_gbs", 6800.0)
     ach = b / (avg_ms * 1e-3) / 1e9
-    return {"avg_launch_ms": avg_ms, "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "bytes_per_launch": b, "vis_per_s": wl.M / (avg_ms * 1e-3)}
+    return {"avg_launch_ms": avg_ms, "launches": launches, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "bytes_per_launch": b, "vis_per_s": wl.M / (avg_ms * 1e-3),
+            "bytes_full_planes": b_full, "frac_full_planes": b_full / (avg_ms * 1e-3) / 1e9 / hbm}
 
 
 def degridding_leg(abi, torch, plan, wl, info, peaks, steps, l2_flush) -> dict:
@@ -270,25 +282,33 @@ def phase_gen_bytes(M, history):
     return sum(8.0 * M * (-(-(h["n_active"] + 1) // 256) * 256) for h in tc_iterations(history))
 
 
-def roofline(prof, info, wl, history, steps, peaks, dom):
+def roofline(prof, info, wl, history, steps, peaks, dom, reach=None):
     """Achieved vs peak for the dominant kernel class `dom`, from its CUDA-event
-    launch durations in `prof` (recorded over the timed region)."""
+    launch durations in `prof` (recorded over the timed region). Grid bytes
+    count the reachable part of each w-plane (pc_plan_reach)."""
     ms = {k: v[2] for k, v in prof.items()}
     launches = prof[dom][0]
     avg_ms = ms[dom] / max(launches, 1)
     hbm = peaks.get("hbm_gbs", 6800.0)
     M, N, G, P = wl.M, wl.N, info["grid_side"], info["n_planes"]
+    cells = reach_cells(info, reach)
+    rows = float(reach["rows"]) if reach else float(G)
     out = {"kernel": dom, "avg_launch_ms": avg_ms, "launches": launches}
     if dom == "grid":
         # 20 B per visibility (complex64 residual + three float32 coordinates)
-        # + the grid planes written once
-        b = 20.0 * M + 8.0 * P * G * G
+        # + the reachable grid cells written once
+        b = 20.0 * M + 8.0 * P * cells
+        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    elif dom == "degrid":
+        # the image read, the reachable grid written (second FFT pass) and read
+        # (interpolation), one complex64 per visibility written
+        b = 4.0 * N * N + 2 * 8.0 * P * cells + 8.0 * M
         out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
     elif dom == "fft_rows":
-        b = 8.0 * P * G * G + 8.0 * P * N * G
+        b = 8.0 * P * cells + 8.0 * P * N * rows
         out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
     elif dom == "fft_cols":
-        b = 8.0 * P * N * G + 16.0 * N * N + 4.0 * N * N
+        b = 8.0 * P * N * rows + 16.0 * N * N + 4.0 * N * N
         out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
     elif dom == "apgd":
         # one S x S FP32 GEMV per iteration (G read from shared memory or L2)
@@ -557,6 +577,11 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def rule_opts(wl, lmax):
+    """Solve options of the workload's exploration rule (R1 needs lambda_max)."""
+    return {"select_rule": 1, "lambda_max": lmax} if wl.rule == "R1" else {}
+
+
 def timed_solves(abi, torch, plan, V, lam, delta, n, l2_flush, **opts):
     """n solves, each bracketed by CUDA events on the launching stream, L2
     flushed before each; returns (per-solve ms, last result)."""
@@ -573,12 +598,12 @@ def timed_solves(abi, torch, plan, V, lam, delta, n, l2_flush, **opts):
     return ms, res
 
 
-def precision_pair(abi, torch, plan, V, lam, delta, n, l2_flush, mixed_ms, mixed_res) -> dict:
+def precision_pair(abi, torch, plan, V, lam, delta, n, l2_flush, mixed_ms, mixed_res, **opts) -> dict:
     """The same solve with the support contraction on FP32 CUDA cores
     (gram_mode 1, the plain path) beside the default split-FP16 tensor-core
     form: solve times and whether both reach the same support and objective."""
-    abi.pc_solve(plan, V, lam, delta, want_mu=False, gram_mode=1)
-    ms, res = timed_solves(abi, torch, plan, V, lam, delta, n, l2_flush, gram_mode=1)
+    abi.pc_solve(plan, V, lam, delta, want_mu=False, gram_mode=1, **opts)
+    ms, res = timed_solves(abi, torch, plan, V, lam, delta, n, l2_flush, gram_mode=1, **opts)
     same = res["idx"].cpu().tolist() == mixed_res["idx"].cpu().tolist()
     dF = abs(res["objective"] - mixed_res["objective"]) / mixed_res["objective"]
     return {"mixed_split_fp16_tensor": {"solve_time_s": statistics.median(mixed_ms) / 1e3,
@@ -597,24 +622,29 @@ def secondary_leg(abi, synth, torch, device, name, steps, l2_flush, peaks) -> di
     roofline and the plain-FP32 contraction beside the default."""
     wl, _, plan, V = make_inputs(abi, synth, name, device)
     info = abi.pc_plan_info(plan)
-    lam = wl.alpha * abi.pc_lambda_max(plan, V)
+    reach = abi.pc_plan_reach(plan)
+    lmax = abi.pc_lambda_max(plan, V)
+    lam = wl.alpha * lmax
+    ro = rule_opts(wl, lmax)
     for _ in range(2):
-        abi.pc_solve(plan, V, lam, wl.delta, want_mu=False)
+        abi.pc_solve(plan, V, lam, wl.delta, want_mu=False, **ro)
     abi.pc_profile_begin()
-    res = abi.pc_solve(plan, V, lam, wl.delta, want_mu=True, history=256)
+    res = abi.pc_solve(plan, V, lam, wl.delta, want_mu=True, history=256, **ro)
     prof = abi.pc_profile_end()
-    ms, res = timed_solves(abi, torch, plan, V, lam, wl.delta, steps, l2_flush)
+    ms, res = timed_solves(abi, torch, plan, V, lam, wl.delta, steps, l2_flush, **ro)
     dom = max(prof, key=lambda c: prof[c][2])
-    rl = roofline(prof, info, wl, res["history"], 1, peaks, dom)
+    rl = roofline(prof, info, wl, res["history"], 1, peaks, dom, reach)
     out = {"workload": f"{name}: {wl.N}x{wl.N} image, M={wl.M} visibilities, {info['n_planes']} w-planes, "
-                       f"{wl.sky_idx.size} sky pixels, lambda={wl.alpha} lambda_max, delta={wl.delta}",
+                       f"{wl.sky_idx.size} sky pixels, lambda={wl.alpha} lambda_max, rule {wl.rule}, "
+                       f"delta={wl.delta}",
            "solve_time_s": statistics.median(ms) / 1e3, "solves_per_s": 1e3 / statistics.median(ms),
            "steps": steps, "iterations": res["iterations"], "support": int(res["idx"].numel()),
            "objective": res["objective"], "converged": res["converged"],
            "kernels_ms": {k: round(v[2], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][2])},
            "roofline": {k: rl[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac")},
-           "gridding_roofline": gridding_roofline(prof, info, wl, peaks)}
-    out["precision"] = precision_pair(abi, torch, plan, V, lam, wl.delta, max(3, steps // 2), l2_flush, ms, res)
+           "gridding_roofline": gridding_roofline(prof, info, wl, peaks, reach)}
+    out["precision"] = precision_pair(abi, torch, plan, V, lam, wl.delta, max(3, steps // 2), l2_flush, ms, res,
+                                      **ro)
     return out
 
 
@@ -631,6 +661,7 @@ def coplanar_gridding_leg(abi, synth, torch, device, names, l2_flush, peaks, rep
         uvw[:, 2] = 0.0
         plan = abi.pc_plan_create(torch.from_numpy(uvw).to(device), wl.N, wl.fov)
         info = abi.pc_plan_info(plan)
+        reach = abi.pc_plan_reach(plan)
         h = torch.from_numpy(wl.noise.astype(np.complex64)).to(device)
         for _ in range(3):
             abi.pc_adjoint_grid(plan, h)
@@ -641,7 +672,7 @@ def coplanar_gridding_leg(abi, synth, torch, device, names, l2_flush, peaks, rep
             abi.pc_adjoint_grid(plan, h)
         prof = abi.pc_profile_end()
         torch.cuda.synchronize()
-        out[name + "_coplanar"] = dict(gridding_roofline(prof, info, wl, peaks), n_planes=info["n_planes"],
+        out[name + "_coplanar"] = dict(gridding_roofline(prof, info, wl, peaks, reach), n_planes=info["n_planes"],
                                        grid_side=info["grid_side"], M=wl.M)
         del plan
     return out
@@ -660,6 +691,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(device)
     wl, uvw, plan, V = make_inputs(abi, synth, args.workload, device, autotune=1 if args.autotune else 0)
     info = abi.pc_plan_info(plan)
+    reach = abi.pc_plan_reach(plan)
     tuning = abi.pc_plan_tuning_info(plan)
     lmax = abi.pc_lambda_max(plan, V)
     lam = wl.alpha * lmax
@@ -690,7 +722,7 @@ def run_ours(args, world, rank, local):
     with ClockSampler(local) as clk:
         # the timed pass: events only around the dominant kernel class and the
         # gridding (for the roofline objects), a handful per solve
-        abi.pc_profile_begin(",".join(sorted({dom, "grid", "phase_gen"})))
+        abi.pc_profile_begin(",".join(sorted({dom, "grid"})))
         for i in range(args.steps):
             flush_l2(l2_flush)
             starts[i].record(stream)
@@ -709,7 +741,7 @@ def run_ours(args, world, rank, local):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
-    rl = roofline(prof_timed, info, wl, res["history"], args.steps, peaks, dom)
+    rl = roofline(prof_timed, info, wl, res["history"], args.steps, peaks, dom, reach)
     grid_ms = prof_timed.get("grid", (1, 1, float("nan")))[2] / max(prof_timed.get("grid", (1,))[0], 1)
     vis_per_s = wl.M / (grid_ms * 1e-3) if grid_ms == grid_ms else None
     gpu_launches = sum(v[1] for v in prof.values())
@@ -792,7 +824,7 @@ def run_ours(args, world, rank, local):
                       "objective": res["objective"], "converged": res["converged"]},
             "precision": precision,
             "gridding_vis_per_s": vis_per_s,
-            "gridding_roofline": gridding_roofline(prof_timed, info, wl, peaks),
+            "gridding_roofline": gridding_roofline(prof_timed, info, wl, peaks, reach),
             "gridding_coplanar": coplanar,
             "phase_gen_roofline": ({k: v for k, v in roofline(prof_timed, info, wl, res["history"], args.steps,
                                                                 peaks, "phase_gen").items() if k != "traffic"}

@@ -164,6 +164,11 @@ void pc_plan_destroy(pc_plan_t plan);
 int pc_plan_info(pc_plan_t plan, int32_t* grid_side, int32_t* tile, int32_t* n_planes,
                  int64_t* n_slots, int32_t* kernel_width, double* dw);
 int pc_plan_tuning_info(pc_plan_t plan, pc_plan_tuning* out_host);
+/* The part of each w-plane's grid that visibilities can reach (the gridding,
+ * the FFT's first pass and the degridding touch nothing else): the number of
+ * reachable grid rows and of reachable 32-column groups. Either pointer may
+ * be NULL. */
+int pc_plan_reach(pc_plan_t plan, int32_t* rows, int32_t* col_groups);
 
 /* ------------------------------------------------------------------ operators */
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "pc_last_error", "pc_abi_version", "pc_adjoint_sparse_noalloc", "pc_lambda_max_positive",
     "pc_profile_begin_classes", "pc_server_create", "pc_server_submit", "pc_server_wait",
     "pc_server_destroy", "pc_plan_tuning_info", "pc_dict_adjoint", "pc_dict_forward_sparse",
-    "pc_dict_lambda_max", "pc_solve_synthesis", "pc_forward_grid", "pc_trim_memory",
+    "pc_dict_lambda_max", "pc_solve_synthesis", "pc_forward_grid", "pc_trim_memory", "pc_plan_reach",
 ]
 
 
@@ -145,6 +145,7 @@ def load(path: str | None = None):
         "pc_plan": (_I32, [_P, _I64, _I32, _D, _P, _P, ctypes.POINTER(_P)]),
         "pc_plan_destroy": (None, [_P]),
         "pc_plan_tuning_info": (_I32, [_P, ctypes.POINTER(pc_plan_tuning)]),
+        "pc_plan_reach": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
         "pc_plan_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                 ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
         "pc_forward_sparse": (_I32, [_P, _P, _P, _I32, _P, _P]),
@@ -251,6 +252,13 @@ def pc_plan_info(plan: Plan) -> dict:
                                ctypes.byref(ns), ctypes.byref(w), ctypes.byref(dw)))
     return dict(grid_side=g.value, tile=t.value, n_planes=p.value, n_slots=ns.value,
                 kernel_width=w.value, dw=dw.value)
+
+
+def pc_plan_reach(plan: Plan) -> dict:
+    """Reachable grid rows and 32-column groups of each w-plane."""
+    r, c = _I32(), _I32()
+    _check(load().pc_plan_reach(plan.handle, ctypes.byref(r), ctypes.byref(c)))
+    return dict(rows=r.value, col_groups=c.value)
 
 
 def pc_plan_tuning_info(plan: Plan) -> dict:

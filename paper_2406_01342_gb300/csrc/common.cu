@@ -196,7 +196,7 @@ const char* const kProfNames[PROF_NCLASSES] = {"plan",     "grid",     "fft_rows
                                                "residual", "gram_fp32", "gram_finalize",
                                                "apgd",     "select",   "misc",     "gram_tc",
                                                "gram_thin", "dict_corr", "dict_columns", "phase_gen",
-                                               "apgd_op"};
+                                               "apgd_op", "degrid"};
 
 struct ProfRec {
   int cls;
@@ -226,12 +226,8 @@ cudaEvent_t pool_event() {
 
 bool prof_active() { return g_prof_on; }
 
-static thread_local int g_prof_mute = 0;
-ProfMute::ProfMute() { ++g_prof_mute; }
-ProfMute::~ProfMute() { --g_prof_mute; }
-
 int prof_start(int cls, cudaStream_t st) {
-  if (!g_prof_on || g_prof_mute > 0 || !((g_prof_mask >> cls) & 1u)) return -1;
+  if (!g_prof_on || !((g_prof_mask >> cls) & 1u)) return -1;
   cudaEvent_t a = pool_event(), b = pool_event();
   if (!a || !b) return -1;
   cudaEventRecord(a, st);

@@ -267,7 +267,7 @@ k_degrid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis, const
 }  // namespace
 
 int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st) {
-  ProfScope prof_scope_(PROF_GRID, st);
+  ProfScope prof_scope_(PROF_DEGRID, st);
   if (p->M <= 0) return PC_OK;
   PC_CUDA(cudaMemsetAsync(y, 0, sizeof(float2) * (size_t)p->M, st));
   prof_scope_.kernels = 1;

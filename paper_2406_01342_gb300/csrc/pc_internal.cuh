@@ -69,21 +69,13 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
                  PROF_GRAM_TC, PROF_GRAM_THIN, PROF_DICT_CORR, PROF_DICT_COLUMNS, PROF_PHASE_GEN,
-                 PROF_APGD_OP, PROF_NCLASSES };
+                 PROF_APGD_OP, PROF_DEGRID, PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
 bool prof_active();   // kernel-class timing is recording
 void prof_stop(int token, cudaStream_t st, int kernels);
 
 // Records the launches of one launcher function; `kernels` counts the CUDA
 // kernels and memsets it issued (set before the scope ends).
-// While one is alive on this thread, kernel-class scopes record nothing (a
-// scope that encloses a whole composite step, e.g. the operator-form
-// reweighting, keeps its launchers' own classes out of the breakdown).
-struct ProfMute {
-  ProfMute();
-  ~ProfMute();
-};
-
 struct ProfScope {
   int token;
   cudaStream_t st;
@@ -340,6 +332,7 @@ struct pc_plan_s {
   uint32_t col_mask = 0;         // G <= 1024: the same for grid columns
   uint32_t* col_bits = nullptr;  // G / 1024 words: bit g set if grid columns 32 g .. 32 g + 31 can hold data
   int* row_pos = nullptr;        // G entries: compact index of a reachable grid row, else -1
+  int n_active_col_groups = 0;   // bits set in col_bits
   float2* tw_in = nullptr;       // G >= 2048: the 512-point one-warp FFT's twiddles [k1 < 16][l < 32]
   // workspaces
   float2* grid = nullptr;        // P x G x G  (b-major rows, a contiguous)

@@ -781,6 +781,8 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
       const int g = s.x % p->nT;                  // a tile column is one 32-column group
       colw[(size_t)g >> 5] |= 1u << (g & 31);
     }
+    p->n_active_col_groups = 0;
+    for (uint32_t word : colw) p->n_active_col_groups += __builtin_popcount(word);
     PC_TRY(dev_alloc_t(p, &p->col_bits, colw.size()));
     PC_CUDA(cudaMemcpyAsync(p->col_bits, colw.data(), sizeof(uint32_t) * colw.size(), cudaMemcpyHostToDevice,
                             st));
@@ -931,6 +933,14 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
     delete p->scache;
   }
   delete p;
+}
+
+extern "C" int pc_plan_reach(pc_plan_t p, int32_t* rows, int32_t* col_groups) {
+  clear_error();
+  if (!p) return fail(PC_ERR_INVALID_ARG, "pc_plan_reach: NULL plan");
+  if (rows) *rows = p->n_active_rows;
+  if (col_groups) *col_groups = p->n_active_col_groups;
+  return PC_OK;
 }
 
 extern "C" int pc_plan(const double* uvw_dev, int64_t M, int32_t N, double fov_rad,

@@ -41,6 +41,7 @@ class Workload:
     alpha: float              # lambda = alpha * lambda_max (Sect. 5.3)
     delta: float              # exploration quality parameter of the PFW select
     seed: int
+    rule: str = "R2"          # exploration rule: "R2" |mu| >= 1 - delta, "R1" Algorithm 2's own set
 
     @property
     def M(self) -> int:
@@ -221,14 +222,19 @@ def large_2048(seed: int = 1002, M: int = 2_000_000, blobs: bool = False) -> Wor
     """2048x2048, FOV 5 deg, 60 stations within 5 km (baselines up to 10 km),
     Earth rotation to M = 2M, 200 log-normal point sources, 15 dB SNR; with
     blobs=True also 10 elliptical Gaussian blobs (FWHM 5-50 px, peak U[0.1, 1]
-    per pixel), the diffuse part of the configuration."""
+    per pixel), the diffuse part of the configuration, solved with the
+    exploration rule of Algorithm 2 at delta = 0.9: on a diffuse sky at
+    lambda = 0.1 lambda_max the normalised rule |mu| >= 1 - delta with delta =
+    0.01 would put ~240k pixels into the first active set."""
     wl = earth_rotation_workload("large_2048_w", seed, 2048, 5.0, 60, 5000.0, 3.14, 10.0, M,
                                  200, 15.0)
     if blobs:
         rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(5)[4])
         bi, bf = gaussian_blobs(wl.N, 10, rng)
         wl.sky_idx, wl.sky_flux = merge_skies(wl.sky_idx, wl.sky_flux, bi, bf)
+        wl.sky_idx = wl.sky_idx.astype(np.int32)
         wl.name = "large_2048_blobs"
+        wl.rule, wl.delta = "R1", 0.9
     return wl
 
 
