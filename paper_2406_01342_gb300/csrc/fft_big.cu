@@ -30,10 +30,24 @@
 //   k_degrid_rows_big  per (reachable row, plane): the N values of Xc centred
 //                      on a length-G row, inverse FFT along i, conjugated ->
 //                      grid_q[b][.] in the column groups that hold data.
+#include <cudaTypedefs.h>
+
 #include "fft_cta.cuh"
+#include "tcgen05.cuh"
 
 namespace pc {
 namespace {
+
+constexpr long long FB_WAIT_CYCLES = 4000000000ll;   // bounded TMA waits (~2 s of SM clock)
+
+// Shared-memory layout of k_fft_cols_big: the FFT exchange buffer Z, then two
+// stage buffers for the compact rows of consecutive planes (TMA boxes of
+// `by` rows of four complex values), each 128-byte aligned.
+template <int R>
+__host__ __device__ constexpr size_t cols_z_bytes() {
+  return ((sizeof(float2) * cfft::Cfg<R>::Z_ELEMS + 127) / 128) * 128;
+}
+__host__ __device__ inline size_t cols_stage_bytes(int n_box, int by) { return (size_t)n_box * by * 32; }
 
 __device__ __forceinline__ bool group_on(const uint32_t* __restrict__ colw, int n) {
   const int g = n >> 5;
@@ -82,16 +96,52 @@ k_fft_rows_big(const float2* __restrict__ grid, float2* __restrict__ Xc, int N, 
   for (int i = t; i < N; i += 32 * R) dst[(size_t)i * 4] = Z[i];
 }
 
+// The compact rows of plane q for image row i are Xc[q][cb][i][0..4), cb <
+// nb: a 2-D TMA box of {4 complex values, by blocks} from the tensor map over
+// Xc viewed as [P nb blocks][N x 4 complex] gathers them into shared memory
+// in compact-row order (the transpose of the pass-1 layout). Thread 0 issues
+// the boxes of plane q + 1 while every thread transforms plane q (two stage
+// buffers, each completing on its own mbarrier), so the loads hide behind the
+// FFTs. Every wait is bounded: on expiry the CTA sets *err, waits (bounded)
+// for the copies it issued and leaves.
 template <int R>
 __global__ void __launch_bounds__(32 * R, R == 16 ? 1 : 2)
-k_fft_cols_big(const float2* __restrict__ Xc, const float4* __restrict__ pix, float* __restrict__ mu, int N,
-               int P, int nb, int wstack, const int* __restrict__ row_pos, const float2* __restrict__ tw,
-               const float2* __restrict__ T2, float scale, unsigned* __restrict__ maxbits) {
+k_fft_cols_big(const __grid_constant__ CUtensorMap xmap, int n_box, int by, const float4* __restrict__ pix,
+               float* __restrict__ mu, int N, int P, int nb, int wstack, const int* __restrict__ row_pos,
+               const float2* __restrict__ tw, const float2* __restrict__ T2, float scale,
+               unsigned* __restrict__ maxbits, int* __restrict__ err) {
   constexpr int G = cfft::Cfg<R>::G;
-  extern __shared__ float2 Z[];
+  extern __shared__ __align__(128) unsigned char fb_sm[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  float2* Z = reinterpret_cast<float2*>(fb_sm);
+  float2* stage[2] = {reinterpret_cast<float2*>(fb_sm + cols_z_bytes<R>()),
+                      reinterpret_cast<float2*>(fb_sm + cols_z_bytes<R>() + cols_stage_bytes(n_box, by))};
   const int i = blockIdx.x;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int hN = N >> 1;
+  const uint32_t tx_bytes = (uint32_t)cols_stage_bytes(n_box, by);
+  if (t == 0) {
+    tc::mbar_init(tc::smem_u32(&s_bar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&s_bar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0: the boxes of plane q into stage buffer q & 1
+  auto issue = [&](int q) {
+    const int b = q & 1;
+    const uint32_t bar = tc::smem_u32(&s_bar[b]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the buffer first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx_bytes) : "memory");
+    for (int j = 0; j < n_box; ++j) {
+      const uint32_t dst = tc::smem_u32(stage[b] + (size_t)j * by * 4);
+      const int x = 8 * i, y = q * nb + j * by;
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+          ::"r"(dst), "l"(reinterpret_cast<uint64_t>(&xmap)), "r"(x), "r"(y), "r"(bar)
+          : "memory");
+    }
+  };
+  if (t == 0) issue(0);
   // compact row of each input register (-1: a row no visibility reaches)
   int cpos[cfft::L];
 #pragma unroll
@@ -109,13 +159,26 @@ k_fft_cols_big(const float2* __restrict__ Xc, const float4* __restrict__ pix, fl
     }
     acc[k] = make_float2(0.f, 0.f);
   }
+  int issued = 1, consumed = 0;
+  bool ok = true;
   for (int q = 0; q < P; ++q) {
-    const float2* src = Xc + (size_t)q * nb * N * 4 + (size_t)i * 4;
+    if (t == 0 && q + 1 < P) {
+      issue(q + 1);
+      issued = q + 2;
+    }
+    const int b = q & 1;
+    const bool got = tc::mbar_wait(tc::smem_u32(&s_bar[b]), (uint32_t)((q >> 1) & 1), nullptr, FB_WAIT_CYCLES);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
+    consumed = q + 1;
+    const float2* src = stage[b];
     float2 u[cfft::L];
 #pragma unroll
     for (int e = 0; e < cfft::L; ++e) {
       const int cc = cpos[e];
-      u[e] = cc >= 0 ? src[(size_t)(cc >> 2) * N * 4 + (cc & 3)] : make_float2(0.f, 0.f);
+      u[e] = cc >= 0 ? src[cc] : make_float2(0.f, 0.f);
     }
     cfft::fft<R>(u, Z, tw, T2);
     const float qf = (float)q;
@@ -126,7 +189,17 @@ k_fft_cols_big(const float2* __restrict__ Xc, const float4* __restrict__ pix, fl
       acc[k].x += v.x;
       acc[k].y += v.y;
     }
-    __syncthreads();                                // Z is free for the next plane
+    __syncthreads();                                // Z and the stage buffer are free again
+  }
+  if (!ok) {
+    // a wait expired: report it, let the copies this CTA issued land (bounded), leave
+    if (t == 0) {
+      atomicExch(err, 1);
+      for (int q = consumed; q < issued; ++q)
+        tc::mbar_wait(tc::smem_u32(&s_bar[q & 1]), (uint32_t)((q >> 1) & 1), nullptr, FB_WAIT_CYCLES);
+    }
+    __syncthreads();
+    return;
   }
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -279,20 +352,55 @@ int launch_fft_rows_big(pc_plan_s* p, cudaStream_t st) {
   return PC_OK;
 }
 
+// The tensor map over the compact pass-1 rows (made once, at plan time): a
+// 2-D float32 tensor of P nb rows of 8 N floats (the N x 4 complex values of
+// one block of four reachable rows), boxes of 8 floats x by rows.
+int make_xc_tensor_map(pc_plan_s* p) {
+  const int nb = compact_blocks(p);
+  // box height a multiple of 4 rows (every box lands 128-byte aligned in
+  // shared memory); a last box that runs past the plane reads rows of the next
+  // plane, or zeros past the tensor, which the kernel ignores
+  p->xmap_by = std::min(256, ((nb + 3) / 4) * 4);
+  p->xmap_boxes = ceil_div(nb, p->xmap_by);
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return fail(PC_ERR_CUDA, "plan: cuTensorMapEncodeTiled is not available");
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)8 * p->N, (cuuint64_t)p->P * nb};
+  const cuuint64_t strides[1] = {(cuuint64_t)8 * p->N * sizeof(float)};
+  const cuuint32_t box[2] = {8, (cuuint32_t)p->xmap_by};
+  const cuuint32_t elem[2] = {1, 1};
+  const CUresult r = encode(&p->xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->xc.p, dims, strides, box, elem,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PC_ERR_CUDA, "plan: tensor map of the compact FFT rows failed (%d)", (int)r);
+  return PC_OK;
+}
+
 int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits, cudaStream_t st) {
   const int nb = compact_blocks(p);
-  PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * p->N * 4));
-  const float2* Xc = p->xc.as<float2>();
   const int ws = p->wstack ? 1 : 0;
+  const size_t stage = cols_stage_bytes(p->xmap_boxes, p->xmap_by);
 #define PC_COLS(RR)                                                                                        \
-  const size_t smem = sizeof(float2) * cfft::Cfg<RR>::Z_ELEMS;                                             \
+  const size_t smem = cols_z_bytes<RR>() + 2 * stage;                                                      \
+  if (smem > 200 * 1024) return fail(PC_ERR_INVALID_ARG, "fft: %d reachable grid rows exceed shared memory", \
+                                     p->n_active_rows);                                                    \
   static bool done = false;                                                                                \
   if (!done) {                                                                                             \
-    PC_TRY(allow(k_fft_cols_big<RR>, smem));                                                               \
+    PC_TRY(allow(k_fft_cols_big<RR>, 200 * 1024));                                                         \
     done = true;                                                                                           \
   }                                                                                                        \
-  k_fft_cols_big<RR><<<p->N, 32 * RR, smem, st>>>(Xc, p->pix_tab, mu, p->N, p->P, nb, ws, p->row_pos,      \
-                                                  p->twiddle, p->tw_in, scale, maxbits);
+  k_fft_cols_big<RR><<<p->N, 32 * RR, smem, st>>>(p->xmap, p->xmap_boxes, p->xmap_by, p->pix_tab, mu, p->N,  \
+                                                  p->P, nb, ws, p->row_pos, p->twiddle, p->tw_in, scale,   \
+                                                  maxbits, p->iscal + 7);
   PC_BIG_DISPATCH(p->G, PC_COLS)
 #undef PC_COLS
   PC_LAUNCH_CHECK();

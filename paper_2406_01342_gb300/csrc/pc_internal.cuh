@@ -1,6 +1,7 @@
 // Internal declarations of the PolyCLEAN GB300 library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -279,6 +280,7 @@ bool fft_cols_big(const pc_plan_s* p);
 int launch_fft_rows_big(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits, cudaStream_t st);
 int launch_degrid_ffts_big(pc_plan_s* p, const float* img, cudaStream_t st);
+int make_xc_tensor_map(pc_plan_s* p);   // after xc is allocated
 // degrid.cu: y = Phi(img) for a dense N x N image (type-2 NUFFT), y cleared first
 int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st);
 
@@ -353,6 +355,8 @@ struct pc_plan_s {
   pc::SolveCache* scache = nullptr; // solver-loop resources (created by the first solve)
   pc::DevBuf degrid_buf;            // forward on a dense image: P x active rows x N (first pass)
   pc::DevBuf xc;                    // G >= 2048: compact pass-1 rows, P x ceil(rows / 4) x N x 4
+  alignas(64) CUtensorMap xmap;     // TMA map over xc (2-D: P ceil(rows / 4) x 8 N floats)
+  int xmap_by = 0, xmap_boxes = 0;  // its box height and boxes per plane
   pc::DevBuf opw;                   // operator-form reweighting: images, visibilities, vectors
   double op_pair_s = 0.0;           // measured time of one degridding + gridding pair (0: not yet)
 

@@ -438,7 +438,7 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   double best = 1e300;
   int best_mode = user_mode, best_piece = p->grid_piece;
   for (int mode : modes) {
-    for (int piece : {256, 512, 1024}) {
+    for (int piece : {256, 512, 1024, 2048, 4096}) {
       p->grid_mode = mode;
       PC_TRY(split_subs(p, piece, st));
       double us = 0.0;
@@ -790,6 +790,7 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
       // the one-CTA passes' compact rows, allocated here (never inside a captured solve)
       const size_t nb = (size_t)ceil_div(std::max(p->n_active_rows, 1), 4);
       PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * N * 4));
+      PC_TRY(make_xc_tensor_map(p));
     }
   }
   PC_CUDA(cudaStreamSynchronize(st));
