@@ -695,10 +695,11 @@ def run_ours(args, world, rank, local):
     tuning = abi.pc_plan_tuning_info(plan)
     lmax = abi.pc_lambda_max(plan, V)
     lam = wl.alpha * lmax
+    ro = rule_opts(wl, lmax)
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
 
     def step():
-        return abi.pc_solve(plan, V, lam, wl.delta, want_mu=True, history=256)
+        return abi.pc_solve(plan, V, lam, wl.delta, want_mu=True, history=256, **ro)
 
     n_warm = max(3, args.warmup)          # at least three untimed warm-up solves
     for _ in range(n_warm):
@@ -747,14 +748,14 @@ def run_ours(args, world, rank, local):
     gpu_launches = sum(v[1] for v in prof.values())
 
     # the secondary legs report an error in their object instead of ending the run
-    def leg(fn, *a):
+    def leg(fn, *a, **kw):
         try:
-            return fn(*a)
+            return fn(*a, **kw)
         except Exception as e:   # noqa: BLE001 -- recorded in the JSON line
             return {"error": f"{type(e).__name__}: {e}"}
 
     precision = leg(precision_pair, abi, torch, plan, V, lam, wl.delta, max(3, args.steps), l2_flush,
-                    step_ms, res) if rank == 0 else None
+                    step_ms, res, **ro) if rank == 0 else None
 
     # end to end through the C ABI on host buffers (plan + lambda_max + solve + copies)
     e2e = None
@@ -762,14 +763,15 @@ def run_ours(args, world, rank, local):
         uvw_h = torch.from_numpy(wl.uvw).pin_memory()
         V_h = V.cpu().pin_memory()
         n_sup = 0
+        host_ro = {"select_rule": 1} if wl.rule == "R1" else {}
         for _ in range(max(3, args.warmup)):
-            r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta)
+            r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta, **host_ro)
         t = []
         for i in range(args.steps):
             flush_l2(l2_flush)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta)
+            r = abi.pc_solve_host(uvw_h.numpy(), V_h.numpy(), wl.N, wl.fov, wl.alpha, wl.delta, **host_ro)
             t.append(time.perf_counter() - t0)
             n_sup = len(r["idx"])
         e2e_s = max_over_ranks(world, sum(t))
@@ -812,8 +814,8 @@ def run_ours(args, world, rank, local):
             "warmup": n_warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {wl.N}x{wl.N} image, M={wl.M} visibilities, "
-                                   f"{info['n_planes']} w-planes, {wl.sky_idx.size} point sources, "
-                                   f"lambda={wl.alpha} lambda_max, delta={wl.delta}",
+                                   f"{info['n_planes']} w-planes, {wl.sky_idx.size} sky pixels, "
+                                   f"lambda={wl.alpha} lambda_max, rule {wl.rule}, delta={wl.delta}",
                        "l2": "flushed between timed steps (256 MB write); the inputs are larger than L2",
                        "plan_tuning": tuning,
                        "certificates_per_solve": certs,

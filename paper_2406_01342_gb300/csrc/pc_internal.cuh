@@ -358,6 +358,7 @@ struct pc_plan_s {
   alignas(64) CUtensorMap xmap;     // TMA map over xc (2-D: P ceil(rows / 4) x 8 N floats)
   int xmap_by = 0, xmap_boxes = 0;  // its box height and boxes per plane
   pc::DevBuf opw;                   // operator-form reweighting: images, visibilities, vectors
+  pc::DevBuf dirty;                 // operator-form reweighting: Re Phi* V of the solve (N x N)
   double op_pair_s = 0.0;           // measured time of one degridding + gridding pair (0: not yet)
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)

@@ -925,6 +925,7 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
   p->degrid_buf.release();
   p->xc.release();
   p->opw.release();
+  p->dirty.release();
   if (p->dict) {
     p->dict->release();
     delete p->dict;

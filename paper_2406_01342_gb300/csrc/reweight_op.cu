@@ -109,6 +109,37 @@ __global__ void k_lz_init(float* __restrict__ v, float* __restrict__ vprev, int 
   }
 }
 
+// Lanczos start vector b_S / ||b_S||, b_S = Re Phi_S^H V read from the
+// dirty image at S: b = G_S x_true + noise is one power step from the sky, so
+// it leans towards the top eigenvectors and Lanczos settles in fewer steps
+// (each an operator pair here) than from all ones; all ones if b_S = 0.
+__global__ void __launch_bounds__(OP_THREADS) k_lz_init_dirty(const float* __restrict__ dirty,
+                                                              const int32_t* __restrict__ idx, int n,
+                                                              float* __restrict__ v, float* __restrict__ vprev,
+                                                              OpState* __restrict__ s) {
+  __shared__ float red[32 + 1];
+  float a[1] = {0.f};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float b = dirty[idx[i]];
+    v[i] = b;
+    vprev[i] = 0.f;
+    a[0] = fmaf(b, b, a[0]);
+  }
+  block_sums<1>(a, red);
+  const bool use = a[0] > 0.f && isfinite(a[0]);
+  const float scale = use ? rsqrtf(a[0]) : 0.f, v0 = rsqrtf((float)n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = use ? v[i] * scale : v0;
+  if (threadIdx.x == 0) {
+    s->L = 1.f;
+    s->t = 1.f;
+    s->theta_prev = 0.f;
+    s->lz_m = 0;
+    s->lz_done = 0;
+    s->it = 0;
+    s->done = 0;
+  }
+}
+
 // One Lanczos step on w = G v_j: alpha = v.w, w -= alpha v_j + beta_{j-1} v_{j-1},
 // beta = ||w||, v_{j+1} = w / beta. The stop test is the Gram kernels' (the
 // top Ritz value changed by at most LZ_TOL over the last 4 steps, from step 8
@@ -317,9 +348,9 @@ int op_pair_seconds(pc_plan_s* p, cudaStream_t st, double* out) {
   return PC_OK;
 }
 
-int run_operator_apgd(pc_plan_s* p, const float2* V, const int32_t* idx, int n, double lambda, double eps,
-                      int max_iter, bool positive, float* x, int* iters_dev, double* L_dev, int* lz_dev,
-                      cudaStream_t st) {
+int run_operator_apgd(pc_plan_s* p, const float2* V, const float* dirty, const int32_t* idx, int n,
+                      double lambda, double eps, int max_iter, bool positive, float* x, int* iters_dev,
+                      double* L_dev, int* lz_dev, cudaStream_t st) {
   if (n <= 0) return PC_OK;
   OpWork w;
   PC_TRY(op_workspace(p, n, &w, st));
@@ -333,7 +364,10 @@ int run_operator_apgd(pc_plan_s* p, const float2* V, const int32_t* idx, int n, 
                                                 : fail(PC_ERR_CUDA, "reweighting: %s",
                                                        cudaGetErrorString(cudaGetLastError()));
   };
-  PC_TRY(book([&] { k_lz_init<<<gb, 256, 0, st>>>(w.v, w.vprev, n, w.s); }));
+  if (dirty)
+    PC_TRY(book([&] { k_lz_init_dirty<<<1, OP_THREADS, 0, st>>>(dirty, idx, n, w.v, w.vprev, w.s); }));
+  else
+    PC_TRY(book([&] { k_lz_init<<<gb, 256, 0, st>>>(w.v, w.vprev, n, w.s); }));
   for (int j = 0; j < LZ_MAX; ++j) {
     PC_TRY(op_apply(p, w, nullptr, idx, n, w.v, w.w, st));
     PC_TRY(book([&] { k_lz_step<<<1, OP_THREADS, 0, st>>>(w.w, w.v, w.vprev, n, w.s); }));

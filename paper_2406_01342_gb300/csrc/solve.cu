@@ -870,8 +870,14 @@ int SolveJob::choose_form(int n_new, int n_act, bool* op) {
 }
 
 int SolveJob::run_apgd_op() {
-  return run_operator_apgd(p, V, p->idxB.as<int32_t>(), n_act, lambda, eps, c.apgd_max, c.positive != 0,
-                           p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->iscal + 5, st);
+  if (!dirty_ready) {
+    // Re Phi* V on every pixel, once per solve: its values on the active set start Lanczos
+    PC_TRY(p->dirty.ensure(sizeof(float) * (size_t)p->N * p->N));
+    PC_TRY(adjoint_grid_impl(p, V, p->dirty.as<float>(), 1.0f, nullptr, st));
+    dirty_ready = true;
+  }
+  return run_operator_apgd(p, V, p->dirty.as<float>(), p->idxB.as<int32_t>(), n_act, lambda, eps, c.apgd_max,
+                           c.positive != 0, p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->iscal + 5, st);
 }
 
 ApgdJob SolveJob::apgd_job() const {

@@ -38,9 +38,10 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out);
 // g(v) = Re Phi_S^H (Phi_S v - V), one degridding + gridding pair per step)
 // on the n atoms idx (raster order), warm start and result in x; iterations,
 // step size and Lanczos steps written to the device scalars given.
-int run_operator_apgd(pc_plan_s* p, const float2* V, const int32_t* idx, int n, double lambda, double eps,
-                      int max_iter, bool positive, float* x, int* iters_dev, double* L_dev, int* lz_dev,
-                      cudaStream_t st);
+// dirty (N x N, may be null): Re Phi* V, whose values at idx start Lanczos.
+int run_operator_apgd(pc_plan_s* p, const float2* V, const float* dirty, const int32_t* idx, int n,
+                      double lambda, double eps, int max_iter, bool positive, float* x, int* iters_dev,
+                      double* L_dev, int* lz_dev, cudaStream_t st);
 // Measured seconds of one degridding + gridding pair on this plan (cached).
 int op_pair_seconds(pc_plan_s* p, cudaStream_t st, double* out);
 
@@ -69,6 +70,7 @@ struct SolveJob {
   bool need_apgd = false;
   bool op_form = false;
   bool gram_valid = true;               // GA holds G of the support (false after an operator-form step)
+  bool dirty_ready = false;             // the plan's dirty image holds Re Phi* V of this solve
   int last_apgd_iters = 0;
   int n_act = 0, ldB = 4;
   double eps = 0.0;
