@@ -109,14 +109,14 @@ __global__ void __launch_bounds__(32 * R, R == 16 ? 1 : 2)
 k_fft_cols_big(const __grid_constant__ CUtensorMap xmap, int n_box, int by, const float4* __restrict__ pix,
                float* __restrict__ mu, int N, int P, int nb, int wstack, const int* __restrict__ row_pos,
                const float2* __restrict__ tw, const float2* __restrict__ T2, float scale,
-               unsigned* __restrict__ maxbits, int* __restrict__ err) {
+               unsigned* __restrict__ maxbits, int* __restrict__ err, const int* __restrict__ img_rows) {
   constexpr int G = cfft::Cfg<R>::G;
   extern __shared__ __align__(128) unsigned char fb_sm[];
   __shared__ __align__(8) uint64_t s_bar[2];
   float2* Z = reinterpret_cast<float2*>(fb_sm);
   float2* stage[2] = {reinterpret_cast<float2*>(fb_sm + cols_z_bytes<R>()),
                       reinterpret_cast<float2*>(fb_sm + cols_z_bytes<R>() + cols_stage_bytes(n_box, by))};
-  const int i = blockIdx.x;
+  const int i = img_rows ? img_rows[blockIdx.x] : (int)blockIdx.x;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int hN = N >> 1;
   const uint32_t tx_bytes = (uint32_t)cols_stage_bytes(n_box, by);
@@ -233,10 +233,10 @@ template <int R>
 __global__ void __launch_bounds__(32 * R, R == 16 ? 1 : 2)
 k_degrid_cols_big(const float* __restrict__ x, const float4* __restrict__ pix, int N, int P, int nb, int n_rows,
                   int wstack, const int* __restrict__ row_pos, const float2* __restrict__ tw,
-                  const float2* __restrict__ T2, float2* __restrict__ Xc) {
+                  const float2* __restrict__ T2, float2* __restrict__ Xc, const int* __restrict__ img_rows) {
   constexpr int G = cfft::Cfg<R>::G;
   extern __shared__ float2 Z[];
-  const int i = blockIdx.x;
+  const int i = img_rows ? img_rows[blockIdx.x] : (int)blockIdx.x;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int hN = N >> 1;
   // input register e sits at row position n, pixel j = (n + N/2) mod G (< N
@@ -283,7 +283,7 @@ template <int R>
 __global__ void __launch_bounds__(32 * R, 2)
 k_degrid_rows_big(const float2* __restrict__ Xc, int N, int nb, const int* __restrict__ active_rows,
                   const uint32_t* __restrict__ colw, const float2* __restrict__ tw, const float2* __restrict__ T2,
-                  float2* __restrict__ grid) {
+                  float2* __restrict__ grid, const uint32_t* __restrict__ img_row_bits) {
   constexpr int G = cfft::Cfg<R>::G;
   extern __shared__ float2 Z[];
   const int c = blockIdx.x, q = blockIdx.y;
@@ -294,7 +294,10 @@ k_degrid_rows_big(const float2* __restrict__ Xc, int N, int nb, const int* __res
 #pragma unroll
   for (int e = 0; e < cfft::L; ++e) {
     const int i = (cfft::pos<R>(t, e) + hN) & (G - 1);
-    u[e] = (cfft::centred_reg<R>(e) && i < N) ? conj2(src[(size_t)i * 4]) : make_float2(0.f, 0.f);
+    // image rows outside the restriction hold zeros (their pass-1 values were not written)
+    const bool on = cfft::centred_reg<R>(e) && i < N &&
+                    (!img_row_bits || ((__ldg(img_row_bits + (i >> 5)) >> (i & 31)) & 1u));
+    u[e] = on ? conj2(src[(size_t)i * 4]) : make_float2(0.f, 0.f);
   }
   cfft::fft<R>(u, Z, tw, T2);
   __syncthreads();
@@ -389,6 +392,9 @@ int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
   const int nb = compact_blocks(p);
   const int ws = p->wstack ? 1 : 0;
   const size_t stage = cols_stage_bytes(p->xmap_boxes, p->xmap_by);
+  const bool restricted = p->n_img_rows > 0;
+  const int rows_img = restricted ? p->n_img_rows : p->N;
+  const int* list = restricted ? p->img_rows : nullptr;
 #define PC_COLS(RR)                                                                                        \
   const size_t smem = cols_z_bytes<RR>() + 2 * stage;                                                      \
   if (smem > 200 * 1024) return fail(PC_ERR_INVALID_ARG, "fft: %d reachable grid rows exceed shared memory", \
@@ -398,9 +404,9 @@ int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
     PC_TRY(allow(k_fft_cols_big<RR>, 200 * 1024));                                                         \
     done = true;                                                                                           \
   }                                                                                                        \
-  k_fft_cols_big<RR><<<p->N, 32 * RR, smem, st>>>(p->xmap, p->xmap_boxes, p->xmap_by, p->pix_tab, mu, p->N,  \
-                                                  p->P, nb, ws, p->row_pos, p->twiddle, p->tw_in, scale,   \
-                                                  maxbits, p->iscal + 7);
+  k_fft_cols_big<RR><<<rows_img, 32 * RR, smem, st>>>(p->xmap, p->xmap_boxes, p->xmap_by, p->pix_tab, mu,     \
+                                                     p->N, p->P, nb, ws, p->row_pos, p->twiddle, p->tw_in,   \
+                                                     scale, maxbits, p->iscal + 7, list);
   PC_BIG_DISPATCH(p->G, PC_COLS)
 #undef PC_COLS
   PC_LAUNCH_CHECK();
@@ -413,6 +419,10 @@ int launch_degrid_ffts_big(pc_plan_s* p, const float* img, cudaStream_t st) {
   PC_TRY(p->xc.ensure(sizeof(float2) * (size_t)p->P * nb * p->N * 4));
   float2* Xc = p->xc.as<float2>();
   const int ws = p->wstack ? 1 : 0;
+  const bool restricted = p->n_img_rows > 0;
+  const int rows_img = restricted ? p->n_img_rows : p->N;
+  const int* list = restricted ? p->img_rows : nullptr;
+  const uint32_t* bits = restricted ? p->img_row_bits : nullptr;
 #define PC_DG(RR)                                                                                          \
   const size_t smem = sizeof(float2) * cfft::Cfg<RR>::Z_ELEMS;                                             \
   static bool done = false;                                                                                \
@@ -421,11 +431,12 @@ int launch_degrid_ffts_big(pc_plan_s* p, const float* img, cudaStream_t st) {
     PC_TRY(allow(k_degrid_rows_big<RR>, smem));                                                            \
     done = true;                                                                                           \
   }                                                                                                        \
-  k_degrid_cols_big<RR><<<p->N, 32 * RR, smem, st>>>(img, p->pix_tab, p->N, p->P, nb, p->n_active_rows,   \
-                                                     ws, p->row_pos, p->twiddle, p->tw_in, Xc);            \
+  k_degrid_cols_big<RR><<<rows_img, 32 * RR, smem, st>>>(img, p->pix_tab, p->N, p->P, nb,                 \
+                                                        p->n_active_rows, ws, p->row_pos, p->twiddle,       \
+                                                        p->tw_in, Xc, list);                                \
   PC_LAUNCH_CHECK();                                                                                       \
   k_degrid_rows_big<RR><<<dim3(p->n_active_rows, p->P), 32 * RR, smem, st>>>(                              \
-      Xc, p->N, nb, p->active_rows, p->col_bits, p->twiddle, p->tw_in, p->grid);
+      Xc, p->N, nb, p->active_rows, p->col_bits, p->twiddle, p->tw_in, p->grid, bits);
   PC_BIG_DISPATCH(p->G, PC_DG)
 #undef PC_DG
   PC_LAUNCH_CHECK();

@@ -360,6 +360,12 @@ struct pc_plan_s {
   pc::DevBuf opw;                   // operator-form reweighting: images, visibilities, vectors
   pc::DevBuf dirty;                 // operator-form reweighting: Re Phi* V of the solve (N x N)
   double op_pair_s = 0.0;           // measured time of one degridding + gridding pair (0: not yet)
+  // While the operator-form reweighting runs, the image rows holding its atoms
+  // (list and bit mask, n_img_rows > 0): the one-CTA passes of G >= 2048 then
+  // transform only those rows on the image side (the others are not needed).
+  const int* img_rows = nullptr;
+  const uint32_t* img_row_bits = nullptr;
+  int n_img_rows = 0;
 
   std::vector<void*> owned;      // every cudaMalloc of the plan (freed on destroy)
 };

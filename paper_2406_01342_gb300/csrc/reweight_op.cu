@@ -29,6 +29,12 @@ namespace pc {
 namespace {
 
 constexpr int OP_THREADS = 1024;
+// Lanczos tolerance of the operator form: each step is an operator pair, and
+// the step size only has to stay an upper bound of the Hessian's top
+// eigenvalue: the top Ritz value rises towards it, so a value that moved by
+// at most 1e-3 over 4 steps is within a few 1e-3 of it and 1.01 x that value
+// (the step-size margin) still bounds it.
+constexpr float LZ_TOL_OP = 1e-3f;
 
 struct OpState {
   float L;          // step size 1.01 x top Ritz value (valid once lz_done)
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(OP_THREADS) k_lz_step(float* __restrict__ w, f
   const int m = j + 1;
   const bool last = (m == n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
   const float theta = tridiag_top(s->al, s->be, m, &s_theta);
-  const bool stop = last || (m >= 8 && fabsf(theta - s->th[m - 5]) <= LZ_TOL * fabsf(theta));
+  const bool stop = last || (m >= 8 && fabsf(theta - s->th[m - 5]) <= LZ_TOL_OP * fabsf(theta));
   __syncthreads();
   if (threadIdx.x == 0) {
     s->th[j] = theta;
@@ -262,13 +268,52 @@ struct OpWork {
   float2* yv;     // M
   float *v, *vprev, *w, *y, *gy, *z, *gz, *gx;   // n each
   OpState* s;
+  int* rows;          // N: image rows holding atoms (ascending), then their count
+  int* row_count;
+  uint32_t* row_bits; // ceil(N / 32) words
 };
+
+// The image rows that hold atoms of S: bit mask and ascending list (one CTA).
+__global__ void __launch_bounds__(OP_THREADS) k_op_rows(const int32_t* __restrict__ idx, int n, int N,
+                                                        uint32_t* __restrict__ bits, int* __restrict__ rows,
+                                                        int* __restrict__ count) {
+  __shared__ int warp_tot[32];
+  const int words = (N + 31) >> 5;
+  for (int k = threadIdx.x; k < words; k += blockDim.x) bits[k] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = idx[i] / N;
+    atomicOr(bits + (r >> 5), 1u << (r & 31));
+  }
+  __syncthreads();
+  // ascending compaction, one bit per row: each thread owns a run of rows
+  const int per = (N + blockDim.x - 1) / blockDim.x;
+  const int r0 = threadIdx.x * per, r1 = min(N, r0 + per);
+  int mine = 0;
+  for (int r = r0; r < r1; ++r) mine += (bits[r >> 5] >> (r & 31)) & 1u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = mine;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += o;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  int base = 0;
+  for (int w = 0; w < warp; ++w) base += warp_tot[w];
+  int pos = base + incl - mine;
+  for (int r = r0; r < r1; ++r)
+    if ((bits[r >> 5] >> (r & 31)) & 1u) rows[pos++] = r;
+  if (threadIdx.x == blockDim.x - 1) *count = pos;
+}
 
 int op_workspace(pc_plan_s* p, int n, OpWork* w, cudaStream_t st) {
   const size_t NN = (size_t)p->N * p->N;
   const size_t nn = (size_t)((n + 63) / 64) * 64;
+  const size_t rows_words = (size_t)(p->N + 31) / 32;
   const size_t bytes = sizeof(float) * 2 * NN + sizeof(float2) * (size_t)std::max<int64_t>(p->M, 1) +
-                       sizeof(float) * 8 * nn + sizeof(OpState) + 256;
+                       sizeof(float) * 8 * nn + sizeof(OpState) + sizeof(int) * ((size_t)p->N + 4) +
+                       sizeof(uint32_t) * rows_words + 512;
   const bool fresh = p->opw.bytes < bytes;
   PC_TRY(p->opw.ensure(bytes));
   char* b = static_cast<char*>(p->opw.p);
@@ -279,6 +324,9 @@ int op_workspace(pc_plan_s* p, int n, OpWork* w, cudaStream_t st) {
   float** vecs[8] = {&w->v, &w->vprev, &w->w, &w->y, &w->gy, &w->z, &w->gz, &w->gx};
   for (int k = 0; k < 8; ++k) *vecs[k] = f + k * nn;
   w->s = reinterpret_cast<OpState*>(f + 8 * nn);
+  w->rows = reinterpret_cast<int*>(reinterpret_cast<char*>(w->s) + ((sizeof(OpState) + 15) / 16) * 16);
+  w->row_count = w->rows + p->N;
+  w->row_bits = reinterpret_cast<uint32_t*>(w->row_count + 4);
   if (fresh) PC_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * NN, st));   // kept zero between uses
   return PC_OK;
 }
@@ -356,6 +404,31 @@ int run_operator_apgd(pc_plan_s* p, const float2* V, const float* dirty, const i
   PC_TRY(op_workspace(p, n, &w, st));
   const int gb = std::min(ceil_div(n, 256), 1024);
   int flag = 0;
+  // the image rows that hold the atoms: the one-CTA FFT passes of the
+  // operator pairs transform only those on the image side
+  struct Restrict {
+    pc_plan_s* p;
+    ~Restrict() {
+      p->n_img_rows = 0;
+      p->img_rows = nullptr;
+      p->img_row_bits = nullptr;
+    }
+  } restrict_guard{p};
+  if (fft_big_size(p->G)) {
+    {
+      ProfScope ps(PROF_APGD_OP, st);
+      ps.kernels = 1;
+      k_op_rows<<<1, OP_THREADS, 0, st>>>(idx, n, p->N, w.row_bits, w.rows, w.row_count);
+      PC_LAUNCH_CHECK();
+    }
+    int n_rows = 0;
+    PC_TRY(read_flag(w.row_count, st, &n_rows));
+    if (n_rows > 0 && n_rows < p->N) {
+      p->img_rows = w.rows;
+      p->img_row_bits = w.row_bits;
+      p->n_img_rows = n_rows;
+    }
+  }
   auto book = [&](auto launch) {                 // a bookkeeping launch, timed as "apgd_op"
     ProfScope ps(PROF_APGD_OP, st);
     ps.kernels = 1;
