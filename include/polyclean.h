@@ -65,8 +65,12 @@ typedef struct {
   int32_t kernel_width;   /* ES kernel width W in grid cells (default 7; 4..8)         */
   int32_t tile;           /* gridding tile side in cells (32, the only supported value) */
   int32_t max_planes;     /* cap on the number of w-planes (default 256)                */
-  int32_t grid_mode;      /* gridding: 0 (default) tensor cores when w-stacking, else CUDA
-                             cores; 1: FP32 CUDA cores; 2: tensor cores whenever w-stacking */
+  int32_t grid_mode;      /* gridding: 0 (default) when w-stacking, mode 3 on grids of side
+                             >= 2048 (kernel_width <= 7), else tensor cores; CUDA cores
+                             without w-stacking. 1: FP32 CUDA cores; 2: tensor cores
+                             whenever w-stacking; 3: FP32 CUDA cores over plane windows,
+                             one CTA per tile, when w-stacking with kernel_width <= 7
+                             (else as 2)                                                 */
   int32_t autotune;       /* 1: time the candidate gridding kernels, gridding sub-problem
                              sizes and FFT kernels on this plan's visibilities and keep
                              the fastest (adds a few ms to plan creation); 0 (default): off */
@@ -78,8 +82,9 @@ typedef struct {
 /* What the plan-time autotuner chose (tuned = 0 when it did not run). */
 typedef struct {
   int32_t tuned;
-  int32_t grid_mode;        /* 1: CUDA cores, 2: tensor cores                        */
-  int32_t grid_piece;       /* gridding sub-problem size in binned slots             */
+  int32_t grid_mode;        /* 1: CUDA cores, 2: tensor cores, 3: plane windows      */
+  int32_t grid_piece;       /* gridding sub-problem size in binned slots (mode 3:
+                               slots per CTA before a tile is split into parts)      */
   int32_t fft_rows_per_cta; /* rows per CTA of the first FFT pass                    */
   double  grid_us;          /* measured time of one gridding with that choice        */
   double  fft_rows_us;      /* measured time of one first FFT pass with that choice  */

@@ -163,6 +163,7 @@ int launch_grid(pc_plan_s* p, const float2* h, cudaStream_t st) {
   prof_scope_.kernels = 2;
   // tensor cores for w-stacked plans (the coplanar case has one plane and
   // would leave 7/8 of the tensor-core tile empty); iscal[7] = timeout flag
+  if (grid_win_mode(p)) return launch_grid_win(p, h, st);
   if (p->wstack && p->grid_mode != 1) return launch_grid_tc(p, h, p->iscal + 7, st);
   const float beta = (float)p->beta;
   const int ws = p->wstack ? 1 : 0;

@@ -267,6 +267,12 @@ int launch_grid(pc_plan_s* p, const float2* r, cudaStream_t st);
 int64_t plan_bytes_estimate(int64_t M, int N, double fov, double w_min, double w_max, int W = 7);
 // grid_tc.cu: tensor-core gridding (w-stacking plans); err_dev set to 1 if a bounded wait expired
 int launch_grid_tc(pc_plan_s* p, const float2* h, int* err_dev, cudaStream_t st);
+// grid_win.cu: CUDA-core gridding over plane windows, one CTA per tile (or
+// part of a heavy tile); w-stacking plans
+int launch_grid_win(pc_plan_s* p, const float2* h, cudaStream_t st);
+bool grid_win_mode(const pc_plan_s* p);   // the plan grids over plane windows
+// plan.cu: window gridding CTAs for at most `cap` slots each
+int split_wsubs(pc_plan_s* p, int cap, cudaStream_t st);
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st);
@@ -302,7 +308,8 @@ struct pc_plan_s {
   double fov = 0, dl = 0, beta = 0;
   double w0 = 0, dw = 1, s_c = 0, w_min = 0, w_max = 0;
   bool wstack = false;
-  int grid_mode = 0;  // 0 auto, 1 CUDA cores, 2 tensor cores (w-stacking only)
+  int grid_mode = 0;  // 0 auto, 1 CUDA cores, 2 tensor cores, 3 CUDA cores over plane
+                      // windows (2 and 3: w-stacking only; else mode 1 runs)
   int grid_piece = 0; // gridding sub-problem size in slots (0: chosen for even waves)
   int fft_R = 0;      // rows per CTA of the first FFT pass (0: 2048 / G)
   int fft_cols_pg = 0; // planes per pass of the second FFT pass (0: default)
@@ -311,7 +318,12 @@ struct pc_plan_s {
   bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
   bool want_tune = false; // the autotuner will run (it may pick the Stockham passes)
   double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0;
+  int Pw = 1;         // plane windows: pairs of plane starts ((P - W) >> 1) + 1 (1 without w-stacking)
   std::vector<int4> sub_ranges;   // (tile, plane group, first slot, end) before splitting
+  std::vector<int2> win_tiles;    // (tile, binned slots) of every tile that holds slots
+  int win_cap = 0;                // window gridding: slots per CTA before a tile is split
+  int n_wsub = 0;
+  int64_t wsub_cap = 0;           // capacity of wsubs (parts of at most 64 slots)
   int sub_cap = 0;                // capacity of subs (the finest split)
   int64_t n_slots = 0;
   int n_sub = 0;
@@ -322,6 +334,8 @@ struct pc_plan_s {
   int2* slot_vis = nullptr;      // {visibility, (a0 + 64) | (b0 + 64) << 8 | plane_start << 16}
   float4* slot_geom = nullptr;   // {gu - a0, gv - b0, xw - plane_start, tau (turns)}
   int4* subs = nullptr;          // gridding sub-problems {tile, plane group, start, end}
+  int* win_off = nullptr;        // first slot of each (tile, plane pair) bin (nT^2 Pw + 1)
+  int4* wsubs = nullptr;         // window gridding CTAs {tile, part, parts, slots}, heaviest first
   int* active_rows = nullptr;    // grid rows b that visibilities can reach (ascending)
   int n_active_rows = 0;
   // image-domain tables

@@ -106,11 +106,16 @@ __global__ void k_uvw_scan(const double* __restrict__ uvw, int64_t M,
   }
 }
 
+// Bins: (tile, pair of plane starts ps >> 1); within a bin the slots are
+// ordered by their tile-local row start b0 (then ps & 1). A sort key is
+// bin << 7 | (b0 + 8) << 1 | (ps & 1), b0 in [-(W - 1), T - 1].
 struct BinGeom {
   double dl, w0, dw, s_c;
   int G, T, nT, W, P;
-  unsigned nbins;
+  int Pw;           // plane-start pairs (plane windows): ((P - W) >> 1) + 1, or 1 without w-stacking
+  unsigned nbins;   // tiles x Pw
 };
+constexpr int kBinSubBits = 7;
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
@@ -151,11 +156,13 @@ __global__ void k_vis_prep(const double* __restrict__ uvw, int64_t M, BinGeom g,
   if (g.P > 1) ps = (int)ceil((w - g.w0) / g.dw - 0.5 * g.W);
   for (int c = 0; c < 4; ++c) {
     int ta = ta0 + (c & 1), tb = tb0 + (c >> 1);
-    unsigned key = g.nbins;
+    unsigned key = g.nbins << kBinSubBits;
     if (ta <= ta1 && tb <= tb1) {
       int tu = ((ta % g.nT) + g.nT) % g.nT;
       int tv = ((tb % g.nT) + g.nT) % g.nT;
-      key = (unsigned)((tv * g.nT + tu) * g.P + ps);
+      const unsigned bin = (unsigned)((tv * g.nT + tu) * g.Pw + (ps >> 1));
+      const unsigned b0l = (unsigned)(b0 - tb * g.T + 8);       // in [1, T + 7]
+      key = (bin << kBinSubBits) | (b0l << 1) | (unsigned)(ps & 1);
     }
     keys[4 * k + c] = key;
     ids[4 * k + c] = (unsigned)(4 * k + c);
@@ -259,8 +266,8 @@ __global__ void k_bin_offsets(const unsigned* __restrict__ keys, int64_t n, unsi
                               int* __restrict__ off) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j > n) return;
-  long long kcur = j < n ? (long long)keys[j] : (long long)nbins;
-  long long kprev = j == 0 ? -1 : (long long)keys[j - 1];
+  long long kcur = j < n ? (long long)(keys[j] >> kBinSubBits) : (long long)nbins;
+  long long kprev = j == 0 ? -1 : (long long)(keys[j - 1] >> kBinSubBits);
   for (long long b = kprev + 1; b <= kcur && b <= (long long)nbins; ++b) off[b] = (int)j;
 }
 
@@ -377,6 +384,27 @@ struct TmpBufs {
 
 // Splits every (tile, plane group) slot range into equal pieces of at most
 // `piece` slots (multiples of 64, the tensor-core stage) and uploads the list.
+// Window gridding CTAs: a tile whose slots exceed `cap` is split into equal
+// parts (each part takes its share of every plane window of the tile and adds
+// its tile to the grid); heaviest CTAs first, so the last wave holds the
+// light ones.
+int split_wsubs(pc_plan_s* p, int cap, cudaStream_t st) {
+  cap = std::max(cap, 64);
+  std::vector<int4> subs;
+  for (const int2& t : p->win_tiles) {
+    const int parts = ceil_div(t.y, cap);
+    for (int k = 0; k < parts; ++k) subs.push_back(make_int4(t.x, k, parts, ceil_div(t.y, parts)));
+  }
+  std::stable_sort(subs.begin(), subs.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+  if ((int64_t)subs.size() > p->wsub_cap) return fail(PC_ERR_CAPACITY, "plan: %zu window CTAs", subs.size());
+  p->n_wsub = (int)subs.size();
+  p->win_cap = cap;
+  if (!subs.empty())
+    PC_CUDA(cudaMemcpyAsync(p->wsubs, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaStreamSynchronize(st));   // the host vector goes out of scope
+  return PC_OK;
+}
+
 static int split_subs(pc_plan_s* p, int piece, cudaStream_t st) {
   std::vector<int4> subs;
   for (const int4& r : p->sub_ranges) {
@@ -434,13 +462,18 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   PC_LAUNCH_CHECK();
   const int user_mode = p->grid_mode;
   std::vector<int> modes = {user_mode};
-  if (user_mode == 0 && p->wstack) modes = {2, 1};
+  if (user_mode == 0 && p->wstack) modes = p->W <= 7 ? std::vector<int>{3, 2, 1} : std::vector<int>{2, 1};
   double best = 1e300;
-  int best_mode = user_mode, best_piece = p->grid_piece;
+  int best_mode = user_mode, best_piece = grid_win_mode(p) ? p->win_cap : p->grid_piece;
   for (int mode : modes) {
-    for (int piece : {256, 512, 1024, 2048, 4096}) {
+    p->grid_mode = mode;
+    const bool win = grid_win_mode(p);
+    // window gridding: slots per CTA before a tile is split; else the sub-problem size
+    const std::vector<int> pieces = win ? std::vector<int>{1024, 4096, 16384, 65536}
+                                        : std::vector<int>{256, 512, 1024, 2048, 4096};
+    for (int piece : pieces) {
       p->grid_mode = mode;
-      PC_TRY(split_subs(p, piece, st));
+      PC_TRY(win ? split_wsubs(p, piece, st) : split_subs(p, piece, st));
       double us = 0.0;
       PC_TRY(time_us(st, 3, [&] { return launch_grid(p, p->resid, st); }, &us));
       if (us < best) {
@@ -451,7 +484,7 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
     }
   }
   p->grid_mode = best_mode;
-  PC_TRY(split_subs(p, best_piece, st));
+  PC_TRY(grid_win_mode(p) ? split_wsubs(p, best_piece, st) : split_subs(p, best_piece, st));
   p->tune_grid_us = best;
   PC_TRY(launch_grid(p, p->resid, st));         // a gridded plane set for the FFT timing
   // first pass: the one-warp register FFT (where G allows it) against the
@@ -670,9 +703,10 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   }
 
   // ---- binning keys
-  const unsigned nbins = (unsigned)((int64_t)p->nT * p->nT * p->P);
-  if ((int64_t)p->nT * p->nT * p->P >= (1ll << 31))
-    return fail(PC_ERR_INVALID_ARG, "plan: too many (tile, plane) bins");
+  p->Pw = p->wstack ? ((p->P - p->W) >> 1) + 1 : 1;
+  const unsigned nbins = (unsigned)((int64_t)p->nT * p->nT * p->Pw);
+  if ((int64_t)p->nT * p->nT * p->Pw >= (1ll << (32 - kBinSubBits)))
+    return fail(PC_ERR_INVALID_ARG, "plan: too many (tile, plane pair) bins");
   const int64_t nkeys = 4 * M;
   unsigned *k0, *k1, *v0, *v1, *hist;
   int* off;
@@ -683,13 +717,13 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   const int nblk = ceil_div(nkeys, RS_ITEMS);
   PC_TRY(tmp.alloc((void**)&hist, sizeof(unsigned) * 256 * (size_t)nblk));
   PC_TRY(tmp.alloc((void**)&off, sizeof(int) * ((size_t)nbins + 1)));
-  BinGeom bg{p->dl, p->w0, p->dw, p->s_c, p->G, p->T, p->nT, p->W, p->P, nbins};
+  BinGeom bg{p->dl, p->w0, p->dw, p->s_c, p->G, p->T, p->nT, p->W, p->P, p->Pw, nbins};
   k_vis_prep<<<ceil_div(M, 256), 256, 0, st>>>(uvw, M, bg, p->vis_fx, k0, v0);
   PC_LAUNCH_CHECK();
 
   // ---- stable radix sort of the keys (values = slot ids)
   int nbits = 1;
-  while ((1ull << nbits) <= nbins) ++nbits;
+  while ((1ull << nbits) <= ((unsigned long long)nbins << kBinSubBits)) ++nbits;
   unsigned *kin = k0, *vin = v0, *kout = k1, *vout = v1;
   for (int shift = 0; shift < nbits; shift += 8) {
     k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(kin, nkeys, shift, hist, nblk);
@@ -728,13 +762,16 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   for (int t = 0; t < p->nT * p->nT; ++t) {
     for (int gq = 0; gq < ngroups; ++gq) {
       int q0 = gq * p->Qg;
+      // plane starts whose footprint meets the group, widened to whole pairs
+      // (the extra slots' footprints miss the group: zero weights there)
       int ps_lo = 0, ps_hi = 0;
       if (p->wstack) {
         ps_lo = std::max(0, q0 - p->W + 1);
-        ps_hi = std::min(p->P - 1, q0 + p->Qg - 1);
+        ps_hi = std::min(p->P - p->W, q0 + p->Qg - 1);
       }
-      int s0 = hoff[(size_t)t * p->P + ps_lo];
-      int s1 = hoff[(size_t)t * p->P + ps_hi + 1];
+      if (ps_hi < ps_lo) continue;
+      int s0 = hoff[(size_t)t * p->Pw + (ps_lo >> 1)];
+      int s1 = hoff[(size_t)t * p->Pw + (ps_hi >> 1) + 1];
       if (s1 > s0) {
         ranges.push_back(make_int4(t, gq, s0, s1));
         total_slots += s1 - s0;
@@ -758,6 +795,21 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   p->sub_cap = (int)(total_slots / 64 + (int64_t)ranges.size() + 1);
   PC_TRY(dev_alloc_t(p, &p->subs, (size_t)p->sub_cap));
   PC_TRY(split_subs(p, piece, st));
+  // window gridding: the bin offsets on the device, the tiles that hold slots,
+  // and the CTA list. Measured (2048^2 / 2M and 4096^2 / 10M): splitting a
+  // tile costs more than it balances once the tiles alone give eight CTAs per
+  // SM, so then only tiles beyond 65536 slots are split; with fewer tiles,
+  // parts of at most 4096 slots
+  PC_TRY(dev_alloc_t(p, &p->win_off, (size_t)nbins + 1));
+  PC_CUDA(cudaMemcpyAsync(p->win_off, off, sizeof(int) * ((size_t)nbins + 1), cudaMemcpyDeviceToDevice, st));
+  p->win_tiles.clear();
+  for (int t = 0; t < p->nT * p->nT; ++t) {
+    const int n = hoff[(size_t)(t + 1) * p->Pw] - hoff[(size_t)t * p->Pw];
+    if (n > 0) p->win_tiles.push_back(make_int2(t, n));
+  }
+  p->wsub_cap = p->n_slots / 64 + (int64_t)p->win_tiles.size() + 1;
+  PC_TRY(dev_alloc_t(p, &p->wsubs, (size_t)p->wsub_cap));
+  PC_TRY(split_wsubs(p, (int64_t)p->win_tiles.size() >= 8ll * n_sm ? 65536 : 4096, st));
   // grid rows that any visibility can reach: the rows of tile rows with a sub-problem
   {
     std::vector<char> row_on(p->nT, 0);
@@ -854,8 +906,8 @@ extern "C" int pc_plan_create(const double* uvw_dev, int64_t M, int32_t N, doubl
   if (T != 32) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: tile %d must be 32", T);
   if (maxP < 1 || maxP > 4096) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: max_planes %d", maxP);
   const int grid_mode = opts ? opts->grid_mode : 0;
-  if (grid_mode < 0 || grid_mode > 2)
-    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: grid_mode %d not in [0, 2]", grid_mode);
+  if (grid_mode < 0 || grid_mode > 3)
+    return fail(PC_ERR_INVALID_ARG, "pc_plan_create: grid_mode %d not in [0, 3]", grid_mode);
   const int tune = opts ? opts->autotune : 0;
   if (tune != 0 && tune != 1) return fail(PC_ERR_INVALID_ARG, "pc_plan_create: autotune must be 0 or 1");
   const int fft_kernel = opts ? opts->fft_kernel : 0;
@@ -886,8 +938,8 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
   clear_error();
   if (!p || !out) return fail(PC_ERR_INVALID_ARG, "pc_plan_tuning_info: NULL argument");
   out->tuned = p->tuned ? 1 : 0;
-  out->grid_mode = (p->wstack && p->grid_mode != 1) ? 2 : 1;
-  out->grid_piece = p->grid_piece;
+  out->grid_mode = grid_win_mode(p) ? 3 : (p->wstack && p->grid_mode != 1) ? 2 : 1;
+  out->grid_piece = grid_win_mode(p) ? p->win_cap : p->grid_piece;
   int R = p->fft_R > 0 ? p->fft_R : 2048 / p->G;
   const bool rw = fft_rows_warp(p) || fft_rows_big(p), cw = fft_cols_warp(p) || fft_cols_big(p);
   out->fft_rows_per_cta = fft_rows_big(p) ? 1 : rw ? 8 : std::min(std::max(R, 1), 32);

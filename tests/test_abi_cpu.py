@@ -56,7 +56,7 @@ def test_plan_create_rejects_bad_arguments_without_a_gpu():
     cases = [(dict(version=abi.PC_ABI_VERSION - 1), "version"), (dict(N=63), "N ="), (dict(N=8), "N ="),
              (dict(fov=0.0), "fov_rad"), (dict(fov=2.0), "fov_rad"), (dict(kernel_width=3), "kernel_width"),
              (dict(kernel_width=9), "kernel_width"), (dict(tile=16), "tile"), (dict(max_planes=5000), "max_planes"),
-             (dict(grid_mode=3), "grid_mode"), (dict(autotune=2), "autotune"), (dict(fft_kernel=2), "fft_kernel")]
+             (dict(grid_mode=4), "grid_mode"), (dict(autotune=2), "autotune"), (dict(fft_kernel=2), "fft_kernel")]
     for kw, needle in cases:
         rc, msg = create(**kw)
         assert rc == abi.PC_ERR_INVALID_ARG, (kw, rc, msg)

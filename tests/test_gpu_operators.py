@@ -58,11 +58,13 @@ def test_forward_sparse(abi, name, kw):
     assert rel_l2(y, ref) <= TOL
 
 
-@pytest.mark.parametrize("grid_mode", [1, 2])
+@pytest.mark.parametrize("grid_mode", [1, 2, 3])
 @pytest.mark.parametrize("name,kw", CASES)
 def test_adjoint_grid(abi, name, kw, grid_mode):
-    """Gridding on FP32 CUDA cores (1) and on the tensor cores with split-FP16
-    operands (2; w-stacked plans), then FFT and epilogue, against the direct sum."""
+    """Gridding on FP32 CUDA cores (1), on the tensor cores with split-FP16
+    operands (2; w-stacked plans) and on FP32 CUDA cores over plane windows
+    with one CTA per tile (3; w-stacked plans), then FFT and epilogue, against
+    the direct sum."""
     wl, V = workload(name, **kw)
     plan = _plan(abi, wl, grid_mode=grid_mode)
     img = abi.pc_adjoint_grid(plan, to_dev(V.astype(np.complex64))).cpu().numpy().ravel()
@@ -304,10 +306,11 @@ def test_empty_and_degenerate(abi):
         abi.pc_plan_create(to_dev(wl.uvw), 63, wl.fov)
 
 
-@pytest.mark.parametrize("grid_mode", [1, 2])
+@pytest.mark.parametrize("grid_mode", [1, 2, 3])
 def test_full_size_medium_sampled(abi, grid_mode):
     """The 512 x 512, M = 200k workload timed by the benchmark: operators on
-    seeded samples of pixels and visibilities."""
+    seeded samples of pixels and visibilities (window gridding splits the
+    heavy tiles near the uv origin into parts here)."""
     wl, V = workload("medium_512_w")
     plan = _plan(abi, wl, grid_mode=grid_mode)
     Vs = V.astype(np.complex64)
@@ -330,7 +333,8 @@ def test_autotuned_plan(abi):
     wl, V = workload("medium_512_w", M=60_000)
     plan = _plan(abi, wl, autotune=1)
     t = abi.pc_plan_tuning_info(plan)
-    assert t["tuned"] and t["grid_mode"] in (1, 2) and t["grid_piece"] in (256, 512, 1024)
+    assert t["tuned"] and t["grid_mode"] in (1, 2, 3)
+    assert t["grid_piece"] in ((1024, 4096, 16384, 65536) if t["grid_mode"] == 3 else (256, 512, 1024, 2048, 4096))
     assert t["fft_rows_per_cta"] in (1, 2, 4, 8, 16, 32)
     assert 0 < t["grid_us"] < 1e5 and 0 < t["fft_rows_us"] < 1e5
     assert t["fft_cols_planes"] in (1, 2, 4, 8) and 0 < t["fft_cols_us"] < 1e5
