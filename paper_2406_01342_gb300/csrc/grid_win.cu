@@ -16,7 +16,10 @@
 // row b = 4w + r for all 32 columns: 32 complex accumulators in registers.
 // Per chunk of 128 slots (every nc-th slot of the window's run, so that each
 // chunk samples all row starts and every warp finds work in it between two
-// block barriers) the CTA evaluates each slot's kernel weights into
+// block barriers; the chunks of all windows form one software pipeline whose
+// slot records and visibility values are loaded one and two chunks ahead,
+// so no global-memory latency falls between two barriers) the CTA evaluates
+// each slot's kernel weights into
 // shared memory (h phi_u at the W columns, phi_v padded with zeros, phi_w at
 // the window's planes); each warp then takes the contiguous run of slots whose
 // rows meet its four rows (read off the b0 order) and, per slot, adds
@@ -30,20 +33,16 @@
 // CTA owns the tile, vector reductions when the tile is split) and their ring
 // slots are cleared for planes 2j + 8 and 2j + 9. No waits, no atomics on
 // shared memory; every cell of a tile's planes is written once per part.
-#include "pc_internal.cuh"
+#include "grid_win.cuh"
 #include "grid_win_spread.inc"
 
 namespace pc {
 namespace {
 
-constexpr int GW_T = 32;                    // tile side (the plan's)
-constexpr int GW_Q = 8;                     // planes per window
-constexpr int GW_C = 128;                   // slots per chunk
-constexpr int GW_THREADS = 256;
-constexpr int GW_RS = GW_T + 1;             // ring row stride (float2): rows one bank pair apart
-constexpr int GW_PS = GW_RS * GW_T + 4;     // ring plane stride (float2): planes four bank pairs apart
-constexpr int GW_FV = 16;                   // padded phi_v entries per slot
-constexpr int GW_FIRST = 48;                // b0 + 8 lies in [1, 39]
+using gwin::pack2;
+using gwin::unpack2;
+constexpr int GW_T = gwin::T, GW_Q = gwin::Q, GW_C = gwin::C, GW_THREADS = gwin::THREADS;
+constexpr int GW_RS = gwin::RS, GW_PS = gwin::PS, GW_MAXW = gwin::MAXW;
 
 // Per-slot rows are padded by one 16-byte unit so that the vector stores of
 // 32 consecutive slots fall on distinct bank groups.
@@ -53,20 +52,14 @@ struct __align__(16) GwShared {
   float4 fv[GW_C][5];           // phi_v(i) at float entry i + 4, zeros elsewhere (+ pad)
   float4 fw[GW_C][3];           // phi_w at the window's 8 planes, 0 off the footprint (+ pad)
   int meta[GW_C];               // (a0 + 8) | (b0 + 8) << 8, tile-local footprint starts
-  int first[GW_FIRST];          // first chunk slot with b0 + 8 >= x (the chunk's count if none)
+  int2 wr[GW_MAXW];             // this CTA's slot range {first, count} in every window
+  int4 desc[4];                 // chunk descriptors n .. n + 3 (ring)
 };
 
 __device__ __forceinline__ void red_add_v4(float2* addr, float2 u, float2 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(u.x), "f"(u.y), "f"(v.x),
                "f"(v.y)
                : "memory");
-}
-
-__device__ __forceinline__ uint64_t pack2(float x, float y) {
-  return (uint64_t)__float_as_uint(x) | ((uint64_t)__float_as_uint(y) << 32);
-}
-__device__ __forceinline__ float2 unpack2(uint64_t v) {
-  return make_float2(__uint_as_float((uint32_t)v), __uint_as_float((uint32_t)(v >> 32)));
 }
 
 // acc[a0 + i] += t * hu[i] for the tile columns a0 + i, i < W: one packed
@@ -129,75 +122,102 @@ k_grid_win(const int4* __restrict__ subs, const int* __restrict__ win_off, const
   const int tu = tile % nT, tv = tile / nT;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = lane >> 2, r = lane & 3, b = 4 * warp + r;
+  const int k = tid & (GW_C - 1), role = tid >> 7;     // prep: slot k, role 0 h phi_u, role 1 phi_v, phi_w
   const float two_over_w = 2.0f / W;
   const size_t GG = (size_t)G * G;
   float2* const tile_base = grid + (size_t)(tv * GW_T) * G + tu * GW_T;
   const bool owner = parts == 1;
 
+  // this part's slot range of every window, the first chunks, the ring cleared
   for (int e = tid; e < GW_Q * GW_PS; e += GW_THREADS) S.ring[e] = make_float2(0.f, 0.f);
+  gwin::schedule(win_off, tile, part, parts, Pw, S.wr, S.desc);
+  {
+    // planes before the first window with slots stay zero
+    const int j0 = S.desc[0].x;
+    planes_out(S, 0, j0 < 0 ? P : 2 * j0, tile_base, GG, G, owner);
+  }
+
   uint64_t acc[GW_T];          // column accumulators, packed (Re, Im)
 #pragma unroll
   for (int c = 0; c < GW_T; ++c) acc[c] = 0ull;
 
-  for (int j = 0; j < Pw; ++j) {
-    const int q0 = 2 * j;
-    const int bs = __ldg(win_off + (size_t)tile * Pw + j), be = __ldg(win_off + (size_t)tile * Pw + j + 1);
-    const long long len = be - bs;
-    const int s0 = bs + (int)(len * part / parts), s1 = bs + (int)(len * (part + 1) / parts);
-    // chunk c takes every nc-th slot from s0 + c: a sample of the whole b0
-    // range (so every warp finds rows in every chunk), still in b0 order
-    const int L = s1 - s0, nc = (L + GW_C - 1) / GW_C;
-    for (int c = 0; c < nc; ++c) {
-      const int cnt = (L - c + nc - 1) / nc;
-      __syncthreads();   // the previous chunk's readers (and the ring clear) are done
-      // ---- weights of one slot per thread pair: role 0 h phi_u, role 1 phi_v and phi_w
+  // registers of the software pipeline: slot records of chunk n (c) and n + 1
+  // (n), the visibility value of chunk n + 1, the slot record of chunk n + 2
+  int2 sv_c = make_int2(0, 0), sv_n = make_int2(0, 0);
+  float4 gm_c = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 h_c = make_float2(0.f, 0.f);
+  {
+    const int4 d0 = S.desc[0], d1 = S.desc[1];
+    if (d0.x >= 0 && k < d0.w) {
+      const int jj = d0.y + d0.z * k;
+      sv_c = slot_vis[jj];
+      gm_c = slot_geom[jj];
+      if (role == 0) h_c = h[sv_c.x];
+    }
+    if (d1.x >= 0 && k < d1.w) sv_n = slot_vis[d1.y + d1.z * k];
+  }
+
+  for (int n = 0;; ++n) {
+    const int4 D = S.desc[n & 3], Dn = S.desc[(n + 1) & 3], Dnn = S.desc[(n + 2) & 3];
+    if (D.x < 0) break;
+    // ---- prefetch: the rest of chunk n + 1 and the slot records of chunk n + 2
+    float4 gm_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 h_n = make_float2(0.f, 0.f);
+    int2 sv_nn = make_int2(0, 0);
+    if (Dn.x >= 0 && k < Dn.w) {
+      gm_n = slot_geom[Dn.y + Dn.z * k];
+      if (role == 0) h_n = h[sv_n.x];
+    }
+    if (Dnn.x >= 0 && k < Dnn.w) sv_nn = slot_vis[Dnn.y + Dnn.z * k];
+    // ---- weights of chunk n (slot k): role 0 h phi_u and the footprint starts,
+    //      role 1 phi_v; phi_w at the window's planes split between the roles
+    const int q0 = 2 * D.x;
+    if (k < D.w) {
+      const int a0 = (sv_c.y & 0xff) - 64, b0 = ((sv_c.y >> 8) & 0xff) - 64;
+      if (role == 0) {
+        float sn, cs;
+        sincospif(2.0f * gm_c.w, &sn, &cs);
+        const float2 hv = cmul(h_c, make_float2(cs, sn));
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float f0 = 2 * m < W ? es_kernel((2 * m - gm_c.x) * two_over_w, beta) : 0.f;
+          const float f1 = 2 * m + 1 < W ? es_kernel((2 * m + 1 - gm_c.x) * two_over_w, beta) : 0.f;
+          S.hu[k][m] = make_float4(hv.x * f0, hv.y * f0, hv.x * f1, hv.y * f1);
+        }
+        S.meta[k] = (a0 + 8) | ((b0 + 8) << 8);
+      }
       {
-        const int k = tid & (GW_C - 1), role = tid >> 7;
-        if (k < cnt) {
-          const int jj = s0 + c + nc * k;
-          const int2 sv = slot_vis[jj];
-          const float4 gm = slot_geom[jj];
-          const int a0 = (sv.y & 0xff) - 64, b0 = ((sv.y >> 8) & 0xff) - 64;
-          if (role == 0) {
-            float2 hv = h[sv.x];
-            float sn, cs;
-            sincospif(2.0f * gm.w, &sn, &cs);
-            hv = cmul(hv, make_float2(cs, sn));
-            float f[8];
+        // phi_w at planes 4 role .. 4 role + 3 of the window (the roles share it)
+        const int d = (sv_c.y >> 16) - q0;             // 0 or 1
+        float g[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) f[i] = i < W ? es_kernel((i - gm.x) * two_over_w, beta) : 0.f;
+        for (int e = 0; e < 4; ++e) {
+          const int qq = 4 * role + e, cw = qq - d;
+          g[e] = (cw >= 0 && cw < W && q0 + qq < P) ? es_kernel((cw - gm_c.z) * two_over_w, beta) : 0.f;
+        }
+        S.fw[k][role] = make_float4(g[0], g[1], g[2], g[3]);
+      }
+      if (role == 1) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
-              S.hu[k][m] = make_float4(hv.x * f[2 * m], hv.y * f[2 * m], hv.x * f[2 * m + 1], hv.y * f[2 * m + 1]);
-            S.meta[k] = (a0 + 8) | ((b0 + 8) << 8);
-            // first-slot table of the chunk's b0 order (ascending within a bin)
-            const int v = b0 + 8;
-            const int pv = k > 0 ? ((slot_vis[jj - nc].y >> 8) & 0xff) - 64 + 8 : -1;
-            for (int x = pv + 1; x <= v; ++x) S.first[x] = k;
-            if (k == cnt - 1)
-              for (int x = v + 1; x < GW_FIRST; ++x) S.first[x] = cnt;
-          } else {
-            float f[GW_FV];
+        for (int m = 0; m < 4; ++m) {
+          float f[4];
 #pragma unroll
-            for (int i = 0; i < GW_FV; ++i)
-              f[i] = (i >= 4 && i < 4 + W) ? es_kernel(((i - 4) - gm.y) * two_over_w, beta) : 0.f;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) S.fv[k][m] = make_float4(f[4 * m], f[4 * m + 1], f[4 * m + 2], f[4 * m + 3]);
-            const int d = (sv.y >> 16) - q0;             // 0 or 1
-            float g[GW_Q];
-#pragma unroll
-            for (int qq = 0; qq < GW_Q; ++qq) {
-              const int cw = qq - d;
-              g[qq] = (cw >= 0 && cw < W && q0 + qq < P) ? es_kernel((cw - gm.z) * two_over_w, beta) : 0.f;
-            }
-            S.fw[k][0] = make_float4(g[0], g[1], g[2], g[3]);
-            S.fw[k][1] = make_float4(g[4], g[5], g[6], g[7]);
+          for (int e = 0; e < 4; ++e) {
+            const int i = 4 * m + e - 4;
+            f[e] = (i >= 0 && i < W) ? es_kernel((i - gm_c.y) * two_over_w, beta) : 0.f;
           }
+          S.fv[k][m] = make_float4(f[0], f[1], f[2], f[3]);
         }
       }
-      __syncthreads();
-      // ---- the slots whose rows meet this warp's rows [4w, 4w + 4)
-      const int lo = S.first[4 * warp - W + 9], hi = S.first[4 * warp + 12];
+    } else if (role == 0 && k < GW_C) {
+      S.meta[k] = 0x7fff0000;                          // beyond every warp's rows
+    }
+    if (tid == 0) S.desc[(n + 3) & 3] = gwin::chunk_after(S.wr, Pw, Dnn);
+    __syncthreads();
+    // ---- this warp's run of slots: rows meeting [4w, 4w + 4), from the b0 order
+    {
+      const int2 run = gwin::warp_run<W>(S.meta, warp, lane);
+      const int lo = run.x, hi = run.y;
 #pragma unroll 1
       for (int jj = lo; jj < hi; ++jj) {
         const int m = S.meta[jj];
@@ -212,8 +232,9 @@ k_grid_win(const int4* __restrict__ subs, const int* __restrict__ win_off, const
         spread<W>(acc, hu, pack2(t, t), a0 + W - 1);
       }
     }
-    if (s1 > s0) {
-      // ---- the window's accumulators into the ring (cell (q0 + q, b, *) is this lane's)
+    if (Dn.x != D.x) {
+      // ---- window D.x ends: its accumulators into the ring (cell (q0 + q, b, *)
+      //      is this lane's), then the planes no later window reaches leave
       if (q0 + q < P) {
         float2* row = S.ring + ((q0 + q) & (GW_Q - 1)) * GW_PS + b * GW_RS;
 #pragma unroll
@@ -221,13 +242,15 @@ k_grid_win(const int4* __restrict__ subs, const int* __restrict__ win_off, const
       }
 #pragma unroll
       for (int c = 0; c < GW_T; ++c) acc[c] = 0ull;
+      __syncthreads();
+      planes_out(S, q0, Dn.x < 0 ? P : 2 * Dn.x, tile_base, GG, G, owner);
     }
-    __syncthreads();
-    // ---- planes 2j and 2j + 1 are final (later windows start at 2j + 2)
-    planes_out(S, q0, min(q0 + 2, P), tile_base, GG, G, owner);
+    __syncthreads();   // chunk n's readers are done before chunk n + 1's weights overwrite
+    sv_c = sv_n;
+    gm_c = gm_n;
+    h_c = h_n;
+    sv_n = sv_nn;
   }
-  __syncthreads();
-  planes_out(S, 2 * Pw, P, tile_base, GG, G, owner);
 }
 
 }  // namespace
@@ -237,13 +260,14 @@ k_grid_win(const int4* __restrict__ subs, const int* __restrict__ win_off, const
 // 1.31 ms; 4096^2 / 10M: 2.8 against 4.9 ms; at 512^2 / 200k the tensor cores
 // win, 0.10 against 0.15 ms).
 bool grid_win_mode(const pc_plan_s* p) {
-  return p->wstack && p->W <= 7 && (p->grid_mode == 3 || (p->grid_mode == 0 && p->G >= 2048));
+  return p->wstack && p->W <= 7 && p->Pw <= GW_MAXW && (p->grid_mode == 3 || (p->grid_mode == 0 && p->G >= 2048));
 }
 
 int launch_grid_win(pc_plan_s* p, const float2* h, cudaStream_t st) {
   if (p->n_wsub == 0) return PC_OK;
-  if (!p->wstack || p->W > 7 || p->T != GW_T)
-    return fail(PC_ERR_INVALID_ARG, "window gridding: needs w-stacking, W <= 7 and 32-cell tiles");
+  if (!p->wstack || p->W > 7 || p->T != GW_T || p->Pw > GW_MAXW)
+    return fail(PC_ERR_INVALID_ARG, "window gridding: needs w-stacking, W <= 7, 32-cell tiles, <= %d windows",
+                GW_MAXW);
   const int smem = (int)sizeof(GwShared);
   const float beta = (float)p->beta;
 #define PC_GW_LAUNCH(WW)                                                                                  \
