@@ -222,6 +222,19 @@ def reach_cells(info, reach):
     return float(reach["rows"]) * 32.0 * reach["col_groups"]
 
 
+# FP32 FMA peak of one GB300: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (unit
+# counts and the maximum SM clock)
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def gridding_flops(M, info):
+    """FP32 flops of one gridding: per visibility and footprint cell (W x W x
+    W cells with w-stacking, W x W without) a complex value times a real
+    weight added to a complex accumulator (2 FMA = 4 flops)."""
+    W = info["kernel_width"]
+    return 4.0 * M * W * W * (W if info["n_planes"] > 1 else 1)
+
+
 def gridding_roofline(prof, info, wl, peaks, reach=None):
     """Gridding (all launches in the timed region: grid clear + spread) against
     the HBM roofline. Algorithmic bytes per launch: 20 B per visibility
@@ -237,9 +250,13 @@ def gridding_roofline(prof, info, wl, peaks, reach=None):
     b_full = 20.0 * wl.M + 8.0 * P * G * G
     hbm = peaks.get("hbm_gbs", 6800.0)
     ach = b / (avg_ms * 1e-3) / 1e9
+    f = gridding_flops(wl.M, info)
     return {"avg_launch_ms": avg_ms, "launches": launches, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "bytes_per_launch": b, "vis_per_s": wl.M / (avg_ms * 1e-3),
-            "bytes_full_planes": b_full, "frac_full_planes": b_full / (avg_ms * 1e-3) / 1e9 / hbm}
+            "bytes_full_planes": b_full, "frac_full_planes": b_full / (avg_ms * 1e-3) / 1e9 / hbm,
+            "alu_flops_per_launch": f, "alu_achieved_tflops": f / (avg_ms * 1e-3) / 1e12,
+            "alu_peak_tflops": FP32_TFLOPS, "alu_frac": f / (avg_ms * 1e-3) / 1e12 / FP32_TFLOPS,
+            "binding": "alu"}
 
 
 def degridding_leg(abi, torch, plan, wl, info, peaks, steps, l2_flush) -> dict:
@@ -295,10 +312,11 @@ def roofline(prof, info, wl, history, steps, peaks, dom, reach=None):
     rows = float(reach["rows"]) if reach else float(G)
     out = {"kernel": dom, "avg_launch_ms": avg_ms, "launches": launches}
     if dom == "grid":
-        # 20 B per visibility (complex64 residual + three float32 coordinates)
-        # + the reachable grid cells written once
-        b = 20.0 * M + 8.0 * P * cells
-        out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+        # the FP32 FMAs of the spread (gridding_flops) against the FP32 peak: the
+        # bytes (20 B per visibility + the reachable cells once) are far below
+        # the HBM roofline (gridding_roofline reports both)
+        f = gridding_flops(M, info)
+        out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=FP32_TFLOPS, unit="TFLOP/s")
     elif dom == "degrid":
         # the image read, the reachable grid written (second FFT pass) and read
         # (interpolation), one complex64 per visibility written
@@ -328,8 +346,7 @@ def roofline(prof, info, wl, history, steps, peaks, dom, reach=None):
         out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
     elif dom in ("gram_fp32", "gram_thin"):
         f = sum(4.0 * M * h["n_new"] * h["n_active"] for h in history) * steps / max(launches, 1)
-        fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
-        out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=fp32, unit="TFLOP/s")
+        out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=FP32_TFLOPS, unit="TFLOP/s")
     elif dom == "residual":
         pairs = sum(M * h["n_support"] for h in history) * steps / max(launches, 1)
         out.update(bound="alu", achieved=pairs / (avg_ms * 1e-3) / 1e9, peak=None,

@@ -39,7 +39,7 @@ def test_tensor_core_iterations_and_phase_bytes():
 
 def test_roofline_arithmetic():
     wl = types.SimpleNamespace(M=200_000, N=512)
-    info = {"grid_side": 1024, "n_planes": 8}
+    info = {"grid_side": 1024, "n_planes": 8, "kernel_width": 7}
     hist = [{"n_new": 873, "n_active": 873, "n_support": 176, "apgd_iterations": 18}]
     peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0}
     steps = 5
@@ -57,6 +57,14 @@ def test_roofline_arithmetic():
     assert g["bytes_per_launch"] == 20.0 * wl.M + 8.0 * 8 * 1024 * 1024
     assert g["avg_launch_ms"] == pytest.approx(0.1)
     assert g["vis_per_s"] == pytest.approx(wl.M / 0.1e-3)
+    # the spread's FP32 work: a complex value times a real weight (2 FMA) per
+    # footprint cell, W^3 cells with w-stacking, W^2 without
+    assert g["alu_flops_per_launch"] == 4.0 * wl.M * 7 ** 3
+    assert g["alu_frac"] == pytest.approx(4.0 * wl.M * 343 / 0.1e-3 / 1e12 / (152 * 128 * 2 * 2.07e9 / 1e12))
+    r = bench.roofline(prof, info, wl, hist, steps, peaks, "grid")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(g["alu_achieved_tflops"])
+    assert bench.gridding_flops(wl.M, dict(info, n_planes=1)) == 4.0 * wl.M * 49
 
 
 def test_traffic_record_needs_the_profiled_sources(tmp_path, monkeypatch):
