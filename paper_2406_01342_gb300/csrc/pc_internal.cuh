@@ -373,7 +373,6 @@ struct pc_plan_s {
   int xmap_by = 0, xmap_boxes = 0;  // its box height and boxes per plane
   pc::DevBuf opw;                   // operator-form reweighting: images, visibilities, vectors
   pc::DevBuf dirty;                 // operator-form reweighting: Re Phi* V of the solve (N x N)
-  pc::DevBuf ritz;                  // operator-form reweighting: the last top Ritz vector (N x N image)
   double op_pair_s = 0.0;           // measured time of one degridding + gridding pair (0: not yet)
   // While the operator-form reweighting runs, the image rows holding its atoms
   // (list and bit mask, n_img_rows > 0): the one-CTA passes of G >= 2048 then

@@ -978,7 +978,6 @@ extern "C" void pc_plan_destroy(pc_plan_t p) {
   p->xc.release();
   p->opw.release();
   p->dirty.release();
-  p->ritz.release();
   if (p->dict) {
     p->dict->release();
     delete p->dict;

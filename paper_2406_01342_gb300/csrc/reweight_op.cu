@@ -39,7 +39,7 @@ constexpr float LZ_TOL_OP = 1e-3f;
 struct OpState {
   float L;          // step size 1.01 x top Ritz value (valid once lz_done)
   float t;          // FISTA momentum
-  int min_steps;    // Lanczos steps before the stop test applies (fewer from a Ritz start)
+  float theta_prev; // unused (kept for layout)
   int lz_m;         // Lanczos steps taken
   int lz_done;
   int it;           // FISTA iterations taken
@@ -107,7 +107,7 @@ __global__ void k_lz_init(float* __restrict__ v, float* __restrict__ vprev, int 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s->L = 1.f;
     s->t = 1.f;
-    s->min_steps = 8;
+    s->theta_prev = 0.f;
     s->lz_m = 0;
     s->lz_done = 0;
     s->it = 0;
@@ -138,119 +138,28 @@ __global__ void __launch_bounds__(OP_THREADS) k_lz_init_dirty(const float* __res
   if (threadIdx.x == 0) {
     s->L = 1.f;
     s->t = 1.f;
-    s->min_steps = 8;
+    s->theta_prev = 0.f;
     s->lz_m = 0;
     s->lz_done = 0;
     s->it = 0;
     s->done = 0;
-  }
-}
-
-// Lanczos start vector from the top Ritz vector of the previous operator-form
-// reweighting of the same solve (an image holding it at that active set):
-// the new active set keeps most of those atoms, so the Hessian's top
-// eigenvector moves little and the Ritz value settles after a few steps (the
-// stop test may then apply from step 5). Falls back to b_S (k_lz_init_dirty's
-// start) when the previous vector has no weight on the new set.
-__global__ void __launch_bounds__(OP_THREADS) k_lz_init_ritz(const float* __restrict__ ritz,
-                                                             const float* __restrict__ dirty,
-                                                             const int32_t* __restrict__ idx, int n,
-                                                             float* __restrict__ v, float* __restrict__ vprev,
-                                                             OpState* __restrict__ s) {
-  __shared__ float red[32 * 2 + 2];
-  float a[2] = {0.f, 0.f};
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int p = idx[i];
-    const float r = ritz[p], b = dirty[p];
-    v[i] = r;
-    vprev[i] = b;                                       // b_S held here until the choice
-    a[0] = fmaf(r, r, a[0]);
-    a[1] = fmaf(b, b, a[1]);
-  }
-  block_sums<2>(a, red);
-  const bool use_r = a[0] > 0.f && isfinite(a[0]);
-  const bool use_b = a[1] > 0.f && isfinite(a[1]);
-  const float sr = use_r ? rsqrtf(a[0]) : 0.f, sb = use_b ? rsqrtf(a[1]) : 0.f, v0 = rsqrtf((float)n);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    v[i] = use_r ? v[i] * sr : use_b ? vprev[i] * sb : v0;
-    vprev[i] = 0.f;
-  }
-  if (threadIdx.x == 0) {
-    s->L = 1.f;
-    s->t = 1.f;
-    s->min_steps = use_r ? 5 : 8;
-    s->lz_m = 0;
-    s->lz_done = 0;
-    s->it = 0;
-    s->done = 0;
-  }
-}
-
-// The top Ritz vector y = Q s of the finished Lanczos run (Q the stored basis,
-// s the top eigenvector of the tridiagonal matrix by three steps of inverse
-// iteration at a shift just above the top Ritz value, where T - shift I is
-// negative definite and the elimination without pivoting is stable), written
-// into the Ritz image at the active set (cleared by the caller before).
-__global__ void __launch_bounds__(OP_THREADS) k_lz_ritz(const float* __restrict__ Q, int nn, int n,
-                                                        const int32_t* __restrict__ idx,
-                                                        const OpState* __restrict__ st, float* __restrict__ ritz) {
-  __shared__ float s_vec[LZ_MAX];
-  const int m = st->lz_m;
-  if (m <= 0) return;
-  if (threadIdx.x == 0) {
-    const double theta = st->th[m - 1];
-    const double shift = theta > 0.0 ? theta * (1.0 + 1e-4) + 1e-30 : 1e-30;
-    double x[LZ_MAX], cp[LZ_MAX], dp[LZ_MAX];
-    for (int i = 0; i < m; ++i) x[i] = 1.0;
-    for (int rep = 0; rep < 3; ++rep) {
-      // (T - shift I) y = x by elimination, then x = y / ||y||
-      double den = (double)st->al[0] - shift;
-      cp[0] = m > 1 ? (double)st->be[0] / den : 0.0;
-      dp[0] = x[0] / den;
-      for (int i = 1; i < m; ++i) {
-        const double bl = st->be[i - 1];
-        den = ((double)st->al[i] - shift) - bl * cp[i - 1];
-        cp[i] = i + 1 < m ? (double)st->be[i] / den : 0.0;
-        dp[i] = (x[i] - bl * dp[i - 1]) / den;
-      }
-      x[m - 1] = dp[m - 1];
-      for (int i = m - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
-      nrm = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-      for (int i = 0; i < m; ++i) x[i] *= nrm;
-    }
-    for (int i = 0; i < m; ++i) s_vec[i] = isfinite(x[i]) ? (float)x[i] : 0.f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float y = 0.f;
-    for (int j = 0; j < m; ++j) y = fmaf(s_vec[j], Q[(size_t)j * nn + i], y);
-    ritz[idx[i]] = y;
   }
 }
 
 // One Lanczos step on w = G v_j: alpha = v.w, w -= alpha v_j + beta_{j-1} v_{j-1},
 // beta = ||w||, v_{j+1} = w / beta. The stop test is the Gram kernels' (the
 // top Ritz value changed by at most LZ_TOL over the last 4 steps, from step 8
-// on; from step 5 after a Ritz start), evaluated after every step rather than
-// every fourth: each step costs an operator pair here, the Ritz value a few
-// microseconds. v_j is kept in Q for the Ritz vector.
+// on), evaluated after every step rather than every fourth: each step costs
+// an operator pair here, the Ritz value a few microseconds.
 __global__ void __launch_bounds__(OP_THREADS) k_lz_step(float* __restrict__ w, float* __restrict__ v,
-                                                        float* __restrict__ vprev, int n, OpState* __restrict__ s,
-                                                        float* __restrict__ Q, int nn) {
+                                                        float* __restrict__ vprev, int n, OpState* __restrict__ s) {
   __shared__ float red[32 * 2 + 2];
   __shared__ float s_theta;
   if (s->lz_done) return;
   const int j = s->lz_m;
   const float beta_prev = j > 0 ? s->be[j - 1] : 0.f;
   float a[1] = {0.f};
-  float* qj = Q + (size_t)j * nn;                     // the basis vector v_j, kept for the Ritz vector
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float vi = v[i];
-    qj[i] = vi;
-    a[0] = fmaf(vi, w[i], a[0]);
-  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[0] = fmaf(v[i], w[i], a[0]);
   block_sums<1>(a, red);
   const float alpha = a[0];
   float b[1] = {0.f};
@@ -269,7 +178,7 @@ __global__ void __launch_bounds__(OP_THREADS) k_lz_step(float* __restrict__ w, f
   const int m = j + 1;
   const bool last = (m == n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
   const float theta = tridiag_top(s->al, s->be, m, &s_theta);
-  const bool stop = last || (m >= s->min_steps && fabsf(theta - s->th[m - 5]) <= LZ_TOL_OP * fabsf(theta));
+  const bool stop = last || (m >= 8 && fabsf(theta - s->th[m - 5]) <= LZ_TOL_OP * fabsf(theta));
   __syncthreads();
   if (threadIdx.x == 0) {
     s->th[j] = theta;
@@ -358,8 +267,6 @@ struct OpWork {
   float* cimg;    // N^2, adjoint output
   float2* yv;     // M
   float *v, *vprev, *w, *y, *gy, *z, *gz, *gx;   // n each
-  float* Q;           // LZ_MAX x nn: the Lanczos basis
-  int nn;             // row stride of Q (n rounded up to 64)
   OpState* s;
   int* rows;          // N: image rows holding atoms (ascending), then their count
   int* row_count;
@@ -405,7 +312,7 @@ int op_workspace(pc_plan_s* p, int n, OpWork* w, cudaStream_t st) {
   const size_t nn = (size_t)((n + 63) / 64) * 64;
   const size_t rows_words = (size_t)(p->N + 31) / 32;
   const size_t bytes = sizeof(float) * 2 * NN + sizeof(float2) * (size_t)std::max<int64_t>(p->M, 1) +
-                       sizeof(float) * (8 + LZ_MAX) * nn + sizeof(OpState) + sizeof(int) * ((size_t)p->N + 4) +
+                       sizeof(float) * 8 * nn + sizeof(OpState) + sizeof(int) * ((size_t)p->N + 4) +
                        sizeof(uint32_t) * rows_words + 512;
   const bool fresh = p->opw.bytes < bytes;
   PC_TRY(p->opw.ensure(bytes));
@@ -416,9 +323,7 @@ int op_workspace(pc_plan_s* p, int n, OpWork* w, cudaStream_t st) {
   float* f = reinterpret_cast<float*>(w->yv + std::max<int64_t>(p->M, 1));
   float** vecs[8] = {&w->v, &w->vprev, &w->w, &w->y, &w->gy, &w->z, &w->gz, &w->gx};
   for (int k = 0; k < 8; ++k) *vecs[k] = f + k * nn;
-  w->Q = f + 8 * nn;
-  w->nn = (int)nn;
-  w->s = reinterpret_cast<OpState*>(f + (8 + LZ_MAX) * nn);
+  w->s = reinterpret_cast<OpState*>(f + 8 * nn);
   w->rows = reinterpret_cast<int*>(reinterpret_cast<char*>(w->s) + ((sizeof(OpState) + 15) / 16) * 16);
   w->row_count = w->rows + p->N;
   w->row_bits = reinterpret_cast<uint32_t*>(w->row_count + 4);
@@ -493,7 +398,7 @@ int op_pair_seconds(pc_plan_s* p, cudaStream_t st, double* out) {
 
 int run_operator_apgd(pc_plan_s* p, const float2* V, const float* dirty, const int32_t* idx, int n,
                       double lambda, double eps, int max_iter, bool positive, float* x, int* iters_dev,
-                      double* L_dev, int* lz_dev, cudaStream_t st, bool ritz_start) {
+                      double* L_dev, int* lz_dev, cudaStream_t st) {
   if (n <= 0) return PC_OK;
   OpWork w;
   PC_TRY(op_workspace(p, n, &w, st));
@@ -532,26 +437,15 @@ int run_operator_apgd(pc_plan_s* p, const float2* V, const float* dirty, const i
                                                 : fail(PC_ERR_CUDA, "reweighting: %s",
                                                        cudaGetErrorString(cudaGetLastError()));
   };
-  // the Ritz image: the previous reweighting's top Ritz vector at its active set
-  const size_t NN = (size_t)p->N * p->N;
-  if (dirty) PC_TRY(p->ritz.ensure(sizeof(float) * NN));
-  float* ritz = dirty ? p->ritz.as<float>() : nullptr;
-  if (dirty && ritz_start)
-    PC_TRY(book([&] { k_lz_init_ritz<<<1, OP_THREADS, 0, st>>>(ritz, dirty, idx, n, w.v, w.vprev, w.s); }));
-  else if (dirty)
+  if (dirty)
     PC_TRY(book([&] { k_lz_init_dirty<<<1, OP_THREADS, 0, st>>>(dirty, idx, n, w.v, w.vprev, w.s); }));
   else
     PC_TRY(book([&] { k_lz_init<<<gb, 256, 0, st>>>(w.v, w.vprev, n, w.s); }));
   for (int j = 0; j < LZ_MAX; ++j) {
     PC_TRY(op_apply(p, w, nullptr, idx, n, w.v, w.w, st));
-    PC_TRY(book([&] { k_lz_step<<<1, OP_THREADS, 0, st>>>(w.w, w.v, w.vprev, n, w.s, w.Q, w.nn); }));
+    PC_TRY(book([&] { k_lz_step<<<1, OP_THREADS, 0, st>>>(w.w, w.v, w.vprev, n, w.s); }));
     PC_TRY(read_flag(&w.s->lz_done, st, &flag));
     if (flag) break;
-  }
-  if (ritz) {
-    // this run's top Ritz vector, the next operator-form reweighting's start
-    PC_CUDA(cudaMemsetAsync(ritz, 0, sizeof(float) * NN, st));
-    PC_TRY(book([&] { k_lz_ritz<<<1, OP_THREADS, 0, st>>>(w.Q, w.nn, n, idx, w.s, ritz); }));
   }
   const float lam = (float)lambda;
   PC_TRY(op_apply(p, w, V, idx, n, x, w.gx, st));                // g(x) at the warm start

@@ -876,13 +876,8 @@ int SolveJob::run_apgd_op() {
     PC_TRY(adjoint_grid_impl(p, V, p->dirty.as<float>(), 1.0f, nullptr, st));
     dirty_ready = true;
   }
-  // Lanczos starts from the previous operator-form reweighting's top Ritz
-  // vector of this solve when there is one, else from b_S
-  PC_TRY(run_operator_apgd(p, V, p->dirty.as<float>(), p->idxB.as<int32_t>(), n_act, lambda, eps, c.apgd_max,
-                           c.positive != 0, p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->iscal + 5, st,
-                           ritz_ready));
-  ritz_ready = true;
-  return PC_OK;
+  return run_operator_apgd(p, V, p->dirty.as<float>(), p->idxB.as<int32_t>(), n_act, lambda, eps, c.apgd_max,
+                           c.positive != 0, p->xB.as<float>(), p->iscal + 2, p->dscal + 2, p->iscal + 5, st);
 }
 
 ApgdJob SolveJob::apgd_job() const {

@@ -41,7 +41,7 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out);
 // dirty (N x N, may be null): Re Phi* V, whose values at idx start Lanczos.
 int run_operator_apgd(pc_plan_s* p, const float2* V, const float* dirty, const int32_t* idx, int n,
                       double lambda, double eps, int max_iter, bool positive, float* x, int* iters_dev,
-                      double* L_dev, int* lz_dev, cudaStream_t st, bool ritz_start = false);
+                      double* L_dev, int* lz_dev, cudaStream_t st);
 // Measured seconds of one degridding + gridding pair on this plan (cached).
 int op_pair_seconds(pc_plan_s* p, cudaStream_t st, double* out);
 
@@ -71,8 +71,6 @@ struct SolveJob {
   bool op_form = false;
   bool gram_valid = true;               // GA holds G of the support (false after an operator-form step)
   bool dirty_ready = false;             // the plan's dirty image holds Re Phi* V of this solve
-  bool ritz_ready = false;              // the plan's Ritz image holds this solve's last operator-form
-                                        // Lanczos vector (the next one starts from it)
   int last_apgd_iters = 0;
   int n_act = 0, ldB = 4;
   double eps = 0.0;
