@@ -44,7 +44,7 @@ struct OpState {
   int lz_done;
   int it;           // FISTA iterations taken
   int done;
-  int pad;
+  int backtracks;   // FISTA steps rejected because L was below the curvature along them
   float al[LZ_MAX], be[LZ_MAX];
   float th[LZ_MAX];  // top Ritz value after each step
 };
@@ -111,6 +111,7 @@ __global__ void k_lz_init(float* __restrict__ v, float* __restrict__ vprev, int 
     s->lz_m = 0;
     s->lz_done = 0;
     s->it = 0;
+    s->backtracks = 0;
     s->done = 0;
   }
 }
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(OP_THREADS) k_lz_init_dirty(const float* __res
     s->lz_m = 0;
     s->lz_done = 0;
     s->it = 0;
+    s->backtracks = 0;
     s->done = 0;
   }
 }
@@ -223,21 +225,28 @@ __global__ void __launch_bounds__(OP_THREADS) k_op_update(float* __restrict__ x,
                                                           const float* __restrict__ z, const float* __restrict__ gz,
                                                           int n, float lam, float eps, int max_iter,
                                                           OpState* __restrict__ s) {
-  __shared__ float red[32 * 3 + 3];
+  __shared__ float red[32 * 4 + 4];
   if (s->done) return;
-  float v[3] = {0.f, 0.f, 0.f};
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float zr = z[i], xr = x[i];
     v[0] += fmaf(zr - xr, 0.5f * (gz[i] + gx[i]), lam * (fabsf(zr) - fabsf(xr)));
     const float d = zr - y[i];
     v[1] = fmaf(d, d, v[1]);
     v[2] = fmaf(zr, zr, v[2]);
+    v[3] = fmaf(d, gz[i] - gy[i], v[3]);            // d^T H d (g is affine: g(z) - g(y) = H d)
   }
-  block_sums<3>(v, red);
-  const float t = s->t;
-  const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
-  const bool accept = v[0] <= 0.f;
-  const float c1 = t / t1, c2 = (t - 1.f) / t1;
+  block_sums<4>(v, red);
+  // Backtracking on L: the curvature d^T H d / |d|^2 along the step is a lower
+  // bound of the Hessian's top eigenvalue; above L, the step 1/L was too long
+  // (the Lanczos estimate fell short): L is raised past it, the step is
+  // rejected and the momentum restarts from x.
+  const float L = s->L;
+  const bool too_long = v[1] > 0.f && v[3] > L * v[1];
+  const float t = too_long ? 1.f : s->t;
+  const float t1 = too_long ? 1.f : 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+  const bool accept = !too_long && v[0] <= 0.f;
+  const float c1 = too_long ? 0.f : t / t1, c2 = too_long ? 0.f : (t - 1.f) / t1;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const float xo = x[i], gxo = gx[i];
     const float xn = accept ? z[i] : xo;
@@ -251,7 +260,13 @@ __global__ void __launch_bounds__(OP_THREADS) k_op_update(float* __restrict__ x,
   if (threadIdx.x == 0) {
     s->t = t1;
     s->it += 1;
-    if (sqrtf(v[1]) <= eps * sqrtf(v[2]) || s->it >= max_iter) s->done = 1;
+    if (too_long) {
+      s->L = 1.05f * (v[3] / v[1]);
+      s->backtracks += 1;
+      if (s->it >= max_iter) s->done = 1;
+    } else if (sqrtf(v[1]) <= eps * sqrtf(v[2]) || s->it >= max_iter) {
+      s->done = 1;
+    }
   }
 }
 

@@ -595,6 +595,10 @@ int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double
     st = own;
   }
   PC_TRY(grow(1024));
+  // support marks cleared: a solve that ended (converged, capped or failed)
+  // after a pruning leaves its support marked, and the first exploration of
+  // the next solve on this plan would add those pixels to its active set
+  PC_CUDA(cudaMemsetAsync(p->mark, 0, (size_t)p->N * p->N, st));
   // ||V||^2 and r = V; counters, the pruned-support count and the tensor-core
   // flag cleared (the gridding flag iscal[7] may still report an earlier call)
   PC_CUDA(cudaMemsetAsync(p->iscal, 0, 7 * sizeof(int32_t), st));

@@ -99,6 +99,27 @@ def test_full_size_solve_invariants(abi, name):
         assert np.isin(idx, wl.sky_idx).mean() >= 0.5
 
 
+@pytest.mark.parametrize("name", ["large_2048_blobs", "fine_4096_w"])
+def test_full_size_solve_objective_against_the_plain_path(abi, name):
+    """The default solve and the solve with every contraction in plain FP32
+    (gram_mode 1: another rounding path through the same Algorithm 2) end
+    within the 1e-4 relative stop tolerance of each other: a trajectory that
+    stops early (a step size below the Lipschitz constant, a premature stop)
+    shows up as a gap (3.4e-4 and 6.4e-4 were seen with a Lanczos start that
+    could underestimate L)."""
+    wl = synth.WORKLOADS[name]()
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    V = _physical_vis(abi, plan, wl)
+    lmax = abi.pc_lambda_max(plan, V)
+    lam = wl.alpha * lmax
+    opts = {"select_rule": 1, "lambda_max": lmax} if wl.rule == "R1" else {}
+    a = abi.pc_solve(plan, V, lam, wl.delta, want_mu=False, **opts)
+    b = abi.pc_solve(plan, V, lam, wl.delta, want_mu=False, gram_mode=1, **opts)
+    assert a["converged"] and b["converged"]
+    assert abs(a["objective"] - b["objective"]) <= 1e-4 * b["objective"], (a["objective"], b["objective"],
+                                                                          a["iterations"], b["iterations"])
+
+
 def clustered_atoms(N: int, S: int, rng, n_clusters: int = 8) -> np.ndarray:
     """S distinct pixels in n_clusters square blocks around random centres (the
     shape of a Frank-Wolfe active set, which gathers around bright sources, so

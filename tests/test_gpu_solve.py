@@ -63,6 +63,27 @@ def test_solve_rule_r1(abi):
     _compare(abi, wl, V, wl.alpha * lmax, 0.9, rule="R1")
 
 
+@pytest.mark.parametrize("rule", ["R2", "R1"])
+def test_repeated_solves_on_one_plan_start_fresh(abi, rule):
+    """A solve leaves nothing behind that the next solve on the same plan
+    sees: the second and third solves repeat the first one's Frank-Wolfe
+    iterations (the first active set holds only what the first exploration
+    selects, not the previous solve's support) and its result."""
+    wl, V = workload("tiny_64_coplanar")
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    Vd = to_dev(V.astype(np.complex64))
+    lmax = abi.pc_lambda_max(plan, Vd)
+    opts = {"select_rule": 1, "lambda_max": lmax} if rule == "R1" else {}
+    delta = 0.9 if rule == "R1" else wl.delta
+    runs = [abi.pc_solve(plan, Vd, wl.alpha * lmax, delta, **opts) for _ in range(3)]
+    first = [h["n_active"] for h in runs[0]["history"]]
+    assert len(runs[0]["history"]) > 1
+    for r in runs[1:]:
+        assert [h["n_active"] for h in r["history"]] == first
+        assert r["idx"].cpu().numpy().tolist() == runs[0]["idx"].cpu().numpy().tolist()
+        assert abs(r["objective"] - runs[0]["objective"]) <= 1e-6 * runs[0]["objective"]
+
+
 def test_lambda_above_lambda_max_gives_zero(abi):
     wl, V = workload("tiny_64_coplanar")
     plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
