@@ -41,7 +41,7 @@ SECONDARY = ("large_2048_blobs", "medium_512_w")
 # Frank-Wolfe iterations, measured on the GPU): the oracle arms scale their
 # per-certificate time by this count, and the GPU arm reports whether its own
 # solve still matches it.
-FW_CERTIFICATES = {"fine_4096_w": 9, "large_2048_blobs": 8, "medium_512_w": 6}
+FW_CERTIFICATES = {"fine_4096_w": 9, "large_2048_blobs": 63, "medium_512_w": 6}
 
 
 def parse():
