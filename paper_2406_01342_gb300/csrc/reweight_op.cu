@@ -29,12 +29,13 @@ namespace pc {
 namespace {
 
 constexpr int OP_THREADS = 1024;
-// Lanczos tolerance of the operator form: each step is an operator pair, and
-// the step size only has to stay an upper bound of the Hessian's top
-// eigenvalue: the top Ritz value rises towards it, so a value that moved by
-// at most 1e-3 over 4 steps is within a few 1e-3 of it and 1.01 x that value
-// (the step-size margin) still bounds it.
-constexpr float LZ_TOL_OP = 1e-3f;
+// Lanczos tolerance of the operator form: each step is an operator pair, so
+// the estimate stops early (the top Ritz value moved by at most 1 % over 4
+// steps, from step 5): it rises towards the Hessian's top eigenvalue, and
+// where 1.01 x that value falls short of the curvature a FISTA step meets,
+// the backtracking of k_op_update raises L (one extra pair per rejection).
+constexpr float LZ_TOL_OP = 1e-2f;
+constexpr int LZ_MIN_OP = 5;       // first step at which the test compares with four steps back
 
 struct OpState {
   float L;          // step size 1.01 x top Ritz value (valid once lz_done)
@@ -149,10 +150,11 @@ __global__ void __launch_bounds__(OP_THREADS) k_lz_init_dirty(const float* __res
 }
 
 // One Lanczos step on w = G v_j: alpha = v.w, w -= alpha v_j + beta_{j-1} v_{j-1},
-// beta = ||w||, v_{j+1} = w / beta. The stop test is the Gram kernels' (the
-// top Ritz value changed by at most LZ_TOL over the last 4 steps, from step 8
-// on), evaluated after every step rather than every fourth: each step costs
-// an operator pair here, the Ritz value a few microseconds.
+// beta = ||w||, v_{j+1} = w / beta. The stop test has the Gram kernels' form
+// (the top Ritz value changed by at most LZ_TOL_OP over the last 4 steps),
+// from step LZ_MIN_OP on, evaluated after every step rather than every
+// fourth: each step costs an operator pair here, the Ritz value a few
+// microseconds.
 __global__ void __launch_bounds__(OP_THREADS) k_lz_step(float* __restrict__ w, float* __restrict__ v,
                                                         float* __restrict__ vprev, int n, OpState* __restrict__ s) {
   __shared__ float red[32 * 2 + 2];
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(OP_THREADS) k_lz_step(float* __restrict__ w, f
   const int m = j + 1;
   const bool last = (m == n) || (m == LZ_MAX) || !(beta > 1e-7f * fabsf(alpha));
   const float theta = tridiag_top(s->al, s->be, m, &s_theta);
-  const bool stop = last || (m >= 8 && fabsf(theta - s->th[m - 5]) <= LZ_TOL_OP * fabsf(theta));
+  const bool stop = last || (m >= LZ_MIN_OP && fabsf(theta - s->th[m - 5]) <= LZ_TOL_OP * fabsf(theta));
   __syncthreads();
   if (threadIdx.x == 0) {
     s->th[j] = theta;
@@ -237,28 +239,32 @@ __global__ void __launch_bounds__(OP_THREADS) k_op_update(float* __restrict__ x,
     v[3] = fmaf(d, gz[i] - gy[i], v[3]);            // d^T H d (g is affine: g(z) - g(y) = H d)
   }
   block_sums<4>(v, red);
-  // Backtracking on L: the curvature d^T H d / |d|^2 along the step is a lower
-  // bound of the Hessian's top eigenvalue; above L, the step 1/L was too long
-  // (the Lanczos estimate fell short): L is raised past it, the step is
-  // rejected and the momentum restarts from x.
+  // Backtracking on L (Beck and Teboulle's FISTA with backtracking, in its
+  // exact form for a quadratic): the step from y is valid when the curvature
+  // d^T H d / |d|^2 along it stays at or below L. Above, L is raised past that
+  // curvature (a lower bound of the Hessian's top eigenvalue) and the step is
+  // taken again from the same y; x, y, their gradients and the momentum are
+  // left as they are. The Lanczos estimate only has to be close.
   const float L = s->L;
   const bool too_long = v[1] > 0.f && v[3] > L * v[1];
-  const float t = too_long ? 1.f : s->t;
-  const float t1 = too_long ? 1.f : 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
-  const bool accept = !too_long && v[0] <= 0.f;
-  const float c1 = too_long ? 0.f : t / t1, c2 = too_long ? 0.f : (t - 1.f) / t1;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float xo = x[i], gxo = gx[i];
-    const float xn = accept ? z[i] : xo;
-    const float gxn = accept ? gz[i] : gxo;
-    y[i] = xn + c1 * (z[i] - xn) + c2 * (xn - xo);
-    gy[i] = gxn + c1 * (gz[i] - gxn) + c2 * (gxn - gxo);
-    x[i] = xn;
-    gx[i] = gxn;
+  if (!too_long) {
+    const float t = s->t;
+    const float t1 = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+    const bool accept = v[0] <= 0.f;
+    const float c1 = t / t1, c2 = (t - 1.f) / t1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float xo = x[i], gxo = gx[i];
+      const float xn = accept ? z[i] : xo;
+      const float gxn = accept ? gz[i] : gxo;
+      y[i] = xn + c1 * (z[i] - xn) + c2 * (xn - xo);
+      gy[i] = gxn + c1 * (gz[i] - gxn) + c2 * (gxn - gxo);
+      x[i] = xn;
+      gx[i] = gxn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s->t = t1;
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    s->t = t1;
     s->it += 1;
     if (too_long) {
       s->L = 1.05f * (v[3] / v[1]);
