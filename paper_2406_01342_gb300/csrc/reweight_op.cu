@@ -30,11 +30,11 @@ namespace {
 
 constexpr int OP_THREADS = 1024;
 // Lanczos tolerance of the operator form: each step is an operator pair, so
-// the estimate stops early (the top Ritz value moved by at most 1 % over 4
+// the estimate stops early (the top Ritz value moved by at most 5 % over 4
 // steps, from step 5): it rises towards the Hessian's top eigenvalue, and
 // where 1.01 x that value falls short of the curvature a FISTA step meets,
 // the backtracking of k_op_update raises L (one extra pair per rejection).
-constexpr float LZ_TOL_OP = 1e-2f;
+constexpr float LZ_TOL_OP = 5e-2f;
 constexpr int LZ_MIN_OP = 5;       // first step at which the test compares with four steps back
 
 struct OpState {
