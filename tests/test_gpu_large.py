@@ -151,11 +151,14 @@ def gram_errors(wl, G, b, V, idx, sub):
     return float(eG.max()), float(eb.max())
 
 
-@pytest.mark.parametrize("name,S", [("medium_512_w", 873), ("large_2048_w", 512), ("fine_4096_w", 512)])
+@pytest.mark.parametrize("name,S", [("medium_512_w", 873), ("large_2048_w", 512), ("fine_4096_w", 512),
+                                    ("fine_4096_w", 100)])
 def test_tensor_core_gram_sampled_at_full_size(abi, name, S):
     """The split-FP16 tensor-core contraction (pc_gram mode 2) at the
     visibility counts the solves use (M = 200k with 873 atoms, the first Gram of
-    the benchmark's solve; M = 2M and 10M with 512): 16 seeded atoms (two
+    the benchmark's solve; M = 2M and 10M with 512; 100 atoms at 10M, a
+    single row of A tiles as the solves' incremental Gram rows): 16 seeded
+    atoms (two
     clusters' worth of neighbours among them), all their 136 distinct G entries
     and their b entries against the FP64 oracle, within 1e-5 of each entry's
     Cauchy-Schwarz bound. The accumulation drift of the tensor core grows with
