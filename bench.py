@@ -279,11 +279,25 @@ def degridding_leg(abi, torch, plan, wl, info, peaks, steps, l2_flush) -> dict:
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     t = sum(ms) / len(ms)
+    # the two stages, timed per class in separate calls: the FFT passes
+    # ("degrid_fft") and the interpolation ("degrid")
+    n_prof = max(steps, 3)
+    abi.pc_profile_begin()
+    for _ in range(n_prof):
+        flush_l2(l2_flush)
+        abi.pc_forward_grid(plan, img, y)
+    torch.cuda.synchronize()
+    stages = abi.pc_profile_end()
+    fft_ms = stages["degrid_fft"][2] / n_prof if "degrid_fft" in stages else 0.0
+    interp_ms = stages["degrid"][2] / n_prof if "degrid" in stages else 0.0
     G, P = info["grid_side"], info["n_planes"]
     byt = 4.0 * wl.N * wl.N + 8.0 * wl.M + 2 * 8.0 * P * G * G
     hbm = peaks.get("hbm_gbs", 6800.0)
+    f = gridding_flops(wl.M, info)
     return {"ms": t, "vis_per_s": wl.M / (t * 1e-3), "achieved_gbs": byt / (t * 1e-3) / 1e9,
-            "peak_gbs": hbm, "frac": byt / (t * 1e-3) / 1e9 / hbm}
+            "peak_gbs": hbm, "frac": byt / (t * 1e-3) / 1e9 / hbm, "fft_ms": fft_ms, "interp_ms": interp_ms,
+            "interp_alu_tflops": f / (interp_ms * 1e-3) / 1e12 if interp_ms else None,
+            "interp_alu_frac": f / (interp_ms * 1e-3) / 1e12 / FP32_TFLOPS if interp_ms else None}
 
 
 def tc_iterations(history):
@@ -318,9 +332,14 @@ def roofline(prof, info, wl, history, steps, peaks, dom, reach=None):
         f = gridding_flops(M, info)
         out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=FP32_TFLOPS, unit="TFLOP/s")
     elif dom == "degrid":
-        # the image read, the reachable grid written (second FFT pass) and read
-        # (interpolation), one complex64 per visibility written
-        b = 4.0 * N * N + 2 * 8.0 * P * cells + 8.0 * M
+        # the interpolation (k_degrid_win / k_degrid): the same FP32 FMAs per
+        # visibility and footprint cell as the gridding's spread, in reverse
+        f = gridding_flops(M, info)
+        out.update(bound="alu", achieved=f / (avg_ms * 1e-3) / 1e12, peak=FP32_TFLOPS, unit="TFLOP/s")
+    elif dom == "degrid_fft":
+        # the degridding's two FFT passes: the image read, the reachable grid
+        # written, the pass-1 rows written and read
+        b = 4.0 * N * N + 8.0 * P * cells + 2 * 8.0 * P * N * rows
         out.update(bound="hbm", achieved=b / (avg_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
     elif dom == "fft_rows":
         b = 8.0 * P * cells + 8.0 * P * N * rows

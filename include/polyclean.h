@@ -70,7 +70,9 @@ typedef struct {
                              without w-stacking. 1: FP32 CUDA cores; 2: tensor cores
                              whenever w-stacking; 3: FP32 CUDA cores over plane windows,
                              one CTA per tile, when w-stacking with kernel_width <= 7
-                             (else as 2)                                                 */
+                             (else as 2). The degridding follows: over plane windows in
+                             mode 3 (one thread per binned slot), else over the fixed
+                             plane groups                                                */
   int32_t autotune;       /* 1: time the candidate gridding kernels, gridding sub-problem
                              sizes and FFT kernels on this plan's visibilities and keep
                              the fastest (adds a few ms to plan creation); 0 (default): off */
@@ -94,6 +96,11 @@ typedef struct {
                                1024; 8 rows per CTA in the first pass, one plane per warp
                                in the second)                                           */
   double  fft_cols_us;      /* measured time of one second FFT pass with that choice */
+  int32_t degrid_piece;     /* mode 3: slots per degridding CTA before a tile is split
+                               into parts (0 in the other modes)                      */
+  int32_t reserved;
+  double  degrid_us;        /* measured time of one degridding interpolation with that
+                               choice (0 when not timed)                              */
 } pc_plan_tuning;
 
 /* Solver options (Algorithm 2 and its sub-solver). Zero fields take defaults. */
@@ -422,7 +429,9 @@ void pc_server_destroy(pc_server_t server);
  * launch of the library; pc_profile_end() synchronises on the recorded
  * events, stops recording and writes one entry per kernel class (at most
  * cap entries; *n_out receives the number of classes seen). Recording costs
- * two event records per launch; it is off unless begun. Not thread-safe. */
+ * two event records per launch; it is off unless begun. Not thread-safe.
+ * The forward operator by degridding records two classes: "degrid_fft" (its
+ * two FFT passes, image to grid planes) and "degrid" (the interpolation). */
 typedef struct {
   char name[32];          /* kernel class, e.g. "grid", "fft_rows", "apgd"        */
   int64_t launches;       /* timed launcher calls of this class                    */

@@ -54,7 +54,8 @@ class pc_plan_tuning(ctypes.Structure):
                 ("grid_piece", ctypes.c_int32), ("fft_rows_per_cta", ctypes.c_int32),
                 ("grid_us", ctypes.c_double), ("fft_rows_us", ctypes.c_double),
                 ("fft_cols_planes", ctypes.c_int32), ("fft_warp", ctypes.c_int32),
-                ("fft_cols_us", ctypes.c_double)]
+                ("fft_cols_us", ctypes.c_double), ("degrid_piece", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("degrid_us", ctypes.c_double)]
 
 
 class pc_server_opts(ctypes.Structure):
@@ -267,7 +268,7 @@ def pc_plan_tuning_info(plan: Plan) -> dict:
     return dict(tuned=bool(t.tuned), grid_mode=t.grid_mode, grid_piece=t.grid_piece,
                 fft_rows_per_cta=t.fft_rows_per_cta, grid_us=t.grid_us, fft_rows_us=t.fft_rows_us,
                 fft_cols_planes=t.fft_cols_planes, fft_cols_us=t.fft_cols_us,
-                fft_warp=t.fft_warp)
+                fft_warp=t.fft_warp, degrid_piece=t.degrid_piece, degrid_us=t.degrid_us)
 
 
 def pc_forward_sparse(plan: Plan, idx: torch.Tensor, x: torch.Tensor, y: torch.Tensor | None = None,

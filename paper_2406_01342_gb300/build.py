@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpolyclean.so")
 
-SOURCES = ["common", "plan", "grid", "grid_tc", "grid_win", "fft", "sparse", "gram_tc", "select", "apgd", "solve", "serve", "dict", "degrid", "noalloc", "fft_big", "reweight_op"]
+SOURCES = ["common", "plan", "grid", "grid_tc", "grid_win", "degrid_win", "fft", "sparse", "gram_tc", "select", "apgd", "solve", "serve", "dict", "degrid", "noalloc", "fft_big", "reweight_op"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}",
           "-Xcompiler", "-Wall"]

@@ -196,7 +196,7 @@ const char* const kProfNames[PROF_NCLASSES] = {"plan",     "grid",     "fft_rows
                                                "residual", "gram_fp32", "gram_finalize",
                                                "apgd",     "select",   "misc",     "gram_tc",
                                                "gram_thin", "dict_corr", "dict_columns", "phase_gen",
-                                               "apgd_op", "degrid"};
+                                               "apgd_op", "degrid", "degrid_fft"};
 
 struct ProfRec {
   int cls;

@@ -266,12 +266,10 @@ k_degrid(const int4* __restrict__ subs, const int2* __restrict__ slot_vis, const
 
 }  // namespace
 
-int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st) {
-  ProfScope prof_scope_(PROF_DEGRID, st);
-  if (p->M <= 0) return PC_OK;
-  PC_CUDA(cudaMemsetAsync(y, 0, sizeof(float2) * (size_t)p->M, st));
-  prof_scope_.kernels = 1;
-  if (p->n_sub == 0 || p->n_active_rows == 0) return PC_OK;
+// The two FFT passes of the degridding (image -> grid planes): class
+// "degrid_fft"; the interpolation is timed as "degrid".
+static int degrid_ffts(pc_plan_s* p, const float* img, cudaStream_t st) {
+  ProfScope prof_scope_(PROF_DEGRID_FFT, st);
   const int N = p->N, G = p->G, n_act = p->n_active_rows;
   const int ws = p->wstack ? 1 : 0;
   if (fft_big_size(G) && p->fft_warp != 0) {
@@ -338,7 +336,25 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
   }
   }
   }
-  {
+  prof_scope_.kernels = 2;
+  return PC_OK;
+}
+
+int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st) {
+  if (p->M <= 0) return PC_OK;
+  if (p->n_sub == 0 || p->n_active_rows == 0) {
+    ProfScope prof_scope_(PROF_DEGRID, st);
+    PC_CUDA(cudaMemsetAsync(y, 0, sizeof(float2) * (size_t)p->M, st));
+    prof_scope_.kernels = 1;
+    return PC_OK;
+  }
+  PC_TRY(degrid_ffts(p, img, st));
+  ProfScope prof_scope_(PROF_DEGRID, st);
+  PC_CUDA(cudaMemsetAsync(y, 0, sizeof(float2) * (size_t)p->M, st));
+  const int G = p->G, ws = p->wstack ? 1 : 0;
+  if (grid_win_mode(p)) {
+    PC_TRY(launch_degrid_win(p, y, st));
+  } else {
     if (p->T != DG_T || p->Qg > 8) return fail(PC_ERR_INVALID_ARG, "forward: needs 32-cell tiles, <= 8 planes");
     const size_t smem = sizeof(float2) * (size_t)p->Qg * DG_T * DG_TP;
     const float beta = (float)p->beta;
@@ -366,7 +382,7 @@ int forward_grid_impl(pc_plan_s* p, const float* img, float2* y, cudaStream_t st
 #undef PC_DEGRID_CASE
     PC_LAUNCH_CHECK();
   }
-  prof_scope_.kernels = 4;
+  prof_scope_.kernels = 2;
   return PC_OK;
 }
 

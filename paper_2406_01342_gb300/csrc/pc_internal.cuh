@@ -70,7 +70,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 enum ProfClass { PROF_PLAN = 0, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_RESIDUAL,
                  PROF_GRAM, PROF_GRAM_FINALIZE, PROF_APGD, PROF_SELECT, PROF_MISC,
                  PROF_GRAM_TC, PROF_GRAM_THIN, PROF_DICT_CORR, PROF_DICT_COLUMNS, PROF_PHASE_GEN,
-                 PROF_APGD_OP, PROF_DEGRID, PROF_NCLASSES };
+                 PROF_APGD_OP, PROF_DEGRID, PROF_DEGRID_FFT, PROF_NCLASSES };
 int prof_start(int cls, cudaStream_t st);
 bool prof_active();   // kernel-class timing is recording
 void prof_stop(int token, cudaStream_t st, int kernels);
@@ -270,9 +270,13 @@ int launch_grid_tc(pc_plan_s* p, const float2* h, int* err_dev, cudaStream_t st)
 // grid_win.cu: CUDA-core gridding over plane windows, one CTA per tile (or
 // part of a heavy tile); w-stacking plans
 int launch_grid_win(pc_plan_s* p, const float2* h, cudaStream_t st);
-bool grid_win_mode(const pc_plan_s* p);   // the plan grids over plane windows
+bool grid_win_mode(const pc_plan_s* p);   // the plan grids (and degrids) over plane windows
+// degrid_win.cu: degridding interpolation over plane windows, one thread per
+// slot (y added to)
+int launch_degrid_win(pc_plan_s* p, float2* y, cudaStream_t st);
 // plan.cu: window gridding CTAs for at most `cap` slots each
 int split_wsubs(pc_plan_s* p, int cap, cudaStream_t st);
+int split_dwsubs(pc_plan_s* p, int cap, cudaStream_t st);
 int launch_fft_rows(pc_plan_s* p, cudaStream_t st);
 int launch_fft_cols_epilogue(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
                              cudaStream_t st);
@@ -317,12 +321,14 @@ struct pc_plan_s {
                       // (-1: both wherever G is 512 or 1024, the sizes those kernels take)
   bool tuned = false; // grid_mode / grid_piece / fft_R picked by the plan-time autotuner
   bool want_tune = false; // the autotuner will run (it may pick the Stockham passes)
-  double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0;
+  double tune_grid_us = 0.0, tune_fft_us = 0.0, tune_fft_cols_us = 0.0, tune_degrid_us = 0.0;
   int Pw = 1;         // plane windows: pairs of plane starts ((P - W) >> 1) + 1 (1 without w-stacking)
   std::vector<int4> sub_ranges;   // (tile, plane group, first slot, end) before splitting
   std::vector<int2> win_tiles;    // (tile, binned slots) of every tile that holds slots
   int win_cap = 0;                // window gridding: slots per CTA before a tile is split
   int n_wsub = 0;
+  int dwin_cap = 0;               // window degridding: slots per CTA before a tile is split
+  int n_dwsub = 0;
   int64_t wsub_cap = 0;           // capacity of wsubs (parts of at most 64 slots)
   int sub_cap = 0;                // capacity of subs (the finest split)
   int64_t n_slots = 0;
@@ -336,6 +342,7 @@ struct pc_plan_s {
   int4* subs = nullptr;          // gridding sub-problems {tile, plane group, start, end}
   int* win_off = nullptr;        // first slot of each (tile, plane pair) bin (nT^2 Pw + 1)
   int4* wsubs = nullptr;         // window gridding CTAs {tile, part, parts, slots}, heaviest first
+  int4* dwsubs = nullptr;        // window degridding CTAs (the same form, their own split)
   int* active_rows = nullptr;    // grid rows b that visibilities can reach (ascending)
   int n_active_rows = 0;
   // image-domain tables

@@ -384,11 +384,10 @@ struct TmpBufs {
 
 // Splits every (tile, plane group) slot range into equal pieces of at most
 // `piece` slots (multiples of 64, the tensor-core stage) and uploads the list.
-// Window gridding CTAs: a tile whose slots exceed `cap` is split into equal
-// parts (each part takes its share of every plane window of the tile and adds
-// its tile to the grid); heaviest CTAs first, so the last wave holds the
-// light ones.
-int split_wsubs(pc_plan_s* p, int cap, cudaStream_t st) {
+// Window CTAs: a tile whose slots exceed `cap` is split into equal parts
+// (each part takes its share of every plane window of the tile); heaviest
+// CTAs first, so the last wave holds the light ones.
+static int split_win_parts(pc_plan_s* p, int cap, int4* dst, int* n_out, cudaStream_t st) {
   cap = std::max(cap, 64);
   std::vector<int4> subs;
   for (const int2& t : p->win_tiles) {
@@ -397,11 +396,25 @@ int split_wsubs(pc_plan_s* p, int cap, cudaStream_t st) {
   }
   std::stable_sort(subs.begin(), subs.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
   if ((int64_t)subs.size() > p->wsub_cap) return fail(PC_ERR_CAPACITY, "plan: %zu window CTAs", subs.size());
-  p->n_wsub = (int)subs.size();
-  p->win_cap = cap;
+  *n_out = (int)subs.size();
   if (!subs.empty())
-    PC_CUDA(cudaMemcpyAsync(p->wsubs, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(dst, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice, st));
   PC_CUDA(cudaStreamSynchronize(st));   // the host vector goes out of scope
+  return PC_OK;
+}
+
+// The window gridding's CTAs (each part adds its tile to the grid).
+int split_wsubs(pc_plan_s* p, int cap, cudaStream_t st) {
+  PC_TRY(split_win_parts(p, cap, p->wsubs, &p->n_wsub, st));
+  p->win_cap = std::max(cap, 64);
+  return PC_OK;
+}
+
+// The window degridding's CTAs (each part reads its tile's planes; no part
+// writes the grid, so the split only costs plane loads).
+int split_dwsubs(pc_plan_s* p, int cap, cudaStream_t st) {
+  PC_TRY(split_win_parts(p, cap, p->dwsubs, &p->n_dwsub, st));
+  p->dwin_cap = std::max(cap, 64);
   return PC_OK;
 }
 
@@ -537,6 +550,23 @@ static int autotune(pc_plan_s* p, cudaStream_t st) {
   p->fft_cols_pg = best_pg;
   p->tune_fft_cols_us = best_cols;
   p->fft_warp = best_rw | best_cw;
+  // window degridding: slots per CTA before a tile is split (into the
+  // residual buffer, cleared below; the grid holds the planes timed above)
+  if (grid_win_mode(p)) {
+    double best_dw = 1e300;
+    int best_cap = p->dwin_cap;
+    for (int cap : {2048, 4096, 8192, 16384}) {
+      PC_TRY(split_dwsubs(p, cap, st));
+      double us = 0.0;
+      PC_TRY(time_us(st, 3, [&] { return launch_degrid_win(p, p->resid, st); }, &us));
+      if (us < best_dw) {
+        best_dw = us;
+        best_cap = cap;
+      }
+    }
+    PC_TRY(split_dwsubs(p, best_cap, st));
+    p->tune_degrid_us = best_dw;
+  }
   p->tuned = true;
   PC_CUDA(cudaMemsetAsync(p->resid, 0, sizeof(float2) * p->M, st));
   PC_CUDA(cudaStreamSynchronize(st));
@@ -810,6 +840,10 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
   p->wsub_cap = p->n_slots / 64 + (int64_t)p->win_tiles.size() + 1;
   PC_TRY(dev_alloc_t(p, &p->wsubs, (size_t)p->wsub_cap));
   PC_TRY(split_wsubs(p, (int64_t)p->win_tiles.size() >= 8ll * n_sm ? 65536 : 4096, st));
+  PC_TRY(dev_alloc_t(p, &p->dwsubs, (size_t)p->wsub_cap));
+  // window degridding: parts of at most 8192 slots (measured best or within
+  // 2 % of the best cap on 2048^2 / 2M and 4096^2 / 10M; the tuner times it)
+  PC_TRY(split_dwsubs(p, 8192, st));
   // grid rows that any visibility can reach: the rows of tile rows with a sub-problem
   {
     std::vector<char> row_on(p->nT, 0);
@@ -948,6 +982,9 @@ extern "C" int pc_plan_tuning_info(pc_plan_t p, pc_plan_tuning* out) {
   out->fft_cols_planes = cw ? 1 : cols_planes_per_pass(p);
   out->fft_cols_us = p->tune_fft_cols_us;
   out->fft_warp = (rw ? 1 : 0) | (cw ? 2 : 0);
+  out->degrid_piece = grid_win_mode(p) ? p->dwin_cap : 0;
+  out->reserved = 0;
+  out->degrid_us = p->tune_degrid_us;
   return PC_OK;
 }
 

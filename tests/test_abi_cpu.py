@@ -61,3 +61,24 @@ def test_plan_create_rejects_bad_arguments_without_a_gpu():
         rc, msg = create(**kw)
         assert rc == abi.PC_ERR_INVALID_ARG, (kw, rc, msg)
         assert needle in msg, (kw, msg)
+
+
+def test_profile_classes_are_known_by_name_without_a_gpu():
+    """pc_profile_begin_classes accepts every kernel class the library times
+    (the degridding's FFT passes and its interpolation separately) and
+    rejects an unknown name; with nothing launched, pc_profile_end reports no
+    class (host bookkeeping only, no GPU is touched)."""
+    from paper_2406_01342_gb300 import abi, build
+    build.build()
+    abi.load()
+    classes = ["grid", "fft_rows", "fft_cols", "residual", "gram_fp32", "gram_finalize", "apgd", "select", "misc",
+               "gram_tc", "gram_thin", "dict_corr", "dict_columns", "phase_gen", "apgd_op", "degrid", "degrid_fft"]
+    abi.pc_profile_begin(",".join(classes))
+    assert abi.pc_profile_end() == {}
+    try:
+        abi.pc_profile_begin("degrid_interp")
+    except abi.PcError as e:
+        assert e.status == abi.PC_ERR_INVALID_ARG
+    else:
+        raise AssertionError("an unknown class name was accepted")
+    assert abi.pc_profile_end() == {}

@@ -65,6 +65,17 @@ def test_roofline_arithmetic():
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(g["alu_achieved_tflops"])
     assert bench.gridding_flops(wl.M, dict(info, n_planes=1)) == 4.0 * wl.M * 49
+    # the degridding's interpolation: the spread's FMAs in reverse, per launch
+    prof["degrid"] = (10, 20, 10 * 0.08)
+    d = bench.roofline(prof, info, wl, hist, steps, peaks, "degrid")
+    assert d["bound"] == "alu" and d["achieved"] == pytest.approx(4.0 * wl.M * 343 / 0.08e-3 / 1e12)
+    # its FFT passes: image read, reachable grid written, pass-1 rows written and read
+    prof["degrid_fft"] = (10, 20, 10 * 0.05)
+    reach = {"rows": 512, "col_groups": 16}
+    f = bench.roofline(prof, info, wl, hist, steps, peaks, "degrid_fft", reach)
+    cells = 512 * 16 * 32
+    assert f["bound"] == "hbm"
+    assert f["achieved"] == pytest.approx((4.0 * 512 * 512 + 8.0 * 8 * cells + 16.0 * 8 * 512 * 512) / 0.05e-3 / 1e9)
 
 
 def test_traffic_record_needs_the_profiled_sources(tmp_path, monkeypatch):

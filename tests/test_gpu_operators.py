@@ -106,13 +106,16 @@ def test_fft_kernels(abi, name, kw):
     assert rel_l2(aw, as_) <= TOL
 
 
+@pytest.mark.parametrize("grid_mode", [2, 3])
 @pytest.mark.parametrize("name,kw", CASES)
-def test_forward_grid(abi, name, kw):
+def test_forward_grid(abi, name, kw, grid_mode):
     """Degridding (the type-2 non-uniform FFT of Sect. 5.2) of a dense random
     image against the direct sum of the forward equation (Sect. 2.2), on all
-    visibilities or a seeded sample of them."""
+    visibilities or a seeded sample of them; grid_mode 3 interpolates over the
+    plane windows (one thread per binned slot), 2 over the fixed plane groups
+    (the coplanar case has one plane and takes the latter in both)."""
     wl, V = workload(name, **kw)
-    plan = _plan(abi, wl)
+    plan = _plan(abi, wl, grid_mode=grid_mode)
     rng = np.random.default_rng(31)
     img = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
     y = abi.pc_forward_grid(plan, to_dev(img)).cpu().numpy()
@@ -199,12 +202,13 @@ def test_forward_grid_big(abi, name, kw):
     assert abs(lhs - rhs) <= 1e-5 * np.sqrt(np.sum(np.abs(y) ** 2) * np.sum(np.abs(h) ** 2))
 
 
+@pytest.mark.parametrize("grid_mode", [2, 3])
 @pytest.mark.parametrize("name,kw", CASES)
-def test_forward_grid_is_the_adjoint_of_adjoint_grid(abi, name, kw):
+def test_forward_grid_is_the_adjoint_of_adjoint_grid(abi, name, kw, grid_mode):
     """Re<Phi x, h> = <x, Phi* h> between the two NUFFT directions of one plan
     (they are built as exact adjoints: equal up to FP32 rounding)."""
     wl, _ = workload(name, **kw)
-    plan = _plan(abi, wl)
+    plan = _plan(abi, wl, grid_mode=grid_mode)
     rng = np.random.default_rng(32)
     x = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
     h = (rng.normal(size=wl.M) + 1j * rng.normal(size=wl.M)).astype(np.complex64)
@@ -339,6 +343,10 @@ def test_autotuned_plan(abi):
     assert 0 < t["grid_us"] < 1e5 and 0 < t["fft_rows_us"] < 1e5
     assert t["fft_cols_planes"] in (1, 2, 4, 8) and 0 < t["fft_cols_us"] < 1e5
     assert t["fft_warp"] in (0, 1, 2, 3)
+    if t["grid_mode"] == 3:
+        assert t["degrid_piece"] in (2048, 4096, 8192, 16384) and 0 < t["degrid_us"] < 1e5
+    else:
+        assert t["degrid_piece"] == 0
     if t["fft_warp"] & 1:
         assert t["fft_rows_per_cta"] == 8
     if t["fft_warp"] & 2:
@@ -349,6 +357,13 @@ def test_autotuned_plan(abi):
     pix = np.union1d(np.sort(np.random.default_rng(9).choice(wl.N * wl.N, 1024, replace=False)), wl.sky_idx)
     ref = operators.adjoint(wl.uvw, wl.N, wl.fov, Vs.astype(np.complex128), pix)
     assert rel_l2(img[pix], ref) <= TOL
+    # the degridding with the tuned choice: a random image on sampled visibilities
+    rng = np.random.default_rng(10)
+    x = rng.normal(size=(wl.N, wl.N)).astype(np.float32)
+    y = abi.pc_forward_grid(plan, to_dev(x)).cpu().numpy()
+    ks = np.sort(rng.choice(wl.M, 300, replace=False))
+    yref = operators.forward(wl.uvw[ks], wl.N, wl.fov, np.arange(wl.N * wl.N), x.ravel().astype(np.float64))
+    assert rel_l2(y[ks], yref) <= TOL
     with pytest.raises(abi.PcError) as e:
         _plan(abi, wl, autotune=2)
     assert e.value.status == abi.PC_ERR_INVALID_ARG
