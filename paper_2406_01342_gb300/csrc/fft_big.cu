@@ -85,15 +85,23 @@ k_fft_rows_big(const float2* __restrict__ grid, float2* __restrict__ Xc, int N, 
   }
   cfft::fft<R>(u, Z, tw, T2);
   __syncthreads();                                  // every warp is done with its row of Z
+  // the kept outputs, staged by frequency: folded into [0, G / 2) and
+  // swizzled (cfft::stage_pos) so the stores are free of bank conflicts
   const int hN = N >> 1;
+  const int k0 = cfft::kept_freq<R>(warp, lane, 0);
+  const int msk = cfft::stage_mask<R, 7>(k0 < G / 2 ? k0 : k0 - G / 2);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const int i = (cfft::kept_freq<R>(warp, lane, k) + hN) & (G - 1);
-    if (i < N) Z[i] = wfft::kept_value<cfft::L>(u, k, lane);
+    const int kf = cfft::kept_freq<R>(warp, lane, k);
+    const int i = (kf + hN) & (G - 1);
+    if (i < N) Z[(kf < G / 2 ? kf : kf - G / 2) ^ msk] = wfft::kept_value<cfft::L>(u, k, lane);
   }
   __syncthreads();
   float2* dst = Xc + (size_t)(q * nb + (c >> 2)) * N * 4 + (c & 3);
-  for (int i = t; i < N; i += 32 * R) dst[(size_t)i * 4] = Z[i];
+  for (int i = t; i < N; i += 32 * R) {
+    const int kf = (i - hN) & (G - 1);
+    dst[(size_t)i * 4] = Z[cfft::stage_pos<R, 7>(kf < G / 2 ? kf : kf - G / 2)];
+  }
 }
 
 // The compact rows of plane q for image row i are Xc[q][cb][i][0..4), cb <
@@ -302,13 +310,21 @@ k_degrid_rows_big(const float2* __restrict__ Xc, int N, int nb, const int* __res
   cfft::fft<R>(u, Z, tw, T2);
   __syncthreads();
   const int warp = t >> 5, lane = t & 31;
+  // staged by frequency, swizzled inside each group of R (cfft::stage_pos:
+  // conflict-free stores); a pair 2h, 2h + 1 stays in one 16-byte slot,
+  // swapped when the swizzle flips bit 0
+  const int msk = cfft::stage_mask<R, 8>(cfft::freq<R>(warp, lane, 0));
 #pragma unroll
-  for (int kp = 0; kp < cfft::L; ++kp) Z[cfft::freq<R>(warp, lane, kp)] = conj2(u[wfft::brev(kp, 4)]);
+  for (int kp = 0; kp < cfft::L; ++kp) Z[cfft::freq<R>(warp, lane, kp) ^ msk] = conj2(u[wfft::brev(kp, 4)]);
   __syncthreads();
   float4* dst = reinterpret_cast<float4*>(grid + ((size_t)q * G + active_rows[c]) * G);
   const float4* s4 = reinterpret_cast<const float4*>(Z);
   for (int h = t; h < G / 2; h += 32 * R)
-    if (group_on(colw, 2 * h)) dst[h] = s4[h];
+    if (group_on(colw, 2 * h)) {
+      const int sp = cfft::stage_pos<R, 8>(2 * h);
+      const float4 v = s4[sp >> 1];
+      dst[h] = (sp & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+    }
 }
 
 template <typename K>

@@ -61,6 +61,27 @@ __device__ __forceinline__ int kept_freq(int k1, int lane, int c) {
   return k1 + R * wfft::kept_freq<L>(c, lane);
 }
 
+// Shared-memory slot of output frequency k (< G) when a CTA stages a
+// transformed row in Z. The 16 lanes of a half-warp hold frequencies
+// k = k1 + R f with f = (lane >> 1) + 16 k' + X (lane & 1) (X = 256; 128 for
+// the kept outputs folded into [0, G / 2)), i.e. multiples of R apart, which
+// would put them on a few of the 16 eight-byte bank pairs. XOR-ing the bits
+// of k1 with bits of f (the low ones, and bit PB for the lane pair) spreads
+// them over all 16; the map is a bijection that keeps every aligned group of
+// R slots in place, so runs of consecutive k stay conflict-free too.
+template <int R, int PB>
+__host__ __device__ __forceinline__ int stage_mask(int k) {
+  constexpr int LR = wfft::log2c(R);
+  const int f = k >> LR;
+  return ((f >> (4 - LR)) & ((1 << (LR - 1)) - 1)) | (((f >> PB) & 1) << (LR - 1));
+}
+template <int R, int PB>
+__host__ __device__ __forceinline__ int stage_pos(int k) {
+  return k ^ stage_mask<R, PB>(k);
+}
+// A lane's outputs differ only in f's bits 4..7 (16 k'; bit 8 or 7 is the
+// lane pair's), which the mask does not read: one mask serves all of them.
+
 // tw[k] = e^{+2 pi i k / G} (G entries); T2[k1 * 32 + l] = e^{+2 pi i l k1 / 512}
 // (k1 < 16). Z: Cfg<R>::Z_ELEMS float2 of shared memory, free on entry; the
 // caller places a __syncthreads() between this call's return and any other
