@@ -240,8 +240,9 @@ k_fft_cols_big(const __grid_constant__ CUtensorMap xmap, int n_box, int by, cons
 template <int R>
 __global__ void __launch_bounds__(32 * R, R == 16 ? 1 : 2)
 k_degrid_cols_big(const float* __restrict__ x, const float4* __restrict__ pix, int N, int P, int nb, int n_rows,
-                  int wstack, const int* __restrict__ row_pos, const float2* __restrict__ tw,
-                  const float2* __restrict__ T2, float2* __restrict__ Xc, const int* __restrict__ img_rows) {
+                  int wstack, const int* __restrict__ row_pos, const int* __restrict__ active_rows,
+                  const float2* __restrict__ tw, const float2* __restrict__ T2, float2* __restrict__ Xc,
+                  const int* __restrict__ img_rows) {
   constexpr int G = cfft::Cfg<R>::G;
   extern __shared__ float2 Z[];
   const int i = img_rows ? img_rows[blockIdx.x] : (int)blockIdx.x;
@@ -263,10 +264,12 @@ k_degrid_cols_big(const float* __restrict__ x, const float4* __restrict__ pix, i
       tz[e] = make_float2(pt.z, pt.w);
     }
   }
-  // compact row of each output register (-1: not a reachable row)
-  int cpos[cfft::L];
+  // which output registers are reachable rows (bit kp), and the lane's
+  // staging mask (cfft::stage_mask: conflict-free stores by frequency)
+  unsigned reach = 0;
 #pragma unroll
-  for (int kp = 0; kp < cfft::L; ++kp) cpos[kp] = __ldg(row_pos + cfft::freq<R>(warp, lane, kp));
+  for (int kp = 0; kp < cfft::L; ++kp) reach |= (__ldg(row_pos + cfft::freq<R>(warp, lane, kp)) >= 0 ? 1u : 0u) << kp;
+  const int msk = cfft::stage_mask<R, 8>(cfft::freq<R>(warp, lane, 0));
   for (int q = 0; q < P; ++q) {
     const float qf = (float)q;
     float2 u[cfft::L];
@@ -279,10 +282,11 @@ k_degrid_cols_big(const float* __restrict__ x, const float4* __restrict__ pix, i
     __syncthreads();                                // Z free: stage the reachable rows' values
 #pragma unroll
     for (int kp = 0; kp < cfft::L; ++kp)
-      if (cpos[kp] >= 0) Z[cpos[kp]] = conj2(u[wfft::brev(kp, 4)]);
+      if ((reach >> kp) & 1u) Z[cfft::freq<R>(warp, lane, kp) ^ msk] = conj2(u[wfft::brev(kp, 4)]);
     __syncthreads();
     float2* dst = Xc + (size_t)q * nb * N * 4 + (size_t)i * 4;
-    for (int c = t; c < n_rows; c += 32 * R) dst[(size_t)(c >> 2) * N * 4 + (c & 3)] = Z[c];
+    for (int c = t; c < n_rows; c += 32 * R)
+      dst[(size_t)(c >> 2) * N * 4 + (c & 3)] = Z[cfft::stage_pos<R, 8>(__ldg(active_rows + c))];
     __syncthreads();
   }
 }
@@ -364,7 +368,7 @@ int launch_fft_rows_big(pc_plan_s* p, cudaStream_t st) {
   }                                                                                                        \
   k_fft_rows_big<RR><<<dim3(p->n_active_rows, p->P), 32 * RR, smem, st>>>(p->grid, Xc, p->N, nb,           \
                                                                            p->active_rows, p->col_bits,    \
-                                                                           p->twiddle, p->tw_in);
+                                                                           p->tw_big, p->tw_in);
   PC_BIG_DISPATCH(p->G, PC_ROWS)
 #undef PC_ROWS
   PC_LAUNCH_CHECK();
@@ -421,7 +425,7 @@ int launch_fft_cols_big(pc_plan_s* p, float* mu, float scale, unsigned* maxbits,
     done = true;                                                                                           \
   }                                                                                                        \
   k_fft_cols_big<RR><<<rows_img, 32 * RR, smem, st>>>(p->xmap, p->xmap_boxes, p->xmap_by, p->pix_tab, mu,     \
-                                                     p->N, p->P, nb, ws, p->row_pos, p->twiddle, p->tw_in,   \
+                                                     p->N, p->P, nb, ws, p->row_pos, p->tw_big, p->tw_in,   \
                                                      scale, maxbits, p->iscal + 7, list);
   PC_BIG_DISPATCH(p->G, PC_COLS)
 #undef PC_COLS
@@ -448,11 +452,11 @@ int launch_degrid_ffts_big(pc_plan_s* p, const float* img, cudaStream_t st) {
     done = true;                                                                                           \
   }                                                                                                        \
   k_degrid_cols_big<RR><<<rows_img, 32 * RR, smem, st>>>(img, p->pix_tab, p->N, p->P, nb,                 \
-                                                        p->n_active_rows, ws, p->row_pos, p->twiddle,       \
-                                                        p->tw_in, Xc, list);                                \
+                                                        p->n_active_rows, ws, p->row_pos, p->active_rows,   \
+                                                        p->tw_big, p->tw_in, Xc, list);                    \
   PC_LAUNCH_CHECK();                                                                                       \
   k_degrid_rows_big<RR><<<dim3(p->n_active_rows, p->P), 32 * RR, smem, st>>>(                              \
-      Xc, p->N, nb, p->active_rows, p->col_bits, p->twiddle, p->tw_in, p->grid, bits);
+      Xc, p->N, nb, p->active_rows, p->col_bits, p->tw_big, p->tw_in, p->grid, bits);
   PC_BIG_DISPATCH(p->G, PC_DG)
 #undef PC_DG
   PC_LAUNCH_CHECK();

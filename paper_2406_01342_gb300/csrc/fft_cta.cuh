@@ -82,7 +82,8 @@ __host__ __device__ __forceinline__ int stage_pos(int k) {
 // A lane's outputs differ only in f's bits 4..7 (16 k'; bit 8 or 7 is the
 // lane pair's), which the mask does not read: one mask serves all of them.
 
-// tw[k] = e^{+2 pi i k / G} (G entries); T2[k1 * 32 + l] = e^{+2 pi i l k1 / 512}
+// tw[k1 * 512 + n'] = e^{+2 pi i n' k1 / G} (R x 512 = G entries: a warp's
+// reads for one k1 are contiguous); T2[k1 * 32 + l] = e^{+2 pi i l k1 / 512}
 // (k1 < 16). Z: Cfg<R>::Z_ELEMS float2 of shared memory, free on entry; the
 // caller places a __syncthreads() between this call's return and any other
 // use of Z.
@@ -99,7 +100,7 @@ __device__ __forceinline__ void fft(float2 (&u)[L], float2* Z, const float2* __r
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) {
       float2 y = u[j * R + wfft::brev(k1, LR)];
-      if (k1 > 0) y = cmul(y, __ldg(tw + ((np * k1) & (G - 1))));
+      if (k1 > 0) y = cmul(y, __ldg(tw + k1 * 512 + np));
       Z[k1 * ZS + np] = y;
     }
   }

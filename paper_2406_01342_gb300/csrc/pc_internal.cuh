@@ -357,6 +357,7 @@ struct pc_plan_s {
   int* row_pos = nullptr;        // G entries: compact index of a reachable grid row, else -1
   int n_active_col_groups = 0;   // bits set in col_bits
   float2* tw_in = nullptr;       // G >= 2048: the 512-point one-warp FFT's twiddles [k1 < 16][l < 32]
+  float2* tw_big = nullptr;      // G >= 2048: the one-CTA FFT's first-step twiddles [k1 < G / 512][n' < 512]
   // workspaces
   float2* grid = nullptr;        // P x G x G  (b-major rows, a contiguous)
   float2* fft1 = nullptr;        // P x N x G  (after the pass along a)

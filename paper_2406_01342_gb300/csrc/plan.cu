@@ -695,6 +695,12 @@ static int build_plan(pc_plan_s* p, const double* uvw, cudaStream_t st, int max_
       for (int l = 0; l < 32; ++l) t2[(size_t)k1 * 32 + l] = tw[(size_t)(k1 * l * step) % p->G];
     PC_TRY(dev_alloc_t(p, &p->tw_in, t2.size()));
     PC_CUDA(cudaMemcpyAsync(p->tw_in, t2.data(), sizeof(float2) * t2.size(), cudaMemcpyHostToDevice, st));
+    // its first step's twiddles by (k1, n'): e^{+2 pi i n' k1 / G}, n' < 512
+    std::vector<float2> ta((size_t)p->G);
+    for (int k1 = 0; k1 < p->G / 512; ++k1)
+      for (int n = 0; n < 512; ++n) ta[(size_t)k1 * 512 + n] = tw[((size_t)n * k1) % p->G];
+    PC_TRY(dev_alloc_t(p, &p->tw_big, ta.size()));
+    PC_CUDA(cudaMemcpyAsync(p->tw_big, ta.data(), sizeof(float2) * ta.size(), cudaMemcpyHostToDevice, st));
   }
 
   // ---- workspaces
