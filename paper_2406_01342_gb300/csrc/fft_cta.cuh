@@ -37,7 +37,7 @@ struct Cfg {
 
 // Position n of register e of thread t (u[e], e = j R + r).
 template <int R>
-__device__ __forceinline__ int pos(int t, int e) {
+__host__ __device__ __forceinline__ int pos(int t, int e) {
   return t + 32 * R * (e / R) + 512 * (e % R);
 }
 
@@ -51,13 +51,13 @@ __host__ __device__ constexpr bool centred_reg(int e) {
 
 // Full output frequency k of register u[brev(kp, 4)] of lane `lane` in warp k1.
 template <int R>
-__device__ __forceinline__ int freq(int k1, int lane, int kp) {
+__host__ __device__ __forceinline__ int freq(int k1, int lane, int kp) {
   return k1 + R * ((lane >> 1) + 16 * kp + 256 * (lane & 1));
 }
 
 // Kept output c < 8 (wfft::kept_value<16>) of lane `lane` in warp k1.
 template <int R>
-__device__ __forceinline__ int kept_freq(int k1, int lane, int c) {
+__host__ __device__ __forceinline__ int kept_freq(int k1, int lane, int c) {
   return k1 + R * wfft::kept_freq<L>(c, lane);
 }
 

@@ -158,7 +158,7 @@ __device__ __forceinline__ float2 kept_value(const float2 (&v)[L], int c, int la
 }
 
 template <int L>
-__device__ __forceinline__ int kept_freq(int c, int lane) {
+__host__ __device__ __forceinline__ int kept_freq(int c, int lane) {
   if (L == 32) return lane + 32 * (c < 8 ? c : c + 16);
   return (lane >> 1) + 16 * (c + 8 * (lane & 1)) + 256 * (lane & 1);
 }
