@@ -20,6 +20,12 @@ Readings where the paper gives no value (the GPU path uses the same ones):
   * objective F_k = 1/2 ||V - Phi I_k||^2 + lambda ||I_k||_1, F_0 = 1/2 ||V||^2;
   * tol = 1e-4 (Sect. 6.1), at most max_fw iterations.
 
+Resume (checkpoint / warm start): the state of Algorithm 2 at the start of
+iteration k is (k, S_k, I_k); S0, x0, k0 give it, and the loop then runs
+exactly as it would have from there (F_prev = F(x0) for the first stop test,
+eps_k and the R1 threshold at k = k0, ...). S0 = x0 = None, k0 = 0 is the
+cold start.
+
 positive=True is the positivity-constrained variant (remark in Sect. 5.1):
 candidates only at positive values of the certificate (R2: mu >= 1 - delta;
 R1: eta >= max(eta) - 2 Delta/(k + 2) with eta > 0, Delta from
@@ -84,21 +90,29 @@ def duality_gap(uvw, N, fov, V, lam, idx, x, positive=False) -> float:
 
 
 def frank_wolfe(V, lam, eta_all, columns, lmax, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
-                eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, positive=False):
+                eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, positive=False, S0=None, x0=None, k0=0):
     """Algorithm 2 over an abstract set of atoms (pixels, or the atoms of a
     synthesis dictionary, Sect. 4.3): eta_all(r) is Phi_A*(r) on every atom,
     columns(S) the columns of the measurement operator of the atoms S (sorted).
+    (S0, x0, k0): the state to resume from (see the top of the file).
     Returns (S, x, r, F, iterations, converged, history)."""
     V = np.asarray(V, dtype=np.complex128)
     Delta = (1.0 - delta) * lmax
     S = np.zeros(0, dtype=np.int64)
     x = np.zeros(0)
     r = V.copy()
-    F_prev = 0.5 * float(np.vdot(V, V).real)
+    if S0 is not None and len(S0):
+        S = np.asarray(S0, dtype=np.int64)
+        x = np.asarray(x0, dtype=np.float64)
+        assert S.shape == x.shape and np.all(np.diff(S) > 0)
+        r = V - columns(S) @ x
+        F_prev = 0.5 * float(np.vdot(r, r).real) + lam * float(np.sum(np.abs(x)))
+    else:
+        F_prev = 0.5 * float(np.vdot(V, V).real)
     history = []
     converged = False
-    k = 0
-    for k in range(max_fw):
+    k = k0
+    for k in range(k0, max_fw):
         eta = eta_all(r)                                          # dirty residual, all atoms
         if rule == "R2":
             new = select_r2(eta / lam, delta, positive)
@@ -134,7 +148,7 @@ def frank_wolfe(V, lam, eta_all, columns, lmax, delta=0.01, rule="R2", tol=1e-4,
                             objective=F,
                             rel_improvement=rel, apgd_iterations=int(n_it), L=float(L),
                             eps=eps, n_borderline=n_border,
-                            active=S_next.copy(), support=S.copy(), borderline=border))
+                            active=S_next.copy(), support=S.copy(), x=x.copy(), borderline=border))
         F_prev = F
         if rel < tol:
             converged = True
@@ -143,7 +157,8 @@ def frank_wolfe(V, lam, eta_all, columns, lmax, delta=0.01, rule="R2", tol=1e-4,
 
 
 def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
-          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None, positive=False) -> SolveResult:
+          eps0=1e-2, eps_min=1e-5, apgd_max_iter=10_000, lmax=None, positive=False,
+          S0=None, x0=None, k0=0) -> SolveResult:
     V = np.asarray(V, dtype=np.complex128)
     if lmax is None:
         lmax = (operators.lambda_max_positive if positive else operators.lambda_max)(uvw, N, fov, V)
@@ -154,6 +169,6 @@ def solve(uvw, N, fov, V, lam, delta=0.01, rule="R2", tol=1e-4, max_fw=100,
 
     S, x, r, F, iters, converged, history = frank_wolfe(
         V, lam, lambda r: operators.adjoint(uvw, N, fov, r), columns, lmax, delta, rule, tol, max_fw,
-        eps0, eps_min, apgd_max_iter, positive)
+        eps0, eps_min, apgd_max_iter, positive, S0, x0, k0)
     mu = operators.adjoint(uvw, N, fov, r).reshape(N, N) / lam
     return SolveResult(S, x, mu, F, iters, converged, lam, history)

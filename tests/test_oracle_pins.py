@@ -255,3 +255,50 @@ def test_wide_field_solve_invariants():
     assert all(b <= a * (1 + 1e-12) for a, b in zip(F, F[1:]))
     assert np.abs(res.mu).max() <= 1 + 1e-5
     assert np.allclose(res.mu.ravel()[res.idx], np.sign(res.x), atol=1e-5)
+
+
+@pytest.mark.parametrize("rule,delta", [("R2", None), ("R1", 0.9)])
+def test_resume_from_a_saved_state_repeats_the_rest_of_the_run(rule, delta):
+    """Checkpoint / resume: the state of Algorithm 2 at the start of iteration
+    j is (j, S_j, I_j). A solve resumed from the state an uninterrupted run
+    recorded at the end of its iteration j - 1 repeats that run's iterations
+    j, j + 1, ... (same active sets and supports, same objectives, same stop),
+    for both selection rules (R1's threshold and the eps_k schedule depend on
+    k). A resume that got the iteration index, the first stop test's F or the
+    residual of the saved image wrong would leave the recorded path."""
+    wl = synth.tiny_coplanar()
+    V = _vis(wl)
+    lmax = operators.lambda_max(wl.uvw, wl.N, wl.fov, V)
+    lam = wl.alpha * lmax
+    d = wl.delta if delta is None else delta
+    cold = pfw.solve(wl.uvw, wl.N, wl.fov, V, lam, d, rule=rule, lmax=lmax)
+    assert len(cold.history) >= 4
+    j = 2
+    h = cold.history[j - 1]
+    warm = pfw.solve(wl.uvw, wl.N, wl.fov, V, lam, d, rule=rule, lmax=lmax, S0=h["support"], x0=h["x"], k0=j)
+    assert len(warm.history) == len(cold.history) - j
+    for a, b in zip(cold.history[j:], warm.history):
+        assert a["k"] == b["k"]
+        assert a["active"].tolist() == b["active"].tolist()
+        assert a["support"].tolist() == b["support"].tolist()
+        assert b["objective"] == pytest.approx(a["objective"], rel=1e-12)
+        assert b["rel_improvement"] == pytest.approx(a["rel_improvement"], rel=1e-9, abs=1e-15)
+        assert b["apgd_iterations"] == a["apgd_iterations"] and b["eps"] == a["eps"]
+    assert warm.idx.tolist() == cold.idx.tolist() and warm.converged == cold.converged
+    assert warm.iterations == cold.iterations
+    assert warm.objective == pytest.approx(cold.objective, rel=1e-12)
+
+
+def test_warm_start_at_the_solution_stops_after_one_iteration():
+    """Started from a converged solve's (S, x), the first iteration's relative
+    improvement is below the tolerance: the solve stops there with the same
+    support, and its objective is not above the starting one."""
+    wl = synth.tiny_coplanar()
+    V = _vis(wl)
+    lmax = operators.lambda_max(wl.uvw, wl.N, wl.fov, V)
+    lam = wl.alpha * lmax
+    cold = pfw.solve(wl.uvw, wl.N, wl.fov, V, lam, wl.delta)
+    warm = pfw.solve(wl.uvw, wl.N, wl.fov, V, lam, wl.delta, S0=cold.idx, x0=cold.x)
+    assert warm.converged and len(warm.history) == 1
+    assert warm.idx.tolist() == cold.idx.tolist()
+    assert warm.objective <= cold.objective * (1 + 1e-12)
