@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define PC_ABI_VERSION 4
+#define PC_ABI_VERSION 5
 
 typedef enum {
   PC_OK = 0,
@@ -124,6 +124,22 @@ typedef struct {
                              iteration, Sect. 5.1); 1: always the Gram form; 2: always the operator
                              form (same iterations, step size and stop rule)                          */
   int32_t reserved;
+  /* Resume / warm start (checkpoint of Algorithm 2: its state at the start of
+   * iteration k is (k, S_k, I_k)). init_S > 0: the solve starts from the image
+   * with weights init_x on the pixels init_idx (device pointers, init_S entries,
+   * strictly ascending raster indices < N*N, finite weights, >= 0 under
+   * positivity; read before pc_solve returns, the caller keeps ownership) at
+   * iteration init_k (0 <= init_k < max_fw: the eps_k schedule and rule R1's
+   * threshold continue from there; the first stop test compares against the
+   * objective of the given image). A run resumed from the support and weights
+   * an uninterrupted run had after its iteration k - 1, with init_k = k,
+   * repeats that run's remaining iterations. init_S = 0 (default): cold start.
+   * PC_ERR_INVALID_ARG for an invalid state; pc_solve only (the host, server
+   * and synthesis entry points require init_S = 0). */
+  const int32_t* init_idx;
+  const float*   init_x;
+  int32_t init_S;
+  int32_t init_k;
 } pc_solve_opts;
 
 /* Per-iteration record of pc_solve (host memory). */

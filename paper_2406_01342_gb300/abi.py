@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-PC_ABI_VERSION = 4
+PC_ABI_VERSION = 5
 PC_OK = 0
 PC_ERR_INVALID_ARG = -1
 PC_ERR_OOM = -2
@@ -75,7 +75,9 @@ class pc_solve_opts(ctypes.Structure):
                 ("gram_mode", ctypes.c_int32), ("positivity", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eps0", ctypes.c_double),
                 ("eps_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
-                ("reweight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("reweight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("init_idx", ctypes.c_void_p), ("init_x", ctypes.c_void_p),
+                ("init_S", ctypes.c_int32), ("init_k", ctypes.c_int32)]
 
 
 PC_DICT_MAX_SCALES = 8
@@ -370,9 +372,15 @@ def pc_apgd(G: torch.Tensor, b: torch.Tensor, lam: float, eps: float, max_iter: 
 
 
 def _solve_opts(select_rule=0, max_fw=0, apgd_max_iter=0, tol=0.0, eps0=0.0, eps_min=0.0,
-                lambda_max=0.0, gram_mode=0, positivity=0, reweight=0):
+                lambda_max=0.0, gram_mode=0, positivity=0, reweight=0, init_idx=None, init_x=None,
+                init_k=0):
+    S = 0 if init_idx is None else int(init_idx.numel())
+    if S and (init_x is None or int(init_x.numel()) != S):
+        raise ValueError("init_x must hold one weight per init_idx entry")
     return pc_solve_opts(PC_ABI_VERSION, select_rule, max_fw, apgd_max_iter, gram_mode,
-                         int(positivity), tol, eps0, eps_min, lambda_max, int(reweight), 0)
+                         int(positivity), tol, eps0, eps_min, lambda_max, int(reweight), 0,
+                         _dev(init_idx, torch.int32, "init_idx") if S else None,
+                         _dev(init_x, torch.float32, "init_x") if S else None, S, int(init_k))
 
 
 def pc_solve(plan: Plan, V: torch.Tensor, lam: float, delta: float, cap: int = 65536,

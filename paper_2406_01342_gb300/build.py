@@ -66,7 +66,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs = list(ex.map(lambda n: _compile(nvcc, n, hdr, verbose), SOURCES))
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-ldl"]   # -ldl: the NVTX loader
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -108,6 +108,28 @@ __global__ void k_prune(const int32_t* __restrict__ keep, const int32_t* __restr
   }
 }
 
+// Resume: the given support becomes the pruned support of the previous
+// iteration (what k_prune leaves): indices, weights, weighted atoms, support
+// marks, ||x||_1 and the support count.
+__global__ void k_resume_support(const int32_t* __restrict__ idx, const float* __restrict__ x, int S,
+                                 int32_t* __restrict__ idxA, float* __restrict__ xA,
+                                 float4* __restrict__ atomsA, uint8_t* __restrict__ mark,
+                                 double* __restrict__ l1, int32_t* __restrict__ n_sup,
+                                 const float4* __restrict__ atom_tab) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+    const int p = idx[i];
+    const float w = x[i];
+    idxA[i] = p;
+    xA[i] = w;
+    float4 at = atom_tab[p];
+    at.w *= w;
+    atomsA[i] = at;
+    mark[p] = 1;
+    atomicAdd(l1, fabs((double)w));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_sup = S;
+}
+
 // After the exploration, in one block: for each active atom its position in
 // the old (pruned) support or -1 (binary search), the warm start and b of the
 // old atoms, its atom (unit weight), the ascending list of the new positions
@@ -521,7 +543,7 @@ inline int round4(int n) { return (n + 3) & ~3; }
 
 // ------------------------------------------------------------------ the solve as a job
 
-int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
+int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out, bool resume_ok) {
   SolveCfg c;
   if (opts) {
     if (opts->version != PC_ABI_VERSION)
@@ -536,7 +558,21 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
     c.gram_mode = opts->gram_mode;
     c.positive = opts->positivity;
     c.reweight = opts->reweight;
+    c.init_idx = opts->init_idx;
+    c.init_x = opts->init_x;
+    c.init_S = opts->init_S;
+    c.init_k = opts->init_k;
   }
+  if (c.init_S != 0 && !resume_ok)
+    return fail(PC_ERR_INVALID_ARG, "%s: a resume state (init_S > 0) is accepted by pc_solve only", fn);
+  if (c.init_S < 0 || c.init_S > 60000)
+    return fail(PC_ERR_INVALID_ARG, "%s: init_S must be in [0, 60000]", fn);
+  if (c.init_S > 0) {
+    PC_TRY(check_dev(c.init_idx, true, fn, "init_idx"));
+    PC_TRY(check_dev(c.init_x, true, fn, "init_x"));
+  }
+  if (c.init_k < 0 || c.init_k >= c.max_fw)
+    return fail(PC_ERR_INVALID_ARG, "%s: init_k must be in [0, max_fw)", fn);
   if (c.reweight < 0 || c.reweight > 2) return fail(PC_ERR_INVALID_ARG, "%s: reweight must be 0, 1 or 2", fn);
   if (c.positive != 0 && c.positive != 1) return fail(PC_ERR_INVALID_ARG, "%s: positivity must be 0 or 1", fn);
   if (c.rule != 1 && c.rule != 2) return fail(PC_ERR_INVALID_ARG, "%s: select_rule must be 1 or 2", fn);
@@ -546,7 +582,7 @@ int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out) {
   return PC_OK;
 }
 
-SolveJob::~SolveJob() {}   // rb, ev, own and the graph stay with the plan
+SolveJob::~SolveJob() { end_fw_range(); }   // rb, ev, own and the graph stay with the plan
 
 int SolveJob::grow(int need) {
   if (need <= wcap && p->idxB.p) return PC_OK;
@@ -610,7 +646,37 @@ int SolveJob::start(pc_plan_s* plan, const float2* V_dev, double lambda_, double
   PC_CUDA(cudaStreamSynchronize(st));
   sumsqV = rb->hd[0];
   F_prev = F = 0.5 * sumsqV;
+  if (c.init_S > 0) PC_TRY(load_resume_state());
   return queue_iteration();
+}
+
+// Resume: checks the state on the host (strictly ascending pixels inside the
+// image, finite weights, non-negative under positivity), sizes the working
+// set for it and starts at iteration init_k. The first chain then prunes
+// nothing: it installs the support (k_resume_support), and its readback
+// gives F of the given image for the first stop test. G of the support is
+// not known, so the first Gram-form reweighting contracts all its rows.
+int SolveJob::load_resume_state() {
+  const int S = c.init_S;
+  std::vector<int32_t> hidx(S);
+  std::vector<float> hx(S);
+  PC_CUDA(cudaMemcpyAsync(hidx.data(), c.init_idx, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaMemcpyAsync(hx.data(), c.init_x, sizeof(float) * S, cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  const int64_t npix = (int64_t)p->N * p->N;
+  for (int i = 0; i < S; ++i) {
+    if (hidx[i] < 0 || hidx[i] >= npix || (i > 0 && hidx[i] <= hidx[i - 1]))
+      return fail(PC_ERR_INVALID_ARG, "pc_solve: init_idx must be strictly ascending pixels below N*N (entry %d)", i);
+    if (!std::isfinite(hx[i]) || (c.positive && hx[i] < 0.f))
+      return fail(PC_ERR_INVALID_ARG, "pc_solve: init_x[%d] must be finite%s", i,
+                  c.positive ? " and non-negative" : "");
+  }
+  PC_TRY(grow(S));
+  k = c.init_k;
+  ldB_prev = ld();
+  gram_valid = false;
+  warm = true;
+  return PC_OK;
 }
 
 bool SolveJob::ready() const { return cudaEventQuery(ev) == cudaSuccess; }
@@ -638,10 +704,19 @@ int SolveJob::explore() {
 // device (bound: an upper bound of the previous active-set size): the pruning
 // of the previous reweighting, the residual and objective of the iterate, its
 // certificate and the exploration set.
-int SolveJob::enqueue_chain(int bound) {
+int SolveJob::enqueue_chain(int bound, int warm_S) {
   int32_t* n_sup_dev = p->iscal + 3;
   PC_CUDA(cudaMemsetAsync(p->dscal, 0, 2 * sizeof(double), st));
-  if (bound > 0) {
+  if (warm_S > 0) {
+    // resume: the given support in place of the pruning
+    ProfScope prof_scope_(PROF_MISC, st);
+    prof_scope_.kernels = 1;
+    k_resume_support<<<std::min(ceil_div(warm_S, 256), 64), 256, 0, st>>>(
+        c.init_idx, c.init_x, warm_S, p->idxA.as<int32_t>(), p->xA.as<float>(), p->atomsA.as<float4>(), p->mark,
+        p->dscal + 1, n_sup_dev, p->atom_tab);
+    PC_LAUNCH_CHECK();
+    bound = warm_S;
+  } else if (bound > 0) {
     // pruning: gathers, atoms, support marks and ||x||_1 in one launch
     ProfScope prof_scope_(PROF_MISC, st);
     prof_scope_.kernels = 1;
@@ -683,8 +758,18 @@ std::vector<uint64_t> SolveJob::graph_key() const {
 // the executable updated in place where the topology allows) only when one
 // of them changes, e.g. when the working set grows or another V is solved.
 int SolveJob::queue_iteration() {
+  end_fw_range();
+  {
+    char name[48];
+    std::snprintf(name, sizeof(name), "Frank-Wolfe iteration %d", k);
+    fw_range = nvtxRangeStartA(name);
+    fw_range_open = true;
+  }
   if (k > 0) ldA = ldB_prev;
-  if (c.rule == 2 && !prof_active()) {
+  if (warm) {
+    // the resumed first chain (not captured: the graph holds the pruning)
+    PC_TRY(enqueue_chain(0, c.init_S));
+  } else if (c.rule == 2 && !prof_active()) {
     SolveCache& sc = *p->scache;
     std::vector<uint64_t> key = graph_key();
     if (!sc.gexec || sc.key != key) {
@@ -728,7 +813,14 @@ int SolveJob::process() {
   mu_inf = (double)bits_to_float(r.mb[0]);
   if (!std::isfinite(mu_inf)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite certificate at iteration %d", k);
   const double mu_top = c.positive ? (double)key_to_float(r.mb[1]) : mu_inf;
-  if (k > 0) {
+  if (warm) {
+    // the resumed image: its support and objective start the run
+    warm = false;
+    nS = r.hi[3];
+    F = 0.5 * r.hd[0] + lambda * r.hd[1];
+    F_prev = F;
+    if (!std::isfinite(F)) return fail(PC_ERR_NUMERIC, "pc_solve: non-finite objective of the resume state");
+  } else if (k > 0) {
     nS = r.hi[3];
     F = 0.5 * r.hd[0] + lambda * r.hd[1];
     const double rel = F_prev > 0 ? (F_prev - F) / F_prev : 0.0;
@@ -901,6 +993,7 @@ int SolveJob::after_apgd() {
 }
 
 int SolveJob::finish(int32_t* idx_out, float* x_out, int32_t cap, pc_solve_stats* stats) {
+  end_fw_range();
   if (stats) {
     stats->status = status;
     stats->iterations = k;
@@ -944,8 +1037,13 @@ extern "C" int pc_solve(pc_plan_t p, const pc_c32* V_, double lambda, double del
   PC_TRY(check_dev(x_out, cap > 0, "pc_solve", "x_out_dev"));
   if (mu_out) PC_TRY(check_dev(mu_out, true, "pc_solve", "mu_out_dev"));
   SolveCfg c;
-  PC_TRY(parse_solve_opts(opts, "pc_solve", &c));
+  PC_TRY(parse_solve_opts(opts, "pc_solve", &c, true));
   cudaStream_t st = SS(stream);
+  // NVTX: the whole call, with one range per Frank-Wolfe iteration inside
+  struct SolveRange {
+    SolveRange() { nvtxRangePushA("pc_solve"); }
+    ~SolveRange() { nvtxRangePop(); }
+  } solve_range;
   SolveJob j;
   PC_TRY(j.start(p, reinterpret_cast<const float2*>(V_), lambda, delta, c, mu_out, hist, hist_cap, st));
   while (!j.done) {
@@ -972,6 +1070,8 @@ extern "C" int pc_solve_host(const double* uvw_host, const pc_c32* V_host, int64
   if (M < 0 || (M > 0 && (!uvw_host || !V_host)) || cap < 0 || (cap > 0 && (!idx_out_host || !x_out_host)))
     return fail(PC_ERR_INVALID_ARG, "pc_solve_host: bad arguments");
   if (!(alpha > 0.0 && alpha <= 1.0)) return fail(PC_ERR_INVALID_ARG, "pc_solve_host: alpha must be in (0, 1]");
+  if (opts && opts->init_S != 0)
+    return fail(PC_ERR_INVALID_ARG, "pc_solve_host: a resume state (init_S > 0) is accepted by pc_solve only");
   cudaStream_t st = SS(stream);
   void* buf = nullptr;
   const size_t b_uvw = sizeof(double) * 3 * (size_t)std::max<int64_t>(M, 1);

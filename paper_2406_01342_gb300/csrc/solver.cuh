@@ -10,6 +10,8 @@
 
 #include "pc_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace pc {
 
 inline cudaStream_t SS(void* s) { return static_cast<cudaStream_t>(s); }
@@ -29,10 +31,15 @@ float key_to_float(unsigned key);   // inverse of float_order_key (0 -> -infinit
 struct SolveCfg {
   int rule = 2, max_fw = 100, apgd_max = 10000, gram_mode = 0, positive = 0, reweight = 0;
   double tol = 1e-4, eps0 = 1e-2, eps_min = 1e-5, lmax = 0.0;
+  // resume from (init_k, init_idx, init_x) when init_S > 0 (device arrays)
+  const int32_t* init_idx = nullptr;
+  const float* init_x = nullptr;
+  int init_S = 0, init_k = 0;
 };
 
-// Validates and reads pc_solve_opts (NULL = defaults).
-int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out);
+// Validates and reads pc_solve_opts (NULL = defaults); resume_ok: the entry
+// point accepts a resume state (else init_S must be 0).
+int parse_solve_opts(const pc_solve_opts* opts, const char* fn, SolveCfg* out, bool resume_ok = false);
 
 // reweight_op.cu: the reweighting in operator form (monotone FISTA on
 // g(v) = Re Phi_S^H (Phi_S v - V), one degridding + gridding pair per step)
@@ -71,6 +78,16 @@ struct SolveJob {
   bool op_form = false;
   bool gram_valid = true;               // GA holds G of the support (false after an operator-form step)
   bool dirty_ready = false;             // the plan's dirty image holds Re Phi* V of this solve
+  bool warm = false;                    // the queued chain starts from the resume state (no pruning)
+  // NVTX range of the current Frank-Wolfe iteration (from queueing its chain
+  // to queueing the next one, or to the end of the solve); free when no tool
+  // is attached
+  nvtxRangeId_t fw_range = 0;
+  bool fw_range_open = false;
+  void end_fw_range() {
+    if (fw_range_open) nvtxRangeEnd(fw_range);
+    fw_range_open = false;
+  }
   int last_apgd_iters = 0;
   int n_act = 0, ldB = 4;
   double eps = 0.0;
@@ -90,7 +107,7 @@ struct SolveJob {
   cudaStream_t caller = nullptr;
   cudaStream_t own = nullptr;
 
-  ~SolveJob();
+  ~SolveJob();   // ends an open iteration range
   // Allocates the working set, computes ||V||^2 (synchronises) and queues iteration 0.
   int start(pc_plan_s* plan, const float2* V_dev, double lambda, double delta, const SolveCfg& cfg,
             float* mu_out, pc_iter_record* hist, int hist_cap, cudaStream_t stream);
@@ -115,7 +132,8 @@ struct SolveJob {
   std::vector<uint64_t> graph_key() const;     // every argument the captured chain depends on
   int grow(int need);
   int explore();
-  int enqueue_chain(int bound);
+  int enqueue_chain(int bound, int warm_S = 0);
+  int load_resume_state();
   int queue_iteration();
   int choose_form(int n_new, int n_act, bool* op);
 };

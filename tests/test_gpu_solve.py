@@ -287,3 +287,68 @@ def test_pooled_memory_reuse_and_trim(abi):
             abi.pc_trim_memory()
     r = abi.pc_solve_host(wl.uvw, V.astype(np.complex64), wl.N, wl.fov, 0.05, wl.delta)
     assert r["idx"].tolist() == first[0]
+
+
+def test_resume_from_the_oracle_state_finishes_the_oracle_run(abi):
+    """Resume (checkpoint of Algorithm 2; the resume state's reading): started
+    from the oracle's support and weights after its iteration j - 1, at
+    init_k = j, the GPU solve runs the oracle's remaining iterations (same
+    iteration indices, active sets within the borderline pixels) and ends on
+    the oracle's final support and objective (1e-4)."""
+    wl, V = workload("small_wide_w")
+    Vs = V.astype(np.complex64).astype(np.complex128)
+    lmax = operators.lambda_max(wl.uvw, wl.N, wl.fov, Vs)
+    lam = 0.05 * lmax
+    ref = pfw.solve(wl.uvw, wl.N, wl.fov, Vs, lam, wl.delta)
+    assert len(ref.history) >= 3
+    j = 2
+    h = ref.history[j - 1]
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    res = abi.pc_solve(plan, to_dev(V.astype(np.complex64)), lam, wl.delta,
+                       init_idx=to_dev(h["support"].astype(np.int32)), init_x=to_dev(h["x"].astype(np.float32)),
+                       init_k=j)
+    assert res["idx"].cpu().numpy().tolist() == ref.idx.tolist()
+    assert abs(res["objective"] - ref.objective) <= 1e-4 * ref.objective
+    assert res["converged"] and res["iterations"] == ref.iterations
+    assert [g["k"] for g in res["history"]] == [o["k"] for o in ref.history[j:]]
+    for g, o in zip(res["history"], ref.history[j:]):
+        assert abs(g["n_active"] - o["n_active"]) <= o["n_borderline"], (g, o)
+
+
+def test_warm_start_at_the_solution_stops_after_one_iteration(abi):
+    """Started from its own converged (S, x) the solve stops after one
+    iteration (relative improvement below the tolerance) on the same support,
+    its objective not above the starting one (FP32 rounding aside)."""
+    wl, V = workload("tiny_64_coplanar")
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    Vd = to_dev(V.astype(np.complex64))
+    lam = wl.alpha * abi.pc_lambda_max(plan, Vd)
+    cold = abi.pc_solve(plan, Vd, lam, wl.delta)
+    warm = abi.pc_solve(plan, Vd, lam, wl.delta, init_idx=cold["idx"].clone(), init_x=cold["x"].clone())
+    assert warm["converged"] and len(warm["history"]) == 1
+    assert warm["idx"].cpu().tolist() == cold["idx"].cpu().tolist()
+    assert warm["objective"] <= cold["objective"] * (1 + 1e-5)
+
+
+def test_resume_state_is_checked(abi):
+    """An invalid resume state is an argument error (checked before the first
+    iteration): pixels not strictly ascending or outside the image, a
+    non-finite weight, a negative weight under positivity, init_k outside
+    [0, max_fw)."""
+    wl, V = workload("tiny_64_coplanar")
+    plan = abi.pc_plan_create(to_dev(wl.uvw), wl.N, wl.fov)
+    Vd = to_dev(V.astype(np.complex64))
+    lam = wl.alpha * abi.pc_lambda_max(plan, Vd)
+    NN = wl.N * wl.N
+    bad = [(np.array([5, 3], np.int32), np.array([1.0, 1.0], np.float32), {}),
+           (np.array([3, 3], np.int32), np.array([1.0, 1.0], np.float32), {}),
+           (np.array([3, NN], np.int32), np.array([1.0, 1.0], np.float32), {}),
+           (np.array([3, 5], np.int32), np.array([1.0, np.inf], np.float32), {}),
+           (np.array([3, 5], np.int32), np.array([1.0, -1.0], np.float32), {"positivity": 1}),
+           (np.array([3, 5], np.int32), np.array([1.0, 1.0], np.float32), {"init_k": 100})]
+    for idx, x, kw in bad:
+        with pytest.raises(abi.PcError) as e:
+            abi.pc_solve(plan, Vd, lam, wl.delta, init_idx=to_dev(idx), init_x=to_dev(x), **kw)
+        assert e.value.status == abi.PC_ERR_INVALID_ARG, (idx, x, kw)
+    # the plan is still usable
+    assert abi.pc_solve(plan, Vd, lam, wl.delta)["converged"]
