@@ -84,7 +84,7 @@ k_degrid_win(const int4* __restrict__ subs, const int* __restrict__ win_off, con
       // (a0c, b0c), the corner clamped into the tile; taps of that block
       // outside the footprint get weight zero, so every slot runs the same
       // unclipped tap loop.
-      const int a0c = min(max(a0, 0), DW_T - W), b0c = min(max(b0, 0), DW_T - W);
+      const int a0c = gwin::tap_corner(a0, W), b0c = gwin::tap_corner(b0, W);
       float fu[W], fv[W];
 #pragma unroll
       for (int i = 0; i < W; ++i) {

@@ -31,17 +31,34 @@ __device__ __forceinline__ float2 unpack2(uint64_t v) {
 }
 
 // Chunk descriptor {window j, first slot, slot stride nc, slots} (j < 0: none).
-__device__ __forceinline__ int4 chunk_at(const int2* wr, int j, int c) {
+__host__ __device__ __forceinline__ int4 chunk_at(const int2* wr, int j, int c) {
   const int L = wr[j].y, nc = (L + C - 1) / C;
   return make_int4(j, wr[j].x + c, nc, (L - c + nc - 1) / nc);
 }
-__device__ __forceinline__ int4 chunk_after(const int2* wr, int Pw, int4 d) {
+__host__ __device__ __forceinline__ int4 chunk_after(const int2* wr, int Pw, int4 d) {
   if (d.x < 0) return d;
   const int c = d.y - wr[d.x].x;
   if (c + 1 < d.z) return chunk_at(wr, d.x, c + 1);
   for (int jj = d.x + 1; jj < Pw; ++jj)
     if (wr[jj].y > 0) return chunk_at(wr, jj, 0);
   return make_int4(-1, 0, 1, 0);
+}
+
+// Part `part` of `parts` of the slot range [bs, be): {first, count}; the
+// parts are contiguous and cover the range once.
+__host__ __device__ __forceinline__ int2 part_range(int bs, int be, int part, int parts) {
+  const long long len = be - bs;
+  const int s0 = bs + (int)(len * part / parts), s1 = bs + (int)(len * (part + 1) / parts);
+  return make_int2(s0, s1 - s0);
+}
+
+// The degridding's tap block of a footprint starting at tile-local column
+// (or row) a0 in [-(W - 1), T - 1]: its corner clamped into the tile. The
+// footprint's cells inside the tile are the block's taps i with
+// 0 <= i + corner - a0 < W (the footprint's own tap index); the others get
+// weight zero.
+__host__ __device__ __forceinline__ int tap_corner(int a0, int W) {
+  return a0 < 0 ? 0 : (a0 > T - W ? T - W : a0);
 }
 
 // This part's slot range {first, count} of every window of the tile (all
@@ -51,9 +68,7 @@ __device__ __forceinline__ void schedule(const int* __restrict__ win_off, int ti
                                          int2* wr, int4* desc) {
   for (int t = threadIdx.x; t < Pw; t += blockDim.x) {
     const int bs = __ldg(win_off + (size_t)tile * Pw + t), be = __ldg(win_off + (size_t)tile * Pw + t + 1);
-    const long long len = be - bs;
-    const int s0 = bs + (int)(len * part / parts), s1 = bs + (int)(len * (part + 1) / parts);
-    wr[t] = make_int2(s0, s1 - s0);
+    wr[t] = part_range(bs, be, part, parts);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
