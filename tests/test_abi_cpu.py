@@ -82,3 +82,22 @@ def test_profile_classes_are_known_by_name_without_a_gpu():
     else:
         raise AssertionError("an unknown class name was accepted")
     assert abi.pc_profile_end() == {}
+
+
+def test_resume_arguments_are_checked_by_the_binding_without_a_gpu():
+    """The binding passes a resume state only as device tensors with one
+    weight per index (pc_solve reads them on the device); host tensors and a
+    length mismatch are refused before any library call, and the options
+    struct carries the state's size and iteration index."""
+    import pytest
+    import torch
+    from paper_2406_01342_gb300 import abi
+    idx = torch.tensor([3, 5], dtype=torch.int32)
+    x = torch.tensor([1.0, 2.0], dtype=torch.float32)
+    with pytest.raises(ValueError):
+        abi._solve_opts(init_idx=idx, init_x=x, init_k=2)          # host tensors
+    with pytest.raises(ValueError):
+        abi._solve_opts(init_idx=idx, init_x=x[:1])                # one weight missing
+    o = abi._solve_opts()
+    assert o.init_S == 0 and o.init_k == 0 and not o.init_idx and not o.init_x
+    assert o.version == abi.PC_ABI_VERSION
